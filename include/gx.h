@@ -1,0 +1,203 @@
+/*
+ * gx.h -- C ABI of the GB300 (sm_103a) batched dispatch / implicit-gradient library.
+ *
+ * What it computes (Degleris, El Gamal, Rajagopal, "Scalable and Interactive
+ * Electricity Grid Expansion Planning", arXiv:2410.13055):
+ *
+ *   Eq. 2      dispatch map   x*_s(eta) = argmin c_s(x) s.t. A_s(eta) x <= b_s(eta)
+ *              for every scenario s of a batch: a DC power-flow network with
+ *              generators (0 <= p <= cf*eta_g), curtailable loads (0 <= shed <= L),
+ *              lines (|beta (th_f - th_t)| <= eta_l, |th_f - th_t| <= dtheta_max)
+ *              and batteries (0 <= ch, dis <= eta_b, 0 <= soc <= dur*eta_b,
+ *              soc_t = soc_{t-1} + eff_c ch_t - dis_t / eff_d, soc_{-1} = 0) over T hours;
+ *              c_s = sum c p + eps/2 p^2 + VOLL shed + eps/2 shed^2 + eps/2 (ch^2 + dis^2).
+ *   Sec. 2.2   implicit gradient  d h_s / d eta = (d x*_s / d eta)^T grad h_s, with
+ *              h_s = c_s + kappa * emissions (emissions-aware planning, Sec. 2.1),
+ *              by the implicit function theorem on the active KKT system.
+ *   Sec. 2.2   projected step     eta <- proj_[eta_min, eta_max](eta - alpha (gamma + grad)).
+ *
+ * The dispatch is solved by proximal message passing (ADMM with per-device
+ * proximal operators and per-bus consensus); the gradient by the same message
+ * passing applied to the linearised (active-set) KKT system.
+ *
+ * Conventions
+ *  - Units: MW, MWh, $/MWh, rad.  Line beta is MW per rad.
+ *  - Plan vector eta (length K, FP32, device memory): for each network in the
+ *    order given at create, [generators | lines | batteries] of that network.
+ *  - Injection sign: power into the bus is positive.  Nodal price lambda is the
+ *    multiplier of the bus balance; an interior generator has lambda = c + eps p.
+ *  - Per-scenario arrays are rows of Tp = roundup(T, 4) floats (row-major,
+ *    device-major); hours T..Tp-1 are padding.
+ *
+ * Memory and ownership
+ *  - gx_network_create copies every descriptor array (host memory) and lays out
+ *    one device workspace.  The library never allocates device memory: the caller
+ *    allocates gx_network_device_bytes() bytes (e.g. a torch uint8 tensor) and
+ *    passes it to gx_network_bind, and must keep it alive and unmodified until
+ *    gx_network_destroy.  Output arrays live inside that workspace; their offsets
+ *    come from gx_network_array.
+ *  - Pointers named *_dev are device pointers owned by the caller.
+ *
+ * Errors
+ *  - Every call returns gx_status: 0 OK, > 0 warning, < 0 error.  No C++
+ *    exception crosses the ABI.  gx_status_string gives a static message and
+ *    gx_last_error_message() details of the last error on this thread.
+ *  - Calls enqueue work on the given stream.  gx_dispatch_solve_batch and
+ *    gx_dispatch_grad_batch synchronise that stream every opts.check_every
+ *    iterations to read the convergence flags (documented per call).
+ */
+#ifndef GX_H
+#define GX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int gx_status;
+enum {
+    GX_OK = 0,
+    GX_NOT_CONVERGED = 1,     /* iteration cap reached; outputs hold the last iterate */
+    GX_ERR_INVALID_ARG = -1,  /* a descriptor or argument failed validation */
+    GX_ERR_NONFINITE = -2,    /* a NaN/Inf appeared in the iterate or the inputs */
+    GX_ERR_CUDA = -3,         /* a CUDA runtime call failed */
+    GX_ERR_NO_MEMORY = -4,    /* the bound workspace is too small */
+    GX_ERR_TIMEOUT = -5,      /* a bounded device-side wait gave up */
+    GX_ERR_STATE = -6         /* call out of order (e.g. grad before solve, not bound) */
+};
+
+typedef struct gx_network gx_network; /* opaque */
+
+/* One network (topology and devices).  All arrays are host memory of the stated
+ * length; indices are 0-based.  A bus may carry any number of devices; every bus
+ * has one curtailable load (its profile may be zero). */
+typedef struct {
+    int n_bus, n_gen, n_line, n_bat;
+    const int32_t* gen_bus;      /* [n_gen] */
+    const double* gen_cost;      /* [n_gen] $/MWh, finite */
+    const double* gen_emis;      /* [n_gen] t/MWh (planner's emission rate) */
+    const int32_t* line_from;    /* [n_line] */
+    const int32_t* line_to;      /* [n_line], != line_from */
+    const double* line_beta;     /* [n_line] MW/rad, > 0 */
+    const double* line_dtheta;   /* [n_line] rad, > 0 */
+    const int32_t* bat_bus;      /* [n_bat] */
+    const double* bat_dur;       /* [n_bat] h, > 0 */
+    const double* bat_eff_c;     /* [n_bat] in (0, 1] */
+    const double* bat_eff_d;     /* [n_bat] in (0, 1] */
+} gx_network_desc;
+
+/* One scenario: a horizon of T hours on network `net` (Sec. 2.1: a scenario can
+ * be an hour, a day or a week of operations). */
+typedef struct {
+    int net;                     /* index into the networks given at create */
+    int T;                       /* 1 <= T <= 256 */
+    const double* load;          /* [n_bus * T] MW >= 0, row-major bus x hour */
+    const double* cf;            /* [n_gen * T] capacity factor in [0, 1] */
+    double weight;               /* w_s > 0 (1/S in Eq. 1) */
+} gx_scenario_desc;
+
+typedef struct {
+    /* model (Eq. 2 with the eps regularisation; emissions weight kappa of Sec. 2.1) */
+    double eps;          /* $/MW^2h regularisation on generation, shed, charge, discharge */
+    double voll;         /* $/MWh value of lost load */
+    double kappa;        /* $/t weight of emissions in the planner objective h */
+    /* message passing */
+    double rho;          /* power penalty, $/MW^2h */
+    double rho_theta_c;  /* phase penalty scale: rho_theta_l = rho * rho_theta_c * w_l */
+    int theta_weight;    /* 0: w_l = mean(beta^2) (uniform), 1: w_l = beta_l^2 (per line) */
+    double rho_inner_c;  /* battery inner penalty rho_in = rho * rho_inner_c */
+    int inner_iters;     /* battery inner iterations per outer iteration, >= 1 */
+    double tol;          /* stop when primal and dual relative residuals <= tol */
+    int max_iter;
+    int check_every;     /* iterations between residual checks (host sync) */
+    /* adjoint */
+    double tol_active;   /* a bound is active if its multiplier exceeds tol_active (relative) */
+    double adj_tol;
+    int adj_max_iter;
+    int grad_envelope;   /* 1: for kappa == 0 use the envelope theorem (no adjoint solve) */
+} gx_opts;
+
+enum { GX_WARM_COLD = 0, GX_WARM_PREV = 1, GX_WARM_USER = 2, GX_WARM_LEARNED = 3 };
+
+/* Arrays exported through gx_network_array (FP32 unless noted). */
+enum {
+    GX_ARR_P = 0,        /* [G x Tp] generator output, MW */
+    GX_ARR_SHED = 1,     /* [N x Tp] load shed, MW */
+    GX_ARR_FLOW = 2,     /* [L x Tp] line flow from -> to, MW (beta * delta) */
+    GX_ARR_THETA = 3,    /* [N x Tp] bus angle (consensus average), rad */
+    GX_ARR_CH = 4,       /* [B x Tp] battery charge, MW */
+    GX_ARR_DIS = 5,      /* [B x Tp] battery discharge, MW */
+    GX_ARR_SOC = 6,      /* [B x Tp] state of charge, MWh */
+    GX_ARR_PRICE = 7,    /* [N x Tp] nodal price, $/MWh */
+    GX_ARR_COST = 8,     /* [S] FP64 operating cost c_s (after gx_dispatch_solve_batch) */
+    GX_ARR_H = 9,        /* [S] FP64 planner objective h_s */
+    GX_ARR_ITERS = 10,   /* [S] int32 iterations of the last solve */
+    GX_ARR_RESID = 11,   /* [S x 2] FP64 primal, dual relative residual */
+    GX_ARR_STATUS = 12,  /* [S] int32 per-scenario gx_status of the last solve */
+    GX_ARR_GRAD_S = 13,  /* [sum_s K_net(s)] FP64 per-scenario dh_s/deta of the last grad */
+    GX_ARR_ADJ_ITERS = 14 /* [S] int32 adjoint iterations */
+};
+
+typedef struct {
+    int iters_max;        /* largest per-scenario iteration count */
+    int n_converged;      /* scenarios that met tol */
+    int n_scen;           /* scenarios in the batch */
+    int launches;         /* kernel launches issued by the call */
+    double max_primal, max_dual; /* worst relative residuals at exit */
+} gx_stats;
+
+gx_status gx_opts_default(gx_opts* opts);
+const char* gx_status_string(gx_status s);
+const char* gx_last_error_message(void);
+
+/* Validate and copy the descriptors; lay out the workspace.  No device work.
+ * Errors: GX_ERR_INVALID_ARG (bad index, non-positive beta/dur/eff, T out of
+ * range, negative load, cf outside [0,1], non-finite numbers). */
+gx_status gx_network_create(const gx_network_desc* nets, int n_nets, const gx_scenario_desc* scen, int S,
+                            const gx_opts* opts, gx_network** out);
+gx_status gx_network_destroy(gx_network* net);
+size_t gx_network_device_bytes(const gx_network* net);
+int gx_network_K(const gx_network* net);             /* total plan length */
+int gx_network_S(const gx_network* net);
+/* Upload static data into dev_mem (>= gx_network_device_bytes, 256-byte aligned)
+ * and zero the state.  Asynchronous on `stream`. */
+gx_status gx_network_bind(gx_network* net, void* dev_mem, size_t bytes, void* stream);
+/* Replace the options (rho, tolerances, ...); model constants eps/voll/kappa too.
+ * Recomputes the battery factorisation on the next solve. */
+gx_status gx_network_set_opts(gx_network* net, const gx_opts* opts);
+/* Byte offset (from dev_mem) and element count of array `which` for scenario
+ * `scen` (scen = -1: the whole array over all scenarios). */
+gx_status gx_network_array(const gx_network* net, int which, int scen, size_t* offset_bytes, size_t* count);
+/* Row stride Tp and device counts of scenario s. */
+gx_status gx_network_scenario_info(const gx_network* net, int s, int* T, int* Tp, int* N, int* G, int* L, int* B,
+                                   int* eta_offset);
+
+/* Solve Eq. 2 for the scenarios scen_idx[0..B) (host array; NULL = all S) at plan
+ * eta_dev [K].  warm: GX_WARM_COLD (zero state), GX_WARM_PREV (continue from the
+ * state of the previous solve), GX_WARM_USER (initial prices and angles from
+ * warm_dev: [sum_s N_s Tp_s] prices followed by the same size of angles, in
+ * scenario order of the whole network).  Synchronises `stream` every
+ * check_every iterations.  Returns GX_NOT_CONVERGED if any scenario of the batch
+ * hit max_iter. */
+gx_status gx_dispatch_solve_batch(gx_network* net, const float* eta_dev, const int* scen_idx, int B, int warm,
+                                  const float* warm_dev, gx_stats* stats, void* stream);
+
+/* Implicit gradient of sum_{s in batch} w'_s h_s at the last solve (same batch),
+ * w'_s = w_s * (sum of all weights) / (sum of the batch's weights), written to
+ * grad_dev [K] (FP32, caller-owned; entries of networks outside the batch are 0).
+ * warm: GX_WARM_COLD or GX_WARM_PREV for the adjoint state.  Per-scenario FP64
+ * gradients are kept in GX_ARR_GRAD_S.  Errors: GX_ERR_STATE if no solve. */
+gx_status gx_dispatch_grad_batch(gx_network* net, const float* eta_dev, int warm, float* grad_dev,
+                                 gx_stats* stats, void* stream);
+
+/* eta <- min(max(eta - alpha * (gamma + grad), eta_min), eta_max), elementwise
+ * over K entries, all device pointers (Sec. 2.2 projected step). */
+gx_status gx_plan_step(gx_network* net, float* eta_dev, const float* grad_dev, const float* gamma_dev,
+                       const float* eta_min_dev, const float* eta_max_dev, float alpha, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GX_H */

@@ -1,0 +1,736 @@
+// Host side of the C ABI (include/gx.h): descriptor validation, workspace layout,
+// bind (upload of static data), and the drivers of the solve, gradient and plan step.
+#include "gx_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace gx;
+
+namespace {
+
+thread_local std::string g_err;
+
+gx_status fail(gx_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+
+#define GX_CUDA(call)                                                                     \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(GX_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+struct NetH {
+    int N = 0, G = 0, L = 0, B = 0;
+    std::vector<int> gen_bus, line_from, line_to, bat_bus;
+    std::vector<double> gen_cost, gen_emis, line_beta, line_dth, bat_dur, bat_effc, bat_effd;
+    std::vector<int> gptr, gidx, bptr, bidx, eptr, eidx;
+    std::vector<float> inv_cnt, inv_wsum, dres_w, l_w;
+    std::vector<uint8_t> firm;
+    int gen0 = 0, line0 = 0, bat0 = 0, bus0 = 0, ptr0 = 0, eta0 = 0;
+};
+
+struct ScenH {
+    int net = 0, T = 0, Tp = 0;
+    double weight = 1.0;
+    std::vector<float> load, cf;  // padded rows
+};
+
+// Byte offsets of every array in the workspace (256-byte aligned).
+struct Layout {
+    size_t total = 0;
+    size_t add(size_t bytes) {
+        size_t o = total;
+        total += (bytes + 255) / 256 * 256;
+        return o;
+    }
+};
+
+bool isfin(double x) { return std::isfinite(x); }
+
+}  // namespace
+
+struct gx_network {
+    gx_opts opts{};
+    int n_nets = 0, S = 0, K = 0;
+    std::vector<NetH> nets;
+    std::vector<ScenH> scens;
+    std::vector<ScenDev> sdev;
+    std::vector<int> bus_blk_scen, line_blk_scen, bat_warp_scen, cost_blk_scen, gwarp, k_net;
+    long long bus_el = 0, gen_el = 0, line_el = 0, bat_el = 0;
+    int n_bus_blk = 0, n_line_blk = 0, n_bat_warps = 0, n_cost_blk = 0, n_gwarps = 0, gs_total = 0;
+    int tot_gen = 0, tot_line = 0, tot_bat = 0, tot_bus = 0, tot_ptr = 0;
+    // workspace offsets
+    size_t o_scen, o_bbs, o_lbs, o_bws, o_cbs, o_gwarp, o_knet;
+    size_t o_gbus, o_gcost, o_gemis, o_gfirm, o_lfrom, o_lto, o_lbeta, o_ldth, o_lw, o_bbus, o_bdur, o_beffc, o_beffd;
+    size_t o_gptr, o_gidx, o_bptr, o_bidx, o_eptr, o_eidx, o_icnt, o_iwsum, o_dresw;
+    size_t o_load, o_cf, o_dd;
+    size_t static_end;
+    size_t o_f[16], o_a[16];  // forward / adjoint state arrays, order of StatePtrs
+    size_t o_mgen, o_mload, o_mline, o_mbat;
+    size_t o_done, o_iters, o_status, o_adjit, o_nact, o_inb, o_resid, o_cost, o_h, o_grads, o_wprime;
+    size_t o_flow, o_price, o_shed, o_bpart, o_lpart, o_btpart, o_cpart;
+    Layout lay;
+    // binding
+    uint8_t* dev = nullptr;
+    bool solved = false, adj_ready = false, dd_dirty = true;
+    std::vector<int> in_batch, done_init;
+    std::vector<double> wprime;
+    std::vector<float> dd_host;
+    Ctx ctx{};
+};
+
+static void fill_dd(gx_network* net) {
+    // Thomas pivots of the battery tridiagonal system (one row per battery and scenario):
+    // diag = [1 + g rho_in, 2 + g rho_in, ...], off-diagonal -1, with
+    // g = [a, -k] H^{-1} [a, -k]^T and H = [[eps+rho_in+rho, -rho], [-rho, eps+rho_in+rho]].
+    const double eps = net->opts.eps, rho = net->opts.rho, ri = rho * net->opts.rho_inner_c;
+    net->dd_host.assign((size_t)net->bat_el, 1.0f);
+    for (int s = 0; s < net->S; ++s) {
+        const ScenH& sc = net->scens[s];
+        const NetH& nh = net->nets[sc.net];
+        for (int b = 0; b < nh.B; ++b) {
+            const double a = nh.bat_effc[b], k = 1.0 / nh.bat_effd[b];
+            const double A = eps + ri + rho, det = A * A - rho * rho;
+            const double gc = (A * a - rho * k) / det, gd = (rho * a - A * k) / det;
+            const double g = a * gc - k * gd;
+            double d = 1.0 + g * ri;
+            float* out = net->dd_host.data() + net->sdev[s].e_bat + (size_t)b * sc.Tp;
+            out[0] = (float)d;
+            for (int t = 1; t < sc.T; ++t) {
+                d = (2.0 + g * ri) - 1.0 / d;
+                out[t] = (float)d;
+            }
+        }
+    }
+    net->dd_dirty = true;
+}
+
+static void make_ctx(gx_network* net) {
+    Ctx& c = net->ctx;
+    uint8_t* d = net->dev;
+    auto F = [&](size_t o) { return reinterpret_cast<float*>(d + o); };
+    auto I = [&](size_t o) { return reinterpret_cast<int*>(d + o); };
+    auto D = [&](size_t o) { return reinterpret_cast<double*>(d + o); };
+    auto U8 = [&](size_t o) { return reinterpret_cast<uint8_t*>(d + o); };
+    c.S = net->S;
+    c.n_bus_blk = net->n_bus_blk;
+    c.n_line_blk = net->n_line_blk;
+    c.n_bat_warps = net->n_bat_warps;
+    c.n_cost_blk = net->n_cost_blk;
+    const gx_opts& o = net->opts;
+    c.rho = (float)o.rho;
+    c.eps = (float)o.eps;
+    c.voll = (float)o.voll;
+    c.kappa = (float)o.kappa;
+    c.rho_in = (float)(o.rho * o.rho_inner_c);
+    c.rth_c = (float)(o.rho * o.rho_theta_c);
+    c.tol_act = (float)o.tol_active;
+    c.inner_iters = o.inner_iters;
+    c.scen = reinterpret_cast<const ScenDev*>(d + net->o_scen);
+    c.bus_blk_scen = I(net->o_bbs);
+    c.line_blk_scen = I(net->o_lbs);
+    c.bat_warp_scen = I(net->o_bws);
+    c.cost_blk_scen = I(net->o_cbs);
+    c.g_bus = I(net->o_gbus); c.g_cost = F(net->o_gcost); c.g_emis = F(net->o_gemis); c.g_firm = U8(net->o_gfirm);
+    c.l_from = I(net->o_lfrom); c.l_to = I(net->o_lto); c.l_beta = F(net->o_lbeta); c.l_dth = F(net->o_ldth);
+    c.l_w = F(net->o_lw);
+    c.b_bus = I(net->o_bbus); c.b_dur = F(net->o_bdur); c.b_effc = F(net->o_beffc); c.b_effd = F(net->o_beffd);
+    c.bus_gptr = I(net->o_gptr); c.bus_gidx = I(net->o_gidx);
+    c.bus_bptr = I(net->o_bptr); c.bus_bidx = I(net->o_bidx);
+    c.bus_eptr = I(net->o_eptr); c.bus_eidx = I(net->o_eidx);
+    c.bus_inv_cnt = F(net->o_icnt); c.bus_inv_wsum = F(net->o_iwsum); c.bus_dres_w = F(net->o_dresw);
+    c.load = F(net->o_load); c.cf = F(net->o_cf); c.bat_dd = F(net->o_dd);
+    float** fs[16] = {&c.xg, &c.xl, &c.dl, &c.sg, &c.vf, &c.vt, &c.xb, &c.zc, &c.zd, &c.zs, &c.yc, &c.yd, &c.ys,
+                      &c.u, &c.pbar, &c.thb};
+    float** as[16] = {&c.a_xg, &c.a_xl, &c.a_dl, &c.a_sg, &c.a_vf, &c.a_vt, &c.a_xb, &c.a_zc, &c.a_zd, &c.a_zs,
+                      &c.a_yc, &c.a_yd, &c.a_ys, &c.a_u, &c.a_pbar, &c.a_thb};
+    for (int k = 0; k < 16; ++k) { *fs[k] = F(net->o_f[k]); *as[k] = F(net->o_a[k]); }
+    c.m_gen = U8(net->o_mgen); c.m_load = U8(net->o_mload); c.m_line = U8(net->o_mline); c.m_bat = U8(net->o_mbat);
+    c.done = I(net->o_done); c.iters = I(net->o_iters); c.status = I(net->o_status); c.adj_iters = I(net->o_adjit);
+    c.n_active = I(net->o_nact);
+    c.resid = D(net->o_resid); c.cost = D(net->o_cost); c.hval = D(net->o_h); c.grad_s = D(net->o_grads);
+    c.out_flow = F(net->o_flow); c.out_price = F(net->o_price); c.out_shed = F(net->o_shed);
+    c.bus_part = F(net->o_bpart); c.line_part = F(net->o_lpart); c.bat_part = F(net->o_btpart);
+    c.cost_part = D(net->o_cpart);
+    c.warm = nullptr;
+    c.warm_half = net->bus_el;
+    c.eta = nullptr;
+}
+
+extern "C" {
+
+gx_status gx_opts_default(gx_opts* o) {
+    if (!o) return fail(GX_ERR_INVALID_ARG, "opts is NULL");
+    o->eps = 1e-3;
+    o->voll = 1000.0;
+    o->kappa = 0.0;
+    o->rho = 0.3;
+    o->rho_theta_c = 0.01;
+    o->theta_weight = 0;
+    o->rho_inner_c = 1.0;
+    o->inner_iters = 3;
+    o->tol = 1e-3;
+    o->max_iter = 20000;
+    o->check_every = 20;
+    o->tol_active = 1e-3;
+    o->adj_tol = 1e-3;
+    o->adj_max_iter = 20000;
+    o->grad_envelope = 0;
+    return GX_OK;
+}
+
+const char* gx_status_string(gx_status s) {
+    switch (s) {
+        case GX_OK: return "ok";
+        case GX_NOT_CONVERGED: return "not converged (iteration cap reached)";
+        case GX_ERR_INVALID_ARG: return "invalid argument";
+        case GX_ERR_NONFINITE: return "non-finite value in the iterate";
+        case GX_ERR_CUDA: return "CUDA error";
+        case GX_ERR_NO_MEMORY: return "workspace too small";
+        case GX_ERR_TIMEOUT: return "device wait timed out";
+        case GX_ERR_STATE: return "call out of order";
+        default: return "unknown status";
+    }
+}
+
+const char* gx_last_error_message(void) { return g_err.c_str(); }
+
+static gx_status check_opts(const gx_opts* o) {
+    if (!(o->eps > 0 && isfin(o->eps))) return fail(GX_ERR_INVALID_ARG, "opts.eps must be > 0");
+    if (!(o->voll > 0 && isfin(o->voll))) return fail(GX_ERR_INVALID_ARG, "opts.voll must be > 0");
+    if (!(o->kappa >= 0 && isfin(o->kappa))) return fail(GX_ERR_INVALID_ARG, "opts.kappa must be >= 0");
+    if (!(o->rho > 0 && isfin(o->rho))) return fail(GX_ERR_INVALID_ARG, "opts.rho must be > 0");
+    if (!(o->rho_theta_c > 0 && isfin(o->rho_theta_c))) return fail(GX_ERR_INVALID_ARG, "opts.rho_theta_c must be > 0");
+    if (!(o->rho_inner_c > 0 && isfin(o->rho_inner_c))) return fail(GX_ERR_INVALID_ARG, "opts.rho_inner_c must be > 0");
+    if (o->inner_iters < 1 || o->inner_iters > 1000) return fail(GX_ERR_INVALID_ARG, "opts.inner_iters in [1, 1000]");
+    if (!(o->tol > 0) || !(o->adj_tol > 0)) return fail(GX_ERR_INVALID_ARG, "tolerances must be > 0");
+    if (o->max_iter < 1 || o->adj_max_iter < 1) return fail(GX_ERR_INVALID_ARG, "max_iter must be >= 1");
+    if (o->check_every < 1) return fail(GX_ERR_INVALID_ARG, "check_every must be >= 1");
+    if (!(o->tol_active >= 0)) return fail(GX_ERR_INVALID_ARG, "tol_active must be >= 0");
+    if (o->theta_weight != 0 && o->theta_weight != 1) return fail(GX_ERR_INVALID_ARG, "theta_weight is 0 or 1");
+    return GX_OK;
+}
+
+static void derive_network(NetH& h, const gx_opts& o) {
+    const int N = h.N;
+    h.gptr.assign(N + 1, 0); h.bptr.assign(N + 1, 0); h.eptr.assign(N + 1, 0);
+    for (int g = 0; g < h.G; ++g) h.gptr[h.gen_bus[g] + 1]++;
+    for (int b = 0; b < h.B; ++b) h.bptr[h.bat_bus[b] + 1]++;
+    for (int l = 0; l < h.L; ++l) { h.eptr[h.line_from[l] + 1]++; h.eptr[h.line_to[l] + 1]++; }
+    for (int n = 0; n < N; ++n) { h.gptr[n + 1] += h.gptr[n]; h.bptr[n + 1] += h.bptr[n]; h.eptr[n + 1] += h.eptr[n]; }
+    h.gidx.assign(h.G, 0); h.bidx.assign(h.B, 0); h.eidx.assign(2 * h.L, 0);
+    std::vector<int> fg(h.gptr.begin(), h.gptr.end() - 1), fb(h.bptr.begin(), h.bptr.end() - 1),
+        fe(h.eptr.begin(), h.eptr.end() - 1);
+    for (int g = 0; g < h.G; ++g) h.gidx[fg[h.gen_bus[g]]++] = g;
+    for (int b = 0; b < h.B; ++b) h.bidx[fb[h.bat_bus[b]]++] = b;
+    for (int l = 0; l < h.L; ++l) {
+        h.eidx[fe[h.line_from[l]]++] = 2 * l;
+        h.eidx[fe[h.line_to[l]]++] = 2 * l + 1;
+    }
+    double mb2 = 0;
+    for (int l = 0; l < h.L; ++l) mb2 += h.line_beta[l] * h.line_beta[l];
+    mb2 = h.L ? mb2 / h.L : 1.0;
+    h.l_w.resize(h.L);
+    for (int l = 0; l < h.L; ++l)
+        h.l_w[l] = (float)(o.theta_weight ? h.line_beta[l] * h.line_beta[l] : mb2);
+    h.inv_cnt.resize(N); h.inv_wsum.resize(N); h.dres_w.resize(N);
+    for (int n = 0; n < N; ++n) {
+        const int cnt = 1 + (h.gptr[n + 1] - h.gptr[n]) + (h.bptr[n + 1] - h.bptr[n]) + (h.eptr[n + 1] - h.eptr[n]);
+        h.inv_cnt[n] = 1.0f / cnt;
+        double ws = 0, dw = 0;
+        for (int q = h.eptr[n]; q < h.eptr[n + 1]; ++q) {
+            const int l = h.eidx[q] >> 1;
+            ws += h.l_w[l];
+            dw += (h.l_w[l] / h.line_beta[l]) * (h.l_w[l] / h.line_beta[l]);
+        }
+        h.inv_wsum[n] = ws > 0 ? (float)(1.0 / ws) : 0.f;
+        h.dres_w[n] = (float)dw;
+    }
+}
+
+gx_status gx_network_create(const gx_network_desc* nets, int n_nets, const gx_scenario_desc* scen, int S,
+                            const gx_opts* opts, gx_network** out) {
+    if (!out) return fail(GX_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!nets || n_nets < 1) return fail(GX_ERR_INVALID_ARG, "need at least one network");
+    if (!scen || S < 1) return fail(GX_ERR_INVALID_ARG, "need at least one scenario");
+    gx_opts o;
+    if (opts) o = *opts; else gx_opts_default(&o);
+    if (gx_status st = check_opts(&o)) return st;
+    gx_network* net = new gx_network();
+    net->opts = o;
+    net->n_nets = n_nets;
+    net->S = S;
+    net->nets.resize(n_nets);
+    int K = 0, gen0 = 0, line0 = 0, bat0 = 0, bus0 = 0, ptr0 = 0;
+    for (int k = 0; k < n_nets; ++k) {
+        const gx_network_desc& d = nets[k];
+        NetH& h = net->nets[k];
+        auto bad = [&](const std::string& m) {
+            delete net;
+            return fail(GX_ERR_INVALID_ARG, "network " + std::to_string(k) + ": " + m);
+        };
+        if (d.n_bus < 1 || d.n_gen < 0 || d.n_line < 0 || d.n_bat < 0) return bad("negative or zero sizes");
+        if ((d.n_gen && (!d.gen_bus || !d.gen_cost || !d.gen_emis)) ||
+            (d.n_line && (!d.line_from || !d.line_to || !d.line_beta || !d.line_dtheta)) ||
+            (d.n_bat && (!d.bat_bus || !d.bat_dur || !d.bat_eff_c || !d.bat_eff_d)))
+            return bad("NULL device array");
+        h.N = d.n_bus; h.G = d.n_gen; h.L = d.n_line; h.B = d.n_bat;
+        h.gen_bus.assign(d.gen_bus, d.gen_bus + h.G);
+        h.gen_cost.assign(d.gen_cost, d.gen_cost + h.G);
+        h.gen_emis.assign(d.gen_emis, d.gen_emis + h.G);
+        h.line_from.assign(d.line_from, d.line_from + h.L);
+        h.line_to.assign(d.line_to, d.line_to + h.L);
+        h.line_beta.assign(d.line_beta, d.line_beta + h.L);
+        h.line_dth.assign(d.line_dtheta, d.line_dtheta + h.L);
+        h.bat_bus.assign(d.bat_bus, d.bat_bus + h.B);
+        h.bat_dur.assign(d.bat_dur, d.bat_dur + h.B);
+        h.bat_effc.assign(d.bat_eff_c, d.bat_eff_c + h.B);
+        h.bat_effd.assign(d.bat_eff_d, d.bat_eff_d + h.B);
+        for (int g = 0; g < h.G; ++g) {
+            if (h.gen_bus[g] < 0 || h.gen_bus[g] >= h.N) return bad("gen_bus out of range");
+            if (!isfin(h.gen_cost[g]) || !isfin(h.gen_emis[g])) return bad("non-finite generator data");
+        }
+        for (int l = 0; l < h.L; ++l) {
+            if (h.line_from[l] < 0 || h.line_from[l] >= h.N || h.line_to[l] < 0 || h.line_to[l] >= h.N)
+                return bad("line bus out of range");
+            if (h.line_from[l] == h.line_to[l]) return bad("line with both ends on one bus");
+            if (!(h.line_beta[l] > 0 && isfin(h.line_beta[l]))) return bad("line_beta must be > 0");
+            if (!(h.line_dth[l] > 0 && isfin(h.line_dth[l]))) return bad("line_dtheta must be > 0");
+        }
+        for (int b = 0; b < h.B; ++b) {
+            if (h.bat_bus[b] < 0 || h.bat_bus[b] >= h.N) return bad("bat_bus out of range");
+            if (!(h.bat_dur[b] > 0 && isfin(h.bat_dur[b]))) return bad("bat_dur must be > 0");
+            if (!(h.bat_effc[b] > 0 && h.bat_effc[b] <= 1) || !(h.bat_effd[b] > 0 && h.bat_effd[b] <= 1))
+                return bad("battery efficiency must be in (0, 1]");
+        }
+        derive_network(h, o);
+        h.gen0 = gen0; h.line0 = line0; h.bat0 = bat0; h.bus0 = bus0; h.ptr0 = ptr0; h.eta0 = K;
+        gen0 += h.G; line0 += h.L; bat0 += h.B; bus0 += h.N; ptr0 += h.N + 1; K += h.G + h.L + h.B;
+    }
+    net->K = K;
+    net->tot_gen = gen0; net->tot_line = line0; net->tot_bat = bat0; net->tot_bus = bus0; net->tot_ptr = ptr0;
+    net->scens.resize(S);
+    net->sdev.resize(S);
+    long long eb = 0, eg = 0, el = 0, ebt = 0;
+    int gs = 0;
+    for (int s = 0; s < S; ++s) {
+        const gx_scenario_desc& d = scen[s];
+        auto bad = [&](const std::string& m) {
+            delete net;
+            return fail(GX_ERR_INVALID_ARG, "scenario " + std::to_string(s) + ": " + m);
+        };
+        if (d.net < 0 || d.net >= n_nets) return bad("net index out of range");
+        if (d.T < 1 || d.T > kMaxT) return bad("T must be in [1, 256]");
+        if (!(d.weight > 0 && isfin(d.weight))) return bad("weight must be > 0");
+        const NetH& h = net->nets[d.net];
+        if (!d.load || (h.G && !d.cf)) return bad("NULL load or cf");
+        ScenH& sh = net->scens[s];
+        sh.net = d.net; sh.T = d.T; sh.Tp = (d.T + 3) / 4 * 4; sh.weight = d.weight;
+        sh.load.assign((size_t)h.N * sh.Tp, 0.f);
+        sh.cf.assign((size_t)h.G * sh.Tp, 0.f);
+        double ln2 = 0;
+        for (int n = 0; n < h.N; ++n)
+            for (int t = 0; t < d.T; ++t) {
+                const double v = d.load[(size_t)n * d.T + t];
+                if (!(v >= 0 && isfin(v))) return bad("load must be finite and >= 0");
+                sh.load[(size_t)n * sh.Tp + t] = (float)v;
+                ln2 += v * v;
+            }
+        for (int g = 0; g < h.G; ++g)
+            for (int t = 0; t < d.T; ++t) {
+                const double v = d.cf[(size_t)g * d.T + t];
+                if (!(v >= 0 && v <= 1)) return bad("cf must be in [0, 1]");
+                sh.cf[(size_t)g * sh.Tp + t] = (float)v;
+            }
+        ScenDev& sd = net->sdev[s];
+        std::memset(&sd, 0, sizeof(sd));
+        sd.net = d.net; sd.T = d.T; sd.Tp = sh.Tp; sd.N = h.N; sd.G = h.G; sd.L = h.L; sd.B = h.B;
+        sd.gen0 = h.gen0; sd.line0 = h.line0; sd.bat0 = h.bat0; sd.bus0 = h.bus0; sd.ptr0 = h.ptr0; sd.eta0 = h.eta0;
+        sd.gs0 = gs;
+        gs += h.G + h.L + h.B;
+        sd.e_bus = eb; sd.e_gen = eg; sd.e_line = el; sd.e_bat = ebt;
+        eb += (long long)h.N * sh.Tp; eg += (long long)h.G * sh.Tp; el += (long long)h.L * sh.Tp;
+        ebt += (long long)h.B * sh.Tp;
+        sd.weight = (float)d.weight;
+        sd.load_norm = std::max(std::sqrt(ln2), 1e-30);
+        // block tables
+        sd.bus_blk0 = net->n_bus_blk;
+        sd.bus_nblk = (int)(((long long)h.N * sh.Tp + kBlock - 1) / kBlock);
+        for (int b = 0; b < sd.bus_nblk; ++b) net->bus_blk_scen.push_back(s);
+        net->n_bus_blk += sd.bus_nblk;
+        sd.line_blk0 = net->n_line_blk;
+        sd.line_nblk = (int)(((long long)h.L * sh.Tp + kBlock - 1) / kBlock);
+        for (int b = 0; b < sd.line_nblk; ++b) net->line_blk_scen.push_back(s);
+        net->n_line_blk += sd.line_nblk;
+        sd.bat_w0 = net->n_bat_warps;
+        for (int b = 0; b < h.B; ++b) net->bat_warp_scen.push_back(s);
+        net->n_bat_warps += h.B;
+        sd.cost_blk0 = net->n_cost_blk;
+        const long long work = (long long)(h.G + h.N + h.B) * sh.Tp;
+        const int ncb = (int)std::min<long long>(64, std::max<long long>(1, work / (kBlock * 16)));
+        for (int b = 0; b < ncb; ++b) net->cost_blk_scen.push_back(s);
+        net->n_cost_blk += ncb;
+        for (int r = 0; r < h.G + h.L + h.B; ++r) { net->gwarp.push_back(s); net->gwarp.push_back(r); }
+        net->n_gwarps += h.G + h.L + h.B;
+    }
+    net->gs_total = gs;
+    net->bus_el = eb; net->gen_el = eg; net->line_el = el; net->bat_el = ebt;
+    net->k_net.resize(K);
+    for (int k = 0; k < n_nets; ++k)
+        for (int q = 0; q < net->nets[k].G + net->nets[k].L + net->nets[k].B; ++q) net->k_net[net->nets[k].eta0 + q] = k;
+
+    // ---- layout
+    Layout& L = net->lay;
+    auto I4 = [](long long n) { return (size_t)std::max<long long>(n, 1) * 4; };
+    auto F4 = I4;
+    auto D8 = [](long long n) { return (size_t)std::max<long long>(n, 1) * 8; };
+    auto B1 = [](long long n) { return (size_t)std::max<long long>(n, 1); };
+    net->o_scen = L.add(sizeof(ScenDev) * S);
+    net->o_bbs = L.add(I4(net->n_bus_blk));
+    net->o_lbs = L.add(I4(net->n_line_blk));
+    net->o_bws = L.add(I4(net->n_bat_warps));
+    net->o_cbs = L.add(I4(net->n_cost_blk));
+    net->o_gwarp = L.add(I4(2LL * net->n_gwarps));
+    net->o_knet = L.add(I4(K));
+    net->o_gbus = L.add(I4(gen0)); net->o_gcost = L.add(F4(gen0)); net->o_gemis = L.add(F4(gen0));
+    net->o_gfirm = L.add(B1(gen0));
+    net->o_lfrom = L.add(I4(line0)); net->o_lto = L.add(I4(line0)); net->o_lbeta = L.add(F4(line0));
+    net->o_ldth = L.add(F4(line0)); net->o_lw = L.add(F4(line0));
+    net->o_bbus = L.add(I4(bat0)); net->o_bdur = L.add(F4(bat0)); net->o_beffc = L.add(F4(bat0));
+    net->o_beffd = L.add(F4(bat0));
+    net->o_gptr = L.add(I4(ptr0)); net->o_gidx = L.add(I4(gen0));
+    net->o_bptr = L.add(I4(ptr0)); net->o_bidx = L.add(I4(bat0));
+    net->o_eptr = L.add(I4(ptr0)); net->o_eidx = L.add(I4(2LL * line0));
+    net->o_icnt = L.add(F4(bus0)); net->o_iwsum = L.add(F4(bus0)); net->o_dresw = L.add(F4(bus0));
+    net->o_load = L.add(F4(eb)); net->o_cf = L.add(F4(eg)); net->o_dd = L.add(F4(ebt));
+    net->static_end = L.total;
+    const long long rows[16] = {eg, eb, el, el, el, el, ebt, ebt, ebt, ebt, ebt, ebt, ebt, eb, eb, eb};
+    for (int k = 0; k < 16; ++k) net->o_f[k] = L.add(F4(rows[k]));
+    for (int k = 0; k < 16; ++k) net->o_a[k] = L.add(F4(rows[k]));
+    net->o_mgen = L.add(B1(eg)); net->o_mload = L.add(B1(eb)); net->o_mline = L.add(B1(el)); net->o_mbat = L.add(B1(ebt));
+    net->o_done = L.add(I4(S)); net->o_iters = L.add(I4(S)); net->o_status = L.add(I4(S)); net->o_adjit = L.add(I4(S));
+    net->o_nact = L.add(I4(1)); net->o_inb = L.add(I4(S));
+    net->o_resid = L.add(D8(2LL * S)); net->o_cost = L.add(D8(S)); net->o_h = L.add(D8(S));
+    net->o_grads = L.add(D8(gs)); net->o_wprime = L.add(D8(S));
+    net->o_flow = L.add(F4(el)); net->o_price = L.add(F4(eb)); net->o_shed = L.add(F4(eb));
+    net->o_bpart = L.add(F4((long long)net->n_bus_blk * kBusPart));
+    net->o_lpart = L.add(F4((long long)net->n_line_blk * kDevPart));
+    net->o_btpart = L.add(F4((long long)net->n_bat_warps * kDevPart));
+    net->o_cpart = L.add(D8(2LL * net->n_cost_blk));
+    net->in_batch.assign(S, 0);
+    net->done_init.assign(S, 1);
+    net->wprime.assign(S, 0.0);
+    fill_dd(net);
+    *out = net;
+    return GX_OK;
+}
+
+gx_status gx_network_destroy(gx_network* net) {
+    delete net;
+    return GX_OK;
+}
+
+size_t gx_network_device_bytes(const gx_network* net) { return net ? net->lay.total : 0; }
+int gx_network_K(const gx_network* net) { return net ? net->K : 0; }
+int gx_network_S(const gx_network* net) { return net ? net->S : 0; }
+
+gx_status gx_network_bind(gx_network* net, void* dev_mem, size_t bytes, void* stream) {
+    if (!net) return fail(GX_ERR_INVALID_ARG, "net is NULL");
+    if (!dev_mem) return fail(GX_ERR_INVALID_ARG, "dev_mem is NULL");
+    if (reinterpret_cast<uintptr_t>(dev_mem) % 256) return fail(GX_ERR_INVALID_ARG, "dev_mem must be 256-byte aligned");
+    if (bytes < net->lay.total) return fail(GX_ERR_NO_MEMORY, "workspace smaller than gx_network_device_bytes()");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    net->dev = reinterpret_cast<uint8_t*>(dev_mem);
+    // Stage the static region on the host and upload it in one copy.
+    std::vector<uint8_t> h(net->static_end, 0);
+    auto put = [&](size_t off, const void* src, size_t n) { if (n) std::memcpy(h.data() + off, src, n); };
+    put(net->o_scen, net->sdev.data(), sizeof(ScenDev) * net->S);
+    put(net->o_bbs, net->bus_blk_scen.data(), 4 * net->bus_blk_scen.size());
+    put(net->o_lbs, net->line_blk_scen.data(), 4 * net->line_blk_scen.size());
+    put(net->o_bws, net->bat_warp_scen.data(), 4 * net->bat_warp_scen.size());
+    put(net->o_cbs, net->cost_blk_scen.data(), 4 * net->cost_blk_scen.size());
+    put(net->o_gwarp, net->gwarp.data(), 4 * net->gwarp.size());
+    put(net->o_knet, net->k_net.data(), 4 * net->k_net.size());
+    auto put_f = [&](size_t off, const std::vector<double>& v, size_t base) {
+        float* p = reinterpret_cast<float*>(h.data() + off) + base;
+        for (size_t i = 0; i < v.size(); ++i) p[i] = (float)v[i];
+    };
+    auto put_i = [&](size_t off, const std::vector<int>& v, size_t base) {
+        if (!v.empty()) std::memcpy(reinterpret_cast<int*>(h.data() + off) + base, v.data(), 4 * v.size());
+    };
+    auto put_v = [&](size_t off, const std::vector<float>& v, size_t base) {
+        if (!v.empty()) std::memcpy(reinterpret_cast<float*>(h.data() + off) + base, v.data(), 4 * v.size());
+    };
+    for (const NetH& n : net->nets) {
+        put_i(net->o_gbus, n.gen_bus, n.gen0); put_f(net->o_gcost, n.gen_cost, n.gen0); put_f(net->o_gemis, n.gen_emis, n.gen0);
+        put_i(net->o_lfrom, n.line_from, n.line0); put_i(net->o_lto, n.line_to, n.line0);
+        put_f(net->o_lbeta, n.line_beta, n.line0); put_f(net->o_ldth, n.line_dth, n.line0); put_v(net->o_lw, n.l_w, n.line0);
+        put_i(net->o_bbus, n.bat_bus, n.bat0); put_f(net->o_bdur, n.bat_dur, n.bat0);
+        put_f(net->o_beffc, n.bat_effc, n.bat0); put_f(net->o_beffd, n.bat_effd, n.bat0);
+        put_i(net->o_gptr, n.gptr, n.ptr0); put_i(net->o_gidx, n.gidx, n.gen0);
+        put_i(net->o_bptr, n.bptr, n.ptr0); put_i(net->o_bidx, n.bidx, n.bat0);
+        put_i(net->o_eptr, n.eptr, n.ptr0); put_i(net->o_eidx, n.eidx, 2 * (size_t)n.line0);
+        put_v(net->o_icnt, n.inv_cnt, n.bus0); put_v(net->o_iwsum, n.inv_wsum, n.bus0); put_v(net->o_dresw, n.dres_w, n.bus0);
+    }
+    // generators whose capacity factor is 1 in every hour of every scenario skip the cf read
+    std::vector<uint8_t> firm(std::max(net->tot_gen, 1), 1);
+    for (int s = 0; s < net->S; ++s) {
+        const ScenH& sc = net->scens[s];
+        const NetH& n = net->nets[sc.net];
+        put_v(net->o_load, sc.load, net->sdev[s].e_bus);
+        put_v(net->o_cf, sc.cf, net->sdev[s].e_gen);
+        for (int g = 0; g < n.G; ++g)
+            for (int t = 0; t < sc.T; ++t)
+                if (sc.cf[(size_t)g * sc.Tp + t] != 1.0f) { firm[n.gen0 + g] = 0; break; }
+    }
+    put(net->o_gfirm, firm.data(), net->tot_gen);
+    put_v(net->o_dd, net->dd_host, 0);
+    GX_CUDA(cudaMemcpyAsync(net->dev, h.data(), net->static_end, cudaMemcpyHostToDevice, st));
+    GX_CUDA(cudaMemsetAsync(net->dev + net->static_end, 0, net->lay.total - net->static_end, st));
+    GX_CUDA(cudaStreamSynchronize(st));
+    net->dd_dirty = false;
+    make_ctx(net);
+    net->solved = false;
+    net->adj_ready = false;
+    return GX_OK;
+}
+
+gx_status gx_network_set_opts(gx_network* net, const gx_opts* opts) {
+    if (!net || !opts) return fail(GX_ERR_INVALID_ARG, "NULL argument");
+    if (gx_status st = check_opts(opts)) return st;
+    if (opts->theta_weight != net->opts.theta_weight)
+        return fail(GX_ERR_INVALID_ARG, "theta_weight is fixed at create");
+    net->opts = *opts;
+    fill_dd(net);
+    if (net->dev) make_ctx(net);
+    return GX_OK;
+}
+
+gx_status gx_network_array(const gx_network* net, int which, int scen, size_t* offset, size_t* count) {
+    if (!net || !offset || !count) return fail(GX_ERR_INVALID_ARG, "NULL argument");
+    if (scen < -1 || scen >= net->S) return fail(GX_ERR_INVALID_ARG, "scenario out of range");
+    size_t base = 0, esz = 4;
+    long long e0 = 0, n = 0;
+    const ScenDev* sd = scen >= 0 ? &net->sdev[scen] : nullptr;
+    auto rows = [&](long long el_all, long long e_s, long long per) {
+        if (sd) { e0 = e_s; n = per; } else { e0 = 0; n = el_all; }
+    };
+    switch (which) {
+        case GX_ARR_P: base = net->o_f[0]; rows(net->gen_el, sd ? sd->e_gen : 0, sd ? (long long)sd->G * sd->Tp : 0); break;
+        case GX_ARR_SHED: base = net->o_shed; rows(net->bus_el, sd ? sd->e_bus : 0, sd ? (long long)sd->N * sd->Tp : 0); break;
+        case GX_ARR_FLOW: base = net->o_flow; rows(net->line_el, sd ? sd->e_line : 0, sd ? (long long)sd->L * sd->Tp : 0); break;
+        case GX_ARR_THETA: base = net->o_f[15]; rows(net->bus_el, sd ? sd->e_bus : 0, sd ? (long long)sd->N * sd->Tp : 0); break;
+        case GX_ARR_CH: base = net->o_f[7]; rows(net->bat_el, sd ? sd->e_bat : 0, sd ? (long long)sd->B * sd->Tp : 0); break;
+        case GX_ARR_DIS: base = net->o_f[8]; rows(net->bat_el, sd ? sd->e_bat : 0, sd ? (long long)sd->B * sd->Tp : 0); break;
+        case GX_ARR_SOC: base = net->o_f[9]; rows(net->bat_el, sd ? sd->e_bat : 0, sd ? (long long)sd->B * sd->Tp : 0); break;
+        case GX_ARR_PRICE: base = net->o_price; rows(net->bus_el, sd ? sd->e_bus : 0, sd ? (long long)sd->N * sd->Tp : 0); break;
+        case GX_ARR_COST: base = net->o_cost; esz = 8; rows(net->S, scen, 1); break;
+        case GX_ARR_H: base = net->o_h; esz = 8; rows(net->S, scen, 1); break;
+        case GX_ARR_ITERS: base = net->o_iters; rows(net->S, scen, 1); break;
+        case GX_ARR_RESID: base = net->o_resid; esz = 8; rows(2LL * net->S, 2LL * scen, 2); break;
+        case GX_ARR_STATUS: base = net->o_status; rows(net->S, scen, 1); break;
+        case GX_ARR_GRAD_S: base = net->o_grads; esz = 8;
+            rows(net->gs_total, sd ? sd->gs0 : 0, sd ? (long long)(sd->G + sd->L + sd->B) : 0); break;
+        case GX_ARR_ADJ_ITERS: base = net->o_adjit; rows(net->S, scen, 1); break;
+        default: return fail(GX_ERR_INVALID_ARG, "unknown array id");
+    }
+    *offset = base + (size_t)e0 * esz;
+    *count = (size_t)n;
+    return GX_OK;
+}
+
+gx_status gx_network_scenario_info(const gx_network* net, int s, int* T, int* Tp, int* N, int* G, int* L, int* B,
+                                   int* eta_offset) {
+    if (!net || s < 0 || s >= net->S) return fail(GX_ERR_INVALID_ARG, "bad scenario");
+    const ScenDev& d = net->sdev[s];
+    if (T) *T = d.T;
+    if (Tp) *Tp = d.Tp;
+    if (N) *N = d.N;
+    if (G) *G = d.G;
+    if (L) *L = d.L;
+    if (B) *B = d.B;
+    if (eta_offset) *eta_offset = d.eta0;
+    return GX_OK;
+}
+
+// Iterate the forward (adj = 0) or adjoint (adj = 1) message passing until every
+// scenario of the batch meets its tolerance or the cap is reached.
+static gx_status run_loop(gx_network* net, int adj, cudaStream_t st, int* launches, int* iters_out) {
+    const Ctx& c = net->ctx;
+    const int max_it = adj ? net->opts.adj_max_iter : net->opts.max_iter;
+    const double tol = adj ? net->opts.adj_tol : net->opts.tol;
+    const int every = net->opts.check_every;
+    const int mode = adj ? M_ADJ : M_FWD;
+    int it = 0, nact = 1;
+    while (it < max_it) {
+        const int chunk = std::min(every, max_it - it);
+        for (int j = 0; j < chunk; ++j) {
+            const int want = j == chunk - 1;
+            *launches += launch_dev(c, mode, adj, want, st);
+            *launches += launch_bus(c, mode, adj, want, st);
+        }
+        it += chunk;
+        GX_CUDA(cudaMemsetAsync(c.n_active, 0, sizeof(int), st));
+        *launches += launch_reduce(c, adj, it, tol, it >= max_it, st);
+        GX_CUDA(cudaGetLastError());
+        GX_CUDA(cudaMemcpyAsync(&nact, c.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+        GX_CUDA(cudaStreamSynchronize(st));
+        if (nact == 0) break;
+    }
+    *iters_out = it;
+    return GX_OK;
+}
+
+static gx_status upload_batch(gx_network* net, const int* scen_idx, int B, cudaStream_t st) {
+    std::vector<int>& inb = net->in_batch;
+    if (scen_idx) {
+        if (B < 1 || B > net->S) return fail(GX_ERR_INVALID_ARG, "batch size out of range");
+        std::fill(inb.begin(), inb.end(), 0);
+        for (int i = 0; i < B; ++i) {
+            if (scen_idx[i] < 0 || scen_idx[i] >= net->S) return fail(GX_ERR_INVALID_ARG, "scenario index out of range");
+            inb[scen_idx[i]] = 1;
+        }
+    } else {
+        std::fill(inb.begin(), inb.end(), 1);
+    }
+    for (int s = 0; s < net->S; ++s) net->done_init[s] = inb[s] ? 0 : 1;
+    GX_CUDA(cudaMemcpyAsync(net->dev + net->o_inb, inb.data(), 4 * net->S, cudaMemcpyHostToDevice, st));
+    GX_CUDA(cudaMemcpyAsync(net->dev + net->o_done, net->done_init.data(), 4 * net->S, cudaMemcpyHostToDevice, st));
+    return GX_OK;
+}
+
+static gx_status collect_stats(gx_network* net, int adj, gx_stats* stats, int launches, cudaStream_t st,
+                               gx_status* overall) {
+    std::vector<int> its(net->S), sts(net->S);
+    std::vector<double> res(2 * net->S);
+    GX_CUDA(cudaMemcpyAsync(its.data(), net->dev + (adj ? net->o_adjit : net->o_iters), 4 * net->S,
+                            cudaMemcpyDeviceToHost, st));
+    GX_CUDA(cudaMemcpyAsync(sts.data(), net->dev + net->o_status, 4 * net->S, cudaMemcpyDeviceToHost, st));
+    GX_CUDA(cudaMemcpyAsync(res.data(), net->dev + net->o_resid, 16 * net->S, cudaMemcpyDeviceToHost, st));
+    GX_CUDA(cudaStreamSynchronize(st));
+    gx_stats sx{};
+    sx.launches = launches;
+    gx_status worst = GX_OK;
+    for (int s = 0; s < net->S; ++s) {
+        if (!net->in_batch[s]) continue;
+        sx.n_scen++;
+        sx.iters_max = std::max(sx.iters_max, its[s]);
+        if (sts[s] == GX_OK) sx.n_converged++;
+        sx.max_primal = std::max(sx.max_primal, res[2 * s]);
+        sx.max_dual = std::max(sx.max_dual, res[2 * s + 1]);
+        if (sts[s] < 0) worst = sts[s];
+        else if (sts[s] > 0 && worst == GX_OK) worst = sts[s];
+    }
+    if (stats) *stats = sx;
+    *overall = worst;
+    return GX_OK;
+}
+
+gx_status gx_dispatch_solve_batch(gx_network* net, const float* eta_dev, const int* scen_idx, int B, int warm,
+                                  const float* warm_dev, gx_stats* stats, void* stream) {
+    if (!net) return fail(GX_ERR_INVALID_ARG, "net is NULL");
+    if (!net->dev) return fail(GX_ERR_STATE, "network is not bound");
+    if (!eta_dev) return fail(GX_ERR_INVALID_ARG, "eta_dev is NULL");
+    if (warm < GX_WARM_COLD || warm > GX_WARM_USER) return fail(GX_ERR_INVALID_ARG, "unsupported warm mode");
+    if (warm == GX_WARM_USER && !warm_dev) return fail(GX_ERR_INVALID_ARG, "GX_WARM_USER needs warm_dev");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (gx_status e = upload_batch(net, scen_idx, B, st)) return e;
+    if (net->dd_dirty) {
+        GX_CUDA(cudaMemcpyAsync(net->dev + net->o_dd, net->dd_host.data(), 4 * net->dd_host.size(),
+                                cudaMemcpyHostToDevice, st));
+        GX_CUDA(cudaStreamSynchronize(st));
+        net->dd_dirty = false;
+    }
+    Ctx& c = net->ctx;
+    c.eta = eta_dev;
+    c.warm = warm == GX_WARM_USER ? warm_dev : nullptr;
+    int launches = 0;
+    if (warm != GX_WARM_PREV || !net->solved) {
+        launches += launch_dev(c, M_RESET, 0, 0, st);
+        launches += launch_bus(c, M_RESET, 0, 0, st);
+        launches += launch_bus(c, M_INIT, 0, 0, st);
+    }
+    c.warm = nullptr;
+    int it = 0;
+    if (gx_status e = run_loop(net, 0, st, &launches, &it)) return e;
+    launches += launch_extract(c, reinterpret_cast<const int*>(net->dev + net->o_inb), st);
+    GX_CUDA(cudaGetLastError());
+    gx_status overall;
+    if (gx_status e = collect_stats(net, 0, stats, launches, st, &overall)) return e;
+    net->solved = true;
+    return overall;
+}
+
+gx_status gx_dispatch_grad_batch(gx_network* net, const float* eta_dev, int warm, float* grad_dev, gx_stats* stats,
+                                 void* stream) {
+    if (!net) return fail(GX_ERR_INVALID_ARG, "net is NULL");
+    if (!net->dev) return fail(GX_ERR_STATE, "network is not bound");
+    if (!net->solved) return fail(GX_ERR_STATE, "gx_dispatch_grad_batch needs a solve first");
+    if (!eta_dev || !grad_dev) return fail(GX_ERR_INVALID_ARG, "NULL device pointer");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    Ctx& c = net->ctx;
+    c.eta = eta_dev;
+    c.warm = nullptr;
+    // the batch of the last solve, with weights rescaled to the total weight
+    double wall = 0, wb = 0;
+    for (int s = 0; s < net->S; ++s) {
+        wall += net->scens[s].weight;
+        if (net->in_batch[s]) wb += net->scens[s].weight;
+    }
+    for (int s = 0; s < net->S; ++s) net->wprime[s] = net->in_batch[s] ? net->scens[s].weight * wall / wb : 0.0;
+    GX_CUDA(cudaMemcpyAsync(net->dev + net->o_wprime, net->wprime.data(), 8 * net->S, cudaMemcpyHostToDevice, st));
+    GX_CUDA(cudaMemcpyAsync(net->dev + net->o_done, net->done_init.data(), 4 * net->S, cudaMemcpyHostToDevice, st));
+    int launches = 0;
+    launches += launch_dev(c, M_MASK, 0, 0, st);
+    launches += launch_bus(c, M_MASK, 0, 0, st);
+    const bool envelope = net->opts.grad_envelope && net->opts.kappa == 0.0;
+    gx_status overall = GX_OK;
+    gx_stats sx{};
+    if (!envelope) {
+        if (warm != GX_WARM_PREV || !net->adj_ready) {
+            launches += launch_dev(c, M_RESET, 1, 0, st);
+            launches += launch_bus(c, M_RESET, 1, 0, st);
+        }
+        launches += launch_bus(c, M_INIT, 1, 0, st);
+        int it = 0;
+        if (gx_status e = run_loop(net, 1, st, &launches, &it)) return e;
+        net->adj_ready = true;
+    }
+    const int* inb = reinterpret_cast<const int*>(net->dev + net->o_inb);
+    launches += launch_grad(c, envelope ? 1 : 0, reinterpret_cast<const int*>(net->dev + net->o_gwarp), net->n_gwarps,
+                            inb, st);
+    launches += launch_grad_combine(c, reinterpret_cast<const double*>(net->dev + net->o_wprime),
+                                    reinterpret_cast<const int*>(net->dev + net->o_knet), grad_dev, net->K, st);
+    GX_CUDA(cudaGetLastError());
+    if (!envelope) {
+        if (gx_status e = collect_stats(net, 1, &sx, launches, st, &overall)) return e;
+    } else {
+        GX_CUDA(cudaStreamSynchronize(st));
+        sx.launches = launches;
+    }
+    if (stats) *stats = sx;
+    return overall;
+}
+
+gx_status gx_plan_step(gx_network* net, float* eta_dev, const float* grad_dev, const float* gamma_dev,
+                       const float* eta_min_dev, const float* eta_max_dev, float alpha, void* stream) {
+    if (!net) return fail(GX_ERR_INVALID_ARG, "net is NULL");
+    if (!eta_dev || !grad_dev || !gamma_dev || !eta_min_dev || !eta_max_dev)
+        return fail(GX_ERR_INVALID_ARG, "NULL device pointer");
+    if (!(alpha >= 0) || !std::isfinite(alpha)) return fail(GX_ERR_INVALID_ARG, "alpha must be finite and >= 0");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    launch_plan_step(eta_dev, grad_dev, gamma_dev, eta_min_dev, eta_max_dev, alpha, net->K, st);
+    GX_CUDA(cudaGetLastError());
+    return GX_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,856 @@
+// sm_103a kernels of the batched proximal message-passing dispatch solver and its adjoint.
+//
+// One outer iteration (proximal message passing: ADMM with a proximal step per device
+// and an averaging step per bus) is three launches:
+//   k_line  one thread per (line, hour): phase-dual update and the closed-form line prox
+//   k_bat   one warp per battery: a warm-started inner ADMM on the battery prox QP whose
+//           equality-constrained step is a tridiagonal solve done with warp scans
+//   k_bus   one thread per (bus, hour): generator and load proxes (fused), the bus
+//           consensus (average injection and average angle), the scaled dual update and
+//           the residual partial sums
+// The same kernels run the adjoint (Section 2.2, implicit function theorem): there the
+// clip of every prox becomes a fixed active-set mask and the linear costs come from
+// grad h at the solved dispatch, so the iteration solves the linearised KKT system.
+//
+// Memory: every array is a row of Tp floats per device (hours contiguous), so each warp
+// reads 32 consecutive hours of one row: coalesced 128-byte transactions.  Bus arrays
+// (p_bar, u, theta_bar) are gathered by the device kernels through the same row layout.
+#include "gx_internal.cuh"
+
+#include <cfloat>
+
+namespace gx {
+
+namespace {
+
+__device__ __forceinline__ float clampf(float x, float lo, float hi) { return fminf(fmaxf(x, lo), hi); }
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum NV values over a block of kBlock threads; thread 0 gets the totals in v[].
+template <int NV>
+__device__ __forceinline__ void block_sum(float (&v)[NV], float (*sh)[kBlock / 32]) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        float s = warp_sum(v[k]);
+        if (lane == 0) sh[k][w] = s;
+    }
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            float s = lane < kBlock / 32 ? sh[k][lane] : 0.f;
+            v[k] = warp_sum(s);
+        }
+    }
+}
+
+struct StatePtrs {
+    float *xg, *xl, *dl, *sg, *vf, *vt, *xb, *zc, *zd, *zs, *yc, *yd, *ys, *u, *pbar, *thb;
+};
+
+template <int ADJ>
+__device__ __forceinline__ StatePtrs state(const Ctx& c) {
+    if (ADJ)
+        return StatePtrs{c.a_xg, c.a_xl, c.a_dl, c.a_sg, c.a_vf, c.a_vt, c.a_xb, c.a_zc, c.a_zd, c.a_zs,
+                         c.a_yc, c.a_yd, c.a_ys, c.a_u, c.a_pbar, c.a_thb};
+    return StatePtrs{c.xg, c.xl, c.dl, c.sg, c.vf, c.vt, c.xb, c.zc, c.zd, c.zs,
+                     c.yc, c.yd, c.ys, c.u, c.pbar, c.thb};
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------
+// Line prox.  With delta = th_f - th_t and sigma = th_f + th_t the prox of a lossless DC
+// line separates: sigma = w_f + w_t, and delta minimises the 1-D quadratic
+//   rho/2 [(-beta d - v_f)^2 + (beta d - v_t)^2] + rho_th/4 (d - (w_f - w_t))^2
+// over |beta d| <= eta_l, |d| <= dtheta_max, i.e. the unconstrained minimiser clipped.
+// ------------------------------------------------------------------------------------
+template <int MODE, int ADJ>
+__global__ void __launch_bounds__(kBlock) k_line(const Ctx c, int want_res) {
+    const int blk = blockIdx.x;
+    const int s = c.line_blk_scen[blk];
+    if (c.done[s]) return;
+    const ScenDev sc = c.scen[s];
+    const StatePtrs X = state<ADJ>(c);
+    const int local = (blk - sc.line_blk0) * kBlock + threadIdx.x;
+    const int l = local / sc.Tp;
+    const int t = local - l * sc.Tp;
+    const bool valid = (l < sc.L) && (t < sc.T);
+    float dx2 = 0.f, x2 = 0.f;
+    if (valid) {
+        const long long row = sc.e_line + (long long)l * sc.Tp + t;
+        const int lg = sc.line0 + l;
+        const int f = c.l_from[lg], to = c.l_to[lg];
+        const float beta = c.l_beta[lg];
+        const long long bf = sc.e_bus + (long long)f * sc.Tp + t;
+        const long long bt = sc.e_bus + (long long)to * sc.Tp + t;
+        if (MODE == M_RESET) {
+            float d0 = 0.f, g0 = 0.f;
+            if (!ADJ && c.warm) {
+                const float* th = c.warm + (c.warm_half);
+                d0 = th[bf] - th[bt];
+                g0 = th[bf] + th[bt];
+            }
+            X.dl[row] = d0; X.sg[row] = g0; X.vf[row] = 0.f; X.vt[row] = 0.f;
+        } else {
+            const float d = X.dl[row], g = X.sg[row];
+            float vf = X.vf[row], vt = X.vt[row];
+            const float pbf = X.pbar[bf], uf = X.u[bf], thf = X.thb[bf];
+            const float pbt = X.pbar[bt], ut = X.u[bt], tht = X.thb[bt];
+            // dual update of the previous iteration's phase consensus
+            vf += 0.5f * (g + d) - thf;
+            vt += 0.5f * (g - d) - tht;
+            const float wf = thf - vf, wt = tht - vt;
+            const float tf = -beta * d - pbf - uf;  // power targets of the two terminals
+            const float tt = beta * d - pbt - ut;
+            const float rth = c.rth_c * c.l_w[lg];
+            const float den = 2.f * c.rho * beta * beta + 0.5f * rth;
+            const float dun = (c.rho * beta * (tt - tf) + 0.5f * rth * (wf - wt)) / den;
+            const float etal = fmaxf(c.eta[sc.eta0 + sc.G + l], 0.f);
+            const float capf = etal / beta, dth = c.l_dth[lg];
+            const float cap = fminf(capf, dth);
+            if (MODE == M_MASK) {
+                uint8_t code = AL_FREE;
+                const float over = fabsf(dun) - cap;
+                if (over > 0.f && den * over / beta > c.tol_act) {
+                    const bool flow = capf <= dth;
+                    code = dun > 0.f ? (flow ? AL_FUP : AL_AUP) : (flow ? AL_FLO : AL_ALO);
+                }
+                c.m_line[row] = code;
+            } else {
+                float dn;
+                if (ADJ) dn = c.m_line[row] ? 0.f : dun;
+                else dn = clampf(dun, -cap, cap);
+                X.dl[row] = dn;
+                X.sg[row] = wf + wt;
+                X.vf[row] = vf;
+                X.vt[row] = vt;
+                const float dd = dn - d;
+                dx2 = 2.f * beta * beta * dd * dd;
+                x2 = 2.f * beta * beta * dn * dn;
+            }
+        }
+    }
+    if ((MODE == M_FWD || MODE == M_ADJ) && want_res) {
+        __shared__ float sh[2][kBlock / 32];
+        float v[2] = {dx2, x2};
+        block_sum<2>(v, sh);
+        if (threadIdx.x == 0) {
+            c.line_part[blk * kDevPart + 0] = v[0];
+            c.line_part[blk * kDevPart + 1] = v[1];
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Battery prox, one warp per battery, hours split in contiguous chunks of hpl per lane.
+//   min sum_t eps/2 (c^2 + d^2) + q_c c + q_d d + rho/2 (d - c - v_t)^2
+//   s.t. s_t = s_{t-1} + a c_t - k d_t (s_{-1} = 0), box bounds on c, d, s,
+// solved by inner ADMM (x = (c, d, s) with the dynamics, z = box copy).  The x-step is
+// an equality-constrained QP whose multipliers mu solve a constant tridiagonal system
+// (pivots precomputed in bat_dd); its two Thomas sweeps are first-order linear
+// recurrences evaluated with warp-wide affine scans.
+// ------------------------------------------------------------------------------------
+template <int MODE, int ADJ>
+__global__ void __launch_bounds__(kBlock) k_bat(const Ctx c, int want_res) {
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * kBatWarps + (threadIdx.x >> 5);
+    if (gw >= c.n_bat_warps) return;
+    const int s = c.bat_warp_scen[gw];
+    if (c.done[s]) return;
+    const ScenDev sc = c.scen[s];
+    const StatePtrs X = state<ADJ>(c);
+    const int b = gw - sc.bat_w0;
+    const int bg = sc.bat0 + b;
+    const int T = sc.T;
+    const int hpl = (T + 31) >> 5;
+    const int t0 = lane * hpl;
+    const long long row0 = sc.e_bat + (long long)b * sc.Tp;
+    const long long brow0 = sc.e_bus + (long long)c.b_bus[bg] * sc.Tp;
+
+    if (MODE == M_RESET) {
+        for (int t = lane; t < sc.Tp; t += 32) {
+            const long long r = row0 + t;
+            X.xb[r] = 0.f; X.zc[r] = 0.f; X.zd[r] = 0.f; X.zs[r] = 0.f;
+            X.yc[r] = 0.f; X.yd[r] = 0.f; X.ys[r] = 0.f;
+        }
+        return;
+    }
+    const float rho = c.rho, eps = c.eps, ri = c.rho_in;
+    if (MODE == M_MASK) {
+        // active set from the inner box multipliers of the forward solution
+        for (int t = lane; t < T; t += 32) {
+            const long long r = row0 + t;
+            const float y3[3] = {c.yc[r], c.yd[r], c.ys[r]};
+            uint8_t code = 0;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                uint8_t a = A_FREE;
+                if (y3[q] > c.tol_act) a = A_UP;
+                else if (y3[q] < -c.tol_act) a = A_LO;
+                code |= a << (2 * q);
+            }
+            c.m_bat[r] = code;
+        }
+        return;
+    }
+    const float P = fmaxf(c.eta[sc.eta0 + sc.G + sc.L + b], 0.f);
+    const float E = c.b_dur[bg] * P;
+    const float a = c.b_effc[bg], k = 1.f / c.b_effd[bg];
+    const float Ah = eps + ri + rho;
+    const float det = Ah * Ah - rho * rho;
+    const float idet = 1.f / det;
+    const float gc = (Ah * a - rho * k) * idet;   // d(c)/d(mu)
+    const float gd = (rho * a - Ah * k) * idet;   // d(d)/d(mu)
+
+    float v[kHplMax], zc[kHplMax], zd[kHplMax], zs[kHplMax], yc[kHplMax], yd[kHplMax], ys[kHplMax];
+    float lo[3][kHplMax], hi[3][kHplMax], qc[kHplMax], qd[kHplMax];
+    float idd[kHplMax], iddp[kHplMax];  // 1/dd_t and 1/dd_{t-1} (0 for t = 0)
+    float xb_old[kHplMax];
+#pragma unroll
+    for (int j = 0; j < kHplMax; ++j) {
+        const int t = t0 + j;
+        const bool ok = (j < hpl) && (t < T);
+        v[j] = zc[j] = zd[j] = zs[j] = yc[j] = yd[j] = ys[j] = 0.f;
+        qc[j] = qd[j] = 0.f; idd[j] = iddp[j] = 0.f; xb_old[j] = 0.f;
+        lo[0][j] = lo[1][j] = lo[2][j] = 0.f;
+        hi[0][j] = hi[1][j] = hi[2][j] = 0.f;
+        if (ok) {
+            const long long r = row0 + t;
+            xb_old[j] = X.xb[r];
+            v[j] = xb_old[j] - X.pbar[brow0 + t] - X.u[brow0 + t];
+            zc[j] = X.zc[r]; zd[j] = X.zd[r]; zs[j] = X.zs[r];
+            yc[j] = X.yc[r]; yd[j] = X.yd[r]; ys[j] = X.ys[r];
+            idd[j] = 1.f / c.bat_dd[r];
+            iddp[j] = t > 0 ? 1.f / c.bat_dd[r - 1] : 0.f;
+            if (ADJ) {
+                const uint8_t m = c.m_bat[r];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    const bool fixed = ((m >> (2 * q)) & 3) != A_FREE;
+                    lo[q][j] = fixed ? 0.f : -FLT_MAX;
+                    hi[q][j] = fixed ? 0.f : FLT_MAX;
+                }
+                qc[j] = -eps * c.zc[r];
+                qd[j] = -eps * c.zd[r];
+            } else {
+                hi[0][j] = P; hi[1][j] = P; hi[2][j] = E;
+            }
+        }
+    }
+
+    float cx[kHplMax], dx[kHplMax];
+#pragma unroll
+    for (int j = 0; j < kHplMax; ++j) { cx[j] = 0.f; dx[j] = 0.f; }
+
+    for (int it = 0; it < c.inner_iters; ++it) {
+        float c0[kHplMax], d0[kHplMax], rs[kHplMax], rhs[kHplMax];
+#pragma unroll
+        for (int j = 0; j < kHplMax; ++j) {
+            const float rc = zc[j] - yc[j] / ri, rd = zd[j] - yd[j] / ri;
+            rs[j] = zs[j] - ys[j] / ri;
+            const float b1 = ri * rc - rho * v[j] - qc[j];
+            const float b2 = ri * rd + rho * v[j] - qd[j];
+            c0[j] = (Ah * b1 + rho * b2) * idet;
+            d0[j] = (rho * b1 + Ah * b2) * idet;
+        }
+        // previous hour's r_s for the first hour of the chunk (0 before hour 0)
+        float rs_last = 0.f;
+#pragma unroll
+        for (int j = 0; j < kHplMax; ++j) if (j == hpl - 1) rs_last = rs[j];
+        float rs_prev = __shfl_up_sync(0xffffffffu, rs_last, 1);
+        if (lane == 0) rs_prev = 0.f;
+        // forward sweep y_t = rhs_t + y_{t-1} / dd_{t-1}
+        float A = 1.f, Bv = 0.f;
+#pragma unroll
+        for (int j = 0; j < kHplMax; ++j) {
+            const int t = t0 + j;
+            const bool ok = (j < hpl) && (t < T);
+            const float prev = j == 0 ? rs_prev : rs[j > 0 ? j - 1 : 0];
+            rhs[j] = ok ? ri * (rs[j] - prev - (a * c0[j] - k * d0[j])) : 0.f;
+            if (ok) { A = iddp[j] * A; Bv = iddp[j] * Bv + rhs[j]; }
+        }
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const float Ao = __shfl_up_sync(0xffffffffu, A, o);
+            const float Bo = __shfl_up_sync(0xffffffffu, Bv, o);
+            if (lane >= o) { Bv = A * Bo + Bv; A = A * Ao; }
+        }
+        float yin = __shfl_up_sync(0xffffffffu, Bv, 1);
+        if (lane == 0) yin = 0.f;
+        float yv[kHplMax];
+#pragma unroll
+        for (int j = 0; j < kHplMax; ++j) {
+            const int t = t0 + j;
+            const bool ok = (j < hpl) && (t < T);
+            if (ok) yin = iddp[j] * yin + rhs[j];
+            yv[j] = yin;
+        }
+        // backward sweep mu_t = (y_t + mu_{t+1}) / dd_t, mu_T = 0
+        A = 1.f; Bv = 0.f;
+#pragma unroll
+        for (int j = kHplMax - 1; j >= 0; --j) {
+            const int t = t0 + j;
+            const bool ok = (j < hpl) && (t < T);
+            if (ok) { A = idd[j] * A; Bv = idd[j] * Bv + idd[j] * yv[j]; }
+        }
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const float Ao = __shfl_down_sync(0xffffffffu, A, o);
+            const float Bo = __shfl_down_sync(0xffffffffu, Bv, o);
+            if (lane + o < 32) { Bv = A * Bo + Bv; A = A * Ao; }
+        }
+        float min_ = __shfl_down_sync(0xffffffffu, Bv, 1);
+        if (lane == 31) min_ = 0.f;
+        float mu[kHplMax];
+        float mnext = min_;
+#pragma unroll
+        for (int j = kHplMax - 1; j >= 0; --j) {
+            const int t = t0 + j;
+            const bool ok = (j < hpl) && (t < T);
+            mu[j] = 0.f;
+            if (ok) { mnext = idd[j] * (yv[j] + mnext); mu[j] = mnext; }
+        }
+        // x = (c, d, s), then the box projection and the inner dual step
+#pragma unroll
+        for (int j = 0; j < kHplMax; ++j) {
+            const int t = t0 + j;
+            const bool ok = (j < hpl) && (t < T);
+            if (!ok) continue;
+            float mu_n;
+            if (t + 1 >= T) mu_n = 0.f;
+            else if (j + 1 < hpl) mu_n = mu[j + 1 < kHplMax ? j + 1 : j];
+            else mu_n = min_;
+            const float cc = c0[j] + mu[j] * gc;
+            const float dd_ = d0[j] + mu[j] * gd;
+            const float ss = rs[j] - (mu[j] - mu_n) / ri;
+            const float nzc = clampf(cc + yc[j] / ri, lo[0][j], hi[0][j]);
+            const float nzd = clampf(dd_ + yd[j] / ri, lo[1][j], hi[1][j]);
+            const float nzs = clampf(ss + ys[j] / ri, lo[2][j], hi[2][j]);
+            yc[j] += ri * (cc - nzc);
+            yd[j] += ri * (dd_ - nzd);
+            ys[j] += ri * (ss - nzs);
+            zc[j] = nzc; zd[j] = nzd; zs[j] = nzs;
+            cx[j] = cc; dx[j] = dd_;
+        }
+        // mu_n for a chunk's last hour reads the next lane's first mu: the shuffle above
+        // (min_) is that value because the suffix scan composes whole chunks.
+    }
+    float dx2 = 0.f, x2 = 0.f;
+#pragma unroll
+    for (int j = 0; j < kHplMax; ++j) {
+        const int t = t0 + j;
+        const bool ok = (j < hpl) && (t < T);
+        if (!ok) continue;
+        const long long r = row0 + t;
+        const float xn = dx[j] - cx[j];
+        X.xb[r] = xn;
+        X.zc[r] = zc[j]; X.zd[r] = zd[j]; X.zs[r] = zs[j];
+        X.yc[r] = yc[j]; X.yd[r] = yd[j]; X.ys[r] = ys[j];
+        dx2 += (xn - xb_old[j]) * (xn - xb_old[j]);
+        x2 += xn * xn;
+    }
+    if (want_res) {
+        dx2 = warp_sum(dx2);
+        x2 = warp_sum(x2);
+        if (lane == 0) {
+            c.bat_part[gw * kDevPart + 0] = dx2;
+            c.bat_part[gw * kDevPart + 1] = x2;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Bus kernel: generator and load proxes (closed-form clips), then the consensus step.
+// ------------------------------------------------------------------------------------
+template <int MODE, int ADJ>
+__global__ void __launch_bounds__(kBlock) k_bus(const Ctx c, int want_res) {
+    const int blk = blockIdx.x;
+    const int s = c.bus_blk_scen[blk];
+    if (c.done[s]) return;
+    const ScenDev sc = c.scen[s];
+    const StatePtrs X = state<ADJ>(c);
+    const int local = (blk - sc.bus_blk0) * kBlock + threadIdx.x;
+    const int n = local / sc.Tp;
+    const int t = local - n * sc.Tp;
+    const bool valid = (n < sc.N) && (t < sc.T);
+    float acc[kBusPart] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (valid) {
+        const long long i = sc.e_bus + (long long)n * sc.Tp + t;
+        const int nb = sc.ptr0 + n;
+        const float rho = c.rho, eps = c.eps;
+        const float inv_re = 1.f / (rho + eps);
+        if (MODE == M_RESET) {
+            const float Lnt = c.load[i];
+            X.xl[i] = ADJ ? 0.f : -Lnt;
+            X.u[i] = (!ADJ && c.warm) ? -c.warm[i] / rho : 0.f;
+            X.pbar[i] = 0.f;
+            X.thb[i] = (!ADJ && c.warm) ? c.warm[c.warm_half + i] : 0.f;
+            for (int q = c.bus_gptr[nb]; q < c.bus_gptr[nb + 1]; ++q) {
+                const int g = c.bus_gidx[sc.gen0 + q];
+                X.xg[sc.e_gen + (long long)g * sc.Tp + t] = 0.f;
+            }
+        } else {
+            const float pb = X.pbar[i], uu = X.u[i], thold = X.thb[i];
+            float sum = 0.f, dx2 = 0.f, x2 = 0.f;
+            // generators
+            for (int q = c.bus_gptr[nb]; q < c.bus_gptr[nb + 1]; ++q) {
+                const int g = c.bus_gidx[sc.gen0 + q];
+                const int gg = sc.gen0 + g;
+                const long long r = sc.e_gen + (long long)g * sc.Tp + t;
+                const float x = X.xg[r];
+                float xn = x;
+                if (MODE == M_FWD || MODE == M_ADJ || MODE == M_MASK) {
+                    const float v = x - pb - uu;
+                    if (ADJ) {
+                        const float gh = c.g_cost[gg] + eps * c.xg[r] + c.kappa * c.g_emis[gg];
+                        xn = c.m_gen[r] ? 0.f : (rho * v + gh) * inv_re;
+                    } else {
+                        const float etag = fmaxf(c.eta[sc.eta0 + g], 0.f);
+                        const float cap = c.g_firm[gg] ? etag : c.cf[r] * etag;
+                        const float pun = (rho * v - c.g_cost[gg]) * inv_re;
+                        if (MODE == M_MASK) {
+                            uint8_t code = A_FREE;
+                            if (pun > cap && (rho + eps) * (pun - cap) > c.tol_act) code = A_UP;
+                            else if (pun < 0.f && -(rho + eps) * pun > c.tol_act) code = A_LO;
+                            c.m_gen[r] = code;
+                        } else {
+                            xn = clampf(pun, 0.f, cap);
+                        }
+                    }
+                    if (MODE != M_MASK) X.xg[r] = xn;
+                }
+                sum += xn;
+                dx2 += (xn - x) * (xn - x);
+                x2 += xn * xn;
+            }
+            // load (shed variable; terminal injection shed - L)
+            {
+                const float x = X.xl[i];
+                float xn = x;
+                if (MODE == M_FWD || MODE == M_ADJ || MODE == M_MASK) {
+                    const float v = x - pb - uu;
+                    const float Lnt = c.load[i];
+                    if (ADJ) {
+                        const float gsh = c.voll + eps * (c.xl[i] + Lnt);
+                        xn = c.m_load[i] ? 0.f : (rho * v + gsh) * inv_re;
+                    } else {
+                        const float sun = (rho * (v + Lnt) - c.voll) * inv_re;
+                        if (MODE == M_MASK) {
+                            uint8_t code = A_FREE;
+                            if (sun > Lnt && (rho + eps) * (sun - Lnt) > c.tol_act) code = A_UP;
+                            else if (sun < 0.f && -(rho + eps) * sun > c.tol_act) code = A_LO;
+                            c.m_load[i] = code;
+                        } else {
+                            xn = clampf(sun, 0.f, Lnt) - Lnt;
+                        }
+                    }
+                    if (MODE != M_MASK) X.xl[i] = xn;
+                }
+                sum += xn;
+                dx2 += (xn - x) * (xn - x);
+                x2 += xn * xn;
+            }
+            if (MODE != M_MASK) {
+                // batteries (their prox ran in k_bat this iteration)
+                for (int q = c.bus_bptr[nb]; q < c.bus_bptr[nb + 1]; ++q) {
+                    const int b = c.bus_bidx[sc.bat0 + q];
+                    const float xb = X.xb[sc.e_bat + (long long)b * sc.Tp + t];
+                    sum += xb;
+                    x2 += xb * xb;
+                }
+                // line ends (their prox ran in k_line this iteration)
+                const int e0 = c.bus_eptr[nb], e1 = c.bus_eptr[nb + 1];
+                float ths = 0.f;
+                for (int q = e0; q < e1; ++q) {
+                    const int e = c.bus_eidx[2 * sc.line0 + q];
+                    const int l = e >> 1, side = e & 1;
+                    const long long r = sc.e_line + (long long)l * sc.Tp + t;
+                    const float d = X.dl[r], g = X.sg[r];
+                    const float beta = c.l_beta[sc.line0 + l];
+                    const float p = side ? beta * d : -beta * d;
+                    const float y = side ? 0.5f * (g - d) : 0.5f * (g + d);
+                    sum += p;
+                    x2 += p * p;
+                    ths += c.l_w[sc.line0 + l] * y;
+                }
+                const float icnt = c.bus_inv_cnt[sc.bus0 + n];
+                const float pbn = sum * icnt;
+                const float thn = ths * c.bus_inv_wsum[sc.bus0 + n];
+                if (MODE == M_INIT) {
+                    X.pbar[i] = pbn;
+                    X.thb[i] = thn;
+                } else {
+                    const float un = uu + pbn;
+                    X.pbar[i] = pbn;
+                    X.u[i] = un;
+                    X.thb[i] = thn;
+                    if (want_res) {
+                        const float cnt = 1.f / icnt;
+                        float th2 = 0.f;
+                        for (int q = e0; q < e1; ++q) {
+                            const int e = c.bus_eidx[2 * sc.line0 + q];
+                            const int l = e >> 1, side = e & 1;
+                            const long long r = sc.e_line + (long long)l * sc.Tp + t;
+                            const float d = X.dl[r], g = X.sg[r];
+                            const float beta = c.l_beta[sc.line0 + l];
+                            const float y = side ? 0.5f * (g - d) : 0.5f * (g + d);
+                            th2 += beta * beta * (y - thn) * (y - thn);
+                        }
+                        const float dpb = pbn - pb;
+                        acc[0] = cnt * pbn * pbn;
+                        acc[1] = th2;
+                        acc[2] = dx2 - cnt * dpb * dpb;
+                        acc[3] = (thn - thold) * (thn - thold) * c.bus_dres_w[sc.bus0 + n];
+                        acc[4] = cnt * (rho * un) * (rho * un);
+                        acc[5] = x2;
+                    }
+                }
+            }
+        }
+    }
+    if ((MODE == M_FWD || MODE == M_ADJ) && want_res) {
+        __shared__ float sh[kBusPart][kBlock / 32];
+        block_sum<kBusPart>(acc, sh);
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int q = 0; q < kBusPart; ++q) c.bus_part[blk * kBusPart + q] = acc[q];
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Per-scenario residuals in FP64 and the convergence flags.
+//   primal = sqrt(sum_n |n| pbar^2 + sum_j beta_j^2 (th_j - thbar)^2) / scale
+//            (scale = |L|_2 forward, |x|_2 adjoint)
+//   dual   = sqrt(rho^2 |z^k - z^{k-1}|^2 + sum_j (rho_th_j dthbar / beta_j)^2) / |rho u|_2
+// ------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock) k_reduce(const Ctx c, int adj, int it, double tol, int final_) {
+    const int s = blockIdx.x;
+    if (c.done[s]) return;
+    const ScenDev sc = c.scen[s];
+    double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int b = threadIdx.x; b < sc.bus_nblk; b += kBlock) {
+#pragma unroll
+        for (int q = 0; q < kBusPart; ++q) a[q] += (double)c.bus_part[(sc.bus_blk0 + b) * kBusPart + q];
+    }
+    for (int b = threadIdx.x; b < sc.line_nblk; b += kBlock) {
+        a[6] += (double)c.line_part[(sc.line_blk0 + b) * kDevPart + 0];
+        a[7] += (double)c.line_part[(sc.line_blk0 + b) * kDevPart + 1];
+    }
+    for (int b = threadIdx.x; b < sc.B; b += kBlock) {
+        a[6] += (double)c.bat_part[(sc.bat_w0 + b) * kDevPart + 0];
+        a[7] += (double)c.bat_part[(sc.bat_w0 + b) * kDevPart + 1];
+    }
+    __shared__ double sh[8][kBlock / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const double v = warp_sum_d(a[q]);
+        if (lane == 0) sh[q][w] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            double v = 0;
+            for (int k = 0; k < kBlock / 32; ++k) v += sh[q][k];
+            a[q] = v;
+        }
+        const double rho = c.rho, rth = c.rth_c;
+        const double x2 = a[5] + a[7];
+        const double scale = adj ? fmax(sqrt(x2), 1e-30) : sc.load_norm;
+        const double rp = sqrt(fmax(a[0] + a[1], 0.0)) / scale;
+        const double dz2 = fmax(a[2] + a[6], 0.0);
+        const double rd = sqrt(rho * rho * dz2 + rth * rth * a[3]) / fmax(sqrt(a[4]), 1e-30);
+        c.resid[2 * s + 0] = rp;
+        c.resid[2 * s + 1] = rd;
+        int* itp = adj ? c.adj_iters : c.iters;
+        if (!isfinite(rp) || !isfinite(rd)) {
+            c.status[s] = GX_ERR_NONFINITE;
+            c.done[s] = 1;
+            itp[s] = it;
+        } else if (rp <= tol && rd <= tol) {
+            c.status[s] = GX_OK;
+            c.done[s] = 1;
+            itp[s] = it;
+        } else if (final_) {
+            c.status[s] = GX_NOT_CONVERGED;
+            c.done[s] = 1;
+            itp[s] = it;
+        } else {
+            atomicAdd(c.n_active, 1);
+        }
+    }
+}
+
+// Outputs after a forward solve: price = -rho u, shed = x_load + L, flow = beta delta.
+__global__ void __launch_bounds__(kBlock) k_extract(const Ctx c) {
+    if (blockIdx.x < c.n_bus_blk) {
+        const int blk = blockIdx.x;
+        const int s = c.bus_blk_scen[blk];
+        const ScenDev sc = c.scen[s];
+        const int local = (blk - sc.bus_blk0) * kBlock + threadIdx.x;
+        if (local >= sc.N * sc.Tp) return;
+        const long long i = sc.e_bus + local;
+        c.out_price[i] = -c.rho * c.u[i];
+        c.out_shed[i] = c.xl[i] + c.load[i];
+    } else {
+        const int blk = blockIdx.x - c.n_bus_blk;
+        const int s = c.line_blk_scen[blk];
+        const ScenDev sc = c.scen[s];
+        const int local = (blk - sc.line_blk0) * kBlock + threadIdx.x;
+        if (local >= sc.L * sc.Tp) return;
+        const int l = local / sc.Tp;
+        const long long i = sc.e_line + local;
+        c.out_flow[i] = c.l_beta[sc.line0 + l] * c.dl[i];
+    }
+}
+
+// Operating cost c_s (Eq. 2 objective with the eps terms) and emissions, FP64.
+__global__ void __launch_bounds__(kBlock) k_cost(const Ctx c, const int* in_batch) {
+    const int blk = blockIdx.x;
+    const int s = c.cost_blk_scen[blk];
+    const ScenDev sc = c.scen[s];
+    double cs = 0.0, em = 0.0;
+    if (in_batch[s]) {
+        const int nb = blk - sc.cost_blk0;
+        const int nblk = (s + 1 < c.S ? c.scen[s + 1].cost_blk0 : c.n_cost_blk) - sc.cost_blk0;
+        const int stride = nblk * kBlock;
+        const double eps = c.eps, voll = c.voll;
+        const long long ng = (long long)sc.G * sc.Tp, nn = (long long)sc.N * sc.Tp, nbt = (long long)sc.B * sc.Tp;
+        for (long long i = (long long)nb * kBlock + threadIdx.x; i < ng; i += stride) {
+            const int g = (int)(i / sc.Tp), t = (int)(i - (long long)g * sc.Tp);
+            if (t >= sc.T) continue;
+            const double p = c.xg[sc.e_gen + i];
+            cs += c.g_cost[sc.gen0 + g] * p + 0.5 * eps * p * p;
+            em += c.g_emis[sc.gen0 + g] * p;
+        }
+        for (long long i = (long long)nb * kBlock + threadIdx.x; i < nn; i += stride) {
+            const int t = (int)(i % sc.Tp);
+            if (t >= sc.T) continue;
+            const double sh = (double)c.xl[sc.e_bus + i] + (double)c.load[sc.e_bus + i];
+            cs += voll * sh + 0.5 * eps * sh * sh;
+        }
+        for (long long i = (long long)nb * kBlock + threadIdx.x; i < nbt; i += stride) {
+            const int t = (int)(i % sc.Tp);
+            if (t >= sc.T) continue;
+            const double ch = c.zc[sc.e_bat + i], di = c.zd[sc.e_bat + i];
+            cs += 0.5 * eps * (ch * ch + di * di);
+        }
+    }
+    cs = warp_sum_d(cs);
+    em = warp_sum_d(em);
+    __shared__ double sh[2][kBlock / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) { sh[0][w] = cs; sh[1][w] = em; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0, b = 0;
+        for (int k = 0; k < kBlock / 32; ++k) { a += sh[0][k]; b += sh[1][k]; }
+        c.cost_part[2 * blk] = a;
+        c.cost_part[2 * blk + 1] = b;
+    }
+}
+
+__global__ void k_cost_final(const Ctx c, const int* in_batch) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= c.S || !in_batch[s]) return;
+    const int b0 = c.scen[s].cost_blk0;
+    const int b1 = s + 1 < c.S ? c.scen[s + 1].cost_blk0 : c.n_cost_blk;
+    double a = 0, e = 0;
+    for (int b = b0; b < b1; ++b) { a += c.cost_part[2 * b]; e += c.cost_part[2 * b + 1]; }
+    c.cost[s] = a;
+    c.hval[s] = a + (double)c.kappa * e;
+}
+
+// ------------------------------------------------------------------------------------
+// Gradient assembly: dh_s/deta_k = sum over active upper bounds i of device k of
+// xi_i * d b_i / d eta_k (gen: cf_t, line flow: 1, battery charge/discharge: 1, soc: dur).
+// xi comes from the adjoint prox at its fixed point (or, for h = c, from the forward
+// prox: the envelope theorem).  One warp per (scenario, device); FP64 sums.
+// ------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock) k_grad(const Ctx c, int envelope, const int* gwarp_scen,
+                                                 int n_gwarps, const int* in_batch) {
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5);
+    if (gw >= n_gwarps) return;
+    const int s = gwarp_scen[2 * gw];
+    const int r = gwarp_scen[2 * gw + 1];
+    if (!in_batch[s]) return;
+    const ScenDev sc = c.scen[s];
+    const float rho = c.rho, eps = c.eps;
+    double acc = 0.0;
+    if (r < sc.G) {
+        const int g = r, gg = sc.gen0 + g;
+        const int bus = c.g_bus[gg];
+        const float cost = c.g_cost[gg];
+        for (int t = lane; t < sc.T; t += 32) {
+            const long long rr = sc.e_gen + (long long)g * sc.Tp + t;
+            if (c.m_gen[rr] != A_UP) continue;
+            const long long bi = sc.e_bus + (long long)bus * sc.Tp + t;
+            const float cf = c.g_firm[gg] ? 1.f : c.cf[rr];
+            const float p = c.xg[rr];
+            float xi;
+            if (envelope) {
+                const float v = p - c.pbar[bi] - c.u[bi];
+                xi = -(rho * (v - p) - cost - eps * p);
+            } else {
+                const float v = c.a_xg[rr] - c.a_pbar[bi] - c.a_u[bi];
+                xi = cost + eps * p + c.kappa * c.g_emis[gg] + rho * v;
+            }
+            acc += (double)xi * (double)cf;
+        }
+    } else if (r < sc.G + sc.L) {
+        const int l = r - sc.G, lg = sc.line0 + l;
+        const int f = c.l_from[lg], to = c.l_to[lg];
+        const float beta = c.l_beta[lg];
+        const float rth = c.rth_c * c.l_w[lg];
+        for (int t = lane; t < sc.T; t += 32) {
+            const long long rr = sc.e_line + (long long)l * sc.Tp + t;
+            const uint8_t m = c.m_line[rr];
+            if (m != AL_FUP && m != AL_FLO) continue;
+            const long long bf = sc.e_bus + (long long)f * sc.Tp + t;
+            const long long bt = sc.e_bus + (long long)to * sc.Tp + t;
+            const float* dl = envelope ? c.dl : c.a_dl;
+            const float* sg = envelope ? c.sg : c.a_sg;
+            const float* vfp = envelope ? c.vf : c.a_vf;
+            const float* vtp = envelope ? c.vt : c.a_vt;
+            const float* pb = envelope ? c.pbar : c.a_pbar;
+            const float* uu = envelope ? c.u : c.a_u;
+            const float* th = envelope ? c.thb : c.a_thb;
+            const float d = dl[rr], g = sg[rr];
+            const float vf = vfp[rr] + 0.5f * (g + d) - th[bf];
+            const float vt = vtp[rr] + 0.5f * (g - d) - th[bt];
+            const float wf = th[bf] - vf, wt = th[bt] - vt;
+            const float tf = -beta * d - pb[bf] - uu[bf];
+            const float tt = beta * d - pb[bt] - uu[bt];
+            // derivative of the line prox objective in delta at the frozen delta
+            const float dstar = envelope ? d : 0.f;
+            const float Fp = rho * beta * (beta * dstar + tf) + rho * beta * (beta * dstar - tt) +
+                             0.5f * rth * (dstar - (wf - wt));
+            float xi;
+            if (envelope) xi = (m == AL_FUP) ? Fp / beta : -Fp / beta;
+            else xi = (m == AL_FUP) ? -Fp / beta : Fp / beta;
+            acc += (double)xi;
+        }
+    } else {
+        const int b = r - sc.G - sc.L, bg = sc.bat0 + b;
+        const float dur = c.b_dur[bg];
+        for (int t = lane; t < sc.T; t += 32) {
+            const long long rr = sc.e_bat + (long long)b * sc.Tp + t;
+            const uint8_t m = c.m_bat[rr];
+            const float y3[3] = {envelope ? -c.yc[rr] : c.a_yc[rr], envelope ? -c.yd[rr] : c.a_yd[rr],
+                                 envelope ? -c.ys[rr] : c.a_ys[rr]};
+            const float dbd[3] = {1.f, 1.f, dur};
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+                if (((m >> (2 * q)) & 3) == A_UP) acc += (double)y3[q] * (double)dbd[q];
+        }
+    }
+    acc = warp_sum_d(acc);
+    if (lane == 0) c.grad_s[sc.gs0 + r] = acc;
+}
+
+// grad[k] = sum_s w'_s grad_s[k] over the scenarios of k's network.
+__global__ void k_grad_combine(const Ctx c, const double* wprime, const int* k_net, float* out, int K) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    const int net = k_net[k];
+    double acc = 0.0;
+    for (int s = 0; s < c.S; ++s) {
+        const ScenDev& sc = c.scen[s];
+        if (sc.net != net || wprime[s] == 0.0) continue;
+        acc += wprime[s] * c.grad_s[sc.gs0 + (k - sc.eta0)];
+    }
+    out[k] = (float)acc;
+}
+
+__global__ void k_plan_step(float* eta, const float* grad, const float* gamma, const float* lo, const float* hi,
+                            float alpha, int K) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    const float e = eta[k] - alpha * (gamma[k] + grad[k]);
+    eta[k] = fminf(fmaxf(e, lo[k]), hi[k]);
+}
+
+// ------------------------------------------------------------------------------------
+// launch wrappers
+// ------------------------------------------------------------------------------------
+#define GX_DISPATCH_MODE(KERNEL, GRID, ...)                                              \
+    do {                                                                                 \
+        if (adj) {                                                                       \
+            if (mode == M_ADJ) KERNEL<M_ADJ, 1><<<GRID, kBlock, 0, st>>>(__VA_ARGS__);    \
+            else if (mode == M_RESET) KERNEL<M_RESET, 1><<<GRID, kBlock, 0, st>>>(__VA_ARGS__); \
+            else if (mode == M_INIT) KERNEL<M_INIT, 1><<<GRID, kBlock, 0, st>>>(__VA_ARGS__);   \
+        } else {                                                                         \
+            if (mode == M_FWD) KERNEL<M_FWD, 0><<<GRID, kBlock, 0, st>>>(__VA_ARGS__);    \
+            else if (mode == M_RESET) KERNEL<M_RESET, 0><<<GRID, kBlock, 0, st>>>(__VA_ARGS__); \
+            else if (mode == M_INIT) KERNEL<M_INIT, 0><<<GRID, kBlock, 0, st>>>(__VA_ARGS__);   \
+            else if (mode == M_MASK) KERNEL<M_MASK, 0><<<GRID, kBlock, 0, st>>>(__VA_ARGS__);   \
+        }                                                                                \
+    } while (0)
+
+int launch_dev(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st) {
+    int n = 0;
+    if (mode == M_INIT) return 0;
+    if (c.n_line_blk > 0) { GX_DISPATCH_MODE(k_line, c.n_line_blk, c, want_res); ++n; }
+    if (c.n_bat_warps > 0) {
+        const int grid = (c.n_bat_warps + kBatWarps - 1) / kBatWarps;
+        GX_DISPATCH_MODE(k_bat, grid, c, want_res);
+        ++n;
+    }
+    return n;
+}
+
+int launch_bus(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st) {
+    if (c.n_bus_blk <= 0) return 0;
+    GX_DISPATCH_MODE(k_bus, c.n_bus_blk, c, want_res);
+    return 1;
+}
+
+int launch_reduce(const Ctx& c, int adj, int it, double tol, int final_, cudaStream_t st) {
+    k_reduce<<<c.S, kBlock, 0, st>>>(c, adj, it, tol, final_);
+    return 1;
+}
+
+int launch_extract(const Ctx& c, const int* in_batch, cudaStream_t st) {
+    const int grid = c.n_bus_blk + c.n_line_blk;
+    k_extract<<<grid, kBlock, 0, st>>>(c);
+    k_cost<<<c.n_cost_blk, kBlock, 0, st>>>(c, in_batch);
+    k_cost_final<<<(c.S + 127) / 128, 128, 0, st>>>(c, in_batch);
+    return 3;
+}
+
+int launch_grad(const Ctx& c, int envelope, const int* gwarp_scen, int n_gwarps, const int* in_batch,
+                cudaStream_t st) {
+    const int grid = (n_gwarps + kBlock / 32 - 1) / (kBlock / 32);
+    if (grid > 0) k_grad<<<grid, kBlock, 0, st>>>(c, envelope, gwarp_scen, n_gwarps, in_batch);
+    return 1;
+}
+
+int launch_grad_combine(const Ctx& c, const double* wprime, const int* k_net, float* grad_out, int K,
+                        cudaStream_t st) {
+    k_grad_combine<<<(K + 255) / 256, 256, 0, st>>>(c, wprime, k_net, grad_out, K);
+    return 1;
+}
+
+int launch_plan_step(float* eta, const float* grad, const float* gamma, const float* lo, const float* hi, float alpha,
+                     int K, cudaStream_t st) {
+    k_plan_step<<<(K + 255) / 256, 256, 0, st>>>(eta, grad, gamma, lo, hi, alpha, K);
+    return 1;
+}
+
+}  // namespace gx

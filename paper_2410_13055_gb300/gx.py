@@ -1,0 +1,274 @@
+"""Thin ctypes binding of the C ABI in include/gx.h (argument marshalling only).
+
+Every step of the dispatch solve, the adjoint gradient and the plan step runs in the
+CUDA kernels of ``libgx.so``; this module only converts numpy / torch arguments into
+pointers and sizes.  PyTorch provides the device memory (one uint8 workspace tensor
+per network) and the CUDA stream.  Importing this module raises if the library has
+not been built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgx.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2410_13055_gb300.build` "
+                      "(the CUDA library is the only implementation; there is no fallback)")
+_lib = C.CDLL(LIB_PATH)
+
+# ---------------------------------------------------------------------------- C types
+GX_OK, GX_NOT_CONVERGED = 0, 1
+GX_WARM = {"cold": 0, "prev": 1, "user": 2, "learned": 3}
+ARR = dict(p=0, shed=1, flow=2, theta=3, ch=4, dis=5, soc=6, price=7, cost=8, h=9, iters=10, resid=11,
+           status=12, grad_s=13, adj_iters=14)
+_ARR_DTYPE = dict(cost="float64", h="float64", resid="float64", grad_s="float64", iters="int32",
+                  status="int32", adj_iters="int32")
+
+_i32p = C.POINTER(C.c_int32)
+_f64p = C.POINTER(C.c_double)
+
+
+class NetworkDesc(C.Structure):
+    _fields_ = [("n_bus", C.c_int), ("n_gen", C.c_int), ("n_line", C.c_int), ("n_bat", C.c_int),
+                ("gen_bus", _i32p), ("gen_cost", _f64p), ("gen_emis", _f64p),
+                ("line_from", _i32p), ("line_to", _i32p), ("line_beta", _f64p), ("line_dtheta", _f64p),
+                ("bat_bus", _i32p), ("bat_dur", _f64p), ("bat_eff_c", _f64p), ("bat_eff_d", _f64p)]
+
+
+class ScenarioDesc(C.Structure):
+    _fields_ = [("net", C.c_int), ("T", C.c_int), ("load", _f64p), ("cf", _f64p), ("weight", C.c_double)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("eps", C.c_double), ("voll", C.c_double), ("kappa", C.c_double),
+                ("rho", C.c_double), ("rho_theta_c", C.c_double), ("theta_weight", C.c_int),
+                ("rho_inner_c", C.c_double), ("inner_iters", C.c_int),
+                ("tol", C.c_double), ("max_iter", C.c_int), ("check_every", C.c_int),
+                ("tol_active", C.c_double), ("adj_tol", C.c_double), ("adj_max_iter", C.c_int),
+                ("grad_envelope", C.c_int)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("iters_max", C.c_int), ("n_converged", C.c_int), ("n_scen", C.c_int), ("launches", C.c_int),
+                ("max_primal", C.c_double), ("max_dual", C.c_double)]
+
+    def asdict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_vp = C.c_void_p
+_sz = C.c_size_t
+_SIGS = {
+    "gx_opts_default": (C.c_int, [C.POINTER(Opts)]),
+    "gx_status_string": (C.c_char_p, [C.c_int]),
+    "gx_last_error_message": (C.c_char_p, []),
+    "gx_network_create": (C.c_int, [C.POINTER(NetworkDesc), C.c_int, C.POINTER(ScenarioDesc), C.c_int,
+                                    C.POINTER(Opts), C.POINTER(_vp)]),
+    "gx_network_destroy": (C.c_int, [_vp]),
+    "gx_network_device_bytes": (_sz, [_vp]),
+    "gx_network_K": (C.c_int, [_vp]),
+    "gx_network_S": (C.c_int, [_vp]),
+    "gx_network_bind": (C.c_int, [_vp, _vp, _sz, _vp]),
+    "gx_network_set_opts": (C.c_int, [_vp, C.POINTER(Opts)]),
+    "gx_network_array": (C.c_int, [_vp, C.c_int, C.c_int, C.POINTER(_sz), C.POINTER(_sz)]),
+    "gx_network_scenario_info": (C.c_int, [_vp, C.c_int] + [C.POINTER(C.c_int)] * 7),
+    "gx_dispatch_solve_batch": (C.c_int, [_vp, _vp, C.POINTER(C.c_int), C.c_int, C.c_int, _vp,
+                                          C.POINTER(Stats), _vp]),
+    "gx_dispatch_grad_batch": (C.c_int, [_vp, _vp, C.c_int, _vp, C.POINTER(Stats), _vp]),
+    "gx_plan_step": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, C.c_float, _vp]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = tuple(_SIGS)
+
+
+class GxError(RuntimeError):
+    def __init__(self, status, where):
+        msg = _lib.gx_last_error_message().decode()
+        super().__init__(f"{where}: {_lib.gx_status_string(status).decode()} ({status}): {msg}")
+        self.status = status
+
+
+def _check(status, where, allow_not_converged=True):
+    if status < 0 or (status > 0 and not allow_not_converged):
+        raise GxError(status, where)
+    return status
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    _check(_lib.gx_opts_default(C.byref(o)), "gx_opts_default")
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class Network:
+    """A batch of dispatch scenarios bound to a torch-allocated device workspace.
+
+    nets / scens are the plain dicts of ``paper_2410_13055_gb300.synth``.  Model
+    constants (eps, voll, kappa) and solver options go in ``opts``.
+    """
+
+    def __init__(self, nets, scens, opts: Opts | None = None, device="cuda", **opt_kw):
+        import torch
+        self._keep = []
+        nd = (NetworkDesc * len(nets))()
+        for k, n in enumerate(nets):
+            arrs = dict(
+                gen_bus=np.ascontiguousarray(n["gen_bus"], np.int32),
+                gen_cost=np.ascontiguousarray(n["gen_cost"], np.float64),
+                gen_emis=np.ascontiguousarray(n["gen_emis"], np.float64),
+                line_from=np.ascontiguousarray(n["line_from"], np.int32),
+                line_to=np.ascontiguousarray(n["line_to"], np.int32),
+                line_beta=np.ascontiguousarray(n["line_beta"], np.float64),
+                line_dtheta=np.ascontiguousarray(n["line_dtheta"], np.float64),
+                bat_bus=np.ascontiguousarray(n["bat_bus"], np.int32),
+                bat_dur=np.ascontiguousarray(n["bat_dur"], np.float64),
+                bat_eff_c=np.ascontiguousarray(n["bat_eff_c"], np.float64),
+                bat_eff_d=np.ascontiguousarray(n["bat_eff_d"], np.float64),
+            )
+            self._keep.append(arrs)
+            d = nd[k]
+            d.n_bus, d.n_gen = int(n["n_bus"]), arrs["gen_bus"].size
+            d.n_line, d.n_bat = arrs["line_from"].size, arrs["bat_bus"].size
+            for name, a in arrs.items():
+                ct = _i32p if a.dtype == np.int32 else _f64p
+                setattr(d, name, a.ctypes.data_as(ct))
+        sd = (ScenarioDesc * len(scens))()
+        for s, sc in enumerate(scens):
+            load = np.ascontiguousarray(sc["load"], np.float64)
+            cf = np.ascontiguousarray(sc["cf"], np.float64)
+            self._keep.append((load, cf))
+            d = sd[s]
+            d.net, d.T, d.weight = int(sc["net"]), int(sc["T"]), float(sc["weight"])
+            d.load = load.ctypes.data_as(_f64p)
+            d.cf = cf.ctypes.data_as(_f64p)
+        self.opts = opts if opts is not None else default_opts(**opt_kw)
+        h = C.c_void_p()
+        _check(_lib.gx_network_create(nd, len(nets), sd, len(scens), C.byref(self.opts), C.byref(h)),
+               "gx_network_create", False)
+        self._h = h
+        self._keep = None  # the library copied the descriptors
+        self.K = _lib.gx_network_K(h)
+        self.S = _lib.gx_network_S(h)
+        self.nbytes = _lib.gx_network_device_bytes(h)
+        self.device = torch.device(device)
+        self.ws = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.ws.data_ptr()
+        self._off0 = (-base) % 256
+        _check(_lib.gx_network_bind(h, C.c_void_p(base + self._off0), C.c_size_t(self.nbytes),
+                                    _stream_handle(None)), "gx_network_bind", False)
+        self.info = [self.scenario_info(s) for s in range(self.S)]
+        self.eta_offsets = []
+        off = 0
+        for n in nets:
+            self.eta_offsets.append(off)
+            off += int(n["gen_bus"].size + n["line_from"].size + n["bat_bus"].size)
+        self.last_stats = None
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            _lib.gx_network_destroy(h)
+            self._h = None
+
+    # ------------------------------------------------------------------ metadata
+    def scenario_info(self, s):
+        vals = [C.c_int() for _ in range(7)]
+        _check(_lib.gx_network_scenario_info(self._h, s, *[C.byref(v) for v in vals]), "scenario_info", False)
+        return dict(zip(["T", "Tp", "N", "G", "L", "B", "eta_offset"], [v.value for v in vals]))
+
+    def set_opts(self, opts: Opts | None = None, **kw):
+        if opts is None:
+            opts = Opts.from_buffer_copy(self.opts)
+            for k, v in kw.items():
+                setattr(opts, k, v)
+        _check(_lib.gx_network_set_opts(self._h, C.byref(opts)), "gx_network_set_opts", False)
+        self.opts = opts
+
+    def array(self, which, scen=-1):
+        """A torch view (no copy) of an output array inside the workspace."""
+        import torch
+        off, cnt = C.c_size_t(), C.c_size_t()
+        _check(_lib.gx_network_array(self._h, ARR[which], scen, C.byref(off), C.byref(cnt)), "gx_network_array",
+               False)
+        dt = getattr(torch, _ARR_DTYPE.get(which, "float32"))
+        esz = torch.tensor([], dtype=dt).element_size()
+        start = self._off0 + off.value
+        v = self.ws[start:start + cnt.value * esz].view(dt)
+        if scen >= 0 and which in ("p", "shed", "flow", "theta", "ch", "dis", "soc", "price"):
+            inf = self.info[scen]
+            rows = {"p": "G", "shed": "N", "flow": "L", "theta": "N", "ch": "B", "dis": "B", "soc": "B",
+                    "price": "N"}[which]
+            v = v.view(inf[rows], inf["Tp"])[:, :inf["T"]]
+        return v
+
+    # ------------------------------------------------------------------ compute
+    def solve(self, eta, batch=None, warm="cold", warm_prices=None, warm_angles=None, stream=None):
+        """Eq. 2 for every scenario of the batch at plan eta (FP32 CUDA tensor [K])."""
+        import torch
+        assert eta.is_cuda and eta.dtype == torch.float32 and eta.numel() == self.K and eta.is_contiguous()
+        wd = None
+        if warm == "user":
+            wd = torch.cat([warm_prices.reshape(-1), warm_angles.reshape(-1)]).to(self.device, torch.float32)
+        idx, nb = None, 0
+        if batch is not None:
+            arr = (C.c_int * len(batch))(*[int(b) for b in batch])
+            idx, nb = arr, len(batch)
+        st = Stats()
+        rc = _lib.gx_dispatch_solve_batch(self._h, _ptr(eta), idx, nb, GX_WARM[warm], _ptr(wd), C.byref(st),
+                                          _stream_handle(stream))
+        _check(rc, "gx_dispatch_solve_batch")
+        self.last_stats = st.asdict()
+        self.last_status = rc
+        return rc
+
+    def grad(self, eta, out=None, warm="cold", stream=None):
+        """sum_s w_s dh_s/deta at the last solve (FP32 [K])."""
+        import torch
+        if out is None:
+            out = torch.zeros(self.K, dtype=torch.float32, device=self.device)
+        st = Stats()
+        rc = _lib.gx_dispatch_grad_batch(self._h, _ptr(eta), GX_WARM[warm], _ptr(out), C.byref(st),
+                                         _stream_handle(stream))
+        _check(rc, "gx_dispatch_grad_batch")
+        self.last_grad_stats = st.asdict()
+        self.last_grad_status = rc
+        return out
+
+    def plan_step(self, eta, grad, gamma, eta_min, eta_max, alpha, stream=None):
+        rc = _lib.gx_plan_step(self._h, _ptr(eta), _ptr(grad), _ptr(gamma), _ptr(eta_min), _ptr(eta_max),
+                               C.c_float(alpha), _stream_handle(stream))
+        _check(rc, "gx_plan_step", False)
+        return eta
+
+
+def lib_path():
+    return LIB_PATH
+
+
+def exported_symbols():
+    """Names the binding resolves in libgx.so (every entry point of include/gx.h)."""
+    return EXPORTED

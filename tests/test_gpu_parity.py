@@ -1,0 +1,50 @@
+"""CUDA path vs the FP64 oracle, element by element on the same seeded inputs.
+
+Tolerances (FP32 state, FP64 final reductions), for solves run to a 1e-6 residual:
+objective relative error <= 1e-4, FP64 KKT residuals of the GPU (x, lambda) evaluated
+by the oracle <= 1e-3 (relative), gradient relative error <= 1e-3."""
+import numpy as np
+import pytest
+
+from gpu_util import eta_tensor, gpu_net, pack_x, ref_groups, rel, solution
+from oracle import dispatch, grad as ograd, kkt
+from paper_2410_13055_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TIGHT = dict(tol=1e-6, max_iter=400000, adj_tol=1e-6, adj_max_iter=400000, check_every=50)
+
+
+def _solve_pair(nets, scens, eta, kappa=0.0, **kw):
+    opts = synth.default_opts(kappa=kappa)
+    net = gpu_net(nets, scens, kappa=kappa, **{**TIGHT, **kw})
+    e = eta_tensor(eta)
+    rc = net.solve(e)
+    refs = dispatch.solve_all(nets, scens, np.asarray(eta, float), opts)
+    return net, e, rc, refs
+
+
+def test_tiny_dispatch_parity():
+    nets, scens = synth.tiny()
+    eta = nets[0]["eta_min"]
+    net, e, rc, refs = _solve_pair(nets, scens, eta)
+    assert rc == 0, net.last_stats
+    ref = refs[0]
+    g = solution(net, 0, ref_groups(ref.qp))
+    assert abs(g["cost"] - ref.cost) / ref.cost <= 1e-4
+    res = kkt.residuals(ref.qp, pack_x(ref.qp, g), g["price"])
+    assert res["primal"] <= 1e-3 and res["dual"] <= 1e-3, res
+    assert rel(g["price"], ref.price) <= 1e-3
+    assert rel(g["p"], ref.p) <= 1e-3
+
+
+@pytest.mark.parametrize("kappa", [0.0, 50.0])
+def test_tiny_gradient_parity(kappa):
+    nets, scens = synth.tiny()
+    eta = nets[0]["eta_min"] * 1.1
+    net, e, rc, refs = _solve_pair(nets, scens, eta, kappa=kappa)
+    assert rc == 0
+    gg = net.grad(e).double().cpu().numpy()
+    assert net.last_grad_status == 0, net.last_grad_stats
+    g_ref = ograd.adjoint_grad(refs[0])
+    assert rel(gg, g_ref) <= 1e-3, (gg, g_ref)
