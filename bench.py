@@ -1,0 +1,360 @@
+"""Throughput of the dispatch + implicit-gradient hot path on one GB300.
+
+A step is one implicit-gradient iteration of the planner (Section 2.2): solve every
+scenario's dispatch (Eq. 2) to a 1e-3 relative residual, solve the adjoint of the
+active KKT system to 1e-3 for d h / d eta, and take the projected plan step.  The
+metric is device-hours dispatched + differentiated per second:
+    device-hours = sum_s (generators + lines + batteries + loads) * T_s   per step.
+
+Default workload: the 100-bus network of 16 weekly scenarios (T = 168), emissions
+weight kappa = 50 $/t (so h != c and the adjoint is required).  Starts: "prev"
+(the previous plan's dispatch and adjoint state, the interactive warm start of
+Section 2.2) is the headline; "cold" is reported beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--config medium|scale|batching|tiny]
+                    [--impl gx|reference]
+
+--impl reference times the FP64 oracle (interior point + KKT adjoint) on the host
+cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import resource
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2410_13055_gb300 import synth  # noqa: E402
+
+KAPPA = 50.0
+METRIC = "device-hours dispatched+differentiated/s at 1e-3 residual"
+UNIT = "device-hours/s"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def build_workload(config, rank=0):
+    seed_shift = 1000 * rank  # each rank takes its own shard of independent scenarios
+    if config == "medium":
+        nets, scens = synth.medium(seed=1 + seed_shift)
+    elif config == "scale":
+        nets, scens = synth.scale(seed=3 + seed_shift)
+    elif config == "batching":
+        nets, scens = synth.batching(seed=2 + seed_shift)
+    elif config == "tiny":
+        nets, scens = synth.tiny(seed=0 + seed_shift)
+    else:
+        raise SystemExit(f"unknown config {config}")
+    return nets, scens
+
+
+def algorithmic_bytes(nets, scens):
+    """Algorithmic bytes of one k_bus / k_line / k_bat launch over all scenarios.
+
+    Per hour: bus kernel  gens  x r/w 8 + cf 4 (non-firm) + (eta, cost per row: ~0)
+                          loads x r/w 8 + L 4;  bus u,pbar,thbar r/w 24;
+                          reads line delta,sigma per end 8; battery x 4
+              line kernel delta,sigma,v_f,v_t r/w 32 + bus pbar,u,thbar at both ends 24
+              bat kernel  x,z(3),y(3) r/w 56 + dd 4 + bus pbar,u 8
+    """
+    tot = {"k_bus": 0.0, "k_line": 0.0, "k_bat": 0.0}
+    for sc in scens:
+        n = nets[sc["net"]]
+        T = sc["T"]
+        G, L, B, N = n["gen_bus"].size, n["line_from"].size, n["bat_bus"].size, n["n_bus"]
+        nonfirm = int(np.sum(np.any(sc["cf"] != 1.0, axis=1)))
+        tot["k_bus"] += T * (8 * G + 4 * nonfirm + 12 * N + 24 * N + 8 * 2 * L + 4 * B)
+        tot["k_line"] += T * (32 + 24) * L
+        tot["k_bat"] += T * (56 + 4 + 8) * B
+    return tot
+
+
+def run_gx(args):
+    import torch
+    ws, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2410_13055_gb300 import gx
+    nets, scens = build_workload(args.config, rank)
+    dh = synth.device_hours(nets, scens)
+    net = gx.Network(nets, scens, kappa=KAPPA, tol=1e-3, adj_tol=1e-3, max_iter=50000, adj_max_iter=50000,
+                     check_every=args.check_every)
+    dev = torch.device("cuda", local)
+    eta_min = torch.tensor(np.concatenate([n["eta_min"] for n in nets]), dtype=torch.float32, device=dev)
+    eta_max = torch.tensor(np.concatenate([n["eta_max"] for n in nets]), dtype=torch.float32, device=dev)
+    gamma = torch.tensor(np.concatenate([n["gamma"] for n in nets]), dtype=torch.float32, device=dev)
+    eta = eta_min.clone()
+    grad = torch.zeros_like(eta)
+    flush = torch.empty(int(256e6) // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
+    state = {"alpha": None, "launches": 0, "iters": [], "adj_iters": []}
+
+    def step(warm):
+        rc = net.solve(eta, warm=warm)
+        net.grad(eta, out=grad, warm=warm)
+        if state["alpha"] is None:
+            d = (gamma + grad).abs().max().item()
+            state["alpha"] = 1e-2 * float(eta_min.median().item()) / max(d, 1e-30)
+        net.plan_step(eta, grad, gamma, eta_min, eta_max, state["alpha"])
+        state["launches"] += net.last_stats["launches"] + net.last_grad_stats["launches"] + 1
+        state["iters"].append(net.last_stats["iters_max"])
+        state["adj_iters"].append(net.last_grad_stats["iters_max"])
+        return rc
+
+    # warm-up (also settles the plan trajectory's step size)
+    step("cold")
+    for _ in range(max(args.warmup - 1, 0)):
+        step("prev")
+    torch.cuda.synchronize()
+
+    def timed(warm, K):
+        state["launches"], state["iters"], state["adj_iters"] = 0, [], []
+        evs = []
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(K):
+            flush.fill_(1.0)  # L2 flush between steps, outside the per-step events
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            step(warm)
+            b.record()
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        ms = [a.elapsed_time(b) for a, b in evs]
+        return float(np.sum(ms)), wall, list(state["iters"]), list(state["adj_iters"]), state["launches"]
+
+    clocks = Clocks(local)
+    clocks.start()
+    net.profile(True)
+    ms_prev, wall_prev, it_prev, ait_prev, launches = timed("prev", args.steps)
+    prof = net.profile_read()
+    net.profile(False)
+    clk = clocks.stop()
+    ms_cold, _, it_cold, ait_cold, _ = timed("cold", max(1, min(args.steps, 3)))
+    ms_cold /= max(1, min(args.steps, 3))
+
+    # e2e: the same step through the C ABI with host buffers (pinned), copies inside
+    eta_h = eta.cpu().pin_memory()
+    grad_h = torch.empty_like(grad, device="cpu").pin_memory()
+    cost_h = torch.empty(net.S, dtype=torch.float64).pin_memory()
+    cost_dev = net.array("cost")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        eta.copy_(eta_h, non_blocking=True)
+        net.solve(eta, warm="prev")
+        net.grad(eta, out=grad, warm="prev")
+        grad_h.copy_(grad, non_blocking=True)
+        cost_h.copy_(cost_dev, non_blocking=True)
+    b.record()
+    torch.cuda.synchronize()
+    e2e_ms = a.elapsed_time(b) / args.steps
+
+    # max over ranks
+    ms_step = ms_prev / args.steps
+    if dist is not None:
+        t = torch.tensor([ms_step, e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step, e2e_ms = t.tolist()
+    value = ws * dh / (ms_step / 1e3)
+    peak, peak_kind = _peaks()
+    ab = algorithmic_bytes(nets, scens)
+    roof = None
+    if prof:
+        kinds = {k: v for k, v in prof.items() if v["launches"] > 0}
+        dom = max(kinds, key=lambda k: kinds[k]["ms"]) if kinds else None
+        if dom:
+            avg_ms = kinds[dom]["ms"] / kinds[dom]["samples"]
+            achieved = ab[dom] / (avg_ms / 1e3) / 1e9
+            roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                    "frac": round(achieved / peak, 4), "traffic": None,
+                    "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
+                    "bytes_per_launch": ab[dom], "avg_launch_us": round(avg_ms * 1e3, 2),
+                    "kernels": {k: {"avg_launch_us": round(v["ms"] / v["samples"] * 1e3, 2),
+                                    "bytes_per_launch": ab[k]} for k, v in kinds.items()}}
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    cpu = cpu_baseline(args) if not args.no_cpu_baseline else None
+    out = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.config, "scenarios": len(scens), "device_hours_per_step": dh,
+                   "start": "prev (previous plan's dispatch + adjoint state)", "kappa": KAPPA,
+                   "tol": 1e-3, "l2": "256 MB buffer written between steps, outside the per-step events",
+                   "parallelism": f"replicas x{ws} (independent scenario shards)"},
+        "iterations": {"prev_fwd_median": float(np.median(it_prev)), "prev_adj_median": float(np.median(ait_prev)),
+                       "cold_fwd_median": float(np.median(it_cold)), "cold_adj_median": float(np.median(ait_cold))},
+        "modes": {"prev": round(value, 1), "cold": round(ws * dh / (ms_cold / 1e3), 1), "learned": None},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": round(ws * dh / (e2e_ms / 1e3), 1), "unit": UNIT, "h2d_bytes_per_step": int(eta.numel() * 4),
+                "d2h_bytes_per_step": int(grad.numel() * 4 + net.S * 8)},
+        "clocks": clk,
+        "gpu_launches": int(launches),
+    }
+    print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def _cores_used(cpu_s, wall_s):
+    return max(1, int(round(cpu_s / max(wall_s, 1e-9))))
+
+
+def oracle_step(nets, scens, hours):
+    """FP64 oracle on the first scenario restricted to `hours` hours: solve + adjoint gradient."""
+    from oracle import dispatch, grad as ograd
+    n2, s2 = synth.slice_hours(nets, scens[:1], 0, hours)
+    opts = synth.default_opts(kappa=KAPPA)
+    sol = dispatch.solve(n2[0], s2[0], n2[0]["eta_min"], opts)
+    ograd.adjoint_grad(sol)
+    return synth.device_hours(n2, s2)
+
+
+def cpu_baseline(args, hours=24):
+    nets, scens = build_workload(args.config)
+    r0 = resource.getrusage(resource.RUSAGE_SELF)
+    t0 = time.perf_counter()
+    dh = oracle_step(nets, scens, hours)
+    wall = time.perf_counter() - t0
+    r1 = resource.getrusage(resource.RUSAGE_SELF)
+    cpu_s = (r1.ru_utime - r0.ru_utime) + (r1.ru_stime - r0.ru_stime)
+    return {"value": round(dh / wall, 2), "unit": UNIT, "cores": _cores_used(cpu_s, wall), "kind": "oracle",
+            "sample": f"{args.config} network, scenario 0, hours 0-{hours - 1} ({dh} device-hours): "
+                      f"FP64 interior-point dispatch + KKT adjoint gradient, {wall:.1f} s",
+            "host_threads_available": os.cpu_count()}
+
+
+def run_reference(args):
+    ws, rank = _dist()
+    if rank != 0:
+        return
+    nets, scens = build_workload(args.config)
+    hours = 6
+    for _ in range(args.warmup):
+        oracle_step(nets, scens, hours)
+    r0 = resource.getrusage(resource.RUSAGE_SELF)
+    t0 = time.perf_counter()
+    dh = 0
+    for _ in range(args.steps):
+        dh += oracle_step(nets, scens, hours)
+    wall = time.perf_counter() - t0
+    r1 = resource.getrusage(resource.RUSAGE_SELF)
+    cpu_s = (r1.ru_utime - r0.ru_utime) + (r1.ru_stime - r0.ru_stime)
+    v = dh / wall
+    sample = (f"{args.config} network, scenario 0, hours 0-{hours - 1} per step: FP64 interior-point dispatch + "
+              f"KKT adjoint gradient")
+    out = {"impl": "reference", "metric": METRIC, "value": round(v, 2), "unit": UNIT, "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * wall / args.steps, 2),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.config, "kappa": KAPPA, "sample_hours": hours},
+           "cpu_baseline": {"value": round(v, 2), "unit": UNIT, "cores": _cores_used(cpu_s, wall), "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": round(v, 2), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--config", default="medium")
+    ap.add_argument("--impl", default="gx", choices=["gx", "reference"])
+    ap.add_argument("--check-every", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gx(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -197,6 +197,17 @@ gx_status gx_dispatch_grad_batch(gx_network* net, const float* eta_dev, int warm
 gx_status gx_plan_step(gx_network* net, float* eta_dev, const float* grad_dev, const float* gamma_dev,
                        const float* eta_min_dev, const float* eta_max_dev, float alpha, void* stream);
 
+/* Sampled kernel timing.  While enabled, the solve and gradient loops record CUDA
+ * events on their stream around the bus, line and battery kernels of the last
+ * iteration of every residual-check chunk and accumulate the elapsed times at the
+ * chunk's synchronisation.  Kinds: 0 = bus kernel, 1 = line kernel, 2 = battery
+ * kernel.  Enabling resets the counters.  Uses three CUDA events per kind (created
+ * here, no device memory). */
+gx_status gx_profile_enable(gx_network* net, int on);
+/* ms[k]: summed event time of the sampled launches of kind k; samples[k]: how many
+ * were sampled; launches[k]: all launches of kind k since enabling. */
+gx_status gx_profile_read(const gx_network* net, double* ms, long long* samples, long long* launches);
+
 #ifdef __cplusplus
 }
 #endif

@@ -75,7 +75,7 @@ struct gx_network {
     size_t static_end;
     size_t o_f[16], o_a[16];  // forward / adjoint state arrays, order of StatePtrs
     size_t o_mgen, o_mload, o_mline, o_mbat;
-    size_t o_done, o_iters, o_status, o_adjit, o_nact, o_inb, o_resid, o_cost, o_h, o_grads, o_wprime;
+    size_t o_done, o_iters, o_status, o_adjit, o_nact, o_inb, o_resid, o_rbest, o_cost, o_h, o_grads, o_wprime;
     size_t o_flow, o_price, o_shed, o_bpart, o_lpart, o_btpart, o_cpart;
     Layout lay;
     // binding
@@ -85,6 +85,15 @@ struct gx_network {
     std::vector<double> wprime;
     std::vector<float> dd_host;
     Ctx ctx{};
+    // sampled kernel timing
+    bool prof = false;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    double prof_ms[3] = {0, 0, 0};
+    long long prof_samples[3] = {0, 0, 0}, prof_launches[3] = {0, 0, 0};
+    ~gx_network() {
+        for (auto& e : ev)
+            if (e) cudaEventDestroy(e);
+    }
 };
 
 static void fill_dd(gx_network* net) {
@@ -134,6 +143,7 @@ static void make_ctx(gx_network* net) {
     c.rth_c = (float)(o.rho * o.rho_theta_c);
     c.tol_act = (float)o.tol_active;
     c.inner_iters = o.inner_iters;
+    c.check_every = o.check_every;
     c.scen = reinterpret_cast<const ScenDev*>(d + net->o_scen);
     c.bus_blk_scen = I(net->o_bbs);
     c.line_blk_scen = I(net->o_lbs);
@@ -156,7 +166,7 @@ static void make_ctx(gx_network* net) {
     c.m_gen = U8(net->o_mgen); c.m_load = U8(net->o_mload); c.m_line = U8(net->o_mline); c.m_bat = U8(net->o_mbat);
     c.done = I(net->o_done); c.iters = I(net->o_iters); c.status = I(net->o_status); c.adj_iters = I(net->o_adjit);
     c.n_active = I(net->o_nact);
-    c.resid = D(net->o_resid); c.cost = D(net->o_cost); c.hval = D(net->o_h); c.grad_s = D(net->o_grads);
+    c.resid = D(net->o_resid); c.rbest = D(net->o_rbest); c.cost = D(net->o_cost); c.hval = D(net->o_h); c.grad_s = D(net->o_grads);
     c.out_flow = F(net->o_flow); c.out_price = F(net->o_price); c.out_shed = F(net->o_shed);
     c.bus_part = F(net->o_bpart); c.line_part = F(net->o_lpart); c.bat_part = F(net->o_btpart);
     c.cost_part = D(net->o_cpart);
@@ -419,7 +429,7 @@ gx_status gx_network_create(const gx_network_desc* nets, int n_nets, const gx_sc
     net->o_mgen = L.add(B1(eg)); net->o_mload = L.add(B1(eb)); net->o_mline = L.add(B1(el)); net->o_mbat = L.add(B1(ebt));
     net->o_done = L.add(I4(S)); net->o_iters = L.add(I4(S)); net->o_status = L.add(I4(S)); net->o_adjit = L.add(I4(S));
     net->o_nact = L.add(I4(1)); net->o_inb = L.add(I4(S));
-    net->o_resid = L.add(D8(2LL * S)); net->o_cost = L.add(D8(S)); net->o_h = L.add(D8(S));
+    net->o_resid = L.add(D8(2LL * S)); net->o_rbest = L.add(D8(S)); net->o_cost = L.add(D8(S)); net->o_h = L.add(D8(S));
     net->o_grads = L.add(D8(gs)); net->o_wprime = L.add(D8(S));
     net->o_flow = L.add(F4(el)); net->o_price = L.add(F4(eb)); net->o_shed = L.add(F4(eb));
     net->o_bpart = L.add(F4((long long)net->n_bus_blk * kBusPart));
@@ -573,10 +583,25 @@ static gx_status run_loop(gx_network* net, int adj, cudaStream_t st, int* launch
     int it = 0, nact = 1;
     while (it < max_it) {
         const int chunk = std::min(every, max_it - it);
+        bool sampled = false;
         for (int j = 0; j < chunk; ++j) {
             const int want = j == chunk - 1;
-            *launches += launch_dev(c, mode, adj, want, st);
-            *launches += launch_bus(c, mode, adj, want, st);
+            const bool samp = net->prof && want;
+            if (samp) GX_CUDA(cudaEventRecord(net->ev[0], st));
+            const int nl = launch_line(c, mode, adj, want, st);
+            if (samp) GX_CUDA(cudaEventRecord(net->ev[1], st));
+            const int nb = launch_bat(c, mode, adj, want, st);
+            if (samp) GX_CUDA(cudaEventRecord(net->ev[2], st));
+            const int nu = launch_bus(c, mode, adj, want, st);
+            if (samp) GX_CUDA(cudaEventRecord(net->ev[3], st));
+            *launches += nl + nb + nu;
+            if (net->prof) {
+                net->prof_launches[0] += nu; net->prof_launches[1] += nl; net->prof_launches[2] += nb;
+                if (samp) sampled = true;
+            }
+            if (samp) {
+                net->prof_samples[0] += nu; net->prof_samples[1] += nl; net->prof_samples[2] += nb;
+            }
         }
         it += chunk;
         GX_CUDA(cudaMemsetAsync(c.n_active, 0, sizeof(int), st));
@@ -584,6 +609,13 @@ static gx_status run_loop(gx_network* net, int adj, cudaStream_t st, int* launch
         GX_CUDA(cudaGetLastError());
         GX_CUDA(cudaMemcpyAsync(&nact, c.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
         GX_CUDA(cudaStreamSynchronize(st));
+        if (sampled) {
+            float a = 0, b = 0, u = 0;
+            GX_CUDA(cudaEventElapsedTime(&a, net->ev[0], net->ev[1]));
+            GX_CUDA(cudaEventElapsedTime(&b, net->ev[1], net->ev[2]));
+            GX_CUDA(cudaEventElapsedTime(&u, net->ev[2], net->ev[3]));
+            net->prof_ms[1] += a; net->prof_ms[2] += b; net->prof_ms[0] += u;
+        }
         if (nact == 0) break;
     }
     *iters_out = it;
@@ -730,6 +762,21 @@ gx_status gx_plan_step(gx_network* net, float* eta_dev, const float* grad_dev, c
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     launch_plan_step(eta_dev, grad_dev, gamma_dev, eta_min_dev, eta_max_dev, alpha, net->K, st);
     GX_CUDA(cudaGetLastError());
+    return GX_OK;
+}
+
+gx_status gx_profile_enable(gx_network* net, int on) {
+    if (!net) return fail(GX_ERR_INVALID_ARG, "net is NULL");
+    if (on && !net->ev[0])
+        for (auto& e : net->ev) GX_CUDA(cudaEventCreate(&e));
+    net->prof = on != 0;
+    for (int k = 0; k < 3; ++k) { net->prof_ms[k] = 0; net->prof_samples[k] = 0; net->prof_launches[k] = 0; }
+    return GX_OK;
+}
+
+gx_status gx_profile_read(const gx_network* net, double* ms, long long* samples, long long* launches) {
+    if (!net || !ms || !samples || !launches) return fail(GX_ERR_INVALID_ARG, "NULL argument");
+    for (int k = 0; k < 3; ++k) { ms[k] = net->prof_ms[k]; samples[k] = net->prof_samples[k]; launches[k] = net->prof_launches[k]; }
     return GX_OK;
 }
 

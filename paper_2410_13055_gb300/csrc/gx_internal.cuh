@@ -19,7 +19,7 @@ constexpr int kBatWarps = 8;       // batteries (warps) per block of the battery
 constexpr int kMaxT = 256;         // hours per scenario handled by one warp (8 per lane)
 constexpr int kHplMax = kMaxT / 32;
 constexpr int kBusPart = 6;        // floats per bus-block residual partial
-constexpr int kDevPart = 2;        // floats per line-block / battery-warp partial
+constexpr int kDevPart = 3;        // floats per line-block / battery-warp partial
 
 // Kernel modes.  FWD/ADJ advance the forward or adjoint message passing by one
 // iteration; RESET/INIT prepare a cold or user start; MASK records the active set.
@@ -52,6 +52,7 @@ struct Ctx {
     float rho, eps, voll, kappa, rho_in, rth_c;  // rth_c = rho * rho_theta_c
     float tol_act;
     int inner_iters;
+    int check_every;
     // tables
     const ScenDev* scen;
     const int* bus_blk_scen;   // [n_bus_blk]
@@ -73,7 +74,7 @@ struct Ctx {
     const float* cf;    // [gen rows]
     const float* eta;   // [K] current plan (caller buffer)
     // forward state
-    float* xg; float* xl; float* dl; float* sg; float* vf; float* vt;
+    float* xg; float* xl; float* dl; float* sg; float* vf; float* vt;  // vf/vt hold q = terminal phase + scaled phase dual
     float* xb; float* zc; float* zd; float* zs; float* yc; float* yd; float* ys;
     float* u; float* pbar; float* thb;
     const float* bat_dd;  // Thomas pivots of the battery tridiagonal system [bat rows]
@@ -90,6 +91,7 @@ struct Ctx {
     int* adj_iters;     // [S]
     int* n_active;      // [1]
     double* resid;      // [S*2]
+    double* rbest;      // [S] smallest max(primal, dual) residual of the current solve
     double* cost;       // [S]
     double* hval;       // [S]
     double* grad_s;     // [sum_s K_net]
@@ -104,6 +106,8 @@ struct Ctx {
 
 // Launch wrappers (gx_kernels.cu).  Each returns the number of kernels launched.
 int launch_dev(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st);
+int launch_line(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st);
+int launch_bat(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st);
 int launch_bus(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st);
 int launch_reduce(const Ctx& c, int adj, int it, double tol, int final_, cudaStream_t st);
 int launch_extract(const Ctx& c, const int* in_batch, cudaStream_t st);

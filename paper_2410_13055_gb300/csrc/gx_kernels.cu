@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(kBlock) k_line(const Ctx c, int want_res) {
     const int l = local / sc.Tp;
     const int t = local - l * sc.Tp;
     const bool valid = (l < sc.L) && (t < sc.T);
-    float dx2 = 0.f, x2 = 0.f;
+    float dx2 = 0.f, x2 = 0.f, th2 = 0.f;
     if (valid) {
         const long long row = sc.e_line + (long long)l * sc.Tp + t;
         const int lg = sc.line0 + l;
@@ -97,22 +97,27 @@ __global__ void __launch_bounds__(kBlock) k_line(const Ctx c, int want_res) {
         const long long bf = sc.e_bus + (long long)f * sc.Tp + t;
         const long long bt = sc.e_bus + (long long)to * sc.Tp + t;
         if (MODE == M_RESET) {
-            float d0 = 0.f, g0 = 0.f;
+            float d0 = 0.f, g0 = 0.f, q0f = 0.f, q0t = 0.f;
             if (!ADJ && c.warm) {
-                const float* th = c.warm + (c.warm_half);
+                const float* th = c.warm + c.warm_half;
                 d0 = th[bf] - th[bt];
                 g0 = th[bf] + th[bt];
+                q0f = th[bf];
+                q0t = th[bt];
             }
-            X.dl[row] = d0; X.sg[row] = g0; X.vf[row] = 0.f; X.vt[row] = 0.f;
+            X.dl[row] = d0; X.sg[row] = g0; X.vf[row] = q0f; X.vt[row] = q0t;
         } else {
+            // Phase consensus in exact ADMM form: the line keeps q_j = y_j + v_j (terminal
+            // phase plus its scaled dual); the bus value z is the weighted mean of the q_j,
+            // so the duals v_j = q_j - z keep a zero weighted sum at every bus even under
+            // rounding.
             const float d = X.dl[row], g = X.sg[row];
-            float vf = X.vf[row], vt = X.vt[row];
-            const float pbf = X.pbar[bf], uf = X.u[bf], thf = X.thb[bf];
-            const float pbt = X.pbar[bt], ut = X.u[bt], tht = X.thb[bt];
-            // dual update of the previous iteration's phase consensus
-            vf += 0.5f * (g + d) - thf;
-            vt += 0.5f * (g - d) - tht;
-            const float wf = thf - vf, wt = tht - vt;
+            const float pbf = X.pbar[bf], uf = X.u[bf], zf = X.thb[bf];
+            const float pbt = X.pbar[bt], ut = X.u[bt], zt = X.thb[bt];
+            const float vf = X.vf[row] - zf, vt = X.vt[row] - zt;
+            const float ef = 0.5f * (g + d) - zf, et = 0.5f * (g - d) - zt;  // y - z of the last iteration
+            th2 = beta * beta * (ef * ef + et * et);
+            const float wf = zf - vf, wt = zt - vt;
             const float tf = -beta * d - pbf - uf;  // power targets of the two terminals
             const float tt = beta * d - pbt - ut;
             const float rth = c.rth_c * c.l_w[lg];
@@ -133,10 +138,11 @@ __global__ void __launch_bounds__(kBlock) k_line(const Ctx c, int want_res) {
                 float dn;
                 if (ADJ) dn = c.m_line[row] ? 0.f : dun;
                 else dn = clampf(dun, -cap, cap);
+                const float gn = wf + wt;
                 X.dl[row] = dn;
-                X.sg[row] = wf + wt;
-                X.vf[row] = vf;
-                X.vt[row] = vt;
+                X.sg[row] = gn;
+                X.vf[row] = 0.5f * (gn + dn) + vf;
+                X.vt[row] = 0.5f * (gn - dn) + vt;
                 const float dd = dn - d;
                 dx2 = 2.f * beta * beta * dd * dd;
                 x2 = 2.f * beta * beta * dn * dn;
@@ -144,12 +150,13 @@ __global__ void __launch_bounds__(kBlock) k_line(const Ctx c, int want_res) {
         }
     }
     if ((MODE == M_FWD || MODE == M_ADJ) && want_res) {
-        __shared__ float sh[2][kBlock / 32];
-        float v[2] = {dx2, x2};
-        block_sum<2>(v, sh);
+        __shared__ float sh[3][kBlock / 32];
+        float v[3] = {dx2, x2, th2};
+        block_sum<3>(v, sh);
         if (threadIdx.x == 0) {
             c.line_part[blk * kDevPart + 0] = v[0];
             c.line_part[blk * kDevPart + 1] = v[1];
+            c.line_part[blk * kDevPart + 2] = v[2];
         }
     }
 }
@@ -368,6 +375,7 @@ __global__ void __launch_bounds__(kBlock) k_bat(const Ctx c, int want_res) {
         if (lane == 0) {
             c.bat_part[gw * kDevPart + 0] = dx2;
             c.bat_part[gw * kDevPart + 1] = x2;
+            c.bat_part[gw * kDevPart + 2] = 0.f;
         }
     }
 }
@@ -405,6 +413,7 @@ __global__ void __launch_bounds__(kBlock) k_bus(const Ctx c, int want_res) {
         } else {
             const float pb = X.pbar[i], uu = X.u[i], thold = X.thb[i];
             float sum = 0.f, dx2 = 0.f, x2 = 0.f;
+            float gscale = 0.f;  // adjoint: sum of (grad h / (rho + eps))^2 over free terminals
             // generators
             for (int q = c.bus_gptr[nb]; q < c.bus_gptr[nb + 1]; ++q) {
                 const int g = c.bus_gidx[sc.gen0 + q];
@@ -417,6 +426,7 @@ __global__ void __launch_bounds__(kBlock) k_bus(const Ctx c, int want_res) {
                     if (ADJ) {
                         const float gh = c.g_cost[gg] + eps * c.xg[r] + c.kappa * c.g_emis[gg];
                         xn = c.m_gen[r] ? 0.f : (rho * v + gh) * inv_re;
+                        if (!c.m_gen[r]) gscale += (gh * inv_re) * (gh * inv_re);
                     } else {
                         const float etag = fmaxf(c.eta[sc.eta0 + g], 0.f);
                         const float cap = c.g_firm[gg] ? etag : c.cf[r] * etag;
@@ -446,6 +456,7 @@ __global__ void __launch_bounds__(kBlock) k_bus(const Ctx c, int want_res) {
                     if (ADJ) {
                         const float gsh = c.voll + eps * (c.xl[i] + Lnt);
                         xn = c.m_load[i] ? 0.f : (rho * v + gsh) * inv_re;
+                        if (!c.m_load[i]) gscale += (gsh * inv_re) * (gsh * inv_re);
                     } else {
                         const float sun = (rho * (v + Lnt) - c.voll) * inv_re;
                         if (MODE == M_MASK) {
@@ -478,13 +489,13 @@ __global__ void __launch_bounds__(kBlock) k_bus(const Ctx c, int want_res) {
                     const int e = c.bus_eidx[2 * sc.line0 + q];
                     const int l = e >> 1, side = e & 1;
                     const long long r = sc.e_line + (long long)l * sc.Tp + t;
-                    const float d = X.dl[r], g = X.sg[r];
+                    const float d = X.dl[r];
+                    const float qv = side ? X.vt[r] : X.vf[r];
                     const float beta = c.l_beta[sc.line0 + l];
                     const float p = side ? beta * d : -beta * d;
-                    const float y = side ? 0.5f * (g - d) : 0.5f * (g + d);
                     sum += p;
                     x2 += p * p;
-                    ths += c.l_w[sc.line0 + l] * y;
+                    ths += c.l_w[sc.line0 + l] * qv;
                 }
                 const float icnt = c.bus_inv_cnt[sc.bus0 + n];
                 const float pbn = sum * icnt;
@@ -499,19 +510,9 @@ __global__ void __launch_bounds__(kBlock) k_bus(const Ctx c, int want_res) {
                     X.thb[i] = thn;
                     if (want_res) {
                         const float cnt = 1.f / icnt;
-                        float th2 = 0.f;
-                        for (int q = e0; q < e1; ++q) {
-                            const int e = c.bus_eidx[2 * sc.line0 + q];
-                            const int l = e >> 1, side = e & 1;
-                            const long long r = sc.e_line + (long long)l * sc.Tp + t;
-                            const float d = X.dl[r], g = X.sg[r];
-                            const float beta = c.l_beta[sc.line0 + l];
-                            const float y = side ? 0.5f * (g - d) : 0.5f * (g + d);
-                            th2 += beta * beta * (y - thn) * (y - thn);
-                        }
                         const float dpb = pbn - pb;
                         acc[0] = cnt * pbn * pbn;
-                        acc[1] = th2;
+                        acc[1] = gscale;
                         acc[2] = dx2 - cnt * dpb * dpb;
                         acc[3] = (thn - thold) * (thn - thold) * c.bus_dres_w[sc.bus0 + n];
                         acc[4] = cnt * (rho * un) * (rho * un);
@@ -541,44 +542,49 @@ __global__ void __launch_bounds__(kBlock) k_reduce(const Ctx c, int adj, int it,
     const int s = blockIdx.x;
     if (c.done[s]) return;
     const ScenDev sc = c.scen[s];
-    double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double a[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (int b = threadIdx.x; b < sc.bus_nblk; b += kBlock) {
 #pragma unroll
         for (int q = 0; q < kBusPart; ++q) a[q] += (double)c.bus_part[(sc.bus_blk0 + b) * kBusPart + q];
     }
     for (int b = threadIdx.x; b < sc.line_nblk; b += kBlock) {
-        a[6] += (double)c.line_part[(sc.line_blk0 + b) * kDevPart + 0];
-        a[7] += (double)c.line_part[(sc.line_blk0 + b) * kDevPart + 1];
+#pragma unroll
+        for (int q = 0; q < kDevPart; ++q) a[6 + q] += (double)c.line_part[(sc.line_blk0 + b) * kDevPart + q];
     }
     for (int b = threadIdx.x; b < sc.B; b += kBlock) {
-        a[6] += (double)c.bat_part[(sc.bat_w0 + b) * kDevPart + 0];
-        a[7] += (double)c.bat_part[(sc.bat_w0 + b) * kDevPart + 1];
+#pragma unroll
+        for (int q = 0; q < kDevPart; ++q) a[6 + q] += (double)c.bat_part[(sc.bat_w0 + b) * kDevPart + q];
     }
-    __shared__ double sh[8][kBlock / 32];
+    __shared__ double sh[9][kBlock / 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < 9; ++q) {
         const double v = warp_sum_d(a[q]);
         if (lane == 0) sh[q][w] = v;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
+        for (int q = 0; q < 9; ++q) {
             double v = 0;
             for (int k = 0; k < kBlock / 32; ++k) v += sh[q][k];
             a[q] = v;
         }
+        // a: 0 |n| pbar^2, 1 adjoint scale, 2 bus dz^2, 3 dthbar^2 w, 4 |rho u|^2, 5 bus x^2,
+        //    6 device dx^2, 7 device x^2, 8 phase mismatch (line kernel, one iteration lagged)
         const double rho = c.rho, rth = c.rth_c;
-        const double x2 = a[5] + a[7];
-        const double scale = adj ? fmax(sqrt(x2), 1e-30) : sc.load_norm;
-        const double rp = sqrt(fmax(a[0] + a[1], 0.0)) / scale;
+        const double scale = adj ? fmax(sqrt(a[1]), 1e-30) : sc.load_norm;
+        const double rp = sqrt(fmax(a[0] + a[8], 0.0)) / scale;
         const double dz2 = fmax(a[2] + a[6], 0.0);
         const double rd = sqrt(rho * rho * dz2 + rth * rth * a[3]) / fmax(sqrt(a[4]), 1e-30);
         c.resid[2 * s + 0] = rp;
         c.resid[2 * s + 1] = rd;
+        const double r = fmax(rp, rd);
+        double* best = c.rbest + s;
+        if (it <= c.check_every || !(r >= *best)) *best = r;
         int* itp = adj ? c.adj_iters : c.iters;
-        if (!isfinite(rp) || !isfinite(rd)) {
+        if (!isfinite(rp) || !isfinite(rd) || r > 1e6 * *best) {
+            // non-finite or diverged by six orders of magnitude from the best residual seen
             c.status[s] = GX_ERR_NONFINITE;
             c.done[s] = 1;
             itp[s] = it;
@@ -725,15 +731,14 @@ __global__ void __launch_bounds__(kBlock) k_grad(const Ctx c, int envelope, cons
             const long long bf = sc.e_bus + (long long)f * sc.Tp + t;
             const long long bt = sc.e_bus + (long long)to * sc.Tp + t;
             const float* dl = envelope ? c.dl : c.a_dl;
-            const float* sg = envelope ? c.sg : c.a_sg;
             const float* vfp = envelope ? c.vf : c.a_vf;
             const float* vtp = envelope ? c.vt : c.a_vt;
             const float* pb = envelope ? c.pbar : c.a_pbar;
             const float* uu = envelope ? c.u : c.a_u;
             const float* th = envelope ? c.thb : c.a_thb;
-            const float d = dl[rr], g = sg[rr];
-            const float vf = vfp[rr] + 0.5f * (g + d) - th[bf];
-            const float vt = vtp[rr] + 0.5f * (g - d) - th[bt];
+            const float d = dl[rr];
+            const float vf = vfp[rr] - th[bf];  // v = q - z
+            const float vt = vtp[rr] - th[bt];
             const float wf = th[bf] - vf, wt = th[bt] - vt;
             const float tf = -beta * d - pb[bf] - uu[bf];
             const float tt = beta * d - pb[bt] - uu[bt];
@@ -803,16 +808,21 @@ __global__ void k_plan_step(float* eta, const float* grad, const float* gamma, c
         }                                                                                \
     } while (0)
 
+int launch_line(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st) {
+    if (mode == M_INIT || c.n_line_blk <= 0) return 0;
+    GX_DISPATCH_MODE(k_line, c.n_line_blk, c, want_res);
+    return 1;
+}
+
+int launch_bat(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st) {
+    if (mode == M_INIT || c.n_bat_warps <= 0) return 0;
+    const int grid = (c.n_bat_warps + kBatWarps - 1) / kBatWarps;
+    GX_DISPATCH_MODE(k_bat, grid, c, want_res);
+    return 1;
+}
+
 int launch_dev(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st) {
-    int n = 0;
-    if (mode == M_INIT) return 0;
-    if (c.n_line_blk > 0) { GX_DISPATCH_MODE(k_line, c.n_line_blk, c, want_res); ++n; }
-    if (c.n_bat_warps > 0) {
-        const int grid = (c.n_bat_warps + kBatWarps - 1) / kBatWarps;
-        GX_DISPATCH_MODE(k_bat, grid, c, want_res);
-        ++n;
-    }
-    return n;
+    return launch_line(c, mode, adj, want_res, st) + launch_bat(c, mode, adj, want_res, st);
 }
 
 int launch_bus(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st) {

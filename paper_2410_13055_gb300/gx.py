@@ -81,6 +81,8 @@ _SIGS = {
                                           C.POINTER(Stats), _vp]),
     "gx_dispatch_grad_batch": (C.c_int, [_vp, _vp, C.c_int, _vp, C.POINTER(Stats), _vp]),
     "gx_plan_step": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, C.c_float, _vp]),
+    "gx_profile_enable": (C.c_int, [_vp, C.c_int]),
+    "gx_profile_read": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -257,6 +259,18 @@ class Network:
         self.last_grad_stats = st.asdict()
         self.last_grad_status = rc
         return out
+
+    def profile(self, on=True):
+        """Sampled CUDA-event timing of the bus / line / battery kernels (see gx_profile_enable)."""
+        _check(_lib.gx_profile_enable(self._h, int(bool(on))), "gx_profile_enable", False)
+
+    def profile_read(self):
+        ms = (C.c_double * 3)()
+        sm = (C.c_longlong * 3)()
+        ln = (C.c_longlong * 3)()
+        _check(_lib.gx_profile_read(self._h, ms, sm, ln), "gx_profile_read", False)
+        names = ["k_bus", "k_line", "k_bat"]
+        return {names[k]: {"ms": ms[k], "samples": sm[k], "launches": ln[k]} for k in range(3) if sm[k] > 0}
 
     def plan_step(self, eta, grad, gamma, eta_min, eta_max, alpha, stream=None):
         rc = _lib.gx_plan_step(self._h, _ptr(eta), _ptr(grad), _ptr(gamma), _ptr(eta_min), _ptr(eta_max),

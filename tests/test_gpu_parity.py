@@ -12,7 +12,10 @@ from paper_2410_13055_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-TIGHT = dict(tol=1e-6, max_iter=400000, adj_tol=1e-6, adj_max_iter=400000, check_every=50)
+TIGHT = dict(tol=1e-6, max_iter=200000, adj_tol=1e-5, adj_max_iter=200000, check_every=50)
+# FP32 solutions sit at their bounds to ~1e-4 relative; the KKT check treats a constraint
+# within 1e-3 of its bound as possibly active.
+ACT_TOL = 1e-3
 
 
 def _solve_pair(nets, scens, eta, kappa=0.0, **kw):
@@ -32,7 +35,7 @@ def test_tiny_dispatch_parity():
     ref = refs[0]
     g = solution(net, 0, ref_groups(ref.qp))
     assert abs(g["cost"] - ref.cost) / ref.cost <= 1e-4
-    res = kkt.residuals(ref.qp, pack_x(ref.qp, g), g["price"])
+    res = kkt.residuals(ref.qp, pack_x(ref.qp, g), g["price"], act_tol=ACT_TOL)
     assert res["primal"] <= 1e-3 and res["dual"] <= 1e-3, res
     assert rel(g["price"], ref.price) <= 1e-3
     assert rel(g["p"], ref.p) <= 1e-3
