@@ -29,18 +29,42 @@ def envelope_grad(sol) -> np.ndarray:
     return -(sol.qp.D.T @ sol.z)
 
 
-def active_set(sol, tol_mult=1e-6, tol_slack=1e-6):
-    """Constraints at their bound with a multiplier clearly above zero.
+def active_set(sol, ratio=1.0):
+    """Constraints identified as active at the interior-point solution.
 
-    Both tests are relative: slack against the bound's magnitude, multiplier
-    against the largest multiplier.  A weakly active constraint (at the bound
-    with a vanishing multiplier) is treated as inactive, which gives the
-    one-sided derivative in the direction that keeps it slack.
+    At an interior-point optimum an active constraint has slack s_i -> 0 with a
+    positive multiplier z_i, an inactive one the reverse, so the indicator
+    z_i / s_i separates them by many decades; a constraint counts as active when
+    z_i > ratio * s_i.  Weakly active constraints (both tiny) fall on either side,
+    which changes the derivative only by the (vanishing) multiplier involved.
     """
-    qp = sol.qp
-    zscale = max(1.0, float(np.max(sol.z))) if sol.z.size else 1.0
-    hscale = np.maximum(1.0, np.abs(qp.h))
-    return np.where((sol.s < tol_slack * hscale) & (sol.z > tol_mult * zscale))[0]
+    return np.where(sol.z > ratio * sol.s)[0]
+
+
+def independent_active(qp, act):
+    """Drop the lower row of a box whose two bounds coincide and are both active.
+
+    A generator with capacity factor 0 (or a battery of zero power) has
+    0 <= x <= 0: both rows are tight and the constraint gradients are linearly
+    dependent, so the active KKT matrix is singular.  One row fixes the variable;
+    the upper one is kept because it is the row that depends on eta (its
+    derivative cf * 1 is 0 there anyway).  Lines keep both their rows: their two
+    limits never coincide (eta_l > 0, dtheta_max > 0).
+    """
+    kind = qp.kind
+    ups = {}
+    for i in act:
+        tag = kind[i]
+        if tag is not None and tag[0].endswith("_up"):
+            ups[(tag[0][:-3], tag[1], tag[2])] = i
+    keep = []
+    for i in act:
+        tag = kind[i]
+        if tag is not None and tag[0].endswith("_lo") and tag[0][0] != "f" and tag[0][0] != "a":
+            if (tag[0][:-3], tag[1], tag[2]) in ups:
+                continue
+        keep.append(i)
+    return np.array(keep, dtype=np.int64)
 
 
 def adjoint_grad(sol, kappa=None, act=None) -> np.ndarray:
@@ -49,17 +73,30 @@ def adjoint_grad(sol, kappa=None, act=None) -> np.ndarray:
         kappa = sol.kappa
     if act is None:
         act = active_set(sol)
+    act = independent_active(qp, act)
     g = qp.planner_grad(sol.x, kappa)
     GA = qp.Gm[act]
     n, me, ma = qp.n, qp.m_eq, act.size
     K = sp.bmat([[qp.Q, qp.A.T, GA.T], [qp.A, None, None], [GA, None, None]], format="csc")
     rhs = np.concatenate([g, np.zeros(me + ma)])
-    try:
-        sol_vec = spla.splu(K).solve(rhs)
-        if not np.all(np.isfinite(sol_vec)):
-            raise RuntimeError("non-finite")
-    except Exception:
-        sol_vec = spla.lsqr(K, rhs, atol=1e-14, btol=1e-14, iter_lim=100000)[0]
+    # The active constraints can be linearly dependent (an idle battery held at full or
+    # empty charge over consecutive hours: soc bounds + dynamics + ch, dis >= 0).  The
+    # multipliers are then not unique, but the system is consistent and D_A^T xi is the
+    # same for every solution (the dependent combinations have zero eta-derivative).
+    # Solve it with a small regularisation of the multiplier block, then refine on the
+    # exact system.
+    nm = me + ma
+    delta = 1e-9 * max(1.0, float(np.max(np.abs(qp.Qd))))
+    Kreg = (K - sp.block_diag([sp.csc_matrix((n, n)), delta * sp.identity(nm)])).tocsc()
+    lu = spla.splu(Kreg)
+    sol_vec = lu.solve(rhs)
+    for _ in range(20):
+        r = rhs - K @ sol_vec
+        if np.linalg.norm(r) <= 1e-12 * max(1.0, np.linalg.norm(rhs)):
+            break
+        sol_vec = sol_vec + lu.solve(r)
+    if not np.all(np.isfinite(sol_vec)) or np.linalg.norm(K @ sol_vec - rhs) > 1e-8 * max(1.0, np.linalg.norm(rhs)):
+        raise np.linalg.LinAlgError("active-set KKT system is inconsistent")
     xi = sol_vec[n + me:]
     return qp.D[act].T @ xi
 

@@ -15,7 +15,9 @@ second-order correction).  Each Newton system is reduced to
     [ A             -dI ] [dy] = [r2],     W = diag(z / s),
 
 and solved with a sparse LU factorisation (a library primitive), reused for the
-predictor and the corrector.
+predictor and the corrector, with two steps of iterative refinement.  The best
+iterate (smallest of the relative residuals and gap) is returned; it counts as
+converged at 1e-8 when the end game stalls before `tol`.
 """
 from __future__ import annotations
 
@@ -58,6 +60,8 @@ def solve_qp(Q, q, A, b, G, h, tol=1e-11, max_iter=200, reg=1e-13, verbose=False
     converged = False
     it = 0
     info = {}
+    best = (np.inf, None)
+    stall = 0
     for it in range(1, max_iter + 1):
         rd = Q @ x + q + At @ y + Gt @ z
         rp = A @ x - b
@@ -71,8 +75,19 @@ def solve_qp(Q, q, A, b, G, h, tol=1e-11, max_iter=200, reg=1e-13, verbose=False
         info = dict(e_d=e_d, e_p=e_p, e_g=e_g, gap=gap, obj=obj)
         if verbose:
             print(it, info)
-        if max(e_d, e_p, e_g) < tol and gap < tol:
+        merit = max(e_d, e_p, e_g, gap)
+        if merit < best[0]:
+            best = (merit, (x.copy(), y.copy(), z.copy(), s.copy(), dict(info)))
+            stall = 0
+        else:
+            stall += 1
+        if merit < tol:
             converged = True
+            break
+        # End game: once the iterate is accurate, W = z/s spans many decades and the
+        # Newton systems lose accuracy; stop when the merit no longer improves and
+        # return the best iterate.
+        if stall >= 5 and best[0] < 1e-7:
             break
 
         w = z / s
@@ -80,10 +95,15 @@ def solve_qp(Q, q, A, b, G, h, tol=1e-11, max_iter=200, reg=1e-13, verbose=False
         K = sp.bmat([[H, At], [A, -reg * sp.identity(me)]], format="csc")
         lu = spla.splu(K)
 
+        K0 = sp.bmat([[H, At], [A, None]], format="csr")
+
         def direction(r_sz):
             # ds = -(r_sz + s dz)/z ;  dz = W (G dx + rg) - r_sz / s
             r1 = -rd - Gt @ (w * rg) + Gt @ (r_sz / s)
-            sol = lu.solve(np.concatenate([r1, -rp]))
+            rhs = np.concatenate([r1, -rp])
+            sol = lu.solve(rhs)
+            for _ in range(2):  # iterative refinement against the unregularised system
+                sol = sol + lu.solve(rhs - K0 @ sol)
             dx, dy = sol[:n], sol[n:]
             dz = w * (G @ dx + rg) - r_sz / s
             ds = -(r_sz + s * dz) / z
@@ -104,4 +124,7 @@ def solve_qp(Q, q, A, b, G, h, tol=1e-11, max_iter=200, reg=1e-13, verbose=False
         s = s + alpha * ds
         s = np.maximum(s, 1e-300)
         z = np.maximum(z, 1e-300)
+    if not converged and best[1] is not None:
+        x, y, z, s, info = best[1]
+        converged = best[0] < 1e-8
     return IPMResult(x, y, z, s, it, converged, info)

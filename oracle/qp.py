@@ -19,6 +19,7 @@ Equalities A x = b:
                    - sum_{l from n} beta_l (th_f - th_t) + sum_{l to n} beta_l (th_f - th_t) = L_nt
     dynamics (b,t): soc_t - soc_{t-1} - eff_c ch_t + dis_t / eff_d = 0,  soc_{-1} = 0
     reference (component, t): th_ref = 0   (angles are fixed up to a constant per island)
+    pinned: p_gt = 0 where cf_gt eta_g = 0, sh_nt = 0 where L_nt = 0 (coinciding bounds)
 
 Inequalities G x <= h(eta) = h0 + D eta  (the capacity dependence b(eta) of Eq. 2):
     p <= cf eta_g,  -p <= 0,  sh <= L,  -sh <= 0,
@@ -156,6 +157,22 @@ class DispatchQP:
                 rows.append(r); cols.append(vid("th", int(rb), t)); vals.append(1.0)
                 b.append(0.0)
                 r += 1
+        # A box whose bounds coincide (zero capacity factor, zero load) fixes its
+        # variable: written as an equality so the interior-point method never has
+        # to squeeze two slacks to zero.  Both bounds have zero eta-derivative there
+        # (cf = 0; the load does not depend on eta).
+        cf_in = np.asarray(scen["cf"], dtype=np.float64)
+        self.pinned = set()
+        for g in range(G):
+            for t in range(T):
+                if cf_in[g, t] * eg[g] == 0.0:
+                    rows.append(r); cols.append(vid("p", g, t)); vals.append(1.0); b.append(0.0); r += 1
+                    self.pinned.add(("p", g, t))
+        for n in range(N):
+            for t in range(T):
+                if load[n, t] == 0.0:
+                    rows.append(r); cols.append(vid("sh", n, t)); vals.append(1.0); b.append(0.0); r += 1
+                    self.pinned.add(("sh", n, t))
         self.m_eq = r
         self.A = sp.csr_matrix((vals, (rows, cols)), shape=(r, self.n))
         self.b = np.array(b)
@@ -180,10 +197,14 @@ class DispatchQP:
         cf = np.asarray(scen["cf"], dtype=np.float64)
         for g in range(G):
             for t in range(T):
+                if ("p", g, t) in self.pinned:
+                    continue
                 add_row([(vid("p", g, t), 1.0)], 0.0, g, cf[g, t], ("p_up", g, t))
                 add_row([(vid("p", g, t), -1.0)], 0.0, tag=("p_lo", g, t))
         for n in range(N):
             for t in range(T):
+                if ("sh", n, t) in self.pinned:
+                    continue
                 add_row([(vid("sh", n, t), 1.0)], load[n, t], tag=("sh_up", n, t))
                 add_row([(vid("sh", n, t), -1.0)], 0.0, tag=("sh_lo", n, t))
         for l in range(L):

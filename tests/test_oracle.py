@@ -73,6 +73,24 @@ def test_single_bus_envelope_gradient_closed_form():
     assert abs(g_adj[1]) < 1e-6  # the dear unit is never at its cap
 
 
+def test_zero_capacity_hours_gradient():
+    """A generator with capacity factor 0 in some hours (0 <= p <= 0): the adjoint's
+    active set must stay independent; FD, envelope and adjoint agree."""
+    costs = np.array([0.0, 30.0, 60.0])
+    caps = np.array([120.0, 150.0, 400.0])
+    cf = np.array([[0.0, 0.5, 1.0, 0.0], [1.0, 1.0, 1.0, 1.0], [1.0, 1.0, 1.0, 1.0]])
+    load = np.array([[100.0, 180.0, 300.0, 220.0]])
+    net, eta = network(1, gens=[(0, c, u, e) for c, u, e in zip(costs, caps, [0.0, 0.4, 0.6])])
+    for kappa in (0.0, 50.0):
+        o = opts(kappa=kappa)
+        sol = dispatch.solve(net, scenario(load, cf=cf), eta, o)
+        g_adj = grad.adjoint_grad(sol)
+        g_fd, _ = grad.fd_grad(net, scenario(load, cf=cf), eta, o)
+        assert np.max(np.abs(g_adj - g_fd)) < 1e-5 * max(1.0, np.max(np.abs(g_fd)))
+        if kappa == 0.0:
+            assert np.max(np.abs(grad.envelope_grad(sol) - g_fd)) < 1e-5 * max(1.0, np.max(np.abs(g_fd)))
+
+
 # ---------------------------------------------------------------- lines
 def test_two_bus_congestion():
     """Line flow direction, beta, flow limit and the line-capacity gradient."""
