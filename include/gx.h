@@ -208,6 +208,26 @@ gx_status gx_profile_enable(gx_network* net, int on);
  * were sampled; launches[k]: all launches of kind k since enabling. */
 gx_status gx_profile_read(const gx_network* net, double* ms, long long* samples, long long* launches);
 
+/* Operating cost c_s and planner value h_s of scenario `scen` at the last solve,
+ * computed without allocating any device memory.  The paper has no counterpart; this
+ * entry point exists for callers that cannot allocate device memory (code running
+ * while a CUDA graph is being captured, hosts that give the library a fixed memory
+ * budget, plugins whose device memory belongs to a host framework).
+ *
+ * Same sums as GX_ARR_COST / GX_ARR_H of gx_dispatch_solve_batch, but the per-block
+ * partial sums go to a fixed 64 KiB array compiled into the library (held on every
+ * GPU that loads it until the process exits) instead of the workspace.  Writes one
+ * double to cost_out_dev and, if h_out_dev is not NULL, one to h_out_dev (device
+ * pointers owned by the caller).  Limit: (G + N + B) * Tp <= 16,777,216 for the
+ * scenario (4096 partial-sum slots); larger scenarios return GX_ERR_INVALID_ARG with
+ * a message.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before any
+ * stream capture.  Every call shares the one array, so calls that overlap on the GPU
+ * (different streams, no ordering) race and must not be issued; calls on one stream
+ * are ordered and safe.  Asynchronous on `stream`. */
+gx_status gx_dispatch_cost_noalloc(const gx_network* net, int scen, double* cost_out_dev, double* h_out_dev,
+                                   void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -175,6 +175,12 @@ static void make_ctx(gx_network* net) {
     c.eta = nullptr;
 }
 
+namespace gx {
+const Ctx* gx_internal_ctx(const gx_network* net) { return (net && net->dev) ? &net->ctx : nullptr; }
+ScenDev gx_internal_scen(const gx_network* net, int s) { return net->sdev[s]; }
+gx_status gx_internal_fail(gx_status s, const std::string& msg) { return fail(s, msg); }
+}  // namespace gx
+
 extern "C" {
 
 gx_status gx_opts_default(gx_opts* o) {

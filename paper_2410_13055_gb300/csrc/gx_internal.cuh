@@ -8,6 +8,7 @@
 #pragma once
 
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
 
 #include "../../include/gx.h"
@@ -118,4 +119,11 @@ int launch_grad_combine(const Ctx& c, const double* wprime, const int* k_net, fl
 int launch_plan_step(float* eta, const float* grad, const float* gamma, const float* lo, const float* hi, float alpha,
                      int K, cudaStream_t st);
 
+}  // namespace gx
+
+// Read-only accessors for the no-allocation entry point (gx_noalloc.cu).
+namespace gx {
+const Ctx* gx_internal_ctx(const gx_network* net);        // nullptr if not bound
+ScenDev gx_internal_scen(const gx_network* net, int s);   // s must be in range
+gx_status gx_internal_fail(gx_status s, const std::string& msg);
 }  // namespace gx
