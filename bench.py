@@ -104,10 +104,10 @@ class Clocks:
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def build_workload(config, rank=0):
+def build_workload(config, rank=0, scenarios=None):
     seed_shift = 1000 * rank  # each rank takes its own shard of independent scenarios
     if config == "medium":
-        nets, scens = synth.medium(seed=1 + seed_shift)
+        nets, scens = synth.medium(seed=1 + seed_shift, S=scenarios or 16)
     elif config == "scale":
         nets, scens = synth.scale(seed=3 + seed_shift)
     elif config == "batching":
@@ -150,7 +150,7 @@ def run_gx(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     from paper_2410_13055_gb300 import gx
-    nets, scens = build_workload(args.config, rank)
+    nets, scens = build_workload(args.config, rank, args.scenarios)
     dh = synth.device_hours(nets, scens)
     net = gx.Network(nets, scens, kappa=KAPPA, tol=1e-3, adj_tol=1e-3, max_iter=50000, adj_max_iter=50000,
                      check_every=args.check_every)
@@ -208,6 +208,10 @@ def run_gx(args):
     prof = net.profile_read()
     net.profile(False)
     clk = clocks.stop()
+    if args.quick:
+        print(json.dumps({"quick": True, "ms_per_step": ms_prev / args.steps, "iters": it_prev, "adj_iters": ait_prev,
+                          "profile": prof, "launches": launches}), flush=True)
+        return
     ms_cold, _, it_cold, ait_cold, _ = timed("cold", max(1, min(args.steps, 3)))
     ms_cold /= max(1, min(args.steps, 3))
 
@@ -347,6 +351,8 @@ def main():
     ap.add_argument("--impl", default="gx", choices=["gx", "reference"])
     ap.add_argument("--check-every", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--scenarios", type=int, default=None, help="scenario count of the medium workload (default 16)")
+    ap.add_argument("--quick", action="store_true", help="timed previous-plan steps only (profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -117,6 +117,10 @@ typedef struct {
     double adj_tol;
     int adj_max_iter;
     int grad_envelope;   /* 1: for kappa == 0 use the envelope theorem (no adjoint solve) */
+    double adj_rho;      /* power penalty of the adjoint iteration (its phase and battery inner
+                            penalties scale with it as in the forward); the adjoint's free
+                            devices have curvature eps only, so a penalty near eps converges
+                            far faster than the forward's rho */
 } gx_opts;
 
 enum { GX_WARM_COLD = 0, GX_WARM_PREV = 1, GX_WARM_USER = 2, GX_WARM_LEARNED = 3 };

@@ -71,7 +71,7 @@ struct gx_network {
     size_t o_scen, o_bbs, o_lbs, o_bws, o_cbs, o_gwarp, o_knet;
     size_t o_gbus, o_gcost, o_gemis, o_gfirm, o_lfrom, o_lto, o_lbeta, o_ldth, o_lw, o_bbus, o_bdur, o_beffc, o_beffd;
     size_t o_gptr, o_gidx, o_bptr, o_bidx, o_eptr, o_eidx, o_icnt, o_iwsum, o_dresw;
-    size_t o_load, o_cf, o_dd;
+    size_t o_load, o_cf, o_dd, o_add;
     size_t static_end;
     size_t o_f[16], o_a[16];  // forward / adjoint state arrays, order of StatePtrs
     size_t o_mgen, o_mload, o_mline, o_mbat;
@@ -83,8 +83,8 @@ struct gx_network {
     bool solved = false, adj_ready = false, dd_dirty = true;
     std::vector<int> in_batch, done_init;
     std::vector<double> wprime;
-    std::vector<float> dd_host;
-    Ctx ctx{};
+    std::vector<float> dd_host, add_host;
+    Ctx ctx{}, actx{};
     // sampled kernel timing
     bool prof = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -96,12 +96,12 @@ struct gx_network {
     }
 };
 
-static void fill_dd(gx_network* net) {
+static void fill_dd_for(gx_network* net, double rho, std::vector<float>& out) {
     // Thomas pivots of the battery tridiagonal system (one row per battery and scenario):
     // diag = [1 + g rho_in, 2 + g rho_in, ...], off-diagonal -1, with
     // g = [a, -k] H^{-1} [a, -k]^T and H = [[eps+rho_in+rho, -rho], [-rho, eps+rho_in+rho]].
-    const double eps = net->opts.eps, rho = net->opts.rho, ri = rho * net->opts.rho_inner_c;
-    net->dd_host.assign((size_t)net->bat_el, 1.0f);
+    const double eps = net->opts.eps, ri = rho * net->opts.rho_inner_c;
+    out.assign((size_t)net->bat_el, 1.0f);
     for (int s = 0; s < net->S; ++s) {
         const ScenH& sc = net->scens[s];
         const NetH& nh = net->nets[sc.net];
@@ -111,14 +111,19 @@ static void fill_dd(gx_network* net) {
             const double gc = (A * a - rho * k) / det, gd = (rho * a - A * k) / det;
             const double g = a * gc - k * gd;
             double d = 1.0 + g * ri;
-            float* out = net->dd_host.data() + net->sdev[s].e_bat + (size_t)b * sc.Tp;
-            out[0] = (float)d;
+            float* o = out.data() + net->sdev[s].e_bat + (size_t)b * sc.Tp;
+            o[0] = (float)d;
             for (int t = 1; t < sc.T; ++t) {
                 d = (2.0 + g * ri) - 1.0 / d;
-                out[t] = (float)d;
+                o[t] = (float)d;
             }
         }
     }
+}
+
+static void fill_dd(gx_network* net) {
+    fill_dd_for(net, net->opts.rho, net->dd_host);
+    fill_dd_for(net, net->opts.adj_rho, net->add_host);
     net->dd_dirty = true;
 }
 
@@ -173,6 +178,13 @@ static void make_ctx(gx_network* net) {
     c.warm = nullptr;
     c.warm_half = net->bus_el;
     c.eta = nullptr;
+    // the adjoint iteration: same arrays, its own penalties and battery pivots
+    Ctx& a = net->actx;
+    a = c;
+    a.rho = (float)o.adj_rho;
+    a.rho_in = (float)(o.adj_rho * o.rho_inner_c);
+    a.rth_c = (float)(o.adj_rho * o.rho_theta_c);
+    a.bat_dd = F(net->o_add);
 }
 
 namespace gx {
@@ -200,6 +212,7 @@ gx_status gx_opts_default(gx_opts* o) {
     o->adj_tol = 1e-3;
     o->adj_max_iter = 20000;
     o->grad_envelope = 0;
+    o->adj_rho = 0.005;
     return GX_OK;
 }
 
@@ -224,6 +237,7 @@ static gx_status check_opts(const gx_opts* o) {
     if (!(o->voll > 0 && isfin(o->voll))) return fail(GX_ERR_INVALID_ARG, "opts.voll must be > 0");
     if (!(o->kappa >= 0 && isfin(o->kappa))) return fail(GX_ERR_INVALID_ARG, "opts.kappa must be >= 0");
     if (!(o->rho > 0 && isfin(o->rho))) return fail(GX_ERR_INVALID_ARG, "opts.rho must be > 0");
+    if (!(o->adj_rho > 0 && isfin(o->adj_rho))) return fail(GX_ERR_INVALID_ARG, "opts.adj_rho must be > 0");
     if (!(o->rho_theta_c > 0 && isfin(o->rho_theta_c))) return fail(GX_ERR_INVALID_ARG, "opts.rho_theta_c must be > 0");
     if (!(o->rho_inner_c > 0 && isfin(o->rho_inner_c))) return fail(GX_ERR_INVALID_ARG, "opts.rho_inner_c must be > 0");
     if (o->inner_iters < 1 || o->inner_iters > 1000) return fail(GX_ERR_INVALID_ARG, "opts.inner_iters in [1, 1000]");
@@ -428,6 +442,7 @@ gx_status gx_network_create(const gx_network_desc* nets, int n_nets, const gx_sc
     net->o_eptr = L.add(I4(ptr0)); net->o_eidx = L.add(I4(2LL * line0));
     net->o_icnt = L.add(F4(bus0)); net->o_iwsum = L.add(F4(bus0)); net->o_dresw = L.add(F4(bus0));
     net->o_load = L.add(F4(eb)); net->o_cf = L.add(F4(eg)); net->o_dd = L.add(F4(ebt));
+    net->o_add = L.add(F4(ebt));
     net->static_end = L.total;
     const long long rows[16] = {eg, eb, el, el, el, el, ebt, ebt, ebt, ebt, ebt, ebt, ebt, eb, eb, eb};
     for (int k = 0; k < 16; ++k) net->o_f[k] = L.add(F4(rows[k]));
@@ -510,6 +525,7 @@ gx_status gx_network_bind(gx_network* net, void* dev_mem, size_t bytes, void* st
     }
     put(net->o_gfirm, firm.data(), net->tot_gen);
     put_v(net->o_dd, net->dd_host, 0);
+    put_v(net->o_add, net->add_host, 0);
     GX_CUDA(cudaMemcpyAsync(net->dev, h.data(), net->static_end, cudaMemcpyHostToDevice, st));
     GX_CUDA(cudaMemsetAsync(net->dev + net->static_end, 0, net->lay.total - net->static_end, st));
     GX_CUDA(cudaStreamSynchronize(st));
@@ -581,7 +597,7 @@ gx_status gx_network_scenario_info(const gx_network* net, int s, int* T, int* Tp
 // Iterate the forward (adj = 0) or adjoint (adj = 1) message passing until every
 // scenario of the batch meets its tolerance or the cap is reached.
 static gx_status run_loop(gx_network* net, int adj, cudaStream_t st, int* launches, int* iters_out) {
-    const Ctx& c = net->ctx;
+    const Ctx& c = adj ? net->actx : net->ctx;
     const int max_it = adj ? net->opts.adj_max_iter : net->opts.max_iter;
     const double tol = adj ? net->opts.adj_tol : net->opts.tol;
     const int every = net->opts.check_every;
@@ -685,6 +701,8 @@ gx_status gx_dispatch_solve_batch(gx_network* net, const float* eta_dev, const i
     if (net->dd_dirty) {
         GX_CUDA(cudaMemcpyAsync(net->dev + net->o_dd, net->dd_host.data(), 4 * net->dd_host.size(),
                                 cudaMemcpyHostToDevice, st));
+        GX_CUDA(cudaMemcpyAsync(net->dev + net->o_add, net->add_host.data(), 4 * net->add_host.size(),
+                                cudaMemcpyHostToDevice, st));
         GX_CUDA(cudaStreamSynchronize(st));
         net->dd_dirty = false;
     }
@@ -718,6 +736,9 @@ gx_status gx_dispatch_grad_batch(gx_network* net, const float* eta_dev, int warm
     Ctx& c = net->ctx;
     c.eta = eta_dev;
     c.warm = nullptr;
+    Ctx& ac = net->actx;
+    ac.eta = eta_dev;
+    ac.warm = nullptr;
     // the batch of the last solve, with weights rescaled to the total weight
     double wall = 0, wb = 0;
     for (int s = 0; s < net->S; ++s) {
@@ -735,17 +756,17 @@ gx_status gx_dispatch_grad_batch(gx_network* net, const float* eta_dev, int warm
     gx_stats sx{};
     if (!envelope) {
         if (warm != GX_WARM_PREV || !net->adj_ready) {
-            launches += launch_dev(c, M_RESET, 1, 0, st);
-            launches += launch_bus(c, M_RESET, 1, 0, st);
+            launches += launch_dev(ac, M_RESET, 1, 0, st);
+            launches += launch_bus(ac, M_RESET, 1, 0, st);
         }
-        launches += launch_bus(c, M_INIT, 1, 0, st);
+        launches += launch_bus(ac, M_INIT, 1, 0, st);
         int it = 0;
         if (gx_status e = run_loop(net, 1, st, &launches, &it)) return e;
         net->adj_ready = true;
     }
     const int* inb = reinterpret_cast<const int*>(net->dev + net->o_inb);
-    launches += launch_grad(c, envelope ? 1 : 0, reinterpret_cast<const int*>(net->dev + net->o_gwarp), net->n_gwarps,
-                            inb, st);
+    launches += launch_grad(envelope ? c : ac, envelope ? 1 : 0,
+                            reinterpret_cast<const int*>(net->dev + net->o_gwarp), net->n_gwarps, inb, st);
     launches += launch_grad_combine(c, reinterpret_cast<const double*>(net->dev + net->o_wprime),
                                     reinterpret_cast<const int*>(net->dev + net->o_knet), grad_dev, net->K, st);
     GX_CUDA(cudaGetLastError());

@@ -243,6 +243,15 @@ def scale(seed: int = 3, S: int = 52, T: int = 168):
     return [net], scens
 
 
+def custom(n_bus, n_lines, n_gen, n_bat, T, S=1, seed=0, net_index=0):
+    """A network of the given size with the medium case's distributions and S scenarios."""
+    rng = _rng(seed)
+    net = _bus_network(rng, n_bus, n_lines, n_gen, n_bat, T)
+    base = rng.uniform(50.0, 150.0, size=n_bus)
+    scens = [_bus_scenario(rng, net, net_index, T, 1.0 / S, base) for _ in range(S)]
+    return net, scens
+
+
 CONFIGS = {"tiny": tiny, "medium": medium, "batching": batching, "scale": scale}
 
 

@@ -51,3 +51,43 @@ def test_tiny_gradient_parity(kappa):
     assert net.last_grad_status == 0, net.last_grad_stats
     g_ref = ograd.adjoint_grad(refs[0])
     assert rel(gg, g_ref) <= 1e-3, (gg, g_ref)
+
+
+def test_tiny_plan_trajectory_matches_golden():
+    """Ten projected implicit-gradient steps (Section 2.2) on the GPU follow the oracle's."""
+    import json
+    import os
+
+    import torch
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "tiny_plan.json")))
+    nets, scens = synth.tiny()
+    net = gpu_net(nets, scens, kappa=gold["kappa"], **TIGHT)
+    eta = eta_tensor(gold["eta"][0])
+    gamma = eta_tensor(nets[0]["gamma"])
+    lo, hi = eta_tensor(nets[0]["eta_min"]), eta_tensor(nets[0]["eta_max"])
+    for k in range(len(gold["delta"])):
+        assert net.solve(eta) == 0
+        g = net.grad(eta)
+        delta = (g + gamma).double().cpu().numpy()
+        assert rel(delta, gold["delta"][k]) <= 1e-3, k
+        net.plan_step(eta, g, gamma, lo, hi, gold["alpha"])
+        e = eta.double().cpu().numpy()
+        step = np.asarray(gold["eta"][k + 1]) - np.asarray(gold["eta"][0])
+        assert np.max(np.abs(e - gold["eta"][k + 1])) <= 1e-3 * max(np.max(np.abs(step)), 1e-3), k
+    torch.cuda.synchronize()
+
+
+def test_medium_slice_parity():
+    """100-bus network, one scenario, 24 hours: dispatch, prices and the adjoint gradient."""
+    nets, scens = synth.medium(S=1)
+    nets, scens = synth.slice_hours(nets, scens, 0, 24)
+    eta = nets[0]["eta_min"]
+    net, e, rc, refs = _solve_pair(nets, scens, eta, kappa=50.0, tol=1e-5, adj_tol=1e-5)
+    ref = refs[0]
+    g = solution(net, 0, ref_groups(ref.qp))
+    assert abs(g["cost"] - ref.cost) / ref.cost <= 1e-4
+    res = kkt.residuals(ref.qp, pack_x(ref.qp, g), g["price"], act_tol=ACT_TOL)
+    assert res["primal"] <= 1e-3 and res["dual"] <= 1e-3, res
+    gg = net.grad(e).double().cpu().numpy()
+    g_ref = ograd.adjoint_grad(ref)
+    assert rel(gg, g_ref) <= 1e-3, (net.last_grad_stats, rel(gg, g_ref))
