@@ -201,6 +201,10 @@ gx_status gx_dispatch_grad_batch(gx_network* net, const float* eta_dev, int warm
 gx_status gx_plan_step(gx_network* net, float* eta_dev, const float* grad_dev, const float* gamma_dev,
                        const float* eta_min_dev, const float* eta_max_dev, float alpha, void* stream);
 
+/* Replay each residual-check chunk as one CUDA graph (default on) or launch its kernels
+ * one by one (off).  Results are identical; graphs cut the host launch cost. */
+gx_status gx_network_use_graphs(gx_network* net, int on);
+
 /* Sampled kernel timing.  While enabled, the solve and gradient loops record CUDA
  * events on their stream around the bus, line and battery kernels of the last
  * iteration of every residual-check chunk and accumulate the elapsed times at the

@@ -9,7 +9,8 @@ stationarity residual, so the result measures how far (x, lambda) is from
 satisfying the KKT conditions of the QP in ``qp``:
 
     primal   = max(|A x - b|_inf, |max(G x - h, 0)|_inf) / (1 + |(b, h)|_inf)
-    dual     = |Q x + q + A^T y + G^T z|_inf / (1 + |q|_inf)
+    dual     = |(Q x + q + A^T y + G^T z) / colmax(A)|_inf / (1 + |q|_inf)
+               (colmax: each variable's largest equality coefficient, >= 1)
     comp     = max_i z_i |h_i - G_i x| / (1 + |q|_inf)
 """
 from __future__ import annotations
@@ -17,6 +18,7 @@ from __future__ import annotations
 import numpy as np
 import scipy.sparse as sp
 from scipy.optimize import lsq_linear
+from scipy.sparse.csgraph import connected_components
 
 
 def residuals(qp, x, price, act_tol=1e-5):
@@ -30,22 +32,42 @@ def residuals(qp, x, price, act_tol=1e-5):
     y_bal = -np.asarray(price, float).ravel()
     grad = qp.Qd * x + qp.q + qp.A[:nb].T @ y_bal
     near = np.where(-rg <= act_tol * np.maximum(1.0, np.abs(qp.h)))[0]
-    Afree = qp.A[nb:].T  # dynamics + reference rows: free multipliers
+    Afree = qp.A[nb:].T  # dynamics, reference and fixed-variable rows: free multipliers
     Gn = qp.Gm[near].T
-    M = sp.hstack([Afree, Gn]).tocsr()
+    M = sp.hstack([Afree, Gn]).tocsc()
     nf = Afree.shape[1]
-    lb = np.concatenate([np.full(nf, -np.inf), np.zeros(near.size)])
-    ub = np.full(nf + near.size, np.inf)
+    lb_all = np.concatenate([np.full(nf, -np.inf), np.zeros(near.size)])
+    r = grad.copy()
+    zn = np.zeros(near.size)
     if M.shape[1]:
-        sol = lsq_linear(M.toarray() if M.shape[0] * M.shape[1] < 4e7 else M, -grad, bounds=(lb, ub),
-                         lsmr_tol="auto", tol=1e-13, max_iter=5000)
-        mult = sol.x
-        r = grad + M @ mult
-        zn = mult[nf:]
-    else:
-        r = grad
-        zn = np.zeros(0)
+        # The multipliers only couple variables that share a row: solve the bounded
+        # least-squares problem separately on each connected block (one generator-hour,
+        # one battery's horizon, one hour of angles, ...).
+        n, m = M.shape
+        B = sp.bmat([[None, M], [M.T, None]]).tocsr()
+        B.data[:] = 1.0
+        ncomp, lab = connected_components(B, directed=False)
+        vlab, clab = lab[:n], lab[n:]
+        corder = np.argsort(clab, kind="stable")
+        cstart = np.searchsorted(clab[corder], np.arange(ncomp + 1))
+        vorder = np.argsort(vlab, kind="stable")
+        vstart = np.searchsorted(vlab[vorder], np.arange(ncomp + 1))
+        for k in range(ncomp):
+            cols = corder[cstart[k]:cstart[k + 1]]
+            if cols.size == 0:
+                continue
+            rows = vorder[vstart[k]:vstart[k + 1]]
+            Mk = M[rows][:, cols].toarray()
+            sol = lsq_linear(Mk, -grad[rows], bounds=(lb_all[cols], np.full(cols.size, np.inf)),
+                             method="bvls", tol=1e-13, max_iter=2000)
+            r[rows] = grad[rows] + Mk @ sol.x
+            zc = cols >= nf
+            zn[cols[zc] - nf] = sol.x[zc]
     scale_q = 1.0 + np.max(np.abs(qp.q))
-    dual = np.max(np.abs(r)) / scale_q
+    # Each variable's stationarity residual in its own units: divided by its column's
+    # largest coefficient in the equality rows (beta for an angle, whose balance terms
+    # are beta * price differences; 1 for powers), then relative to the cost scale.
+    colmax = np.maximum(1.0, abs(qp.A).max(axis=0).toarray().ravel())
+    dual = np.max(np.abs(r) / colmax) / scale_q
     comp = float(np.max(zn * np.abs(rg[near]))) / scale_q if zn.size else 0.0
     return dict(primal=float(primal), dual=float(dual), comp=comp)

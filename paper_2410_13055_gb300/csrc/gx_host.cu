@@ -75,7 +75,7 @@ struct gx_network {
     size_t static_end;
     size_t o_f[16], o_a[16];  // forward / adjoint state arrays, order of StatePtrs
     size_t o_mgen, o_mload, o_mline, o_mbat;
-    size_t o_done, o_iters, o_status, o_adjit, o_nact, o_inb, o_resid, o_rbest, o_cost, o_h, o_grads, o_wprime;
+    size_t o_done, o_iters, o_status, o_adjit, o_nact, o_ctr, o_inb, o_resid, o_rbest, o_cost, o_h, o_grads, o_wprime;
     size_t o_flow, o_price, o_shed, o_bpart, o_lpart, o_btpart, o_cpart;
     Layout lay;
     // binding
@@ -85,6 +85,23 @@ struct gx_network {
     std::vector<double> wprime;
     std::vector<float> dd_host, add_host;
     Ctx ctx{}, actx{};
+    // CUDA graphs of one residual-check chunk, keyed by what their captured parameters depend on
+    struct ChunkGraph {
+        bool valid = false;
+        int adj = 0, chunk = 0, prof = 0;
+        const float* eta = nullptr;
+        cudaGraphExec_t exec = nullptr;
+    } graphs[4];
+    int graph_next = 0;
+    cudaStream_t cap_stream = nullptr;
+    int* h_nact = nullptr;  // pinned host copy of the active-scenario count
+    bool use_graphs = true;
+    void drop_graphs() {
+        for (auto& g : graphs) {
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+            g = ChunkGraph{};
+        }
+    }
     // sampled kernel timing
     bool prof = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -93,6 +110,9 @@ struct gx_network {
     ~gx_network() {
         for (auto& e : ev)
             if (e) cudaEventDestroy(e);
+        drop_graphs();
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+        if (h_nact) cudaFreeHost(h_nact);
     }
 };
 
@@ -171,6 +191,8 @@ static void make_ctx(gx_network* net) {
     c.m_gen = U8(net->o_mgen); c.m_load = U8(net->o_mload); c.m_line = U8(net->o_mline); c.m_bat = U8(net->o_mbat);
     c.done = I(net->o_done); c.iters = I(net->o_iters); c.status = I(net->o_status); c.adj_iters = I(net->o_adjit);
     c.n_active = I(net->o_nact);
+    c.iter_ctr = I(net->o_ctr);
+    c.max_it = o.max_iter;
     c.resid = D(net->o_resid); c.rbest = D(net->o_rbest); c.cost = D(net->o_cost); c.hval = D(net->o_h); c.grad_s = D(net->o_grads);
     c.out_flow = F(net->o_flow); c.out_price = F(net->o_price); c.out_shed = F(net->o_shed);
     c.bus_part = F(net->o_bpart); c.line_part = F(net->o_lpart); c.bat_part = F(net->o_btpart);
@@ -185,6 +207,8 @@ static void make_ctx(gx_network* net) {
     a.rho_in = (float)(o.adj_rho * o.rho_inner_c);
     a.rth_c = (float)(o.adj_rho * o.rho_theta_c);
     a.bat_dd = F(net->o_add);
+    a.max_it = o.adj_max_iter;
+    net->drop_graphs();
 }
 
 namespace gx {
@@ -449,7 +473,7 @@ gx_status gx_network_create(const gx_network_desc* nets, int n_nets, const gx_sc
     for (int k = 0; k < 16; ++k) net->o_a[k] = L.add(F4(rows[k]));
     net->o_mgen = L.add(B1(eg)); net->o_mload = L.add(B1(eb)); net->o_mline = L.add(B1(el)); net->o_mbat = L.add(B1(ebt));
     net->o_done = L.add(I4(S)); net->o_iters = L.add(I4(S)); net->o_status = L.add(I4(S)); net->o_adjit = L.add(I4(S));
-    net->o_nact = L.add(I4(1)); net->o_inb = L.add(I4(S));
+    net->o_nact = L.add(I4(1)); net->o_ctr = L.add(I4(1)); net->o_inb = L.add(I4(S));
     net->o_resid = L.add(D8(2LL * S)); net->o_rbest = L.add(D8(S)); net->o_cost = L.add(D8(S)); net->o_h = L.add(D8(S));
     net->o_grads = L.add(D8(gs)); net->o_wprime = L.add(D8(S));
     net->o_flow = L.add(F4(el)); net->o_price = L.add(F4(eb)); net->o_shed = L.add(F4(eb));
@@ -530,6 +554,8 @@ gx_status gx_network_bind(gx_network* net, void* dev_mem, size_t bytes, void* st
     GX_CUDA(cudaMemsetAsync(net->dev + net->static_end, 0, net->lay.total - net->static_end, st));
     GX_CUDA(cudaStreamSynchronize(st));
     net->dd_dirty = false;
+    if (!net->h_nact) GX_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&net->h_nact), sizeof(int), cudaHostAllocDefault));
+    if (!net->cap_stream) GX_CUDA(cudaStreamCreateWithFlags(&net->cap_stream, cudaStreamNonBlocking));
     make_ctx(net);
     net->solved = false;
     net->adj_ready = false;
@@ -594,51 +620,102 @@ gx_status gx_network_scenario_info(const gx_network* net, int s, int* T, int* Tp
     return GX_OK;
 }
 
+// One residual-check chunk: `chunk` iterations (residual partials on the last one), the
+// counter tick, the per-scenario reduction and the copy of the active count to the host.
+static gx_status enqueue_chunk(gx_network* net, const Ctx& c, int adj, int chunk, bool prof, cudaStream_t st,
+                               int* launches) {
+    const int mode = adj ? M_ADJ : M_FWD;
+    const double tol = adj ? net->opts.adj_tol : net->opts.tol;
+    *launches += launch_tick(c, chunk, st);
+    for (int j = 0; j < chunk; ++j) {
+        const int want = j == chunk - 1;
+        const bool samp = prof && want;
+        if (samp) GX_CUDA(cudaEventRecord(net->ev[0], st));
+        const int nl = launch_line(c, mode, adj, want, st);
+        if (samp) GX_CUDA(cudaEventRecord(net->ev[1], st));
+        const int nb = launch_bat(c, mode, adj, want, st);
+        if (samp) GX_CUDA(cudaEventRecord(net->ev[2], st));
+        const int nu = launch_bus(c, mode, adj, want, st);
+        if (samp) GX_CUDA(cudaEventRecord(net->ev[3], st));
+        *launches += nl + nb + nu;
+    }
+    GX_CUDA(cudaMemsetAsync(c.n_active, 0, sizeof(int), st));
+    *launches += launch_reduce(c, adj, tol, st);
+    GX_CUDA(cudaMemcpyAsync(net->h_nact, c.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+    return GX_OK;
+}
+
+// The instantiated graph of a full chunk for (adj, chunk, prof, eta), captured on the
+// library's own stream (capture is not allowed on the legacy default stream).
+static gx_status chunk_graph(gx_network* net, const Ctx& c, int adj, int chunk, bool prof, cudaGraphExec_t* out) {
+    for (auto& g : net->graphs)
+        if (g.valid && g.adj == adj && g.chunk == chunk && g.prof == (int)prof && g.eta == c.eta) {
+            *out = g.exec;
+            return GX_OK;
+        }
+    auto& g = net->graphs[net->graph_next];
+    net->graph_next = (net->graph_next + 1) % 4;
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g = gx_network::ChunkGraph{};
+    cudaGraph_t graph = nullptr;
+    int dummy = 0;
+    GX_CUDA(cudaStreamBeginCapture(net->cap_stream, cudaStreamCaptureModeThreadLocal));
+    gx_status e = enqueue_chunk(net, c, adj, chunk, prof, net->cap_stream, &dummy);
+    cudaError_t ce = cudaStreamEndCapture(net->cap_stream, &graph);
+    if (e) return e;
+    if (ce != cudaSuccess) return fail(GX_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(ce));
+    ce = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return fail(GX_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ce));
+    g.valid = true;
+    g.adj = adj; g.chunk = chunk; g.prof = prof; g.eta = c.eta;
+    *out = g.exec;
+    return GX_OK;
+}
+
 // Iterate the forward (adj = 0) or adjoint (adj = 1) message passing until every
-// scenario of the batch meets its tolerance or the cap is reached.
+// scenario of the batch meets its tolerance or the cap is reached.  Each chunk of
+// check_every iterations is replayed as one CUDA graph; the stream is synchronised
+// once per chunk to read the number of scenarios still iterating.
 static gx_status run_loop(gx_network* net, int adj, cudaStream_t st, int* launches, int* iters_out) {
     const Ctx& c = adj ? net->actx : net->ctx;
     const int max_it = adj ? net->opts.adj_max_iter : net->opts.max_iter;
-    const double tol = adj ? net->opts.adj_tol : net->opts.tol;
     const int every = net->opts.check_every;
-    const int mode = adj ? M_ADJ : M_FWD;
-    int it = 0, nact = 1;
+    const bool prof = net->prof;
+    int it = 0;
+    GX_CUDA(cudaMemsetAsync(c.iter_ctr, 0, sizeof(int), st));
     while (it < max_it) {
         const int chunk = std::min(every, max_it - it);
-        bool sampled = false;
-        for (int j = 0; j < chunk; ++j) {
-            const int want = j == chunk - 1;
-            const bool samp = net->prof && want;
-            if (samp) GX_CUDA(cudaEventRecord(net->ev[0], st));
-            const int nl = launch_line(c, mode, adj, want, st);
-            if (samp) GX_CUDA(cudaEventRecord(net->ev[1], st));
-            const int nb = launch_bat(c, mode, adj, want, st);
-            if (samp) GX_CUDA(cudaEventRecord(net->ev[2], st));
-            const int nu = launch_bus(c, mode, adj, want, st);
-            if (samp) GX_CUDA(cudaEventRecord(net->ev[3], st));
-            *launches += nl + nb + nu;
-            if (net->prof) {
-                net->prof_launches[0] += nu; net->prof_launches[1] += nl; net->prof_launches[2] += nb;
-                if (samp) sampled = true;
-            }
-            if (samp) {
-                net->prof_samples[0] += nu; net->prof_samples[1] += nl; net->prof_samples[2] += nb;
-            }
+        int nk = 0;
+        if (net->use_graphs && chunk == every) {
+            cudaGraphExec_t exec = nullptr;
+            if (gx_status e = chunk_graph(net, c, adj, chunk, prof, &exec)) return e;
+            GX_CUDA(cudaGraphLaunch(exec, st));
+            // count the kernels of the replayed chunk
+            nk = 2 + chunk * ((c.n_line_blk > 0) + (c.n_bat_warps > 0) + (c.n_bus_blk > 0));
+        } else {
+            if (gx_status e = enqueue_chunk(net, c, adj, chunk, prof, st, &nk)) return e;
+        }
+        *launches += nk;
+        if (prof) {
+            net->prof_launches[0] += chunk * (c.n_bus_blk > 0);
+            net->prof_launches[1] += chunk * (c.n_line_blk > 0);
+            net->prof_launches[2] += chunk * (c.n_bat_warps > 0);
+            net->prof_samples[0] += (c.n_bus_blk > 0);
+            net->prof_samples[1] += (c.n_line_blk > 0);
+            net->prof_samples[2] += (c.n_bat_warps > 0);
         }
         it += chunk;
-        GX_CUDA(cudaMemsetAsync(c.n_active, 0, sizeof(int), st));
-        *launches += launch_reduce(c, adj, it, tol, it >= max_it, st);
         GX_CUDA(cudaGetLastError());
-        GX_CUDA(cudaMemcpyAsync(&nact, c.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
         GX_CUDA(cudaStreamSynchronize(st));
-        if (sampled) {
+        if (prof) {
             float a = 0, b = 0, u = 0;
             GX_CUDA(cudaEventElapsedTime(&a, net->ev[0], net->ev[1]));
             GX_CUDA(cudaEventElapsedTime(&b, net->ev[1], net->ev[2]));
             GX_CUDA(cudaEventElapsedTime(&u, net->ev[2], net->ev[3]));
             net->prof_ms[1] += a; net->prof_ms[2] += b; net->prof_ms[0] += u;
         }
-        if (nact == 0) break;
+        if (*net->h_nact == 0) break;
     }
     *iters_out = it;
     return GX_OK;
@@ -789,6 +866,12 @@ gx_status gx_plan_step(gx_network* net, float* eta_dev, const float* grad_dev, c
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     launch_plan_step(eta_dev, grad_dev, gamma_dev, eta_min_dev, eta_max_dev, alpha, net->K, st);
     GX_CUDA(cudaGetLastError());
+    return GX_OK;
+}
+
+gx_status gx_network_use_graphs(gx_network* net, int on) {
+    if (!net) return fail(GX_ERR_INVALID_ARG, "net is NULL");
+    net->use_graphs = on != 0;
     return GX_OK;
 }
 

@@ -16,7 +16,7 @@
 namespace gx {
 
 constexpr int kBlock = 256;        // threads per block of the bus / line / generic kernels
-constexpr int kBatWarps = 8;       // batteries (warps) per block of the battery kernel
+constexpr int kBatWarps = 2;       // batteries (warps) per block of the battery kernel
 constexpr int kMaxT = 256;         // hours per scenario handled by one warp (8 per lane)
 constexpr int kHplMax = kMaxT / 32;
 constexpr int kBusPart = 6;        // floats per bus-block residual partial
@@ -54,6 +54,8 @@ struct Ctx {
     float tol_act;
     int inner_iters;
     int check_every;
+    int max_it;          // iteration cap of the loop this context drives
+    int* iter_ctr;       // device iteration counter of the current loop
     // tables
     const ScenDev* scen;
     const int* bus_blk_scen;   // [n_bus_blk]
@@ -110,7 +112,8 @@ int launch_dev(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st);
 int launch_line(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st);
 int launch_bat(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st);
 int launch_bus(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st);
-int launch_reduce(const Ctx& c, int adj, int it, double tol, int final_, cudaStream_t st);
+int launch_reduce(const Ctx& c, int adj, double tol, cudaStream_t st);
+int launch_tick(const Ctx& c, int chunk, cudaStream_t st);
 int launch_extract(const Ctx& c, const int* in_batch, cudaStream_t st);
 int launch_grad(const Ctx& c, int envelope, const int* gwarp_scen, int n_gwarps, const int* in_batch,
                 cudaStream_t st);

@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(kBlock) k_line(const Ctx c, int want_res) {
 // recurrences evaluated with warp-wide affine scans.
 // ------------------------------------------------------------------------------------
 template <int MODE, int ADJ>
-__global__ void __launch_bounds__(kBlock) k_bat(const Ctx c, int want_res) {
+__global__ void __launch_bounds__(kBatWarps * 32) k_bat(const Ctx c, int want_res) {
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * kBatWarps + (threadIdx.x >> 5);
     if (gw >= c.n_bat_warps) return;
@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(kBlock) k_bat(const Ctx c, int want_res) {
         }
         return;
     }
-    const float rho = c.rho, eps = c.eps, ri = c.rho_in;
+    const float rho = c.rho, eps = c.eps, ri = c.rho_in, iri = 1.f / c.rho_in;
     if (MODE == M_MASK) {
         // active set from the inner box multipliers of the forward solution
         for (int t = lane; t < T; t += 32) {
@@ -266,8 +266,8 @@ __global__ void __launch_bounds__(kBlock) k_bat(const Ctx c, int want_res) {
         float c0[kHplMax], d0[kHplMax], rs[kHplMax], rhs[kHplMax];
 #pragma unroll
         for (int j = 0; j < kHplMax; ++j) {
-            const float rc = zc[j] - yc[j] / ri, rd = zd[j] - yd[j] / ri;
-            rs[j] = zs[j] - ys[j] / ri;
+            const float rc = zc[j] - yc[j] * iri, rd = zd[j] - yd[j] * iri;
+            rs[j] = zs[j] - ys[j] * iri;
             const float b1 = ri * rc - rho * v[j] - qc[j];
             const float b2 = ri * rd + rho * v[j] - qd[j];
             c0[j] = (Ah * b1 + rho * b2) * idet;
@@ -342,10 +342,10 @@ __global__ void __launch_bounds__(kBlock) k_bat(const Ctx c, int want_res) {
             else mu_n = min_;
             const float cc = c0[j] + mu[j] * gc;
             const float dd_ = d0[j] + mu[j] * gd;
-            const float ss = rs[j] - (mu[j] - mu_n) / ri;
-            const float nzc = clampf(cc + yc[j] / ri, lo[0][j], hi[0][j]);
-            const float nzd = clampf(dd_ + yd[j] / ri, lo[1][j], hi[1][j]);
-            const float nzs = clampf(ss + ys[j] / ri, lo[2][j], hi[2][j]);
+            const float ss = rs[j] - (mu[j] - mu_n) * iri;
+            const float nzc = clampf(cc + yc[j] * iri, lo[0][j], hi[0][j]);
+            const float nzd = clampf(dd_ + yd[j] * iri, lo[1][j], hi[1][j]);
+            const float nzs = clampf(ss + ys[j] * iri, lo[2][j], hi[2][j]);
             yc[j] += ri * (cc - nzc);
             yd[j] += ri * (dd_ - nzd);
             ys[j] += ri * (ss - nzs);
@@ -538,9 +538,16 @@ __global__ void __launch_bounds__(kBlock) k_bus(const Ctx c, int want_res) {
 //            (scale = |L|_2 forward, |x|_2 adjoint)
 //   dual   = sqrt(rho^2 |z^k - z^{k-1}|^2 + sum_j (rho_th_j dthbar / beta_j)^2) / |rho u|_2
 // ------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kBlock) k_reduce(const Ctx c, int adj, int it, double tol, int final_) {
+// Advance the loop's device iteration counter by one chunk (one thread).
+__global__ void k_tick(int* ctr, int chunk) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *ctr += chunk;
+}
+
+__global__ void __launch_bounds__(kBlock) k_reduce(const Ctx c, int adj, double tol) {
     const int s = blockIdx.x;
     if (c.done[s]) return;
+    const int it = *c.iter_ctr;
+    const int final_ = it >= c.max_it;
     const ScenDev sc = c.scen[s];
     double a[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (int b = threadIdx.x; b < sc.bus_nblk; b += kBlock) {
@@ -814,10 +821,22 @@ int launch_line(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st) 
     return 1;
 }
 
+#define GX_DISPATCH_MODE_BS(KERNEL, GRID, BS, ...)                                        \
+    do {                                                                                    \
+        if (adj) {                                                                          \
+            if (mode == M_ADJ) KERNEL<M_ADJ, 1><<<GRID, BS, 0, st>>>(__VA_ARGS__);           \
+            else if (mode == M_RESET) KERNEL<M_RESET, 1><<<GRID, BS, 0, st>>>(__VA_ARGS__);  \
+        } else {                                                                            \
+            if (mode == M_FWD) KERNEL<M_FWD, 0><<<GRID, BS, 0, st>>>(__VA_ARGS__);           \
+            else if (mode == M_RESET) KERNEL<M_RESET, 0><<<GRID, BS, 0, st>>>(__VA_ARGS__);  \
+            else if (mode == M_MASK) KERNEL<M_MASK, 0><<<GRID, BS, 0, st>>>(__VA_ARGS__);    \
+        }                                                                                   \
+    } while (0)
+
 int launch_bat(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st) {
     if (mode == M_INIT || c.n_bat_warps <= 0) return 0;
     const int grid = (c.n_bat_warps + kBatWarps - 1) / kBatWarps;
-    GX_DISPATCH_MODE(k_bat, grid, c, want_res);
+    GX_DISPATCH_MODE_BS(k_bat, grid, kBatWarps * 32, c, want_res);
     return 1;
 }
 
@@ -831,8 +850,13 @@ int launch_bus(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st) {
     return 1;
 }
 
-int launch_reduce(const Ctx& c, int adj, int it, double tol, int final_, cudaStream_t st) {
-    k_reduce<<<c.S, kBlock, 0, st>>>(c, adj, it, tol, final_);
+int launch_reduce(const Ctx& c, int adj, double tol, cudaStream_t st) {
+    k_reduce<<<c.S, kBlock, 0, st>>>(c, adj, tol);
+    return 1;
+}
+
+int launch_tick(const Ctx& c, int chunk, cudaStream_t st) {
+    k_tick<<<1, 32, 0, st>>>(c.iter_ctr, chunk);
     return 1;
 }
 

@@ -82,6 +82,7 @@ _SIGS = {
     "gx_dispatch_grad_batch": (C.c_int, [_vp, _vp, C.c_int, _vp, C.POINTER(Stats), _vp]),
     "gx_plan_step": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, C.c_float, _vp]),
     "gx_profile_enable": (C.c_int, [_vp, C.c_int]),
+    "gx_network_use_graphs": (C.c_int, [_vp, C.c_int]),
     "gx_profile_read": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
     "gx_dispatch_cost_noalloc": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp]),
 }
@@ -184,6 +185,7 @@ class Network:
         _check(_lib.gx_network_bind(h, C.c_void_p(base + self._off0), C.c_size_t(self.nbytes),
                                     _stream_handle(None)), "gx_network_bind", False)
         self.info = [self.scenario_info(s) for s in range(self.S)]
+        self.weights = np.array([float(sc["weight"]) for sc in scens])
         self.eta_offsets = []
         off = 0
         for n in nets:
@@ -260,6 +262,10 @@ class Network:
         self.last_grad_stats = st.asdict()
         self.last_grad_status = rc
         return out
+
+    def use_graphs(self, on=True):
+        """Replay residual-check chunks as CUDA graphs (default) or launch kernel by kernel."""
+        _check(_lib.gx_network_use_graphs(self._h, int(bool(on))), "gx_network_use_graphs", False)
 
     def profile(self, on=True):
         """Sampled CUDA-event timing of the bus / line / battery kernels (see gx_profile_enable)."""

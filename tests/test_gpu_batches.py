@@ -136,3 +136,19 @@ def test_medium_full_size_properties():
     fd = (vals[0] - vals[1]) / 2.0
     lin = float(np.dot(g.double().cpu().numpy(), d))
     assert abs(fd - lin) <= 2e-2 * abs(fd), (fd, lin)
+
+
+def test_graph_replay_matches_eager_launches_bitwise():
+    """Chunks replayed as CUDA graphs run the same kernels in the same order."""
+    nets, scens = synth.tiny()
+    e = eta_tensor(nets[0]["eta_min"])
+    out = []
+    for graphs in (True, False):
+        net = gpu_net(nets, scens, kappa=50.0, tol=1e-5, adj_tol=1e-4, max_iter=50000, adj_max_iter=50000)
+        net.use_graphs(graphs)
+        assert net.solve(e) == 0
+        g = net.grad(e).cpu().numpy().copy()
+        out.append((net.array("p", 0).cpu().numpy().copy(), g, net.last_stats["iters_max"]))
+    assert out[0][2] == out[1][2]
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
