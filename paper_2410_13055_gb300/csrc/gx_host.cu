@@ -93,7 +93,8 @@ struct gx_network {
         cudaGraphExec_t exec = nullptr;
     } graphs[4];
     int graph_next = 0;
-    cudaStream_t cap_stream = nullptr;
+    cudaStream_t cap_stream = nullptr, cap_stream2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int* h_nact = nullptr;  // pinned host copy of the active-scenario count
     bool use_graphs = true;
     void drop_graphs() {
@@ -112,6 +113,9 @@ struct gx_network {
             if (e) cudaEventDestroy(e);
         drop_graphs();
         if (cap_stream) cudaStreamDestroy(cap_stream);
+        if (cap_stream2) cudaStreamDestroy(cap_stream2);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
         if (h_nact) cudaFreeHost(h_nact);
     }
 };
@@ -208,6 +212,10 @@ static void make_ctx(gx_network* net) {
     a.rth_c = (float)(o.adj_rho * o.rho_theta_c);
     a.bat_dd = F(net->o_add);
     a.max_it = o.adj_max_iter;
+    a.rho_ratio = (float)(o.rho / o.adj_rho);
+    a.adj_from_fwd = 1;
+    c.rho_ratio = 1.f;
+    c.adj_from_fwd = 0;
     net->drop_graphs();
 }
 
@@ -556,6 +564,9 @@ gx_status gx_network_bind(gx_network* net, void* dev_mem, size_t bytes, void* st
     net->dd_dirty = false;
     if (!net->h_nact) GX_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&net->h_nact), sizeof(int), cudaHostAllocDefault));
     if (!net->cap_stream) GX_CUDA(cudaStreamCreateWithFlags(&net->cap_stream, cudaStreamNonBlocking));
+    if (!net->cap_stream2) GX_CUDA(cudaStreamCreateWithFlags(&net->cap_stream2, cudaStreamNonBlocking));
+    if (!net->ev_fork) GX_CUDA(cudaEventCreateWithFlags(&net->ev_fork, cudaEventDisableTiming));
+    if (!net->ev_join) GX_CUDA(cudaEventCreateWithFlags(&net->ev_join, cudaEventDisableTiming));
     make_ctx(net);
     net->solved = false;
     net->adj_ready = false;
@@ -620,33 +631,51 @@ gx_status gx_network_scenario_info(const gx_network* net, int s, int* T, int* Tp
     return GX_OK;
 }
 
-// One residual-check chunk: `chunk` iterations (residual partials on the last one), the
-// counter tick, the per-scenario reduction and the copy of the active count to the host.
-static gx_status enqueue_chunk(gx_network* net, const Ctx& c, int adj, int chunk, bool prof, cudaStream_t st,
-                               int* launches) {
+// Part of one residual-check chunk: iterations [j0, j1) of `chunk` (residual partials on
+// the chunk's last iteration), optionally preceded by the counter tick and followed by the
+// per-scenario reduction and the copy of the active count to the host.  With `prof` the
+// chunk's last iteration is bracketed by timing events (eager launches only).
+static gx_status enqueue_iters(gx_network* net, const Ctx& c, int adj, int chunk, int j0, int j1, bool tick,
+                               bool reduce, bool prof, cudaStream_t st, int* launches) {
     const int mode = adj ? M_ADJ : M_FWD;
     const double tol = adj ? net->opts.adj_tol : net->opts.tol;
-    *launches += launch_tick(c, chunk, st);
-    for (int j = 0; j < chunk; ++j) {
+    if (tick) *launches += launch_tick(c, chunk, st);
+    // While capturing, the line and battery proxes are two branches of the graph: they
+    // are independent and both feed the bus kernel.
+    const bool fork = (st == net->cap_stream) && c.n_bat_warps > 0 && c.n_line_blk > 0;
+    for (int j = j0; j < j1; ++j) {
         const int want = j == chunk - 1;
         const bool samp = prof && want;
-        if (samp) GX_CUDA(cudaEventRecord(net->ev[0], st));
-        const int nl = launch_line(c, mode, adj, want, st);
-        if (samp) GX_CUDA(cudaEventRecord(net->ev[1], st));
-        const int nb = launch_bat(c, mode, adj, want, st);
-        if (samp) GX_CUDA(cudaEventRecord(net->ev[2], st));
+        int nl = 0, nb = 0;
+        if (fork) {
+            GX_CUDA(cudaEventRecord(net->ev_fork, st));
+            GX_CUDA(cudaStreamWaitEvent(net->cap_stream2, net->ev_fork, 0));
+            nb = launch_bat(c, mode, adj, want, net->cap_stream2);
+            GX_CUDA(cudaEventRecord(net->ev_join, net->cap_stream2));
+            nl = launch_line(c, mode, adj, want, st);
+            GX_CUDA(cudaStreamWaitEvent(st, net->ev_join, 0));
+        } else {
+            if (samp) GX_CUDA(cudaEventRecord(net->ev[0], st));
+            nl = launch_line(c, mode, adj, want, st);
+            if (samp) GX_CUDA(cudaEventRecord(net->ev[1], st));
+            nb = launch_bat(c, mode, adj, want, st);
+            if (samp) GX_CUDA(cudaEventRecord(net->ev[2], st));
+        }
         const int nu = launch_bus(c, mode, adj, want, st);
         if (samp) GX_CUDA(cudaEventRecord(net->ev[3], st));
         *launches += nl + nb + nu;
     }
-    GX_CUDA(cudaMemsetAsync(c.n_active, 0, sizeof(int), st));
-    *launches += launch_reduce(c, adj, tol, st);
-    GX_CUDA(cudaMemcpyAsync(net->h_nact, c.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (reduce) {
+        GX_CUDA(cudaMemsetAsync(c.n_active, 0, sizeof(int), st));
+        *launches += launch_reduce(c, adj, tol, st);
+        GX_CUDA(cudaMemcpyAsync(net->h_nact, c.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+    }
     return GX_OK;
 }
 
-// The instantiated graph of a full chunk for (adj, chunk, prof, eta), captured on the
-// library's own stream (capture is not allowed on the legacy default stream).
+// The instantiated graph of a chunk (all of it, or all but its last iteration when the
+// kernels are being timed), captured on the library's own stream (capture is not allowed
+// on the legacy default stream).  Cached by everything its parameters depend on.
 static gx_status chunk_graph(gx_network* net, const Ctx& c, int adj, int chunk, bool prof, cudaGraphExec_t* out) {
     for (auto& g : net->graphs)
         if (g.valid && g.adj == adj && g.chunk == chunk && g.prof == (int)prof && g.eta == c.eta) {
@@ -660,7 +689,8 @@ static gx_status chunk_graph(gx_network* net, const Ctx& c, int adj, int chunk, 
     cudaGraph_t graph = nullptr;
     int dummy = 0;
     GX_CUDA(cudaStreamBeginCapture(net->cap_stream, cudaStreamCaptureModeThreadLocal));
-    gx_status e = enqueue_chunk(net, c, adj, chunk, prof, net->cap_stream, &dummy);
+    gx_status e = prof ? enqueue_iters(net, c, adj, chunk, 0, chunk - 1, true, false, false, net->cap_stream, &dummy)
+                       : enqueue_iters(net, c, adj, chunk, 0, chunk, true, true, false, net->cap_stream, &dummy);
     cudaError_t ce = cudaStreamEndCapture(net->cap_stream, &graph);
     if (e) return e;
     if (ce != cudaSuccess) return fail(GX_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(ce));
@@ -676,25 +706,33 @@ static gx_status chunk_graph(gx_network* net, const Ctx& c, int adj, int chunk, 
 // Iterate the forward (adj = 0) or adjoint (adj = 1) message passing until every
 // scenario of the batch meets its tolerance or the cap is reached.  Each chunk of
 // check_every iterations is replayed as one CUDA graph; the stream is synchronised
-// once per chunk to read the number of scenarios still iterating.
+// once per chunk to read the number of scenarios still iterating.  While kernels are
+// being timed, a chunk's last iteration and its reduction run as eager launches
+// bracketed by events (event times cannot be read from graph-recorded events).
 static gx_status run_loop(gx_network* net, int adj, cudaStream_t st, int* launches, int* iters_out) {
     const Ctx& c = adj ? net->actx : net->ctx;
     const int max_it = adj ? net->opts.adj_max_iter : net->opts.max_iter;
     const int every = net->opts.check_every;
     const bool prof = net->prof;
+    const int per_it = (c.n_line_blk > 0) + (c.n_bat_warps > 0) + (c.n_bus_blk > 0);
     int it = 0;
     GX_CUDA(cudaMemsetAsync(c.iter_ctr, 0, sizeof(int), st));
     while (it < max_it) {
         const int chunk = std::min(every, max_it - it);
         int nk = 0;
-        if (net->use_graphs && chunk == every) {
+        if (net->use_graphs && chunk == every && (!prof || chunk > 1)) {
             cudaGraphExec_t exec = nullptr;
             if (gx_status e = chunk_graph(net, c, adj, chunk, prof, &exec)) return e;
             GX_CUDA(cudaGraphLaunch(exec, st));
-            // count the kernels of the replayed chunk
-            nk = 2 + chunk * ((c.n_line_blk > 0) + (c.n_bat_warps > 0) + (c.n_bus_blk > 0));
+            if (prof) {
+                nk = 1 + (chunk - 1) * per_it;
+                if (gx_status e = enqueue_iters(net, c, adj, chunk, chunk - 1, chunk, false, true, true, st, &nk))
+                    return e;
+            } else {
+                nk = 2 + chunk * per_it;
+            }
         } else {
-            if (gx_status e = enqueue_chunk(net, c, adj, chunk, prof, st, &nk)) return e;
+            if (gx_status e = enqueue_iters(net, c, adj, chunk, 0, chunk, true, true, prof, st, &nk)) return e;
         }
         *launches += nk;
         if (prof) {

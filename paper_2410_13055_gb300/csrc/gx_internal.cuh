@@ -52,6 +52,8 @@ struct Ctx {
     // options
     float rho, eps, voll, kappa, rho_in, rth_c;  // rth_c = rho * rho_theta_c
     float tol_act;
+    float rho_ratio;     // adjoint context: forward rho / adjoint rho (scaled-dual conversion)
+    int adj_from_fwd;    // adjoint RESET starts from the negated forward duals
     int inner_iters;
     int check_every;
     int max_it;          // iteration cap of the loop this context drives

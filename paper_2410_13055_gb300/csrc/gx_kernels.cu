@@ -105,6 +105,12 @@ __global__ void __launch_bounds__(kBlock) k_line(const Ctx c, int want_res) {
                 q0f = th[bf];
                 q0t = th[bt];
             }
+            if (ADJ && c.adj_from_fwd) {
+                // h = c part of the adjoint: phase duals are the negated forward ones
+                // (scaled duals convert with rho_f / rho_a); adjoint phases start at 0
+                q0f = -c.rho_ratio * (c.vf[row] - c.thb[bf]);
+                q0t = -c.rho_ratio * (c.vt[row] - c.thb[bt]);
+            }
             X.dl[row] = d0; X.sg[row] = g0; X.vf[row] = q0f; X.vt[row] = q0t;
         } else {
             // Phase consensus in exact ADMM form: the line keeps q_j = y_j + v_j (terminal
@@ -188,10 +194,14 @@ __global__ void __launch_bounds__(kBatWarps * 32) k_bat(const Ctx c, int want_re
     const long long brow0 = sc.e_bus + (long long)c.b_bus[bg] * sc.Tp;
 
     if (MODE == M_RESET) {
+        const bool neg = ADJ && c.adj_from_fwd;
         for (int t = lane; t < sc.Tp; t += 32) {
             const long long r = row0 + t;
             X.xb[r] = 0.f; X.zc[r] = 0.f; X.zd[r] = 0.f; X.zs[r] = 0.f;
-            X.yc[r] = 0.f; X.yd[r] = 0.f; X.ys[r] = 0.f;
+            // h = c part of the adjoint: box multipliers are the negated forward ones
+            X.yc[r] = neg ? -c.yc[r] : 0.f;
+            X.yd[r] = neg ? -c.yd[r] : 0.f;
+            X.ys[r] = neg ? -c.ys[r] : 0.f;
         }
         return;
     }
@@ -403,7 +413,8 @@ __global__ void __launch_bounds__(kBlock) k_bus(const Ctx c, int want_res) {
         if (MODE == M_RESET) {
             const float Lnt = c.load[i];
             X.xl[i] = ADJ ? 0.f : -Lnt;
-            X.u[i] = (!ADJ && c.warm) ? -c.warm[i] / rho : 0.f;
+            if (ADJ) X.u[i] = c.adj_from_fwd ? -c.rho_ratio * c.u[i] : 0.f;
+            else X.u[i] = c.warm ? -c.warm[i] / rho : 0.f;
             X.pbar[i] = 0.f;
             X.thb[i] = (!ADJ && c.warm) ? c.warm[c.warm_half + i] : 0.f;
             for (int q = c.bus_gptr[nb]; q < c.bus_gptr[nb + 1]; ++q) {

@@ -82,7 +82,7 @@ def test_medium_slice_parity():
     nets, scens = synth.medium(S=1)
     nets, scens = synth.slice_hours(nets, scens, 0, 24)
     eta = nets[0]["eta_min"]
-    net, e, rc, refs = _solve_pair(nets, scens, eta, kappa=50.0, tol=1e-5, adj_tol=1e-5)
+    net, e, rc, refs = _solve_pair(nets, scens, eta, kappa=50.0, tol=1e-6, adj_tol=1e-5)
     ref = refs[0]
     g = solution(net, 0, ref_groups(ref.qp))
     assert abs(g["cost"] - ref.cost) / ref.cost <= 1e-4
