@@ -141,6 +141,23 @@ def algorithmic_bytes(nets, scens):
     return tot
 
 
+# DRAM bytes (read + write) per launch from one ncu capture of the solver kernels on the
+# 100-bus network with 64 scenarios (profiles/solver_kernels_medium64_full.md); valid only
+# while gx_kernels.cu is the source that was profiled.
+PROFILED = {"sha256_prefix": "1b17609d60880f7a", "scenarios": 64, "config": "medium",
+            "source": "profiles/solver_kernels_medium64_full.md",
+            "traffic": {"k_bus": 65.710848e6, "k_line": 38.754304e6, "k_bat": 21.126912e6}}
+
+
+def profiled_traffic(config, n_scen, kernel):
+    import hashlib
+    src = os.path.join(ROOT, "paper_2410_13055_gb300", "csrc", "gx_kernels.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if sha != PROFILED["sha256_prefix"] or config != PROFILED["config"] or kernel not in PROFILED["traffic"]:
+        return None
+    return PROFILED["traffic"][kernel] * n_scen / PROFILED["scenarios"]
+
+
 def run_gx(args):
     import torch
     ws, rank = _dist()
@@ -255,8 +272,11 @@ def run_gx(args):
         if dom:
             avg_ms = kinds[dom]["ms"] / kinds[dom]["samples"]
             achieved = ab[dom] / (avg_ms / 1e3) / 1e9
+            tr = profiled_traffic(args.config, len(scens), dom)
             roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                    "frac": round(achieved / peak, 4), "traffic": None,
+                    "frac": round(achieved / peak, 4), "traffic": tr,
+                    "traffic_note": (f"ncu dram read+write per launch, scaled by scenarios from {PROFILED['source']}"
+                                     if tr is not None else "kernel changed since the ncu capture"),
                     "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
                     "bytes_per_launch": ab[dom], "avg_launch_us": round(avg_ms * 1e3, 2),
                     "kernels": {k: {"avg_launch_us": round(v["ms"] / v["samples"] * 1e3, 2),

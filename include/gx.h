@@ -216,6 +216,36 @@ gx_status gx_profile_enable(gx_network* net, int on);
  * were sampled; launches[k]: all launches of kind k since enabling. */
 gx_status gx_profile_read(const gx_network* net, double* ms, long long* samples, long long* launches);
 
+/* ------------------------------------------------------------------------------
+ * Learned warm start (not in the paper): a 3-layer message-passing network over the
+ * bus-hour graph of a bound network (node (n, t) linked to (m, t) when a line joins
+ * n and m; hidden width 64; BF16 tensor-core layers with FP32 accumulation) maps
+ * plan-derived node features to nodal prices and angles.  Its predictions, in the
+ * layout of GX_WARM_USER ([sum_s N_s Tp_s] prices then the same size of angles), warm
+ * start gx_dispatch_solve_batch.  Parameters: FP32 master copy of gx_gnn_num_params()
+ * floats (layout documented in paper_2410_13055_gb300/csrc/gx_gnn.cu); the device
+ * workspace is caller-allocated like the network's.
+ * ------------------------------------------------------------------------------ */
+typedef struct gx_gnn gx_gnn;
+size_t gx_gnn_num_params(void);
+/* hidden must be 64, layers 3.  The network must be bound and outlive the gx_gnn. */
+gx_status gx_gnn_create(const gx_network* net, int hidden, int layers, gx_gnn** out);
+size_t gx_gnn_device_bytes(const gx_gnn* gnn);
+/* Zero the workspace and initialise the parameters from `seed` (synchronises `stream`). */
+gx_status gx_gnn_bind(gx_gnn* gnn, void* dev_mem, size_t bytes, uint64_t seed, void* stream);
+gx_status gx_gnn_set_params(gx_gnn* gnn, const float* host_params, size_t n, void* stream);
+/* which = 0: parameters, 1: gradients of the last gx_gnn_train_step (synchronises). */
+gx_status gx_gnn_get_params(const gx_gnn* gnn, float* host_out, size_t n, int which, void* stream);
+/* Predicted prices ($/MWh) and angles (rad) at plan eta_dev into out_dev [2 * bus rows]. */
+gx_status gx_gnn_predict(gx_gnn* gnn, const float* eta_dev, float* out_dev, void* stream);
+/* One Adam step (lr > 0; lr = 0 only computes gradients) on the mean squared error
+ * against target_dev (same layout as out_dev; prices compared in $/100 MWh units,
+ * angles weighted by w_theta); padding hours are excluded.  loss_host (nullable)
+ * receives the loss before the step (synchronises). */
+gx_status gx_gnn_train_step(gx_gnn* gnn, const float* eta_dev, const float* target_dev, float lr, float w_theta,
+                            double* loss_host, void* stream);
+gx_status gx_gnn_destroy(gx_gnn* gnn);
+
 /* Operating cost c_s and planner value h_s of scenario `scen` at the last solve,
  * computed without allocating any device memory.  The paper has no counterpart; this
  * entry point exists for callers that cannot allocate device memory (code running

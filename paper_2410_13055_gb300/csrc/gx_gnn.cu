@@ -1,0 +1,623 @@
+// Warm-start graph network: node features, BF16 tensor-core layers with FP32
+// accumulation, neighbour aggregation, loss, backward and Adam, all on the GPU.
+//
+// Nodes are the bus-hour rows of a bound gx_network (scenario-major, bus-major, hour
+// contiguous: the layout of the nodal price and angle arrays), so a prediction is
+// directly a user warm start of gx_dispatch_solve_batch.  With F input features
+// (10 used, padded to 16), hidden width 64 and 3 layers:
+//
+//   h0 = relu(x W_in + b_in)
+//   h_k = h_{k-1} + relu([h_{k-1}, mean_{m in N(n)} h_{k-1,m}] W_k + b_k)
+//   y = h_3 W_out + b_out,   y0 ~ price / 100, y1 ~ angle
+//
+// GEMMs use mma.sync.m16n8k16 with BF16 operands (activations converted on load,
+// weights kept as BF16 copies of FP32 master parameters) and FP32 accumulators.
+#include "gx_internal.cuh"
+
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+#include <random>
+#include <string>
+#include <vector>
+
+namespace gx {
+
+constexpr int kH = 64;
+constexpr int kLayers = 3;
+constexpr int kFin = 16;
+constexpr int kFused = 10;
+// parameter vector layout (FP32 master copy)
+constexpr int kOffWin = 0;                        // [kFin][kH]
+constexpr int kOffBin = kOffWin + kFin * kH;      // [kH]
+constexpr int kLayerSz = 2 * kH * kH + kH;        // W_k [2H][H] + b_k [H]
+constexpr int kOffL0 = kOffBin + kH;
+constexpr int kOffWout = kOffL0 + kLayers * kLayerSz;  // [kH][2]
+constexpr int kOffBout = kOffWout + kH * 2;            // [2]
+constexpr int kNParam = kOffBout + 2;
+
+namespace {
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ int scen_of_row(const ScenDev* sc, int S, long long row) {
+    int lo = 0, hi = S - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (sc[mid].e_bus <= row) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------- features
+__global__ void k_features(const Ctx c, const float* __restrict__ eta, float* __restrict__ X, long long M) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    const int s = scen_of_row(c.scen, c.S, i);
+    const ScenDev sc = c.scen[s];
+    const long long loc = i - sc.e_bus;
+    const int n = (int)(loc / sc.Tp), t = (int)(loc - (long long)n * sc.Tp);
+    float f[kFin];
+#pragma unroll
+    for (int k = 0; k < kFin; ++k) f[k] = 0.f;
+    if (t < sc.T) {
+        const int nb = sc.ptr0 + n;
+        float avail = 0.f, costw = 0.f, freec = 0.f, dear = 0.f;
+        for (int q = c.bus_gptr[nb]; q < c.bus_gptr[nb + 1]; ++q) {
+            const int g = c.bus_gidx[sc.gen0 + q];
+            const float cap = c.cf[sc.e_gen + (long long)g * sc.Tp + t] * fmaxf(eta[sc.eta0 + g], 0.f);
+            const float cost = c.g_cost[sc.gen0 + g];
+            avail += cap;
+            if (cost == 0.f) freec += cap;
+            else { dear += cap; costw += cap * cost; }
+        }
+        float bat = 0.f;
+        for (int q = c.bus_bptr[nb]; q < c.bus_bptr[nb + 1]; ++q)
+            bat += fmaxf(eta[sc.eta0 + sc.G + sc.L + c.bus_bidx[sc.bat0 + q]], 0.f);
+        float lin = 0.f;
+        for (int q = c.bus_eptr[nb]; q < c.bus_eptr[nb + 1]; ++q)
+            lin += fmaxf(eta[sc.eta0 + sc.G + (c.bus_eidx[2 * sc.line0 + q] >> 1)], 0.f);
+        const float L = c.load[i];
+        const float h = (float)(t % 24);
+        f[0] = L * 0.01f;
+        f[1] = avail * 0.01f;
+        f[2] = dear > 0.f ? costw / dear * 0.01f : 0.f;
+        f[3] = freec * 0.01f;
+        f[4] = bat * 0.01f;
+        f[5] = lin * 0.01f;
+        f[6] = sinf(6.283185307179586f * h / 24.f);
+        f[7] = cosf(6.283185307179586f * h / 24.f);
+        f[8] = (L - freec) * 0.01f;
+        f[9] = 1.f;
+    }
+    float4* o = reinterpret_cast<float4*>(X + i * kFin);
+#pragma unroll
+    for (int k = 0; k < kFin / 4; ++k) o[k] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
+}
+
+// ---------------------------------------------------------------- dense layers
+// Z = A Bt^T (+ bias); H = (resid +) relu(Z).  A: [M][K] FP32, split at K1 between two
+// row-major arrays (concatenation [A1, A2] without materialising it); Bt: [N][K] BF16.
+// One warp computes 16 rows x N columns; a block has 4 warps (64 rows).
+template <int K, int N>
+__global__ void __launch_bounds__(128) k_gemm_fwd(const float* __restrict__ A1, const float* __restrict__ A2, int K1,
+                                                  const __nv_bfloat16* __restrict__ Bt, const float* __restrict__ bias,
+                                                  const float* __restrict__ resid, float* __restrict__ Z,
+                                                  float* __restrict__ H, long long M, int relu) {
+    __shared__ __align__(16) __nv_bfloat16 sB[N * K];
+    for (int i = threadIdx.x; i < N * K / 8; i += blockDim.x)
+        reinterpret_cast<uint4*>(sB)[i] = reinterpret_cast<const uint4*>(Bt)[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, q = lane & 3;
+    const long long row0 = ((long long)blockIdx.x * 4 + warp) * 16;
+    if (row0 >= M) return;
+    const int K2 = K - K1;
+    auto Aat = [&](long long r, int k) -> float {
+        if (r >= M) return 0.f;
+        return k < K1 ? A1[r * K1 + k] : A2[r * K2 + (k - K1)];
+    };
+    float acc[N / 8][4];
+#pragma unroll
+    for (int j = 0; j < N / 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+#pragma unroll
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        uint32_t a[4];
+        const long long r0 = row0 + g, r1 = row0 + g + 8;
+        const int c0 = k0 + 2 * q, c1 = k0 + 2 * q + 8;
+        a[0] = pack_bf16(Aat(r0, c0), Aat(r0, c0 + 1));
+        a[1] = pack_bf16(Aat(r1, c0), Aat(r1, c0 + 1));
+        a[2] = pack_bf16(Aat(r0, c1), Aat(r0, c1 + 1));
+        a[3] = pack_bf16(Aat(r1, c1), Aat(r1, c1 + 1));
+#pragma unroll
+        for (int j = 0; j < N / 8; ++j) {
+            const __nv_bfloat16* bp = sB + (j * 8 + g) * K + k0 + 2 * q;
+            const uint32_t b0 = *reinterpret_cast<const uint32_t*>(bp);
+            const uint32_t b1 = *reinterpret_cast<const uint32_t*>(bp + 8);
+            mma_bf16(acc[j], a, b0, b1);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < N / 8; ++j) {
+        const int col = j * 8 + 2 * q;
+#pragma unroll
+        for (int hlf = 0; hlf < 2; ++hlf) {
+            const long long r = row0 + g + 8 * hlf;
+            if (r >= M) continue;
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                float z = acc[j][2 * hlf + e] + (bias ? bias[col + e] : 0.f);
+                if (Z) Z[r * N + col + e] = z;
+                if (H) {
+                    float hv = relu ? fmaxf(z, 0.f) : z;
+                    if (resid) hv += resid[r * N + col + e];
+                    H[r * N + col + e] = hv;
+                }
+            }
+        }
+    }
+}
+
+// dW[K][N] += A^T dZ over all rows (A = [A1, A2] split at K1, dZ: [M][N]).  Warp w owns
+// dW rows 16w..16w+15; the block reduces a chunk of kChunk rows with mma and adds its
+// partial into dW with atomics.
+constexpr int kChunk = 256;
+template <int K, int N>
+__global__ void k_gemm_wgrad(const float* __restrict__ A1, const float* __restrict__ A2, int K1,
+                             const float* __restrict__ dZ, long long M, float* __restrict__ dW) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, q = lane & 3;
+    const int K2 = K - K1;
+    const int kk0 = warp * 16;
+    auto Aat = [&](long long r, int k) -> float {
+        if (r >= M) return 0.f;
+        return k < K1 ? A1[r * K1 + k] : A2[r * K2 + (k - K1)];
+    };
+    auto Dat = [&](long long r, int n) -> float { return r < M ? dZ[r * N + n] : 0.f; };
+    float acc[N / 8][4];
+#pragma unroll
+    for (int j = 0; j < N / 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+    const long long m_begin = (long long)blockIdx.x * kChunk;
+    for (long long m0 = m_begin; m0 < m_begin + kChunk && m0 < M; m0 += 16) {
+        // A operand: rows = kk (16 of this warp), cols = m (reduction)
+        uint32_t a[4];
+        const long long mc0 = m0 + 2 * q, mc1 = m0 + 2 * q + 8;
+        a[0] = pack_bf16(Aat(mc0, kk0 + g), Aat(mc0 + 1, kk0 + g));
+        a[1] = pack_bf16(Aat(mc0, kk0 + g + 8), Aat(mc0 + 1, kk0 + g + 8));
+        a[2] = pack_bf16(Aat(mc1, kk0 + g), Aat(mc1 + 1, kk0 + g));
+        a[3] = pack_bf16(Aat(mc1, kk0 + g + 8), Aat(mc1 + 1, kk0 + g + 8));
+#pragma unroll
+        for (int j = 0; j < N / 8; ++j) {
+            const int n = j * 8 + g;
+            const uint32_t b0 = pack_bf16(Dat(mc0, n), Dat(mc0 + 1, n));
+            const uint32_t b1 = pack_bf16(Dat(mc1, n), Dat(mc1 + 1, n));
+            mma_bf16(acc[j], a, b0, b1);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < N / 8; ++j) {
+        const int col = j * 8 + 2 * q;
+        atomicAdd(&dW[(kk0 + g) * N + col], acc[j][0]);
+        atomicAdd(&dW[(kk0 + g) * N + col + 1], acc[j][1]);
+        atomicAdd(&dW[(kk0 + g + 8) * N + col], acc[j][2]);
+        atomicAdd(&dW[(kk0 + g + 8) * N + col + 1], acc[j][3]);
+    }
+}
+
+// column sums of dZ [M][N] into db[N] (FP32 atomics per block)
+template <int N>
+__global__ void k_colsum(const float* __restrict__ dZ, long long M, float* __restrict__ db) {
+    __shared__ float sh[N];
+    for (int i = threadIdx.x; i < N; i += blockDim.x) sh[i] = 0.f;
+    __syncthreads();
+    const long long r0 = (long long)blockIdx.x * kChunk;
+    for (long long r = r0 + threadIdx.x / N; r < r0 + kChunk && r < M; r += blockDim.x / N)
+        atomicAdd(&sh[threadIdx.x % N], dZ[r * N + threadIdx.x % N]);
+    __syncthreads();
+    for (int i = threadIdx.x; i < N; i += blockDim.x) atomicAdd(&db[i], sh[i]);
+}
+
+// ---------------------------------------------------------------- aggregation
+// out[i] = mean over neighbour buses m of in[(m, t)], or (transpose) out[i] += sum over
+// neighbours m of in[(m, t)] / deg(m).  One warp per node, two features per lane.
+template <int TRANSPOSE>
+__global__ void k_agg(const Ctx c, const float* __restrict__ in, float* __restrict__ out, long long M) {
+    const long long i = (long long)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    if (i >= M) return;
+    const int lane = threadIdx.x & 31;
+    const int s = scen_of_row(c.scen, c.S, i);
+    const ScenDev sc = c.scen[s];
+    const long long loc = i - sc.e_bus;
+    const int n = (int)(loc / sc.Tp), t = (int)(loc - (long long)n * sc.Tp);
+    const int nb = sc.ptr0 + n;
+    const int e0 = c.bus_eptr[nb], e1 = c.bus_eptr[nb + 1];
+    float a0 = 0.f, a1 = 0.f;
+    for (int qq = e0; qq < e1; ++qq) {
+        const int e = c.bus_eidx[2 * sc.line0 + qq];
+        const int l = e >> 1;
+        const int m = (e & 1) ? c.l_from[sc.line0 + l] : c.l_to[sc.line0 + l];
+        const long long j = sc.e_bus + (long long)m * sc.Tp + t;
+        float w = 1.f;
+        if (TRANSPOSE) {
+            const int mb = sc.ptr0 + m;
+            w = 1.f / (float)(c.bus_eptr[mb + 1] - c.bus_eptr[mb]);
+        }
+        const float2 v = reinterpret_cast<const float2*>(in + j * kH)[lane];
+        a0 += w * v.x;
+        a1 += w * v.y;
+    }
+    if (!TRANSPOSE) {
+        const float w = e1 > e0 ? 1.f / (float)(e1 - e0) : 0.f;
+        reinterpret_cast<float2*>(out + i * kH)[lane] = make_float2(a0 * w, a1 * w);
+    } else {
+        float2* o = reinterpret_cast<float2*>(out + i * kH) + lane;
+        const float2 prev = *o;
+        *o = make_float2(prev.x + a0, prev.y + a1);
+    }
+}
+
+// ---------------------------------------------------------------- head, loss, backward head
+__global__ void k_head(const float* __restrict__ H, const float* __restrict__ P, float* __restrict__ Y, long long M) {
+    const long long i = (long long)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    if (i >= M) return;
+    const int lane = threadIdx.x & 31;
+    const float2 h = reinterpret_cast<const float2*>(H + i * kH)[lane];
+    const float* W = P + kOffWout;
+    float y0 = h.x * W[(2 * lane) * 2 + 0] + h.y * W[(2 * lane + 1) * 2 + 0];
+    float y1 = h.x * W[(2 * lane) * 2 + 1] + h.y * W[(2 * lane + 1) * 2 + 1];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        y0 += __shfl_xor_sync(0xffffffffu, y0, o);
+        y1 += __shfl_xor_sync(0xffffffffu, y1, o);
+    }
+    if (lane == 0) {
+        Y[2 * i] = y0 + P[kOffBout];
+        Y[2 * i + 1] = y1 + P[kOffBout + 1];
+    }
+}
+
+// loss over valid nodes (hour < T); dY = d loss / d y; target layout [prices | angles]
+__global__ void k_loss(const Ctx c, const float* __restrict__ Y, const float* __restrict__ tgt, long long M,
+                       double inv_count, float w_theta, float* __restrict__ dY, double* __restrict__ loss) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double l = 0.0;
+    if (i < M) {
+        const int s = scen_of_row(c.scen, c.S, i);
+        const ScenDev sc = c.scen[s];
+        const long long loc = i - sc.e_bus;
+        const int t = (int)(loc % sc.Tp);
+        float d0 = 0.f, d1 = 0.f;
+        if (t < sc.T) {
+            d0 = Y[2 * i] - tgt[i] * 0.01f;
+            d1 = Y[2 * i + 1] - tgt[M + i];
+            l = (double)d0 * d0 + (double)w_theta * d1 * d1;
+        }
+        dY[2 * i] = (float)(2.0 * d0 * inv_count);
+        dY[2 * i + 1] = (float)(2.0 * w_theta * d1 * inv_count);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+    if ((threadIdx.x & 31) == 0 && l != 0.0) atomicAdd(loss, l * inv_count);
+}
+
+// dW_out += H^T dY, db_out += sum dY, dH = dY W_out^T
+__global__ void k_head_back(const float* __restrict__ H, const float* __restrict__ dY, const float* __restrict__ P,
+                            float* __restrict__ G, float* __restrict__ dH, long long M) {
+    const long long i = (long long)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    if (i >= M) return;
+    const int lane = threadIdx.x & 31;
+    const float2 h = reinterpret_cast<const float2*>(H + i * kH)[lane];
+    const float d0 = dY[2 * i], d1 = dY[2 * i + 1];
+    const float* W = P + kOffWout;
+    float* GW = G + kOffWout;
+    if (d0 != 0.f || d1 != 0.f) {
+        atomicAdd(&GW[(2 * lane) * 2 + 0], h.x * d0);
+        atomicAdd(&GW[(2 * lane) * 2 + 1], h.x * d1);
+        atomicAdd(&GW[(2 * lane + 1) * 2 + 0], h.y * d0);
+        atomicAdd(&GW[(2 * lane + 1) * 2 + 1], h.y * d1);
+        if (lane == 0) {
+            atomicAdd(&G[kOffBout], d0);
+            atomicAdd(&G[kOffBout + 1], d1);
+        }
+    }
+    reinterpret_cast<float2*>(dH + i * kH)[lane] =
+        make_float2(d0 * W[(2 * lane) * 2] + d1 * W[(2 * lane) * 2 + 1],
+                    d0 * W[(2 * lane + 1) * 2] + d1 * W[(2 * lane + 1) * 2 + 1]);
+}
+
+// dZ = dH * (Z > 0)
+__global__ void k_relu_back(const float* __restrict__ dH, const float* __restrict__ Z, float* __restrict__ dZ,
+                            long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dZ[i] = Z[i] > 0.f ? dH[i] : 0.f;
+}
+
+// dH[:, 0:64] += dCat[:, 0:64]  (dCat is [M][128])
+__global__ void k_add_half(float* __restrict__ dH, const float* __restrict__ dCat, long long M) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M * kH) return;
+    const long long r = i / kH;
+    const int k = (int)(i - r * kH);
+    dH[i] += dCat[r * 2 * kH + k];
+}
+
+// dAgg = dCat[:, 64:128] as a contiguous [M][64] array
+__global__ void k_take_half(const float* __restrict__ dCat, float* __restrict__ out, long long M) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M * kH) return;
+    const long long r = i / kH;
+    const int k = (int)(i - r * kH);
+    out[i] = dCat[r * 2 * kH + kH + k];
+}
+
+__global__ void k_adam(float* __restrict__ P, const float* __restrict__ G, float* __restrict__ m1,
+                       float* __restrict__ m2, int n, float lr, float b1, float b2, float eps, float c1, float c2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float g = G[i];
+    const float a = b1 * m1[i] + (1.f - b1) * g;
+    const float b = b2 * m2[i] + (1.f - b2) * g * g;
+    m1[i] = a;
+    m2[i] = b;
+    P[i] -= lr * (a / c1) / (sqrtf(b / c2) + eps);
+}
+
+// BF16 copies of the GEMM weights: W_in^T [H][Fin]; W_k^T [H][2H] (forward) and W_k [2H][H]
+// (backward: dCat = dZ W_k^T uses B^T = W_k as stored).
+__global__ void k_to_bf16(const float* __restrict__ P, __nv_bfloat16* __restrict__ win_t,
+                          __nv_bfloat16* __restrict__ wk_t, __nv_bfloat16* __restrict__ wk) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < kFin * kH) {
+        const int k = i / kH, n = i % kH;
+        win_t[n * kFin + k] = __float2bfloat16(P[kOffWin + i]);
+    }
+    if (i < kLayers * 2 * kH * kH) {
+        const int l = i / (2 * kH * kH), j = i % (2 * kH * kH);
+        const int k = j / kH, n = j % kH;
+        const float v = P[kOffL0 + l * kLayerSz + j];
+        wk_t[l * 2 * kH * kH + n * 2 * kH + k] = __float2bfloat16(v);
+        wk[l * 2 * kH * kH + k * kH + n] = __float2bfloat16(v);
+    }
+}
+
+// predictions in the warm-start layout: prices ($/MWh) then angles (rad)
+__global__ void k_unpack(const float* __restrict__ Y, float* __restrict__ out, long long M) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    out[i] = 100.f * Y[2 * i];
+    out[M + i] = Y[2 * i + 1];
+}
+
+}  // namespace
+}  // namespace gx
+
+using namespace gx;
+
+struct gx_gnn {
+    const gx_network* net = nullptr;
+    long long M = 0;
+    double valid = 0;  // nodes with hour < T
+    size_t bytes = 0;
+    uint8_t* dev = nullptr;
+    // offsets
+    size_t o_P, o_G, o_m1, o_m2, o_win_t, o_wk_t, o_wk, o_X, o_Z0, o_Hs, o_Zs, o_Agg, o_Y, o_dY, o_dH, o_dZ, o_dCat,
+        o_dAgg, o_loss;
+    int step = 0;
+};
+
+namespace {
+size_t lay_add(size_t& total, size_t bytes) {
+    const size_t o = total;
+    total += (bytes + 255) / 256 * 256;
+    return o;
+}
+}  // namespace
+
+extern "C" {
+
+size_t gx_gnn_num_params(void) { return (size_t)kNParam; }
+
+gx_status gx_gnn_create(const gx_network* net, int hidden, int layers, gx_gnn** out) {
+    if (!net || !out) return gx_internal_fail(GX_ERR_INVALID_ARG, "NULL argument");
+    if (hidden != kH || layers != kLayers)
+        return gx_internal_fail(GX_ERR_INVALID_ARG, "the warm-start network has hidden width 64 and 3 layers");
+    const Ctx* c = gx_internal_ctx(net);
+    if (!c) return gx_internal_fail(GX_ERR_STATE, "network is not bound");
+    gx_gnn* g = new gx_gnn();
+    g->net = net;
+    long long M = 0;
+    double valid = 0;
+    for (int s = 0; s < c->S; ++s) {
+        const ScenDev d = gx_internal_scen(net, s);
+        M += (long long)d.N * d.Tp;
+        valid += (double)d.N * d.T;
+    }
+    g->M = M;
+    g->valid = valid;
+    size_t t = 0;
+    const size_t P = (size_t)kNParam * 4;
+    g->o_P = lay_add(t, P); g->o_G = lay_add(t, P); g->o_m1 = lay_add(t, P); g->o_m2 = lay_add(t, P);
+    g->o_win_t = lay_add(t, 2 * kFin * kH);
+    g->o_wk_t = lay_add(t, 2 * (size_t)kLayers * 2 * kH * kH);
+    g->o_wk = lay_add(t, 2 * (size_t)kLayers * 2 * kH * kH);
+    g->o_X = lay_add(t, 4 * (size_t)M * kFin);
+    g->o_Z0 = lay_add(t, 4 * (size_t)M * kH);
+    g->o_Hs = lay_add(t, 4 * (size_t)M * kH * (kLayers + 1));
+    g->o_Zs = lay_add(t, 4 * (size_t)M * kH * kLayers);
+    g->o_Agg = lay_add(t, 4 * (size_t)M * kH * kLayers);
+    g->o_Y = lay_add(t, 4 * (size_t)M * 2);
+    g->o_dY = lay_add(t, 4 * (size_t)M * 2);
+    g->o_dH = lay_add(t, 4 * (size_t)M * kH);
+    g->o_dZ = lay_add(t, 4 * (size_t)M * kH);
+    g->o_dCat = lay_add(t, 4 * (size_t)M * 2 * kH);
+    g->o_dAgg = lay_add(t, 4 * (size_t)M * kH);
+    g->o_loss = lay_add(t, 8);
+    g->bytes = t;
+    *out = g;
+    return GX_OK;
+}
+
+size_t gx_gnn_device_bytes(const gx_gnn* g) { return g ? g->bytes : 0; }
+
+gx_status gx_gnn_destroy(gx_gnn* g) {
+    delete g;
+    return GX_OK;
+}
+
+static gx_status gnn_refresh_bf16(gx_gnn* g, cudaStream_t st) {
+    const int n = kLayers * 2 * kH * kH;
+    k_to_bf16<<<(n + 255) / 256, 256, 0, st>>>(reinterpret_cast<const float*>(g->dev + g->o_P),
+                                                reinterpret_cast<__nv_bfloat16*>(g->dev + g->o_win_t),
+                                                reinterpret_cast<__nv_bfloat16*>(g->dev + g->o_wk_t),
+                                                reinterpret_cast<__nv_bfloat16*>(g->dev + g->o_wk));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return gx_internal_fail(GX_ERR_CUDA, std::string("k_to_bf16: ") + cudaGetErrorString(e));
+    return GX_OK;
+}
+
+gx_status gx_gnn_set_params(gx_gnn* g, const float* host, size_t n, void* stream) {
+    if (!g || !g->dev || !host) return gx_internal_fail(GX_ERR_INVALID_ARG, "NULL argument or unbound network");
+    if (n != (size_t)kNParam) return gx_internal_fail(GX_ERR_INVALID_ARG, "parameter count mismatch");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(g->dev + g->o_P, host, 4 * n, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return gx_internal_fail(GX_ERR_CUDA, cudaGetErrorString(e));
+    return gnn_refresh_bf16(g, st);
+}
+
+gx_status gx_gnn_get_params(const gx_gnn* g, float* host, size_t n, int which, void* stream) {
+    if (!g || !g->dev || !host) return gx_internal_fail(GX_ERR_INVALID_ARG, "NULL argument or unbound network");
+    if (n != (size_t)kNParam) return gx_internal_fail(GX_ERR_INVALID_ARG, "parameter count mismatch");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(host, g->dev + (which ? g->o_G : g->o_P), 4 * n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return gx_internal_fail(GX_ERR_CUDA, cudaGetErrorString(e));
+    return GX_OK;
+}
+
+gx_status gx_gnn_bind(gx_gnn* g, void* dev, size_t bytes, uint64_t seed, void* stream) {
+    if (!g || !dev) return gx_internal_fail(GX_ERR_INVALID_ARG, "NULL argument");
+    if (reinterpret_cast<uintptr_t>(dev) % 256) return gx_internal_fail(GX_ERR_INVALID_ARG, "dev must be 256-byte aligned");
+    if (bytes < g->bytes) return gx_internal_fail(GX_ERR_NO_MEMORY, "GNN workspace too small");
+    g->dev = reinterpret_cast<uint8_t*>(dev);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(g->dev, 0, g->bytes, st);
+    if (e != cudaSuccess) return gx_internal_fail(GX_ERR_CUDA, cudaGetErrorString(e));
+    // He-style initialisation from a seeded host generator (biases 0)
+    std::vector<float> P(kNParam, 0.f);
+    std::mt19937_64 rng(seed);
+    std::normal_distribution<float> nd(0.f, 1.f);
+    for (int k = 0; k < kFused; ++k)
+        for (int n = 0; n < kH; ++n) P[kOffWin + k * kH + n] = nd(rng) * std::sqrt(2.f / kFused);
+    for (int l = 0; l < kLayers; ++l)
+        for (int j = 0; j < 2 * kH * kH; ++j) P[kOffL0 + l * kLayerSz + j] = nd(rng) * std::sqrt(1.f / (2 * kH));
+    for (int j = 0; j < kH * 2; ++j) P[kOffWout + j] = nd(rng) * std::sqrt(1.f / kH);
+    g->step = 0;
+    return gx_gnn_set_params(g, P.data(), P.size(), stream);
+}
+
+static void gnn_forward(gx_gnn* g, const float* eta, cudaStream_t st) {
+    const Ctx& c = *gx_internal_ctx(g->net);
+    const long long M = g->M;
+    auto F = [&](size_t o) { return reinterpret_cast<float*>(g->dev + o); };
+    auto B = [&](size_t o) { return reinterpret_cast<const __nv_bfloat16*>(g->dev + o); };
+    float* P = F(g->o_P);
+    k_features<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(c, eta, F(g->o_X), M);
+    const unsigned gb = (unsigned)((M + 63) / 64);
+    float* H0 = F(g->o_Hs);
+    k_gemm_fwd<kFin, kH><<<gb, 128, 0, st>>>(F(g->o_X), nullptr, kFin, B(g->o_win_t), P + kOffBin, nullptr,
+                                               F(g->o_Z0), H0, M, 1);
+    for (int l = 0; l < kLayers; ++l) {
+        float* Hl = F(g->o_Hs) + (size_t)l * M * kH;
+        float* Hn = F(g->o_Hs) + (size_t)(l + 1) * M * kH;
+        float* Ag = F(g->o_Agg) + (size_t)l * M * kH;
+        float* Zl = F(g->o_Zs) + (size_t)l * M * kH;
+        k_agg<0><<<(unsigned)((M + 7) / 8), 256, 0, st>>>(c, Hl, Ag, M);
+        k_gemm_fwd<2 * kH, kH><<<gb, 128, 0, st>>>(Hl, Ag, kH, B(g->o_wk_t) + (size_t)l * 2 * kH * kH,
+                                                    P + kOffL0 + l * kLayerSz + 2 * kH * kH, Hl, Zl, Hn, M, 1);
+    }
+    k_head<<<(unsigned)((M + 7) / 8), 256, 0, st>>>(F(g->o_Hs) + (size_t)kLayers * M * kH, P, F(g->o_Y), M);
+}
+
+gx_status gx_gnn_predict(gx_gnn* g, const float* eta_dev, float* out_dev, void* stream) {
+    if (!g || !g->dev || !eta_dev || !out_dev) return gx_internal_fail(GX_ERR_INVALID_ARG, "NULL argument or unbound");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    gnn_forward(g, eta_dev, st);
+    k_unpack<<<(unsigned)((g->M + 255) / 256), 256, 0, st>>>(reinterpret_cast<float*>(g->dev + g->o_Y), out_dev, g->M);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return gx_internal_fail(GX_ERR_CUDA, std::string("gnn predict: ") + cudaGetErrorString(e));
+    return GX_OK;
+}
+
+gx_status gx_gnn_train_step(gx_gnn* g, const float* eta_dev, const float* target_dev, float lr, float w_theta,
+                            double* loss_host, void* stream) {
+    if (!g || !g->dev || !eta_dev || !target_dev) return gx_internal_fail(GX_ERR_INVALID_ARG, "NULL argument or unbound");
+    if (!(lr >= 0.f) || !(w_theta >= 0.f)) return gx_internal_fail(GX_ERR_INVALID_ARG, "lr and w_theta must be >= 0");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const Ctx& c = *gx_internal_ctx(g->net);
+    const long long M = g->M;
+    auto F = [&](size_t o) { return reinterpret_cast<float*>(g->dev + o); };
+    auto B = [&](size_t o) { return reinterpret_cast<const __nv_bfloat16*>(g->dev + o); };
+    gnn_forward(g, eta_dev, st);
+    float* P = F(g->o_P);
+    float* G = F(g->o_G);
+    cudaMemsetAsync(G, 0, 4 * (size_t)kNParam, st);
+    cudaMemsetAsync(g->dev + g->o_loss, 0, 8, st);
+    k_loss<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(c, F(g->o_Y), target_dev, M, 1.0 / g->valid, w_theta,
+                                                        F(g->o_dY), reinterpret_cast<double*>(g->dev + g->o_loss));
+    float* dH = F(g->o_dH);
+    k_head_back<<<(unsigned)((M + 7) / 8), 256, 0, st>>>(F(g->o_Hs) + (size_t)kLayers * M * kH, F(g->o_dY), P, G,
+                                                         dH, M);
+    const unsigned ew = (unsigned)((M * kH + 255) / 256);
+    const unsigned nchunk = (unsigned)((M + kChunk - 1) / kChunk);
+    for (int l = kLayers - 1; l >= 0; --l) {
+        float* Hl = F(g->o_Hs) + (size_t)l * M * kH;
+        float* Ag = F(g->o_Agg) + (size_t)l * M * kH;
+        float* Zl = F(g->o_Zs) + (size_t)l * M * kH;
+        float* dZ = F(g->o_dZ);
+        k_relu_back<<<ew, 256, 0, st>>>(dH, Zl, dZ, M * kH);
+        float* GW = G + kOffL0 + l * kLayerSz;
+        k_gemm_wgrad<2 * kH, kH><<<nchunk, 8 * 32, 0, st>>>(Hl, Ag, kH, dZ, M, GW);
+        k_colsum<kH><<<nchunk, 256, 0, st>>>(dZ, M, GW + 2 * kH * kH);
+        // dCat = dZ W_l^T : B^T = W_l as stored ([2H][H], BF16)
+        k_gemm_fwd<kH, 2 * kH><<<(unsigned)((M + 63) / 64), 128, 0, st>>>(
+            dZ, nullptr, kH, B(g->o_wk) + (size_t)l * 2 * kH * kH, nullptr, nullptr, nullptr, F(g->o_dCat), M, 0);
+        // residual: dH stays; add the direct half and the transposed aggregation of the other half
+        k_add_half<<<ew, 256, 0, st>>>(dH, F(g->o_dCat), M);
+        k_take_half<<<ew, 256, 0, st>>>(F(g->o_dCat), F(g->o_dAgg), M);
+        k_agg<1><<<(unsigned)((M + 7) / 8), 256, 0, st>>>(c, F(g->o_dAgg), dH, M);
+    }
+    float* dZ0 = F(g->o_dZ);
+    k_relu_back<<<ew, 256, 0, st>>>(dH, F(g->o_Z0), dZ0, M * kH);
+    k_gemm_wgrad<kFin, kH><<<nchunk, 32, 0, st>>>(F(g->o_X), nullptr, kFin, dZ0, M, G + kOffWin);
+    k_colsum<kH><<<nchunk, 256, 0, st>>>(dZ0, M, G + kOffBin);
+    if (lr > 0.f) {
+        g->step += 1;
+        const float b1 = 0.9f, b2 = 0.999f;
+        const float c1 = 1.f - std::pow(b1, (float)g->step), c2 = 1.f - std::pow(b2, (float)g->step);
+        k_adam<<<(kNParam + 255) / 256, 256, 0, st>>>(P, G, F(g->o_m1), F(g->o_m2), kNParam, lr, b1, b2, 1e-8f, c1, c2);
+        if (gx_status s = gnn_refresh_bf16(g, st)) return s;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return gx_internal_fail(GX_ERR_CUDA, std::string("gnn train: ") + cudaGetErrorString(e));
+    if (loss_host) {
+        e = cudaMemcpyAsync(loss_host, g->dev + g->o_loss, 8, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return gx_internal_fail(GX_ERR_CUDA, cudaGetErrorString(e));
+    }
+    return GX_OK;
+}
+
+}  // extern "C"

@@ -85,6 +85,15 @@ _SIGS = {
     "gx_network_use_graphs": (C.c_int, [_vp, C.c_int]),
     "gx_profile_read": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
     "gx_dispatch_cost_noalloc": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp]),
+    "gx_gnn_num_params": (_sz, []),
+    "gx_gnn_create": (C.c_int, [_vp, C.c_int, C.c_int, C.POINTER(_vp)]),
+    "gx_gnn_device_bytes": (_sz, [_vp]),
+    "gx_gnn_bind": (C.c_int, [_vp, _vp, _sz, C.c_uint64, _vp]),
+    "gx_gnn_set_params": (C.c_int, [_vp, _vp, _sz, _vp]),
+    "gx_gnn_get_params": (C.c_int, [_vp, _vp, _sz, C.c_int, _vp]),
+    "gx_gnn_predict": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "gx_gnn_train_step": (C.c_int, [_vp, _vp, _vp, C.c_float, C.c_float, C.POINTER(C.c_double), _vp]),
+    "gx_gnn_destroy": (C.c_int, [_vp]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -284,6 +293,56 @@ class Network:
                                C.c_float(alpha), _stream_handle(stream))
         _check(rc, "gx_plan_step", False)
         return eta
+
+
+class WarmStartGNN:
+    """The learned warm start of a bound ``Network`` (kernels in csrc/gx_gnn.cu)."""
+
+    def __init__(self, net: Network, seed=0):
+        import torch
+        h = C.c_void_p()
+        _check(_lib.gx_gnn_create(net._h, 64, 3, C.byref(h)), "gx_gnn_create", False)
+        self._h = h
+        self.net = net  # keeps the network alive
+        self.nparam = int(_lib.gx_gnn_num_params())
+        nb = _lib.gx_gnn_device_bytes(h)
+        self.ws = torch.empty(nb + 256, dtype=torch.uint8, device=net.device)
+        base = self.ws.data_ptr()
+        off = (-base) % 256
+        _check(_lib.gx_gnn_bind(h, C.c_void_p(base + off), C.c_size_t(nb), C.c_uint64(seed), _stream_handle(None)),
+               "gx_gnn_bind", False)
+        self.M = int(sum(inf["N"] * inf["Tp"] for inf in net.info))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            _lib.gx_gnn_destroy(h)
+            self._h = None
+
+    def params(self, which=0):
+        out = np.empty(self.nparam, np.float32)
+        _check(_lib.gx_gnn_get_params(self._h, out.ctypes.data_as(C.c_void_p), out.size, which,
+                                      _stream_handle(None)), "gx_gnn_get_params", False)
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, np.float32)
+        _check(_lib.gx_gnn_set_params(self._h, p.ctypes.data_as(C.c_void_p), p.size, _stream_handle(None)),
+               "gx_gnn_set_params", False)
+
+    def predict(self, eta, out=None):
+        """[2 * bus rows]: prices ($/MWh) then angles, the user warm-start layout."""
+        import torch
+        if out is None:
+            out = torch.empty(2 * self.M, dtype=torch.float32, device=self.net.device)
+        _check(_lib.gx_gnn_predict(self._h, _ptr(eta), _ptr(out), _stream_handle(None)), "gx_gnn_predict", False)
+        return out
+
+    def train_step(self, eta, target, lr, w_theta=1.0):
+        loss = C.c_double()
+        _check(_lib.gx_gnn_train_step(self._h, _ptr(eta), _ptr(target), C.c_float(lr), C.c_float(w_theta),
+                                      C.byref(loss), _stream_handle(None)), "gx_gnn_train_step", False)
+        return loss.value
 
 
 def lib_path():

@@ -1,0 +1,93 @@
+"""GPU warm-start network (BF16 tensor-core layers, FP32 accumulation) against the FP64
+CPU reference: activations within 2e-2 relative, gradients with cosine > 0.999."""
+import numpy as np
+import pytest
+
+from gpu_util import eta_tensor, gpu_net
+from oracle import gnn as ognn
+from paper_2410_13055_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+H, FIN = 64, 16
+
+
+def pack(p):
+    """CPU parameter dict -> the GPU's flat FP32 layout (input rows padded to 16)."""
+    win = np.zeros((FIN, H)); win[:p["W_in"].shape[0]] = p["W_in"]
+    parts = [win.ravel(), p["b_in"]]
+    for k in range(3):
+        parts += [p[f"W{k}"].ravel(), p[f"b{k}"]]
+    parts += [p["W_out"].ravel(), p["b_out"]]
+    return np.concatenate(parts).astype(np.float32)
+
+
+def unpack_grads(v, p):
+    out, o = {}, 0
+    win = v[o:o + FIN * H].reshape(FIN, H); o += FIN * H
+    out["W_in"] = win[:p["W_in"].shape[0]]
+    out["b_in"] = v[o:o + H]; o += H
+    for k in range(3):
+        out[f"W{k}"] = v[o:o + 2 * H * H].reshape(2 * H, H); o += 2 * H * H
+        out[f"b{k}"] = v[o:o + H]; o += H
+    out["W_out"] = v[o:o + 2 * H].reshape(H, 2); o += 2 * H
+    out["b_out"] = v[o:o + 2]
+    return out
+
+
+def _setup():
+    from paper_2410_13055_gb300 import gx
+    nets, scens = synth.tiny()
+    net = gpu_net(nets, scens)
+    w = gx.WarmStartGNN(net, seed=1)
+    rng = np.random.default_rng(4)
+    p = ognn.init_params(rng, H=H)
+    for k in p:
+        if k.startswith("b"):
+            p[k] = 0.1 * rng.standard_normal(p[k].shape)
+    w.set_params(pack(p))
+    eta = nets[0]["eta_min"] * 1.05
+    X = ognn.features(nets[0], scens[0], eta)
+    A = ognn.agg_matrix(nets[0], scens[0]["T"])
+    return net, w, p, eta, X, A
+
+
+def test_gnn_forward_matches_cpu_reference():
+    net, w, p, eta, X, A = _setup()
+    y_cpu, _ = ognn.forward(p, X, A)
+    out = w.predict(eta_tensor(eta)).cpu().numpy()
+    M = X.shape[0]
+    y_gpu = np.stack([out[:M] / 100.0, out[M:]], axis=1)
+    err = np.linalg.norm(y_gpu - y_cpu) / np.linalg.norm(y_cpu)
+    assert err <= 2e-2, err
+
+
+def test_gnn_gradients_match_cpu_reference():
+    import torch
+    net, w, p, eta, X, A = _setup()
+    rng = np.random.default_rng(5)
+    M = X.shape[0]
+    target = rng.standard_normal((M, 2))
+    g_cpu = ognn.backward(p, X, A, target, w_theta=0.5)
+    tgt = torch.tensor(np.concatenate([100.0 * target[:, 0], target[:, 1]]), dtype=torch.float32, device="cuda")
+    loss = w.train_step(eta_tensor(eta), tgt, lr=0.0, w_theta=0.5)
+    assert abs(loss - ognn.loss(p, X, A, target, w_theta=0.5)) <= 2e-2 * abs(loss)
+    g_gpu = unpack_grads(w.params(which=1), p)
+    for k in g_cpu:
+        a, b = g_gpu[k].ravel().astype(float), g_cpu[k].ravel()
+        cos = a @ b / (np.linalg.norm(a) * np.linalg.norm(b) + 1e-30)
+        assert cos > 0.999, (k, cos)
+
+
+def test_gnn_training_reduces_loss():
+    import torch
+    net, w, p, eta, X, A = _setup()
+    M = X.shape[0]
+    rng = np.random.default_rng(6)
+    target = np.stack([np.sin(np.arange(M) / 7.0), 0.1 * np.cos(np.arange(M) / 5.0)], 1)
+    tgt = torch.tensor(np.concatenate([100.0 * target[:, 0], target[:, 1]]), dtype=torch.float32, device="cuda")
+    e = eta_tensor(eta)
+    first = w.train_step(e, tgt, lr=1e-3)
+    for _ in range(200):
+        last = w.train_step(e, tgt, lr=1e-3)
+    assert last < 0.5 * first, (first, last)
