@@ -392,146 +392,254 @@ __global__ void __launch_bounds__(kBatWarps * 32) k_bat(const Ctx c, int want_re
 
 // ------------------------------------------------------------------------------------
 // Bus kernel: generator and load proxes (closed-form clips), then the consensus step.
+//
+// A block covers 256 consecutive (bus, hour) items of one scenario, i.e. a few whole
+// buses.  It first stages those buses' device lists (generator rows with their cost,
+// plan value, emission rate and firm flag; line ends with beta and phase weight;
+// battery rows; bus constants) in shared memory, so each thread's per-hour loads no
+// longer wait on a chain of index lookups.  Blocks whose lists do not fit read them
+// from global memory instead (same arithmetic).
 // ------------------------------------------------------------------------------------
+constexpr int kStGen = 512, kStEnd = 512, kStBat = 128, kStBus = 72;
+
+struct BusStage {
+    int ok, n0;
+    int gp[kStBus + 1], ep[kStBus + 1], bp[kStBus + 1];
+    float icnt[kStBus], iwsum[kStBus], dresw[kStBus];
+    int grow[kStGen];
+    float gcost[kStGen], geta[kStGen], gemis[kStGen];
+    unsigned char gfirm[kStGen];
+    int ecode[kStEnd];
+    float ebeta[kStEnd], ew[kStEnd];
+    int brow[kStBat];
+};
+
+// per-bus device lists, from shared memory (staged) or global memory
+struct SrcStaged {
+    const BusStage& S;
+    int nl;
+    __device__ int g0() const { return S.gp[nl]; }
+    __device__ int g1() const { return S.gp[nl + 1]; }
+    __device__ int grow(int q) const { return S.grow[q]; }
+    __device__ float gcost(int q) const { return S.gcost[q]; }
+    __device__ float geta(int q) const { return S.geta[q]; }
+    __device__ float gemis(int q) const { return S.gemis[q]; }
+    __device__ bool gfirm(int q) const { return S.gfirm[q]; }
+    __device__ int e0() const { return S.ep[nl]; }
+    __device__ int e1() const { return S.ep[nl + 1]; }
+    __device__ int ecode(int q) const { return S.ecode[q]; }
+    __device__ float ebeta(int q) const { return S.ebeta[q]; }
+    __device__ float ew(int q) const { return S.ew[q]; }
+    __device__ int b0() const { return S.bp[nl]; }
+    __device__ int b1() const { return S.bp[nl + 1]; }
+    __device__ int brow(int q) const { return S.brow[q]; }
+    __device__ float icnt() const { return S.icnt[nl]; }
+    __device__ float iwsum() const { return S.iwsum[nl]; }
+    __device__ float dresw() const { return S.dresw[nl]; }
+};
+
+struct SrcGlobal {
+    const Ctx& c;
+    const ScenDev& sc;
+    int n;
+    __device__ int g0() const { return c.bus_gptr[sc.ptr0 + n]; }
+    __device__ int g1() const { return c.bus_gptr[sc.ptr0 + n + 1]; }
+    __device__ int grow(int q) const { return c.bus_gidx[sc.gen0 + q]; }
+    __device__ float gcost(int q) const { return c.g_cost[sc.gen0 + grow(q)]; }
+    __device__ float geta(int q) const { return fmaxf(c.eta[sc.eta0 + grow(q)], 0.f); }
+    __device__ float gemis(int q) const { return c.g_emis[sc.gen0 + grow(q)]; }
+    __device__ bool gfirm(int q) const { return c.g_firm[sc.gen0 + grow(q)]; }
+    __device__ int e0() const { return c.bus_eptr[sc.ptr0 + n]; }
+    __device__ int e1() const { return c.bus_eptr[sc.ptr0 + n + 1]; }
+    __device__ int ecode(int q) const { return c.bus_eidx[2 * sc.line0 + q]; }
+    __device__ float ebeta(int q) const { return c.l_beta[sc.line0 + (ecode(q) >> 1)]; }
+    __device__ float ew(int q) const { return c.l_w[sc.line0 + (ecode(q) >> 1)]; }
+    __device__ int b0() const { return c.bus_bptr[sc.ptr0 + n]; }
+    __device__ int b1() const { return c.bus_bptr[sc.ptr0 + n + 1]; }
+    __device__ int brow(int q) const { return c.bus_bidx[sc.bat0 + q]; }
+    __device__ float icnt() const { return c.bus_inv_cnt[sc.bus0 + n]; }
+    __device__ float iwsum() const { return c.bus_inv_wsum[sc.bus0 + n]; }
+    __device__ float dresw() const { return c.bus_dres_w[sc.bus0 + n]; }
+};
+
+template <int MODE, int ADJ, class Src>
+__device__ __forceinline__ void bus_item(const Ctx& c, const ScenDev& sc, const StatePtrs& X, const Src& B, int n,
+                                         int t, int want_res, float (&acc)[kBusPart]) {
+    const long long i = sc.e_bus + (long long)n * sc.Tp + t;
+    const float rho = c.rho, eps = c.eps;
+    const float inv_re = 1.f / (rho + eps);
+    if (MODE == M_RESET) {
+        const float Lnt = c.load[i];
+        X.xl[i] = ADJ ? 0.f : -Lnt;
+        if (ADJ) X.u[i] = c.adj_from_fwd ? -c.rho_ratio * c.u[i] : 0.f;
+        else X.u[i] = c.warm ? -c.warm[i] / rho : 0.f;
+        X.pbar[i] = 0.f;
+        X.thb[i] = (!ADJ && c.warm) ? c.warm[c.warm_half + i] : 0.f;
+        for (int q = B.g0(); q < B.g1(); ++q) X.xg[sc.e_gen + (long long)B.grow(q) * sc.Tp + t] = 0.f;
+        return;
+    }
+    const float pb = X.pbar[i], uu = X.u[i], thold = X.thb[i];
+    float sum = 0.f, dx2 = 0.f, x2 = 0.f;
+    float gscale = 0.f;  // adjoint: sum of (grad h / (rho + eps))^2 over free terminals
+    // generators
+    for (int q = B.g0(); q < B.g1(); ++q) {
+        const long long r = sc.e_gen + (long long)B.grow(q) * sc.Tp + t;
+        const float x = X.xg[r];
+        float xn = x;
+        if (MODE == M_FWD || MODE == M_ADJ || MODE == M_MASK) {
+            const float v = x - pb - uu;
+            if (ADJ) {
+                const float gh = B.gcost(q) + eps * c.xg[r] + c.kappa * B.gemis(q);
+                const bool fixed = c.m_gen[r] != 0;
+                xn = fixed ? 0.f : (rho * v + gh) * inv_re;
+                if (!fixed) gscale += (gh * inv_re) * (gh * inv_re);
+            } else {
+                const float etag = B.geta(q);
+                const float cap = B.gfirm(q) ? etag : c.cf[r] * etag;
+                const float pun = (rho * v - B.gcost(q)) * inv_re;
+                if (MODE == M_MASK) {
+                    uint8_t code = A_FREE;
+                    if (pun > cap && (rho + eps) * (pun - cap) > c.tol_act) code = A_UP;
+                    else if (pun < 0.f && -(rho + eps) * pun > c.tol_act) code = A_LO;
+                    c.m_gen[r] = code;
+                } else {
+                    xn = clampf(pun, 0.f, cap);
+                }
+            }
+            if (MODE != M_MASK) X.xg[r] = xn;
+        }
+        sum += xn;
+        dx2 += (xn - x) * (xn - x);
+        x2 += xn * xn;
+    }
+    // load (shed variable; terminal injection shed - L)
+    {
+        const float x = X.xl[i];
+        float xn = x;
+        if (MODE == M_FWD || MODE == M_ADJ || MODE == M_MASK) {
+            const float v = x - pb - uu;
+            const float Lnt = c.load[i];
+            if (ADJ) {
+                const float gsh = c.voll + eps * (c.xl[i] + Lnt);
+                const bool fixed = c.m_load[i] != 0;
+                xn = fixed ? 0.f : (rho * v + gsh) * inv_re;
+                if (!fixed) gscale += (gsh * inv_re) * (gsh * inv_re);
+            } else {
+                const float sun = (rho * (v + Lnt) - c.voll) * inv_re;
+                if (MODE == M_MASK) {
+                    uint8_t code = A_FREE;
+                    if (sun > Lnt && (rho + eps) * (sun - Lnt) > c.tol_act) code = A_UP;
+                    else if (sun < 0.f && -(rho + eps) * sun > c.tol_act) code = A_LO;
+                    c.m_load[i] = code;
+                } else {
+                    xn = clampf(sun, 0.f, Lnt) - Lnt;
+                }
+            }
+            if (MODE != M_MASK) X.xl[i] = xn;
+        }
+        sum += xn;
+        dx2 += (xn - x) * (xn - x);
+        x2 += xn * xn;
+    }
+    if (MODE == M_MASK) return;
+    // batteries (their prox ran in k_bat this iteration)
+    for (int q = B.b0(); q < B.b1(); ++q) {
+        const float xb = X.xb[sc.e_bat + (long long)B.brow(q) * sc.Tp + t];
+        sum += xb;
+        x2 += xb * xb;
+    }
+    // line ends (their prox ran in k_line this iteration)
+    float ths = 0.f;
+    for (int q = B.e0(); q < B.e1(); ++q) {
+        const int e = B.ecode(q);
+        const int side = e & 1;
+        const long long r = sc.e_line + (long long)(e >> 1) * sc.Tp + t;
+        const float d = X.dl[r];
+        const float qv = side ? X.vt[r] : X.vf[r];
+        const float beta = B.ebeta(q);
+        const float p = side ? beta * d : -beta * d;
+        sum += p;
+        x2 += p * p;
+        ths += B.ew(q) * qv;
+    }
+    const float icnt = B.icnt();
+    const float pbn = sum * icnt;
+    const float thn = ths * B.iwsum();
+    if (MODE == M_INIT) {
+        X.pbar[i] = pbn;
+        X.thb[i] = thn;
+        return;
+    }
+    const float un = uu + pbn;
+    X.pbar[i] = pbn;
+    X.u[i] = un;
+    X.thb[i] = thn;
+    if (want_res) {
+        const float cnt = 1.f / icnt;
+        const float dpb = pbn - pb;
+        acc[0] = cnt * pbn * pbn;
+        acc[1] = gscale;
+        acc[2] = dx2 - cnt * dpb * dpb;
+        acc[3] = (thn - thold) * (thn - thold) * B.dresw();
+        acc[4] = cnt * (rho * un) * (rho * un);
+        acc[5] = x2;
+    }
+}
+
 template <int MODE, int ADJ>
 __global__ void __launch_bounds__(kBlock) k_bus(const Ctx c, int want_res) {
+    __shared__ BusStage S;
     const int blk = blockIdx.x;
     const int s = c.bus_blk_scen[blk];
-    if (c.done[s]) return;
+    if (c.done[s]) return;  // block-uniform
     const ScenDev sc = c.scen[s];
     const StatePtrs X = state<ADJ>(c);
-    const int local = (blk - sc.bus_blk0) * kBlock + threadIdx.x;
+    const int item0 = (blk - sc.bus_blk0) * kBlock;
+    const int last = min(item0 + kBlock, sc.N * sc.Tp) - 1;
+    const int n0 = item0 / sc.Tp, n1 = last / sc.Tp;
+    const int nbus = n1 - n0 + 1;
+    // stage this block's buses
+    const int pb0 = sc.ptr0 + n0;
+    const int gb = c.bus_gptr[pb0], gcnt = c.bus_gptr[pb0 + nbus] - gb;
+    const int eb = c.bus_eptr[pb0], ecnt = c.bus_eptr[pb0 + nbus] - eb;
+    const int bb = c.bus_bptr[pb0], bcnt = c.bus_bptr[pb0 + nbus] - bb;
+    const bool ok = nbus <= kStBus && gcnt <= kStGen && ecnt <= kStEnd && bcnt <= kStBat;
+    if (ok) {
+        for (int k = threadIdx.x; k <= nbus; k += kBlock) {
+            S.gp[k] = c.bus_gptr[pb0 + k] - gb;
+            S.ep[k] = c.bus_eptr[pb0 + k] - eb;
+            S.bp[k] = c.bus_bptr[pb0 + k] - bb;
+            if (k < nbus) {
+                S.icnt[k] = c.bus_inv_cnt[sc.bus0 + n0 + k];
+                S.iwsum[k] = c.bus_inv_wsum[sc.bus0 + n0 + k];
+                S.dresw[k] = c.bus_dres_w[sc.bus0 + n0 + k];
+            }
+        }
+        for (int k = threadIdx.x; k < gcnt; k += kBlock) {
+            const int g = c.bus_gidx[sc.gen0 + gb + k];
+            S.grow[k] = g;
+            S.gcost[k] = c.g_cost[sc.gen0 + g];
+            S.geta[k] = fmaxf(c.eta[sc.eta0 + g], 0.f);
+            S.gemis[k] = c.g_emis[sc.gen0 + g];
+            S.gfirm[k] = c.g_firm[sc.gen0 + g];
+        }
+        for (int k = threadIdx.x; k < ecnt; k += kBlock) {
+            const int e = c.bus_eidx[2 * sc.line0 + eb + k];
+            S.ecode[k] = e;
+            S.ebeta[k] = c.l_beta[sc.line0 + (e >> 1)];
+            S.ew[k] = c.l_w[sc.line0 + (e >> 1)];
+        }
+        for (int k = threadIdx.x; k < bcnt; k += kBlock) S.brow[k] = c.bus_bidx[sc.bat0 + bb + k];
+    }
+    __syncthreads();
+    const int local = item0 + threadIdx.x;
     const int n = local / sc.Tp;
     const int t = local - n * sc.Tp;
     const bool valid = (n < sc.N) && (t < sc.T);
     float acc[kBusPart] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (valid) {
-        const long long i = sc.e_bus + (long long)n * sc.Tp + t;
-        const int nb = sc.ptr0 + n;
-        const float rho = c.rho, eps = c.eps;
-        const float inv_re = 1.f / (rho + eps);
-        if (MODE == M_RESET) {
-            const float Lnt = c.load[i];
-            X.xl[i] = ADJ ? 0.f : -Lnt;
-            if (ADJ) X.u[i] = c.adj_from_fwd ? -c.rho_ratio * c.u[i] : 0.f;
-            else X.u[i] = c.warm ? -c.warm[i] / rho : 0.f;
-            X.pbar[i] = 0.f;
-            X.thb[i] = (!ADJ && c.warm) ? c.warm[c.warm_half + i] : 0.f;
-            for (int q = c.bus_gptr[nb]; q < c.bus_gptr[nb + 1]; ++q) {
-                const int g = c.bus_gidx[sc.gen0 + q];
-                X.xg[sc.e_gen + (long long)g * sc.Tp + t] = 0.f;
-            }
-        } else {
-            const float pb = X.pbar[i], uu = X.u[i], thold = X.thb[i];
-            float sum = 0.f, dx2 = 0.f, x2 = 0.f;
-            float gscale = 0.f;  // adjoint: sum of (grad h / (rho + eps))^2 over free terminals
-            // generators
-            for (int q = c.bus_gptr[nb]; q < c.bus_gptr[nb + 1]; ++q) {
-                const int g = c.bus_gidx[sc.gen0 + q];
-                const int gg = sc.gen0 + g;
-                const long long r = sc.e_gen + (long long)g * sc.Tp + t;
-                const float x = X.xg[r];
-                float xn = x;
-                if (MODE == M_FWD || MODE == M_ADJ || MODE == M_MASK) {
-                    const float v = x - pb - uu;
-                    if (ADJ) {
-                        const float gh = c.g_cost[gg] + eps * c.xg[r] + c.kappa * c.g_emis[gg];
-                        xn = c.m_gen[r] ? 0.f : (rho * v + gh) * inv_re;
-                        if (!c.m_gen[r]) gscale += (gh * inv_re) * (gh * inv_re);
-                    } else {
-                        const float etag = fmaxf(c.eta[sc.eta0 + g], 0.f);
-                        const float cap = c.g_firm[gg] ? etag : c.cf[r] * etag;
-                        const float pun = (rho * v - c.g_cost[gg]) * inv_re;
-                        if (MODE == M_MASK) {
-                            uint8_t code = A_FREE;
-                            if (pun > cap && (rho + eps) * (pun - cap) > c.tol_act) code = A_UP;
-                            else if (pun < 0.f && -(rho + eps) * pun > c.tol_act) code = A_LO;
-                            c.m_gen[r] = code;
-                        } else {
-                            xn = clampf(pun, 0.f, cap);
-                        }
-                    }
-                    if (MODE != M_MASK) X.xg[r] = xn;
-                }
-                sum += xn;
-                dx2 += (xn - x) * (xn - x);
-                x2 += xn * xn;
-            }
-            // load (shed variable; terminal injection shed - L)
-            {
-                const float x = X.xl[i];
-                float xn = x;
-                if (MODE == M_FWD || MODE == M_ADJ || MODE == M_MASK) {
-                    const float v = x - pb - uu;
-                    const float Lnt = c.load[i];
-                    if (ADJ) {
-                        const float gsh = c.voll + eps * (c.xl[i] + Lnt);
-                        xn = c.m_load[i] ? 0.f : (rho * v + gsh) * inv_re;
-                        if (!c.m_load[i]) gscale += (gsh * inv_re) * (gsh * inv_re);
-                    } else {
-                        const float sun = (rho * (v + Lnt) - c.voll) * inv_re;
-                        if (MODE == M_MASK) {
-                            uint8_t code = A_FREE;
-                            if (sun > Lnt && (rho + eps) * (sun - Lnt) > c.tol_act) code = A_UP;
-                            else if (sun < 0.f && -(rho + eps) * sun > c.tol_act) code = A_LO;
-                            c.m_load[i] = code;
-                        } else {
-                            xn = clampf(sun, 0.f, Lnt) - Lnt;
-                        }
-                    }
-                    if (MODE != M_MASK) X.xl[i] = xn;
-                }
-                sum += xn;
-                dx2 += (xn - x) * (xn - x);
-                x2 += xn * xn;
-            }
-            if (MODE != M_MASK) {
-                // batteries (their prox ran in k_bat this iteration)
-                for (int q = c.bus_bptr[nb]; q < c.bus_bptr[nb + 1]; ++q) {
-                    const int b = c.bus_bidx[sc.bat0 + q];
-                    const float xb = X.xb[sc.e_bat + (long long)b * sc.Tp + t];
-                    sum += xb;
-                    x2 += xb * xb;
-                }
-                // line ends (their prox ran in k_line this iteration)
-                const int e0 = c.bus_eptr[nb], e1 = c.bus_eptr[nb + 1];
-                float ths = 0.f;
-                for (int q = e0; q < e1; ++q) {
-                    const int e = c.bus_eidx[2 * sc.line0 + q];
-                    const int l = e >> 1, side = e & 1;
-                    const long long r = sc.e_line + (long long)l * sc.Tp + t;
-                    const float d = X.dl[r];
-                    const float qv = side ? X.vt[r] : X.vf[r];
-                    const float beta = c.l_beta[sc.line0 + l];
-                    const float p = side ? beta * d : -beta * d;
-                    sum += p;
-                    x2 += p * p;
-                    ths += c.l_w[sc.line0 + l] * qv;
-                }
-                const float icnt = c.bus_inv_cnt[sc.bus0 + n];
-                const float pbn = sum * icnt;
-                const float thn = ths * c.bus_inv_wsum[sc.bus0 + n];
-                if (MODE == M_INIT) {
-                    X.pbar[i] = pbn;
-                    X.thb[i] = thn;
-                } else {
-                    const float un = uu + pbn;
-                    X.pbar[i] = pbn;
-                    X.u[i] = un;
-                    X.thb[i] = thn;
-                    if (want_res) {
-                        const float cnt = 1.f / icnt;
-                        const float dpb = pbn - pb;
-                        acc[0] = cnt * pbn * pbn;
-                        acc[1] = gscale;
-                        acc[2] = dx2 - cnt * dpb * dpb;
-                        acc[3] = (thn - thold) * (thn - thold) * c.bus_dres_w[sc.bus0 + n];
-                        acc[4] = cnt * (rho * un) * (rho * un);
-                        acc[5] = x2;
-                    }
-                }
-            }
-        }
+        if (ok) bus_item<MODE, ADJ>(c, sc, X, SrcStaged{S, n - n0}, n, t, want_res, acc);
+        else bus_item<MODE, ADJ>(c, sc, X, SrcGlobal{c, sc, n}, n, t, want_res, acc);
     }
     if ((MODE == M_FWD || MODE == M_ADJ) && want_res) {
         __shared__ float sh[kBusPart][kBlock / 32];
