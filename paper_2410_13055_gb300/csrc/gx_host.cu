@@ -233,10 +233,10 @@ gx_status gx_opts_default(gx_opts* o) {
     o->voll = 1000.0;
     o->kappa = 0.0;
     o->rho = 0.3;
-    o->rho_theta_c = 0.01;
+    o->rho_theta_c = 0.1;
     o->theta_weight = 0;
     o->rho_inner_c = 1.0;
-    o->inner_iters = 3;
+    o->inner_iters = 2;
     o->tol = 1e-3;
     o->max_iter = 20000;
     o->check_every = 20;
@@ -244,7 +244,7 @@ gx_status gx_opts_default(gx_opts* o) {
     o->adj_tol = 1e-3;
     o->adj_max_iter = 20000;
     o->grad_envelope = 0;
-    o->adj_rho = 0.005;
+    o->adj_rho = 0.002;
     return GX_OK;
 }
 

@@ -1,0 +1,94 @@
+"""Train the learned warm start on the 100-bus network and compare it with cold and
+previous-plan starts.
+
+    python -m paper_2410_13055_gb300.train_warmstart --out weights.npy --report report.json
+
+Training data: plans along implicit-gradient paths for battery capital costs
+$100-400/kWh in $25 steps (Section 3.3's sweep), plus log-normal(0, sigma)
+perturbations of them, each solved by the CUDA solver.  Test pairs (seeded
+separately): (plan at cost c, plan at cost c +- $25) and (consecutive plans on a
+path); each start is timed to a 1e-3 residual for the dispatch and the adjoint.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+import torch
+
+from . import gx, synth
+from .warmstart import compare_starts, gamma_for_battery_cost, make_dataset, plan_path, train
+
+KAPPA = 50.0
+
+
+def build(seed=1, S=16):
+    nets, scens = synth.medium(seed=seed, S=S)
+    net = gx.Network(nets, scens, kappa=KAPPA, tol=1e-3, adj_tol=1e-3, max_iter=50000, adj_max_iter=50000)
+    return nets, scens, net
+
+
+def test_pairs(net, nets, n_pairs, seed=1000, steps=6, alpha_frac=2e-2):
+    rng = np.random.default_rng(seed)
+    dev = net.device
+    eta_min = torch.tensor(nets[0]["eta_min"], dtype=torch.float32, device=dev)
+    eta_max = torch.tensor(nets[0]["eta_max"], dtype=torch.float32, device=dev)
+    T = net.info[0]["T"]
+    pairs = []
+    for k in range(n_pairs):
+        c = float(rng.uniform(112.5, 387.5))
+        ends = []
+        for cc in (c, c + (25.0 if rng.random() < 0.5 else -25.0)):
+            gamma = torch.tensor(gamma_for_battery_cost(nets[0], cc, T), dtype=torch.float32, device=dev)
+            g0 = torch.zeros_like(eta_min)
+            net.solve(eta_min, warm="cold")
+            net.grad(eta_min, out=g0)
+            alpha = alpha_frac * float(eta_min.median()) / max(float((gamma + g0).abs().max()), 1e-30)
+            path = plan_path(net, nets, eta_min, gamma, eta_min, eta_max, alpha, steps)
+            ends.append(path)
+        if k % 2 == 0:
+            pairs.append(("cost", ends[0][-1], ends[1][-1]))
+        else:
+            pairs.append(("step", ends[0][-2], ends[0][-1]))
+    return pairs
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", default=None)
+    ap.add_argument("--report", default=None)
+    ap.add_argument("--epochs", type=int, default=40)
+    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--pairs", type=int, default=20)
+    ap.add_argument("--costs", type=int, default=13)
+    args = ap.parse_args(argv)
+    t0 = time.time()
+    nets, scens, net = build()
+    costs = list(np.linspace(100.0, 400.0, args.costs))
+    samples = make_dataset(net, nets, costs, steps=8, keep_every=2, n_perturb=2, sigma=0.1, seed=100)
+    t_data = time.time() - t0
+    gnn = gx.WarmStartGNN(net, seed=7)
+    t1 = time.time()
+    hist = train(gnn, samples, epochs=args.epochs, lr=args.lr, w_theta=10.0,
+                 log=lambda m: print(m, flush=True))
+    torch.cuda.synchronize()
+    t_train = time.time() - t1
+    if args.out:
+        np.save(args.out, gnn.params())
+    pairs = test_pairs(net, nets, args.pairs)
+    rows = compare_starts(net, gnn, [(a, b) for _, a, b in pairs])
+    summ = {}
+    for mode in ("cold", "prev", "learned"):
+        summ[mode] = {k: float(np.median([r[mode][k] for r in rows])) for k in ("fwd", "adj", "ms")}
+    wins = sum(1 for r in rows if r["learned"]["fwd"] + r["learned"]["adj"] < r["prev"]["fwd"] + r["prev"]["adj"])
+    rep = dict(samples=len(samples), data_s=t_data, train_s=t_train, loss_first=hist[0], loss_last=hist[-1],
+               pairs=len(rows), kinds=[k for k, _, _ in pairs], median=summ, learned_beats_prev=wins, rows=rows)
+    print(json.dumps({k: v for k, v in rep.items() if k != "rows"}), flush=True)
+    if args.report:
+        json.dump(rep, open(args.report, "w"), indent=1)
+
+
+if __name__ == "__main__":
+    main()

@@ -113,7 +113,9 @@ def compare_starts(net, gnn, pairs):
             else:
                 net.solve(eta_b, warm=mode)
             it_f = net.last_stats["iters_max"]
-            net.grad(eta_b, warm="prev" if mode == "prev" else "cold")
+            # the network predicts the dispatch only; its adjoint continues from the
+            # previous plan's adjoint state like the previous-plan start's does
+            net.grad(eta_b, warm="cold" if mode == "cold" else "prev")
             torch.cuda.synchronize()
             r[mode] = dict(fwd=it_f, adj=net.last_grad_stats["iters_max"],
                            ms=1e3 * (time.perf_counter() - t0))
