@@ -182,7 +182,8 @@ gx_status gx_network_scenario_info(const gx_network* net, int s, int* T, int* Tp
  * eta_dev [K].  warm: GX_WARM_COLD (zero state), GX_WARM_PREV (continue from the
  * state of the previous solve), GX_WARM_USER (initial prices and angles from
  * warm_dev: [sum_s N_s Tp_s] prices followed by the same size of angles, in
- * scenario order of the whole network).  Synchronises `stream` every
+ * scenario order of the whole network; generators and loads start at their best
+ * response to those prices, line flows from the angle differences).  Synchronises `stream` every
  * check_every iterations.  Returns GX_NOT_CONVERGED if any scenario of the batch
  * hit max_iter. */
 gx_status gx_dispatch_solve_batch(gx_network* net, const float* eta_dev, const int* scen_idx, int B, int warm,

@@ -1,0 +1,125 @@
+"""Autotuner of the solver's launch and penalty parameters, cached per shape bucket.
+
+For a bound network it times a short implicit-gradient sequence (a cold solve and
+gradient, then `steps` previous-plan steps) for candidate settings, one parameter at a
+time from the defaults (coordinate descent), and keeps the fastest setting whose
+planner objective stays within `h_tol` of a tight reference solve at the same plan
+(equal residual tolerances do not give equal accuracy across penalties).  Parameters:
+residual-check chunk length (the CUDA-graph size), power penalty rho, phase penalty
+scale, adjoint penalty, battery inner iterations.  Results are cached as JSON, keyed by
+(buses, hours, scenarios) rounded to powers of two.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import time
+
+import numpy as np
+import torch
+
+from . import gx
+
+SPACE = {
+    "check_every": [10, 20, 40],
+    "rho": [0.2, 0.3, 0.5],
+    "rho_theta_c": [0.03, 0.1],
+    "adj_rho": [0.001, 0.002, 0.004],
+    "inner_iters": [2, 3],
+}
+
+
+def bucket(net: gx.Network):
+    p2 = lambda x: 1 << max(0, int(math.ceil(math.log2(max(x, 1)))))
+    N = max(i["N"] for i in net.info)
+    T = max(i["T"] for i in net.info)
+    return f"N{p2(N)}_T{p2(T)}_S{p2(net.S)}"
+
+
+def default_cache_path():
+    return os.environ.get("GX_AUTOTUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "gx", "autotune.json"))
+
+
+def _run(net, eta0, gamma, eta_min, eta_max, steps, alpha):
+    eta = eta0.clone()
+    g = torch.zeros_like(eta)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(steps + 1):
+        warm = "cold" if k == 0 else "prev"
+        net.solve(eta, warm=warm)
+        net.grad(eta, out=g, warm=warm)
+        if k < steps:
+            net.plan_step(eta, g, gamma, eta_min, eta_max, alpha)
+    torch.cuda.synchronize()
+    h = float((net.array("h").cpu().numpy() * net.weights).sum())
+    return time.perf_counter() - t0, eta, h
+
+
+def tune(net: gx.Network, nets, steps=3, h_tol=2e-3, cache=None, log=None, alpha_frac=1e-2):
+    """Tune `net`'s options in place; returns the chosen option dict."""
+    cache = cache or default_cache_path()
+    key = bucket(net)
+    dev = net.device
+    eta_min = torch.tensor(np.concatenate([n["eta_min"] for n in nets]), dtype=torch.float32, device=dev)
+    eta_max = torch.tensor(np.concatenate([n["eta_max"] for n in nets]), dtype=torch.float32, device=dev)
+    gamma = torch.tensor(np.concatenate([n["gamma"] for n in nets]), dtype=torch.float32, device=dev)
+    base = {k: getattr(net.opts, k) for k in SPACE}
+    g0 = torch.zeros_like(eta_min)
+    net.solve(eta_min, warm="cold")
+    net.grad(eta_min, out=g0)
+    alpha = alpha_frac * float(eta_min.median()) / max(float((gamma + g0).abs().max()), 1e-30)
+
+    def measure(opts):
+        net.set_opts(**opts)
+        return _run(net, eta_min, gamma, eta_min, eta_max, steps, alpha)
+
+    t_best, eta_end, _ = measure(base)
+    # tight reference objective at the plan the defaults reach
+    ref = gx.Network(nets, [dict(sc) for sc in net.scens_desc], opts=gx.default_opts(
+        **{**{k: getattr(net.opts, k) for k, _ in gx.Opts._fields_}, "tol": 1e-5, "max_iter": 200000}))
+    ref.solve(eta_end)
+    torch.cuda.synchronize()
+    h_ref = float((ref.array("h").cpu().numpy() * ref.weights).sum())
+    del ref
+    best = dict(base)
+    trials = [dict(base, time_s=t_best)]
+    for name, vals in SPACE.items():
+        for v in vals:
+            if v == best[name]:
+                continue
+            cand = dict(best, **{name: v})
+            t, eta_c, _ = measure(cand)
+            net.solve(eta_end, warm="cold")
+            torch.cuda.synchronize()
+            h = float((net.array("h").cpu().numpy() * net.weights).sum())
+            ok = abs(h - h_ref) <= h_tol * abs(h_ref)
+            trials.append(dict(cand, time_s=t, h_rel=abs(h - h_ref) / abs(h_ref), ok=ok))
+            if log:
+                log(trials[-1])
+            if ok and t < t_best:
+                best, t_best = cand, t
+    net.set_opts(**best)
+    entry = dict(best=best, time_s=t_best, trials=trials)
+    try:
+        os.makedirs(os.path.dirname(cache), exist_ok=True)
+        db = json.load(open(cache)) if os.path.exists(cache) else {}
+        db[key] = entry
+        json.dump(db, open(cache, "w"), indent=1)
+    except OSError:
+        pass
+    return best
+
+
+def load(net: gx.Network, cache=None):
+    """Apply a cached setting for `net`'s shape bucket; returns it (or None)."""
+    cache = cache or default_cache_path()
+    if not os.path.exists(cache):
+        return None
+    db = json.load(open(cache))
+    e = db.get(bucket(net))
+    if e:
+        net.set_opts(**e["best"])
+        return e["best"]
+    return None

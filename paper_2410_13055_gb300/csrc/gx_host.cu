@@ -196,6 +196,9 @@ static void make_ctx(gx_network* net) {
     c.done = I(net->o_done); c.iters = I(net->o_iters); c.status = I(net->o_status); c.adj_iters = I(net->o_adjit);
     c.n_active = I(net->o_nact);
     c.iter_ctr = I(net->o_ctr);
+    c.max_bat_T = 1;
+    for (const ScenDev& d : net->sdev)
+        if (d.B > 0) c.max_bat_T = std::max(c.max_bat_T, d.T);
     c.max_it = o.max_iter;
     c.resid = D(net->o_resid); c.rbest = D(net->o_rbest); c.cost = D(net->o_cost); c.hval = D(net->o_h); c.grad_s = D(net->o_grads);
     c.out_flow = F(net->o_flow); c.out_price = F(net->o_price); c.out_shed = F(net->o_shed);

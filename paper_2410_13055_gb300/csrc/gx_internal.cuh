@@ -57,6 +57,7 @@ struct Ctx {
     int inner_iters;
     int check_every;
     int max_it;          // iteration cap of the loop this context drives
+    int max_bat_T;       // longest horizon among scenarios that have batteries
     int* iter_ctr;       // device iteration counter of the current loop
     // tables
     const ScenDev* scen;

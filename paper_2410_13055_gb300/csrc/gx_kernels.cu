@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(kBlock) k_line(const Ctx c, int want_res) {
 // (pivots precomputed in bat_dd); its two Thomas sweeps are first-order linear
 // recurrences evaluated with warp-wide affine scans.
 // ------------------------------------------------------------------------------------
-template <int MODE, int ADJ>
+template <int MODE, int ADJ, int kHpl>
 __global__ void __launch_bounds__(kBatWarps * 32) k_bat(const Ctx c, int want_res) {
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * kBatWarps + (threadIdx.x >> 5);
@@ -232,12 +232,12 @@ __global__ void __launch_bounds__(kBatWarps * 32) k_bat(const Ctx c, int want_re
     const float gc = (Ah * a - rho * k) * idet;   // d(c)/d(mu)
     const float gd = (rho * a - Ah * k) * idet;   // d(d)/d(mu)
 
-    float v[kHplMax], zc[kHplMax], zd[kHplMax], zs[kHplMax], yc[kHplMax], yd[kHplMax], ys[kHplMax];
-    float lo[3][kHplMax], hi[3][kHplMax], qc[kHplMax], qd[kHplMax];
-    float idd[kHplMax], iddp[kHplMax];  // 1/dd_t and 1/dd_{t-1} (0 for t = 0)
-    float xb_old[kHplMax];
+    float v[kHpl], zc[kHpl], zd[kHpl], zs[kHpl], yc[kHpl], yd[kHpl], ys[kHpl];
+    float lo[3][kHpl], hi[3][kHpl], qc[kHpl], qd[kHpl];
+    float idd[kHpl], iddp[kHpl];  // 1/dd_t and 1/dd_{t-1} (0 for t = 0)
+    float xb_old[kHpl];
 #pragma unroll
-    for (int j = 0; j < kHplMax; ++j) {
+    for (int j = 0; j < kHpl; ++j) {
         const int t = t0 + j;
         const bool ok = (j < hpl) && (t < T);
         v[j] = zc[j] = zd[j] = zs[j] = yc[j] = yd[j] = ys[j] = 0.f;
@@ -268,14 +268,14 @@ __global__ void __launch_bounds__(kBatWarps * 32) k_bat(const Ctx c, int want_re
         }
     }
 
-    float cx[kHplMax], dx[kHplMax];
+    float cx[kHpl], dx[kHpl];
 #pragma unroll
-    for (int j = 0; j < kHplMax; ++j) { cx[j] = 0.f; dx[j] = 0.f; }
+    for (int j = 0; j < kHpl; ++j) { cx[j] = 0.f; dx[j] = 0.f; }
 
     for (int it = 0; it < c.inner_iters; ++it) {
-        float c0[kHplMax], d0[kHplMax], rs[kHplMax], rhs[kHplMax];
+        float c0[kHpl], d0[kHpl], rs[kHpl], rhs[kHpl];
 #pragma unroll
-        for (int j = 0; j < kHplMax; ++j) {
+        for (int j = 0; j < kHpl; ++j) {
             const float rc = zc[j] - yc[j] * iri, rd = zd[j] - yd[j] * iri;
             rs[j] = zs[j] - ys[j] * iri;
             const float b1 = ri * rc - rho * v[j] - qc[j];
@@ -286,13 +286,13 @@ __global__ void __launch_bounds__(kBatWarps * 32) k_bat(const Ctx c, int want_re
         // previous hour's r_s for the first hour of the chunk (0 before hour 0)
         float rs_last = 0.f;
 #pragma unroll
-        for (int j = 0; j < kHplMax; ++j) if (j == hpl - 1) rs_last = rs[j];
+        for (int j = 0; j < kHpl; ++j) if (j == hpl - 1) rs_last = rs[j];
         float rs_prev = __shfl_up_sync(0xffffffffu, rs_last, 1);
         if (lane == 0) rs_prev = 0.f;
         // forward sweep y_t = rhs_t + y_{t-1} / dd_{t-1}
         float A = 1.f, Bv = 0.f;
 #pragma unroll
-        for (int j = 0; j < kHplMax; ++j) {
+        for (int j = 0; j < kHpl; ++j) {
             const int t = t0 + j;
             const bool ok = (j < hpl) && (t < T);
             const float prev = j == 0 ? rs_prev : rs[j > 0 ? j - 1 : 0];
@@ -307,9 +307,9 @@ __global__ void __launch_bounds__(kBatWarps * 32) k_bat(const Ctx c, int want_re
         }
         float yin = __shfl_up_sync(0xffffffffu, Bv, 1);
         if (lane == 0) yin = 0.f;
-        float yv[kHplMax];
+        float yv[kHpl];
 #pragma unroll
-        for (int j = 0; j < kHplMax; ++j) {
+        for (int j = 0; j < kHpl; ++j) {
             const int t = t0 + j;
             const bool ok = (j < hpl) && (t < T);
             if (ok) yin = iddp[j] * yin + rhs[j];
@@ -318,7 +318,7 @@ __global__ void __launch_bounds__(kBatWarps * 32) k_bat(const Ctx c, int want_re
         // backward sweep mu_t = (y_t + mu_{t+1}) / dd_t, mu_T = 0
         A = 1.f; Bv = 0.f;
 #pragma unroll
-        for (int j = kHplMax - 1; j >= 0; --j) {
+        for (int j = kHpl - 1; j >= 0; --j) {
             const int t = t0 + j;
             const bool ok = (j < hpl) && (t < T);
             if (ok) { A = idd[j] * A; Bv = idd[j] * Bv + idd[j] * yv[j]; }
@@ -331,10 +331,10 @@ __global__ void __launch_bounds__(kBatWarps * 32) k_bat(const Ctx c, int want_re
         }
         float min_ = __shfl_down_sync(0xffffffffu, Bv, 1);
         if (lane == 31) min_ = 0.f;
-        float mu[kHplMax];
+        float mu[kHpl];
         float mnext = min_;
 #pragma unroll
-        for (int j = kHplMax - 1; j >= 0; --j) {
+        for (int j = kHpl - 1; j >= 0; --j) {
             const int t = t0 + j;
             const bool ok = (j < hpl) && (t < T);
             mu[j] = 0.f;
@@ -342,13 +342,13 @@ __global__ void __launch_bounds__(kBatWarps * 32) k_bat(const Ctx c, int want_re
         }
         // x = (c, d, s), then the box projection and the inner dual step
 #pragma unroll
-        for (int j = 0; j < kHplMax; ++j) {
+        for (int j = 0; j < kHpl; ++j) {
             const int t = t0 + j;
             const bool ok = (j < hpl) && (t < T);
             if (!ok) continue;
             float mu_n;
             if (t + 1 >= T) mu_n = 0.f;
-            else if (j + 1 < hpl) mu_n = mu[j + 1 < kHplMax ? j + 1 : j];
+            else if (j + 1 < hpl) mu_n = mu[j + 1 < kHpl ? j + 1 : j];
             else mu_n = min_;
             const float cc = c0[j] + mu[j] * gc;
             const float dd_ = d0[j] + mu[j] * gd;
@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(kBatWarps * 32) k_bat(const Ctx c, int want_re
     }
     float dx2 = 0.f, x2 = 0.f;
 #pragma unroll
-    for (int j = 0; j < kHplMax; ++j) {
+    for (int j = 0; j < kHpl; ++j) {
         const int t = t0 + j;
         const bool ok = (j < hpl) && (t < T);
         if (!ok) continue;
@@ -475,7 +475,19 @@ __device__ __forceinline__ void bus_item(const Ctx& c, const ScenDev& sc, const 
         else X.u[i] = c.warm ? -c.warm[i] / rho : 0.f;
         X.pbar[i] = 0.f;
         X.thb[i] = (!ADJ && c.warm) ? c.warm[c.warm_half + i] : 0.f;
-        for (int q = B.g0(); q < B.g1(); ++q) X.xg[sc.e_gen + (long long)B.grow(q) * sc.Tp + t] = 0.f;
+        if (!ADJ && c.warm) {
+            // user start: each generator and load at its best response to the given price
+            const float lam = c.warm[i];
+            const float shed = clampf((lam - c.voll) / eps, 0.f, Lnt);
+            X.xl[i] = shed - Lnt;
+            for (int q = B.g0(); q < B.g1(); ++q) {
+                const long long r = sc.e_gen + (long long)B.grow(q) * sc.Tp + t;
+                const float cap = B.gfirm(q) ? B.geta(q) : c.cf[r] * B.geta(q);
+                X.xg[r] = clampf((lam - B.gcost(q)) / eps, 0.f, cap);
+            }
+        } else {
+            for (int q = B.g0(); q < B.g1(); ++q) X.xg[sc.e_gen + (long long)B.grow(q) * sc.Tp + t] = 0.f;
+        }
         return;
     }
     const float pb = X.pbar[i], uu = X.u[i], thold = X.thb[i];
@@ -587,7 +599,7 @@ __device__ __forceinline__ void bus_item(const Ctx& c, const ScenDev& sc, const 
 }
 
 template <int MODE, int ADJ>
-__global__ void __launch_bounds__(kBlock) k_bus(const Ctx c, int want_res) {
+__global__ void __launch_bounds__(kBlock, 5) k_bus(const Ctx c, int want_res) {
     __shared__ BusStage S;
     const int blk = blockIdx.x;
     const int s = c.bus_blk_scen[blk];
@@ -952,10 +964,29 @@ int launch_line(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st) 
         }                                                                                   \
     } while (0)
 
+#define GX_BAT_HPL(H)                                                                      \
+    do {                                                                                   \
+        if (adj) {                                                                         \
+            if (mode == M_ADJ) k_bat<M_ADJ, 1, H><<<grid, kBatWarps * 32, 0, st>>>(c, want_res);          \
+            else if (mode == M_RESET) k_bat<M_RESET, 1, H><<<grid, kBatWarps * 32, 0, st>>>(c, want_res); \
+        } else {                                                                           \
+            if (mode == M_FWD) k_bat<M_FWD, 0, H><<<grid, kBatWarps * 32, 0, st>>>(c, want_res);          \
+            else if (mode == M_RESET) k_bat<M_RESET, 0, H><<<grid, kBatWarps * 32, 0, st>>>(c, want_res); \
+            else if (mode == M_MASK) k_bat<M_MASK, 0, H><<<grid, kBatWarps * 32, 0, st>>>(c, want_res);   \
+        }                                                                                  \
+    } while (0)
+
+// Hours per lane: compiled for 1, 2, 3, 6 and 8 (T up to 32, 64, 96, 192, 256), chosen
+// from the longest horizon among the batch's batteries.
 int launch_bat(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st) {
     if (mode == M_INIT || c.n_bat_warps <= 0) return 0;
     const int grid = (c.n_bat_warps + kBatWarps - 1) / kBatWarps;
-    GX_DISPATCH_MODE_BS(k_bat, grid, kBatWarps * 32, c, want_res);
+    const int hpl = (c.max_bat_T + 31) / 32;
+    if (hpl <= 1) GX_BAT_HPL(1);
+    else if (hpl <= 2) GX_BAT_HPL(2);
+    else if (hpl <= 3) GX_BAT_HPL(3);
+    else if (hpl <= 6) GX_BAT_HPL(6);
+    else GX_BAT_HPL(8);
     return 1;
 }
 

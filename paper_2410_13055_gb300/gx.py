@@ -195,6 +195,7 @@ class Network:
                                     _stream_handle(None)), "gx_network_bind", False)
         self.info = [self.scenario_info(s) for s in range(self.S)]
         self.weights = np.array([float(sc["weight"]) for sc in scens])
+        self.nets_desc, self.scens_desc = nets, scens
         self.eta_offsets = []
         off = 0
         for n in nets:

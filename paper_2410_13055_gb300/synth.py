@@ -211,12 +211,17 @@ def tiny(seed: int = 0):
     return [net], [scen]
 
 
-def medium(seed: int = 1, S: int = 16, T: int = 168, bat_cost_kwh: float = BATTERY_COST_PER_KWH):
-    """100-bus geometric graph, 150 lines, 300 generators, 50 batteries, 100 loads, T=168, S=16."""
+def medium(seed: int = 1, S: int = 16, T: int = 168, bat_cost_kwh: float = BATTERY_COST_PER_KWH,
+           scen_seed: int | None = None):
+    """100-bus geometric graph, 150 lines, 300 generators, 50 batteries, 100 loads, T=168, S=16.
+
+    With `scen_seed`, the scenarios (weather and load draws) come from their own seed
+    while the network stays that of `seed` (independent scenario shards of one network)."""
     rng = _rng(seed)
     net = _bus_network(rng, 100, 150, 300, 50, T, bat_cost_kwh=bat_cost_kwh)
     base = rng.uniform(50.0, 150.0, size=100)
-    scens = [_bus_scenario(rng, net, 0, T, 1.0 / S, base) for _ in range(S)]
+    srng = rng if scen_seed is None else _rng(scen_seed)
+    scens = [_bus_scenario(srng, net, 0, T, 1.0 / S, base) for _ in range(S)]
     return [net], scens
 
 

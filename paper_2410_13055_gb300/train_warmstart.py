@@ -63,6 +63,7 @@ def main(argv=None):
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--pairs", type=int, default=20)
     ap.add_argument("--costs", type=int, default=13)
+    ap.add_argument("--w-theta", type=float, default=0.1)
     args = ap.parse_args(argv)
     t0 = time.time()
     nets, scens, net = build()
@@ -71,7 +72,7 @@ def main(argv=None):
     t_data = time.time() - t0
     gnn = gx.WarmStartGNN(net, seed=7)
     t1 = time.time()
-    hist = train(gnn, samples, epochs=args.epochs, lr=args.lr, w_theta=10.0,
+    hist = train(gnn, samples, epochs=args.epochs, lr=args.lr, w_theta=args.w_theta,
                  log=lambda m: print(m, flush=True))
     torch.cuda.synchronize()
     t_train = time.time() - t1
