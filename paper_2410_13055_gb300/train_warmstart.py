@@ -19,7 +19,7 @@ import numpy as np
 import torch
 
 from . import gx, synth
-from .warmstart import compare_starts, gamma_for_battery_cost, make_dataset, plan_path, train
+from .warmstart import compare_starts, gamma_for_battery_cost, make_dataset, plan_path, targets, train
 
 KAPPA = 50.0
 
@@ -30,7 +30,7 @@ def build(seed=1, S=16):
     return nets, scens, net
 
 
-def test_pairs(net, nets, n_pairs, seed=1000, steps=6, alpha_frac=2e-2):
+def test_pairs(net, nets, n_pairs, seed=1000, steps=10, alpha_frac=4e-2):
     rng = np.random.default_rng(seed)
     dev = net.device
     eta_min = torch.tensor(nets[0]["eta_min"], dtype=torch.float32, device=dev)
@@ -38,9 +38,9 @@ def test_pairs(net, nets, n_pairs, seed=1000, steps=6, alpha_frac=2e-2):
     T = net.info[0]["T"]
     pairs = []
     for k in range(n_pairs):
-        c = float(rng.uniform(112.5, 387.5))
+        c = float(rng.uniform(175.0, 325.0))
         ends = []
-        for cc in (c, c + (25.0 if rng.random() < 0.5 else -25.0)):
+        for cc in (c, c + (75.0 if rng.random() < 0.5 else -75.0)):
             gamma = torch.tensor(gamma_for_battery_cost(nets[0], cc, T), dtype=torch.float32, device=dev)
             g0 = torch.zeros_like(eta_min)
             net.solve(eta_min, warm="cold")
@@ -84,7 +84,16 @@ def main(argv=None):
     for mode in ("cold", "prev", "learned"):
         summ[mode] = {k: float(np.median([r[mode][k] for r in rows])) for k in ("fwd", "adj", "ms")}
     wins = sum(1 for r in rows if r["learned"]["fwd"] + r["learned"]["adj"] < r["prev"]["fwd"] + r["prev"]["adj"])
+    # prediction error on held-out plans (the first scenario-hours of each test plan)
+    errs = []
+    for _, _, eta_b in pairs:
+        net.solve(eta_b, warm="cold")
+        tgt = targets(net)
+        pred = gnn.predict(eta_b)
+        M = tgt.numel() // 2
+        errs.append(float(torch.sqrt(torch.mean((pred[:M].clamp(0, 200) - tgt[:M]) ** 2))))
     rep = dict(samples=len(samples), data_s=t_data, train_s=t_train, loss_first=hist[0], loss_last=hist[-1],
+               price_rmse_test=float(np.median(errs)),
                pairs=len(rows), kinds=[k for k, _, _ in pairs], median=summ, learned_beats_prev=wins, rows=rows)
     print(json.dumps({k: v for k, v in rep.items() if k != "rows"}), flush=True)
     if args.report:

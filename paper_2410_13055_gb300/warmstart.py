@@ -27,7 +27,9 @@ def gamma_for_battery_cost(net, cost_per_kwh, T):
 def targets(net: gx.Network):
     """[prices | angles] of the last solve in the warm-start layout; angles relative to
     bus 0 of each scenario-hour (the solver's angles are defined up to that constant)."""
-    price = net.array("price").clone()
+    # prices clipped to [0, 200] $/MWh: the rare value-of-lost-load hours would dominate
+    # the squared error; a warm start needs the ordinary price level right
+    price = net.array("price").clone().clamp_(0.0, 200.0)
     theta = net.array("theta").clone()
     for s, inf in enumerate(net.info):
         off = sum(i["N"] * i["Tp"] for i in net.info[:s])

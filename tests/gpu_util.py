@@ -47,19 +47,3 @@ def rel(a, b):
     a = np.asarray(a, float); b = np.asarray(b, float)
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
 
-
-def kink_devices(ref, mult_tol=0.5, slack_tol=1e-4):
-    """Plan entries whose derivative is not unique at the oracle solution: a device
-    with a weakly active bound (multiplier below mult_tol, $/MWh) or a bound that is
-    almost tight but inactive.  At such a kink the one-sided derivatives differ."""
-    qp = ref.qp
-    bad = set()
-    hscale = np.maximum(1.0, np.abs(qp.h))
-    for i, tag in enumerate(qp.kind):
-        if tag is None or qp.D[i].nnz == 0:
-            continue
-        weak = (ref.z[i] > ref.s[i]) and ref.z[i] < mult_tol
-        near = (ref.z[i] <= ref.s[i]) and ref.s[i] < slack_tol * hscale[i]
-        if weak or near:
-            bad.update(qp.D[i].indices.tolist())
-    return np.array(sorted(bad), dtype=np.int64)
