@@ -115,9 +115,9 @@ def compare_starts(net, gnn, pairs):
             else:
                 net.solve(eta_b, warm=mode)
             it_f = net.last_stats["iters_max"]
-            # the network predicts the dispatch only; its adjoint continues from the
-            # previous plan's adjoint state like the previous-plan start's does
-            net.grad(eta_b, warm="cold" if mode == "cold" else "prev")
+            # every start's adjoint begins at the negated forward duals (exact for the
+            # h = c part; measured faster than the previous plan's adjoint state)
+            net.grad(eta_b, warm="cold")
             torch.cuda.synchronize()
             r[mode] = dict(fwd=it_f, adj=net.last_grad_stats["iters_max"],
                            ms=1e3 * (time.perf_counter() - t0))
