@@ -184,9 +184,9 @@ def run_gx(args):
 
     def step(warm):
         rc = net.solve(eta, warm=warm)
-        # the adjoint always starts from the negated forward duals (exact for the h = c
-        # part); measured faster than continuing the previous plan's adjoint state
-        net.grad(eta, out=grad, warm="cold")
+        # previous-plan adjoint state for the small steps of a plan loop (measured faster
+        # than the negated-forward-dual start there; the latter wins after large changes)
+        net.grad(eta, out=grad, warm="cold" if warm == "cold" else "prev")
         if dist is not None and args.config == "medium":
             # the one collective of a plan step: sum the ranks' partial gradients
             from paper_2410_13055_gb300.sharding import allreduce_sum
@@ -254,7 +254,7 @@ def run_gx(args):
             gnn.predict(eta_l, out=wbuf)
             net.solve(eta_l, warm="user", warm_prices=wbuf[:Mh], warm_angles=wbuf[Mh:])
             it_l.append(net.last_stats["iters_max"])
-            net.grad(eta_l, out=grad, warm="cold")
+            net.grad(eta_l, out=grad, warm="prev")
             net.plan_step(eta_l, grad, gamma, eta_min, eta_max, state["alpha"])
             b.record()
             torch.cuda.synchronize()
@@ -283,7 +283,7 @@ def run_gx(args):
     for _ in range(args.steps):
         eta.copy_(eta_h, non_blocking=True)
         net.solve(eta, warm="prev")
-        net.grad(eta, out=grad, warm="cold")
+        net.grad(eta, out=grad, warm="prev")
         net.plan_step(eta, grad, gamma, eta_min, eta_max, state["alpha"])
         eta_h.copy_(eta, non_blocking=True)
         grad_h.copy_(grad, non_blocking=True)
@@ -314,7 +314,7 @@ def run_gx(args):
         for _ in range(args.steps):
             for (nt, sl), e, g in zip(singles, e_s, g_s):
                 nt.solve(e, warm="prev")
-                nt.grad(e, out=g, warm="cold")
+                nt.grad(e, out=g, warm="prev")
                 nt.plan_step(e, g, gamma[sl].contiguous(), eta_min[sl].contiguous(), eta_max[sl].contiguous(),
                              state["alpha"])
         b.record()
@@ -359,7 +359,7 @@ def run_gx(args):
         "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.config, "scenarios": len(scens), "device_hours_per_step": dh,
-                   "start": "prev (previous plan's dispatch state; adjoint from the negated forward duals)",
+                   "start": "prev (previous plan's dispatch and adjoint state)",
                    "kappa": KAPPA,
                    "tol": 1e-3, "l2": "256 MB buffer written between steps, outside the per-step events",
                    "parallelism": f"replicas x{ws} (independent scenario shards)"},

@@ -433,7 +433,7 @@ gx_status gx_network_create(const gx_network_desc* nets, int n_nets, const gx_sc
         for (int b = 0; b < sd.bus_nblk; ++b) net->bus_blk_scen.push_back(s);
         net->n_bus_blk += sd.bus_nblk;
         sd.line_blk0 = net->n_line_blk;
-        sd.line_nblk = (int)(((long long)h.L * sh.Tp + kBlock - 1) / kBlock);
+        sd.line_nblk = (int)(((long long)h.L * sh.Tp + kBlock * kLineItems - 1) / (kBlock * kLineItems));
         for (int b = 0; b < sd.line_nblk; ++b) net->line_blk_scen.push_back(s);
         net->n_line_blk += sd.line_nblk;
         sd.bat_w0 = net->n_bat_warps;

@@ -77,6 +77,87 @@ __device__ __forceinline__ StatePtrs state(const Ctx& c) {
 //   rho/2 [(-beta d - v_f)^2 + (beta d - v_t)^2] + rho_th/4 (d - (w_f - w_t))^2
 // over |beta d| <= eta_l, |d| <= dtheta_max, i.e. the unconstrained minimiser clipped.
 // ------------------------------------------------------------------------------------
+// One line-hour of the line prox (all modes).  FWD/ADJ callers pass the loaded state
+// so two items per thread can have all their loads in flight before any store.
+struct LineIn {
+    long long row, bf, bt;
+    int lg, l;
+    bool valid;
+    float d, g, qf, qt, pbf, uf, zf, pbt, ut, zt, beta, w, capf, dth;
+    uint8_t mask;
+};
+
+template <int MODE, int ADJ>
+__device__ __forceinline__ void line_index(const Ctx& c, const ScenDev& sc, int local, LineIn& L) {
+    L.l = local / sc.Tp;
+    const int t = local - L.l * sc.Tp;
+    L.valid = (L.l < sc.L) && (t < sc.T);
+    if (!L.valid) return;
+    L.row = sc.e_line + (long long)L.l * sc.Tp + t;
+    L.lg = sc.line0 + L.l;
+    L.bf = sc.e_bus + (long long)c.l_from[L.lg] * sc.Tp + t;
+    L.bt = sc.e_bus + (long long)c.l_to[L.lg] * sc.Tp + t;
+}
+
+template <int MODE, int ADJ>
+__device__ __forceinline__ void line_load(const Ctx& c, const ScenDev& sc, const StatePtrs& X, LineIn& L) {
+    if (!L.valid) return;
+    L.d = X.dl[L.row]; L.g = X.sg[L.row]; L.qf = X.vf[L.row]; L.qt = X.vt[L.row];
+    L.pbf = X.pbar[L.bf]; L.uf = X.u[L.bf]; L.zf = X.thb[L.bf];
+    L.pbt = X.pbar[L.bt]; L.ut = X.u[L.bt]; L.zt = X.thb[L.bt];
+    L.beta = c.l_beta[L.lg]; L.w = c.l_w[L.lg]; L.dth = c.l_dth[L.lg];
+    L.capf = fmaxf(c.eta[sc.eta0 + sc.G + L.l], 0.f) / L.beta;
+    L.mask = ADJ ? c.m_line[L.row] : 0;
+}
+
+// Phase consensus in exact ADMM form: the line keeps q_j = y_j + v_j (terminal phase
+// plus its scaled dual); the bus value z is the weighted mean of the q_j, so the duals
+// v_j = q_j - z keep a zero weighted sum at every bus even under rounding.
+template <int MODE, int ADJ>
+__device__ __forceinline__ void line_compute(const Ctx& c, const StatePtrs& X, const LineIn& L, float& dx2,
+                                             float& x2, float& th2) {
+    if (!L.valid) return;
+    const float beta = L.beta, d = L.d, g = L.g;
+    const float vf = L.qf - L.zf, vt = L.qt - L.zt;
+    const float ef = 0.5f * (g + d) - L.zf, et = 0.5f * (g - d) - L.zt;  // y - z of the last iteration
+    th2 += beta * beta * (ef * ef + et * et);
+    const float wf = L.zf - vf, wt = L.zt - vt;
+    const float tf = -beta * d - L.pbf - L.uf;  // power targets of the two terminals
+    const float tt = beta * d - L.pbt - L.ut;
+    const float rth = c.rth_c * L.w;
+    const float den = 2.f * c.rho * beta * beta + 0.5f * rth;
+    const float dun = (c.rho * beta * (tt - tf) + 0.5f * rth * (wf - wt)) / den;
+    const float cap = fminf(L.capf, L.dth);
+    if (MODE == M_MASK) {
+        uint8_t code = AL_FREE;
+        const float over = fabsf(dun) - cap;
+        if (over > 0.f && den * over / beta > c.tol_act) {
+            const bool flow = L.capf <= L.dth;
+            code = dun > 0.f ? (flow ? AL_FUP : AL_AUP) : (flow ? AL_FLO : AL_ALO);
+        }
+        c.m_line[L.row] = code;
+        return;
+    }
+    float dn;
+    if (ADJ) dn = L.mask ? 0.f : dun;
+    else dn = clampf(dun, -cap, cap);
+    const float gn = wf + wt;
+    X.dl[L.row] = dn;
+    X.sg[L.row] = gn;
+    X.vf[L.row] = 0.5f * (gn + dn) + vf;
+    X.vt[L.row] = 0.5f * (gn - dn) + vt;
+    const float dd = dn - d;
+    dx2 += 2.f * beta * beta * dd * dd;
+    x2 += 2.f * beta * beta * dn * dn;
+}
+
+// ------------------------------------------------------------------------------------
+// Line prox.  With delta = th_f - th_t and sigma = th_f + th_t the prox of a lossless DC
+// line separates: sigma = w_f + w_t, and delta minimises the 1-D quadratic
+//   rho/2 [(-beta d - v_f)^2 + (beta d - v_t)^2] + rho_th/4 (d - (w_f - w_t))^2
+// over |beta d| <= eta_l, |d| <= dtheta_max, i.e. the unconstrained minimiser clipped.
+// Each thread handles kLineItems line-hours of its block.
+// ------------------------------------------------------------------------------------
 template <int MODE, int ADJ>
 __global__ void __launch_bounds__(kBlock) k_line(const Ctx c, int want_res) {
     const int blk = blockIdx.x;
@@ -84,77 +165,38 @@ __global__ void __launch_bounds__(kBlock) k_line(const Ctx c, int want_res) {
     if (c.done[s]) return;
     const ScenDev sc = c.scen[s];
     const StatePtrs X = state<ADJ>(c);
-    const int local = (blk - sc.line_blk0) * kBlock + threadIdx.x;
-    const int l = local / sc.Tp;
-    const int t = local - l * sc.Tp;
-    const bool valid = (l < sc.L) && (t < sc.T);
+    const int base = (blk - sc.line_blk0) * kBlock * kLineItems + threadIdx.x;
     float dx2 = 0.f, x2 = 0.f, th2 = 0.f;
-    if (valid) {
-        const long long row = sc.e_line + (long long)l * sc.Tp + t;
-        const int lg = sc.line0 + l;
-        const int f = c.l_from[lg], to = c.l_to[lg];
-        const float beta = c.l_beta[lg];
-        const long long bf = sc.e_bus + (long long)f * sc.Tp + t;
-        const long long bt = sc.e_bus + (long long)to * sc.Tp + t;
-        if (MODE == M_RESET) {
+    if (MODE == M_RESET) {
+        for (int r = 0; r < kLineItems; ++r) {
+            LineIn L;
+            line_index<MODE, ADJ>(c, sc, base + r * kBlock, L);
+            if (!L.valid) continue;
             float d0 = 0.f, g0 = 0.f, q0f = 0.f, q0t = 0.f;
             if (!ADJ && c.warm) {
                 const float* th = c.warm + c.warm_half;
-                d0 = th[bf] - th[bt];
-                g0 = th[bf] + th[bt];
-                q0f = th[bf];
-                q0t = th[bt];
+                d0 = th[L.bf] - th[L.bt];
+                g0 = th[L.bf] + th[L.bt];
+                q0f = th[L.bf];
+                q0t = th[L.bt];
             }
             if (ADJ && c.adj_from_fwd) {
                 // h = c part of the adjoint: phase duals are the negated forward ones
                 // (scaled duals convert with rho_f / rho_a); adjoint phases start at 0
-                q0f = -c.rho_ratio * (c.vf[row] - c.thb[bf]);
-                q0t = -c.rho_ratio * (c.vt[row] - c.thb[bt]);
+                q0f = -c.rho_ratio * (c.vf[L.row] - c.thb[L.bf]);
+                q0t = -c.rho_ratio * (c.vt[L.row] - c.thb[L.bt]);
             }
-            X.dl[row] = d0; X.sg[row] = g0; X.vf[row] = q0f; X.vt[row] = q0t;
-        } else {
-            // Phase consensus in exact ADMM form: the line keeps q_j = y_j + v_j (terminal
-            // phase plus its scaled dual); the bus value z is the weighted mean of the q_j,
-            // so the duals v_j = q_j - z keep a zero weighted sum at every bus even under
-            // rounding.
-            const float d = X.dl[row], g = X.sg[row];
-            const float pbf = X.pbar[bf], uf = X.u[bf], zf = X.thb[bf];
-            const float pbt = X.pbar[bt], ut = X.u[bt], zt = X.thb[bt];
-            const float vf = X.vf[row] - zf, vt = X.vt[row] - zt;
-            const float ef = 0.5f * (g + d) - zf, et = 0.5f * (g - d) - zt;  // y - z of the last iteration
-            th2 = beta * beta * (ef * ef + et * et);
-            const float wf = zf - vf, wt = zt - vt;
-            const float tf = -beta * d - pbf - uf;  // power targets of the two terminals
-            const float tt = beta * d - pbt - ut;
-            const float rth = c.rth_c * c.l_w[lg];
-            const float den = 2.f * c.rho * beta * beta + 0.5f * rth;
-            const float dun = (c.rho * beta * (tt - tf) + 0.5f * rth * (wf - wt)) / den;
-            const float etal = fmaxf(c.eta[sc.eta0 + sc.G + l], 0.f);
-            const float capf = etal / beta, dth = c.l_dth[lg];
-            const float cap = fminf(capf, dth);
-            if (MODE == M_MASK) {
-                uint8_t code = AL_FREE;
-                const float over = fabsf(dun) - cap;
-                if (over > 0.f && den * over / beta > c.tol_act) {
-                    const bool flow = capf <= dth;
-                    code = dun > 0.f ? (flow ? AL_FUP : AL_AUP) : (flow ? AL_FLO : AL_ALO);
-                }
-                c.m_line[row] = code;
-            } else {
-                float dn;
-                if (ADJ) dn = c.m_line[row] ? 0.f : dun;
-                else dn = clampf(dun, -cap, cap);
-                const float gn = wf + wt;
-                X.dl[row] = dn;
-                X.sg[row] = gn;
-                X.vf[row] = 0.5f * (gn + dn) + vf;
-                X.vt[row] = 0.5f * (gn - dn) + vt;
-                const float dd = dn - d;
-                dx2 = 2.f * beta * beta * dd * dd;
-                x2 = 2.f * beta * beta * dn * dn;
-            }
+            X.dl[L.row] = d0; X.sg[L.row] = g0; X.vf[L.row] = q0f; X.vt[L.row] = q0t;
         }
+        return;
     }
+    LineIn L[kLineItems];
+#pragma unroll
+    for (int r = 0; r < kLineItems; ++r) line_index<MODE, ADJ>(c, sc, base + r * kBlock, L[r]);
+#pragma unroll
+    for (int r = 0; r < kLineItems; ++r) line_load<MODE, ADJ>(c, sc, X, L[r]);
+#pragma unroll
+    for (int r = 0; r < kLineItems; ++r) line_compute<MODE, ADJ>(c, X, L[r], dx2, x2, th2);
     if ((MODE == M_FWD || MODE == M_ADJ) && want_res) {
         __shared__ float sh[3][kBlock / 32];
         float v[3] = {dx2, x2, th2};
@@ -755,11 +797,13 @@ __global__ void __launch_bounds__(kBlock) k_extract(const Ctx c) {
         const int blk = blockIdx.x - c.n_bus_blk;
         const int s = c.line_blk_scen[blk];
         const ScenDev sc = c.scen[s];
-        const int local = (blk - sc.line_blk0) * kBlock + threadIdx.x;
-        if (local >= sc.L * sc.Tp) return;
-        const int l = local / sc.Tp;
-        const long long i = sc.e_line + local;
-        c.out_flow[i] = c.l_beta[sc.line0 + l] * c.dl[i];
+        for (int r = 0; r < kLineItems; ++r) {
+            const int local = (blk - sc.line_blk0) * kBlock * kLineItems + r * kBlock + threadIdx.x;
+            if (local >= sc.L * sc.Tp) return;
+            const int l = local / sc.Tp;
+            const long long i = sc.e_line + local;
+            c.out_flow[i] = c.l_beta[sc.line0 + l] * c.dl[i];
+        }
     }
 }
 
