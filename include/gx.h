@@ -206,15 +206,28 @@ gx_status gx_plan_step(gx_network* net, float* eta_dev, const float* grad_dev, c
  * one by one (off).  Results are identical; graphs cut the host launch cost. */
 gx_status gx_network_use_graphs(gx_network* net, int on);
 
+/* Cluster-resident solver (default off).  A scenario whose state fits the shared memory
+ * of a thread-block cluster (1 to 16 CTAs; each CTA holds every device for a range of
+ * hours, batteries exchange their hours over distributed shared memory) runs its whole
+ * forward or adjoint loop in one persistent launch that tests its own convergence.
+ * Other scenarios, and all of them while this is off, run on the per-iteration kernels.
+ * The two paths take the same iterates up to the summation order of the residual
+ * partials (so possibly a different stopping chunk). */
+gx_status gx_network_use_persistent(gx_network* net, int on);
+/* *cluster_ctas: CTAs of the cluster scenario `scen` runs on, 0 if it runs on the
+ * per-iteration kernels (not resident, not launchable on this device, or switched off). */
+gx_status gx_network_persistent_info(const gx_network* net, int scen, int* cluster_ctas);
+
 /* Sampled kernel timing.  While enabled, the solve and gradient loops record CUDA
  * events on their stream around the bus, line and battery kernels of the last
  * iteration of every residual-check chunk and accumulate the elapsed times at the
- * chunk's synchronisation.  Kinds: 0 = bus kernel, 1 = line kernel, 2 = battery
- * kernel.  Enabling resets the counters.  Uses three CUDA events per kind (created
- * here, no device memory). */
+ * chunk's synchronisation, and around each call's cluster-resident launches.  Kinds:
+ * 0 = bus kernel, 1 = line kernel, 2 = battery kernel, 3 = cluster-resident launches
+ * (all of them timed).  Enabling resets the counters.  Uses four CUDA events (created
+ * here, no device memory); timing synchronises the stream after resident launches. */
 gx_status gx_profile_enable(gx_network* net, int on);
-/* ms[k]: summed event time of the sampled launches of kind k; samples[k]: how many
- * were sampled; launches[k]: all launches of kind k since enabling. */
+/* Arrays of 4.  ms[k]: summed event time of the sampled launches of kind k; samples[k]:
+ * how many were sampled; launches[k]: all launches of kind k since enabling. */
 gx_status gx_profile_read(const gx_network* net, double* ms, long long* samples, long long* launches);
 
 /* ------------------------------------------------------------------------------

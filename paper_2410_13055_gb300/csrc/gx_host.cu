@@ -6,6 +6,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -64,11 +66,30 @@ struct gx_network {
     std::vector<ScenH> scens;
     std::vector<ScenDev> sdev;
     std::vector<int> bus_blk_scen, line_blk_scen, bat_warp_scen, cost_blk_scen, gwarp, k_net;
+    std::vector<BusBlk> bus_blk;       // bus-kernel block records (single-hour kernel)
+    std::vector<BusBlk> bus4_blk;      // bus-kernel block records (hour-quad kernel)
+    std::vector<int> line4_blk_scen;   // scenario of each hour-quad line block
+    int n_bus4_blk = 0, n_line4_blk = 0;
+    std::vector<int> pool;             // their pool records (words)
+    std::vector<int2> prep;            // (pool word, eta index) of each generator plan value
+    std::vector<uint8_t> firm;         // generator has capacity factor 1 in every hour of every scenario
+    // cluster-resident solver: scenarios grouped by (cluster size, hours per battery lane)
+    struct CrsGroup {
+        int C = 0, hpl = 0, first = 0, n = 0;
+        size_t smem = 0;
+        bool ok = false;  // launchable on this device (checked at bind)
+    };
+    std::vector<CrsGroup> crs_groups;
+    std::vector<int> crs_list;         // scenario indices, group by group
+    std::vector<int> crs_group;        // per scenario: its group, -1 = per-iteration kernels only
+    std::vector<int> done_loop;        // done flags of the per-iteration loop (cluster-resident ones set)
+    bool use_crs = false;
     long long bus_el = 0, gen_el = 0, line_el = 0, bat_el = 0;
     int n_bus_blk = 0, n_line_blk = 0, n_bat_warps = 0, n_cost_blk = 0, n_gwarps = 0, gs_total = 0;
     int tot_gen = 0, tot_line = 0, tot_bat = 0, tot_bus = 0, tot_ptr = 0;
     // workspace offsets
-    size_t o_scen, o_bbs, o_lbs, o_bws, o_cbs, o_gwarp, o_knet;
+    size_t o_scen, o_bbs, o_lbs, o_bws, o_cbs, o_gwarp, o_knet, o_busblk, o_pool, o_prep, o_crs;
+    size_t o_bus4blk, o_l4bs;
     size_t o_gbus, o_gcost, o_gemis, o_gfirm, o_lfrom, o_lto, o_lbeta, o_ldth, o_lw, o_bbus, o_bdur, o_beffc, o_beffd;
     size_t o_gptr, o_gidx, o_bptr, o_bidx, o_eptr, o_eidx, o_icnt, o_iwsum, o_dresw;
     size_t o_load, o_cf, o_dd, o_add;
@@ -106,8 +127,8 @@ struct gx_network {
     // sampled kernel timing
     bool prof = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-    double prof_ms[3] = {0, 0, 0};
-    long long prof_samples[3] = {0, 0, 0}, prof_launches[3] = {0, 0, 0};
+    double prof_ms[4] = {0, 0, 0, 0};
+    long long prof_samples[4] = {0, 0, 0, 0}, prof_launches[4] = {0, 0, 0, 0};
     ~gx_network() {
         for (auto& e : ev)
             if (e) cudaEventDestroy(e);
@@ -175,6 +196,14 @@ static void make_ctx(gx_network* net) {
     c.check_every = o.check_every;
     c.scen = reinterpret_cast<const ScenDev*>(d + net->o_scen);
     c.bus_blk_scen = I(net->o_bbs);
+    c.bus_blk = reinterpret_cast<const BusBlk*>(d + net->o_busblk);
+    c.bus4_blk = reinterpret_cast<const BusBlk*>(d + net->o_bus4blk);
+    c.line4_blk_scen = I(net->o_l4bs);
+    c.n_bus4_blk = net->n_bus4_blk;
+    c.n_line4_blk = net->n_line4_blk;
+    c.pool = I(net->o_pool);
+    c.prep = reinterpret_cast<const int2*>(d + net->o_prep);
+    c.n_prep = (int)net->prep.size();
     c.line_blk_scen = I(net->o_lbs);
     c.bat_warp_scen = I(net->o_bws);
     c.cost_blk_scen = I(net->o_cbs);
@@ -321,6 +350,140 @@ static void derive_network(NetH& h, const gx_opts& o) {
     }
 }
 
+// Cluster-resident groups.  A scenario takes the smallest cluster (1, 2, 4, 8 or 16 CTAs)
+// whose per-CTA shared-memory image fits kCrsSmemBudget; scenarios that fit none run on
+// the per-iteration kernels.  Scenarios with the same cluster size and battery lane
+// width form one launch, sized for the largest image among them.
+constexpr size_t kCrsSmemBudget = 200 * 1024;
+
+static int crs_hpl_bucket(int T) {
+    const int h = (T + 31) / 32;
+    return h <= 1 ? 1 : h <= 2 ? 2 : h <= 3 ? 3 : h <= 6 ? 6 : 8;
+}
+
+static void build_crs_groups(gx_network* net) {
+    net->crs_groups.clear();
+    net->crs_list.clear();
+    net->crs_group.assign(net->S, -1);
+    std::map<std::pair<int, int>, std::vector<int>> by;
+    std::map<std::pair<int, int>, size_t> smem;
+    for (int s = 0; s < net->S; ++s) {
+        const ScenDev& sd = net->sdev[s];
+        for (int C = 1; C <= kCrsMaxC; C *= 2) {
+            const int H = (sd.T + C - 1) / C, nbo = (sd.B + C - 1) / C;
+            const size_t bytes = crs_offsets(sd.N, sd.G, sd.L, sd.B, H, nbo, sd.T).total;
+            if (bytes <= kCrsSmemBudget) {
+                const auto key = std::make_pair(C, crs_hpl_bucket(sd.T));
+                by[key].push_back(s);
+                smem[key] = std::max(smem[key], bytes);
+                break;
+            }
+        }
+    }
+    for (auto& kv : by) {
+        gx_network::CrsGroup g;
+        g.C = kv.first.first;
+        g.hpl = kv.first.second;
+        g.first = (int)net->crs_list.size();
+        g.n = (int)kv.second.size();
+        g.smem = smem[kv.first];
+        for (int s : kv.second) {
+            net->crs_group[s] = (int)net->crs_groups.size();
+            net->crs_list.push_back(s);
+        }
+        net->crs_groups.push_back(g);
+    }
+}
+
+// Bus-kernel block records and the pool records of the bus ranges they cover.  Blocks of
+// scenarios on the same network with the same bus range share one pool record.
+static void build_bus_blocks(gx_network* net) {
+    auto fbits = [](float f) { int w; std::memcpy(&w, &f, 4); return w; };
+    std::map<std::tuple<int, int, int>, std::pair<int, int>> rec_of;  // (net, n0, n1) -> (offset, words)
+    net->bus_blk.clear();
+    net->bus4_blk.clear();
+    net->pool.clear();
+    net->prep.clear();
+    for (int quad = 0; quad < 2; ++quad)
+    for (int s = 0; s < net->S; ++s) {
+        const ScenDev& sd = net->sdev[s];
+        const NetH& h = net->nets[sd.net];
+        const int per_bus = quad ? sd.Tp / 4 : sd.Tp;  // items per bus row
+        const long long nitems = (long long)sd.N * per_bus;
+        const int nblk = quad ? sd.bus4_nblk : sd.bus_nblk;
+        for (int b = 0; b < nblk; ++b) {
+            BusBlk r{};
+            r.e_bus = sd.e_bus; r.e_gen = sd.e_gen; r.e_line = sd.e_line; r.e_bat = sd.e_bat;
+            r.s = s;
+            r.item0 = b * kBlock;
+            const int last = (int)std::min<long long>((long long)r.item0 + kBlock, nitems) - 1;
+            r.n0 = r.item0 / per_bus;
+            const int n1 = last / per_bus;
+            r.Tp = sd.Tp; r.T = sd.T; r.nitems = (int)nitems;
+            const auto key = std::make_tuple(sd.net, r.n0, n1);
+            auto it = rec_of.find(key);
+            if (it == rec_of.end()) {
+                const int nbus = n1 - r.n0 + 1;
+                const int gb = h.gptr[r.n0], gcnt = h.gptr[n1 + 1] - gb;
+                const int eb = h.eptr[r.n0], ecnt = h.eptr[n1 + 1] - eb;
+                const int bb = h.bptr[r.n0], bcnt = h.bptr[n1 + 1] - bb;
+                int o[kPoolHdr] = {};
+                int w = kPoolHdr;
+                o[kPH_GP] = w; w += nbus + 1;
+                o[kPH_EP] = w; w += nbus + 1;
+                o[kPH_BP] = w; w += nbus + 1;
+                o[kPH_IC] = w; w += nbus;
+                o[kPH_IW] = w; w += nbus;
+                o[kPH_DR] = w; w += nbus;
+                o[kPH_GROW] = w; w += gcnt;
+                o[kPH_GCOST] = w; w += gcnt;
+                o[kPH_GEMIS] = w; w += gcnt;
+                o[kPH_GFIRM] = w; w += gcnt;
+                o[kPH_GETA] = w; w += gcnt;
+                o[kPH_ECODE] = w; w += ecnt;
+                o[kPH_EBETA] = w; w += ecnt;
+                o[kPH_EW] = w; w += ecnt;
+                o[kPH_BROW] = w; w += bcnt;
+                const int words = (w + 3) / 4 * 4;
+                o[kPH_NBUS] = nbus; o[kPH_GCNT] = gcnt; o[kPH_ECNT] = ecnt; o[kPH_BCNT] = bcnt;
+                const int off = (int)net->pool.size();
+                net->pool.resize(net->pool.size() + words, 0);
+                int* p = net->pool.data() + off;
+                std::memcpy(p, o, sizeof(o));
+                for (int k = 0; k <= nbus; ++k) {
+                    p[o[kPH_GP] + k] = h.gptr[r.n0 + k] - gb;
+                    p[o[kPH_EP] + k] = h.eptr[r.n0 + k] - eb;
+                    p[o[kPH_BP] + k] = h.bptr[r.n0 + k] - bb;
+                }
+                for (int k = 0; k < nbus; ++k) {
+                    p[o[kPH_IC] + k] = fbits(h.inv_cnt[r.n0 + k]);
+                    p[o[kPH_IW] + k] = fbits(h.inv_wsum[r.n0 + k]);
+                    p[o[kPH_DR] + k] = fbits(h.dres_w[r.n0 + k]);
+                }
+                for (int k = 0; k < gcnt; ++k) {
+                    const int g = h.gidx[gb + k];
+                    p[o[kPH_GROW] + k] = g;
+                    p[o[kPH_GCOST] + k] = fbits((float)h.gen_cost[g]);
+                    p[o[kPH_GEMIS] + k] = fbits((float)h.gen_emis[g]);
+                    p[o[kPH_GFIRM] + k] = net->firm[h.gen0 + g];
+                    net->prep.push_back(int2{off + o[kPH_GETA] + k, h.eta0 + g});
+                }
+                for (int k = 0; k < ecnt; ++k) {
+                    const int e = h.eidx[eb + k];
+                    p[o[kPH_ECODE] + k] = e;
+                    p[o[kPH_EBETA] + k] = fbits((float)h.line_beta[e >> 1]);
+                    p[o[kPH_EW] + k] = fbits(h.l_w[e >> 1]);
+                }
+                for (int k = 0; k < bcnt; ++k) p[o[kPH_BROW] + k] = h.bidx[bb + k];
+                it = rec_of.emplace(key, std::make_pair(off, words)).first;
+            }
+            r.pool = it->second.first;
+            r.words = it->second.second;
+            (quad ? net->bus4_blk : net->bus_blk).push_back(r);
+        }
+    }
+}
+
 gx_status gx_network_create(const gx_network_desc* nets, int n_nets, const gx_scenario_desc* scen, int S,
                             const gx_opts* opts, gx_network** out) {
     if (!out) return fail(GX_ERR_INVALID_ARG, "out is NULL");
@@ -436,6 +599,13 @@ gx_status gx_network_create(const gx_network_desc* nets, int n_nets, const gx_sc
         sd.line_nblk = (int)(((long long)h.L * sh.Tp + kBlock * kLineItems - 1) / (kBlock * kLineItems));
         for (int b = 0; b < sd.line_nblk; ++b) net->line_blk_scen.push_back(s);
         net->n_line_blk += sd.line_nblk;
+        sd.bus4_blk0 = net->n_bus4_blk;
+        sd.bus4_nblk = (int)(((long long)h.N * (sh.Tp / 4) + kBlock - 1) / kBlock);
+        net->n_bus4_blk += sd.bus4_nblk;
+        sd.line4_blk0 = net->n_line4_blk;
+        sd.line4_nblk = (int)(((long long)h.L * (sh.Tp / 4) + kBlock - 1) / kBlock);
+        for (int b = 0; b < sd.line4_nblk; ++b) net->line4_blk_scen.push_back(s);
+        net->n_line4_blk += sd.line4_nblk;
         sd.bat_w0 = net->n_bat_warps;
         for (int b = 0; b < h.B; ++b) net->bat_warp_scen.push_back(s);
         net->n_bat_warps += h.B;
@@ -449,6 +619,17 @@ gx_status gx_network_create(const gx_network_desc* nets, int n_nets, const gx_sc
     }
     net->gs_total = gs;
     net->bus_el = eb; net->gen_el = eg; net->line_el = el; net->bat_el = ebt;
+    // generators whose capacity factor is 1 in every hour of every scenario skip the cf read
+    net->firm.assign(std::max(net->tot_gen, 1), 1);
+    for (int s = 0; s < S; ++s) {
+        const ScenH& sc = net->scens[s];
+        const NetH& n = net->nets[sc.net];
+        for (int g = 0; g < n.G; ++g)
+            for (int t = 0; t < sc.T; ++t)
+                if (sc.cf[(size_t)g * sc.Tp + t] != 1.0f) { net->firm[n.gen0 + g] = 0; break; }
+    }
+    build_bus_blocks(net);
+    build_crs_groups(net);
     net->k_net.resize(K);
     for (int k = 0; k < n_nets; ++k)
         for (int q = 0; q < net->nets[k].G + net->nets[k].L + net->nets[k].B; ++q) net->k_net[net->nets[k].eta0 + q] = k;
@@ -466,6 +647,12 @@ gx_status gx_network_create(const gx_network_desc* nets, int n_nets, const gx_sc
     net->o_cbs = L.add(I4(net->n_cost_blk));
     net->o_gwarp = L.add(I4(2LL * net->n_gwarps));
     net->o_knet = L.add(I4(K));
+    net->o_busblk = L.add(sizeof(BusBlk) * std::max<size_t>(net->bus_blk.size(), 1));
+    net->o_pool = L.add(I4((long long)net->pool.size()));
+    net->o_prep = L.add(8 * std::max<size_t>(net->prep.size(), 1));
+    net->o_crs = L.add(I4((long long)net->crs_list.size()));
+    net->o_bus4blk = L.add(sizeof(BusBlk) * std::max<size_t>(net->bus4_blk.size(), 1));
+    net->o_l4bs = L.add(I4(net->n_line4_blk));
     net->o_gbus = L.add(I4(gen0)); net->o_gcost = L.add(F4(gen0)); net->o_gemis = L.add(F4(gen0));
     net->o_gfirm = L.add(B1(gen0));
     net->o_lfrom = L.add(I4(line0)); net->o_lto = L.add(I4(line0)); net->o_lbeta = L.add(F4(line0));
@@ -488,8 +675,8 @@ gx_status gx_network_create(const gx_network_desc* nets, int n_nets, const gx_sc
     net->o_resid = L.add(D8(2LL * S)); net->o_rbest = L.add(D8(S)); net->o_cost = L.add(D8(S)); net->o_h = L.add(D8(S));
     net->o_grads = L.add(D8(gs)); net->o_wprime = L.add(D8(S));
     net->o_flow = L.add(F4(el)); net->o_price = L.add(F4(eb)); net->o_shed = L.add(F4(eb));
-    net->o_bpart = L.add(F4((long long)net->n_bus_blk * kBusPart));
-    net->o_lpart = L.add(F4((long long)net->n_line_blk * kDevPart));
+    net->o_bpart = L.add(F4((long long)net->n_bus4_blk * kBusPart));
+    net->o_lpart = L.add(F4((long long)net->n_line4_blk * kDevPart));
     net->o_btpart = L.add(F4((long long)net->n_bat_warps * kDevPart));
     net->o_cpart = L.add(D8(2LL * net->n_cost_blk));
     net->in_batch.assign(S, 0);
@@ -526,6 +713,12 @@ gx_status gx_network_bind(gx_network* net, void* dev_mem, size_t bytes, void* st
     put(net->o_cbs, net->cost_blk_scen.data(), 4 * net->cost_blk_scen.size());
     put(net->o_gwarp, net->gwarp.data(), 4 * net->gwarp.size());
     put(net->o_knet, net->k_net.data(), 4 * net->k_net.size());
+    put(net->o_busblk, net->bus_blk.data(), sizeof(BusBlk) * net->bus_blk.size());
+    put(net->o_pool, net->pool.data(), 4 * net->pool.size());
+    put(net->o_prep, net->prep.data(), 8 * net->prep.size());
+    put(net->o_crs, net->crs_list.data(), 4 * net->crs_list.size());
+    put(net->o_bus4blk, net->bus4_blk.data(), sizeof(BusBlk) * net->bus4_blk.size());
+    put(net->o_l4bs, net->line4_blk_scen.data(), 4 * net->line4_blk_scen.size());
     auto put_f = [&](size_t off, const std::vector<double>& v, size_t base) {
         float* p = reinterpret_cast<float*>(h.data() + off) + base;
         for (size_t i = 0; i < v.size(); ++i) p[i] = (float)v[i];
@@ -547,18 +740,12 @@ gx_status gx_network_bind(gx_network* net, void* dev_mem, size_t bytes, void* st
         put_i(net->o_eptr, n.eptr, n.ptr0); put_i(net->o_eidx, n.eidx, 2 * (size_t)n.line0);
         put_v(net->o_icnt, n.inv_cnt, n.bus0); put_v(net->o_iwsum, n.inv_wsum, n.bus0); put_v(net->o_dresw, n.dres_w, n.bus0);
     }
-    // generators whose capacity factor is 1 in every hour of every scenario skip the cf read
-    std::vector<uint8_t> firm(std::max(net->tot_gen, 1), 1);
     for (int s = 0; s < net->S; ++s) {
         const ScenH& sc = net->scens[s];
-        const NetH& n = net->nets[sc.net];
         put_v(net->o_load, sc.load, net->sdev[s].e_bus);
         put_v(net->o_cf, sc.cf, net->sdev[s].e_gen);
-        for (int g = 0; g < n.G; ++g)
-            for (int t = 0; t < sc.T; ++t)
-                if (sc.cf[(size_t)g * sc.Tp + t] != 1.0f) { firm[n.gen0 + g] = 0; break; }
     }
-    put(net->o_gfirm, firm.data(), net->tot_gen);
+    put(net->o_gfirm, net->firm.data(), net->tot_gen);
     put_v(net->o_dd, net->dd_host, 0);
     put_v(net->o_add, net->add_host, 0);
     GX_CUDA(cudaMemcpyAsync(net->dev, h.data(), net->static_end, cudaMemcpyHostToDevice, st));
@@ -571,6 +758,12 @@ gx_status gx_network_bind(gx_network* net, void* dev_mem, size_t bytes, void* st
     if (!net->ev_fork) GX_CUDA(cudaEventCreateWithFlags(&net->ev_fork, cudaEventDisableTiming));
     if (!net->ev_join) GX_CUDA(cudaEventCreateWithFlags(&net->ev_join, cudaEventDisableTiming));
     make_ctx(net);
+    for (auto& g : net->crs_groups) {
+        g.ok = true;
+        for (int adj = 0; adj < 2 && g.ok; ++adj)
+            g.ok = crs_prepare(adj, g.hpl, g.C, g.smem) == cudaSuccess && crs_max_clusters(adj, g.hpl, g.C, g.smem) >= 1;
+        cudaGetLastError();
+    }
     net->solved = false;
     net->adj_ready = false;
     return GX_OK;
@@ -706,6 +899,54 @@ static gx_status chunk_graph(gx_network* net, const Ctx& c, int adj, int chunk, 
     return GX_OK;
 }
 
+static bool crs_on(const gx_network* net, int s) {
+    const int g = net->crs_group[s];
+    return net->use_crs && g >= 0 && net->crs_groups[g].ok;
+}
+
+// Run the batch's cluster-resident scenarios (one persistent launch per group) and set
+// up the done flags of the per-iteration loop so that it skips them.  *n_stream: the
+// batch's scenarios left for that loop.
+static gx_status run_crs(gx_network* net, int adj, cudaStream_t st, int* launches, int* n_stream) {
+    const Ctx& c = adj ? net->actx : net->ctx;
+    const double tol = adj ? net->opts.adj_tol : net->opts.tol;
+    std::vector<int> want(net->crs_groups.size(), 0);
+    int ns = 0, nc = 0;
+    for (int s = 0; s < net->S; ++s) {
+        if (!net->in_batch[s]) continue;
+        if (crs_on(net, s)) { want[net->crs_group[s]] = 1; ++nc; }
+        else ++ns;
+    }
+    *n_stream = ns;
+    if (nc == 0) return GX_OK;
+    const int* inb = reinterpret_cast<const int*>(net->dev + net->o_inb);
+    const int* list = reinterpret_cast<const int*>(net->dev + net->o_crs);
+    if (net->prof) GX_CUDA(cudaEventRecord(net->ev[0], st));
+    int nl = 0;
+    for (size_t k = 0; k < net->crs_groups.size(); ++k) {
+        const auto& g = net->crs_groups[k];
+        if (!want[k]) continue;
+        nl += launch_crs(c, adj, list + g.first, g.n, inb, g.C, g.hpl, g.smem, tol, st);
+    }
+    GX_CUDA(cudaGetLastError());
+    *launches += nl;
+    if (net->prof) {
+        GX_CUDA(cudaEventRecord(net->ev[1], st));
+        GX_CUDA(cudaEventSynchronize(net->ev[1]));
+        float ms = 0;
+        GX_CUDA(cudaEventElapsedTime(&ms, net->ev[0], net->ev[1]));
+        net->prof_ms[3] += ms;
+        net->prof_samples[3] += nl;
+        net->prof_launches[3] += nl;
+    }
+    if (ns > 0) {
+        net->done_loop.assign(net->S, 1);
+        for (int s = 0; s < net->S; ++s) net->done_loop[s] = (net->in_batch[s] && !crs_on(net, s)) ? 0 : 1;
+        GX_CUDA(cudaMemcpyAsync(net->dev + net->o_done, net->done_loop.data(), 4 * net->S, cudaMemcpyHostToDevice, st));
+    }
+    return GX_OK;
+}
+
 // Iterate the forward (adj = 0) or adjoint (adj = 1) message passing until every
 // scenario of the batch meets its tolerance or the cap is reached.  Each chunk of
 // check_every iterations is replayed as one CUDA graph; the stream is synchronised
@@ -827,15 +1068,17 @@ gx_status gx_dispatch_solve_batch(gx_network* net, const float* eta_dev, const i
     Ctx& c = net->ctx;
     c.eta = eta_dev;
     c.warm = warm == GX_WARM_USER ? warm_dev : nullptr;
-    int launches = 0;
+    int launches = launch_prep(c, st);
     if (warm != GX_WARM_PREV || !net->solved) {
         launches += launch_dev(c, M_RESET, 0, 0, st);
         launches += launch_bus(c, M_RESET, 0, 0, st);
         launches += launch_bus(c, M_INIT, 0, 0, st);
     }
     c.warm = nullptr;
-    int it = 0;
-    if (gx_status e = run_loop(net, 0, st, &launches, &it)) return e;
+    int it = 0, ns = 0;
+    if (gx_status e = run_crs(net, 0, st, &launches, &ns)) return e;
+    if (ns > 0)
+        if (gx_status e = run_loop(net, 0, st, &launches, &it)) return e;
     launches += launch_extract(c, reinterpret_cast<const int*>(net->dev + net->o_inb), st);
     GX_CUDA(cudaGetLastError());
     gx_status overall;
@@ -866,7 +1109,7 @@ gx_status gx_dispatch_grad_batch(gx_network* net, const float* eta_dev, int warm
     for (int s = 0; s < net->S; ++s) net->wprime[s] = net->in_batch[s] ? net->scens[s].weight * wall / wb : 0.0;
     GX_CUDA(cudaMemcpyAsync(net->dev + net->o_wprime, net->wprime.data(), 8 * net->S, cudaMemcpyHostToDevice, st));
     GX_CUDA(cudaMemcpyAsync(net->dev + net->o_done, net->done_init.data(), 4 * net->S, cudaMemcpyHostToDevice, st));
-    int launches = 0;
+    int launches = launch_prep(c, st);
     launches += launch_dev(c, M_MASK, 0, 0, st);
     launches += launch_bus(c, M_MASK, 0, 0, st);
     const bool envelope = net->opts.grad_envelope && net->opts.kappa == 0.0;
@@ -878,8 +1121,10 @@ gx_status gx_dispatch_grad_batch(gx_network* net, const float* eta_dev, int warm
             launches += launch_bus(ac, M_RESET, 1, 0, st);
         }
         launches += launch_bus(ac, M_INIT, 1, 0, st);
-        int it = 0;
-        if (gx_status e = run_loop(net, 1, st, &launches, &it)) return e;
+        int it = 0, ns = 0;
+        if (gx_status e = run_crs(net, 1, st, &launches, &ns)) return e;
+        if (ns > 0)
+            if (gx_status e = run_loop(net, 1, st, &launches, &it)) return e;
         net->adj_ready = true;
     }
     const int* inb = reinterpret_cast<const int*>(net->dev + net->o_inb);
@@ -916,18 +1161,31 @@ gx_status gx_network_use_graphs(gx_network* net, int on) {
     return GX_OK;
 }
 
+gx_status gx_network_use_persistent(gx_network* net, int on) {
+    if (!net) return fail(GX_ERR_INVALID_ARG, "net is NULL");
+    net->use_crs = on != 0;
+    return GX_OK;
+}
+
+gx_status gx_network_persistent_info(const gx_network* net, int scen, int* cluster_ctas) {
+    if (!net || !cluster_ctas) return fail(GX_ERR_INVALID_ARG, "NULL argument");
+    if (scen < 0 || scen >= net->S) return fail(GX_ERR_INVALID_ARG, "scenario out of range");
+    *cluster_ctas = crs_on(net, scen) ? net->crs_groups[net->crs_group[scen]].C : 0;
+    return GX_OK;
+}
+
 gx_status gx_profile_enable(gx_network* net, int on) {
     if (!net) return fail(GX_ERR_INVALID_ARG, "net is NULL");
     if (on && !net->ev[0])
         for (auto& e : net->ev) GX_CUDA(cudaEventCreate(&e));
     net->prof = on != 0;
-    for (int k = 0; k < 3; ++k) { net->prof_ms[k] = 0; net->prof_samples[k] = 0; net->prof_launches[k] = 0; }
+    for (int k = 0; k < 4; ++k) { net->prof_ms[k] = 0; net->prof_samples[k] = 0; net->prof_launches[k] = 0; }
     return GX_OK;
 }
 
 gx_status gx_profile_read(const gx_network* net, double* ms, long long* samples, long long* launches) {
     if (!net || !ms || !samples || !launches) return fail(GX_ERR_INVALID_ARG, "NULL argument");
-    for (int k = 0; k < 3; ++k) { ms[k] = net->prof_ms[k]; samples[k] = net->prof_samples[k]; launches[k] = net->prof_launches[k]; }
+    for (int k = 0; k < 4; ++k) { ms[k] = net->prof_ms[k]; samples[k] = net->prof_samples[k]; launches[k] = net->prof_launches[k]; }
     return GX_OK;
 }
 

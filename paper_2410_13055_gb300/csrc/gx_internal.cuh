@@ -23,6 +23,74 @@ constexpr int kHplMax = kMaxT / 32;
 constexpr int kBusPart = 6;        // floats per bus-block residual partial
 constexpr int kDevPart = 3;        // floats per line-block / battery-warp partial
 
+// Bus-kernel pool record: the static data of the buses one bus block covers.  A header
+// of kPoolHdr words (counts, then the word offset of each array within the record),
+// then the arrays; floats are stored as their bit patterns.  Records are a multiple of 4
+// words (16 bytes) long so a block can copy its record with 16-byte loads.
+enum : int {
+    kPH_NBUS = 0, kPH_GCNT, kPH_ECNT, kPH_BCNT,
+    kPH_GP, kPH_EP, kPH_BP,             // [nbus + 1] device-list pointers, relative to the record
+    kPH_IC, kPH_IW, kPH_DR,             // [nbus] 1/terminals, 1/sum of phase weights, dual-residual weight
+    kPH_GROW, kPH_GCOST, kPH_GEMIS, kPH_GFIRM, kPH_GETA,  // [gcnt] generator row in its network, ...
+    kPH_ECODE, kPH_EBETA, kPH_EW,       // [ecnt] line end 2*l + side, beta_l, phase weight w_l
+    kPH_BROW,                           // [bcnt] battery row in its network
+    kPoolHdr = 20
+};
+constexpr int kPoolMax = 3072;  // longest record (words) staged in shared memory
+
+// Cluster-resident solver: one thread-block cluster of C CTAs per scenario, CTA r owning
+// hours [r*H, (r+1)*H) of every device (H = ceil(T / C)), its state in shared memory.
+constexpr int kCrsThreads = 256;
+constexpr int kCrsMaxC = 16;
+constexpr int kCrsRed = 10;  // residual partial sums per rank (9 used)
+constexpr int kCrsBatState = 7;  // per owned battery-hour: zc zd zs yc yd ys xb
+
+// Byte offsets in a CTA's dynamic shared memory, identical on every rank of a cluster
+// (remote ranks are addressed at the same offsets).
+struct CrsOff {
+    size_t red, wred, flag;
+    size_t pbar, u, thb, xl, ld, aux;  // [N*H] bus-hours (aux: adjoint load gradient, NaN if fixed)
+    size_t xg, cap;                    // [G*H] (cap: forward capacity, adjoint cost gradient or NaN)
+    size_t dl, sg, vf, vt;             // [L*H]
+    size_t xb;                         // [B*H]
+    size_t lcap;                       // [L] flow limit as an angle, eta_l / beta_l
+    size_t bst;                        // [nbo][kCrsBatState][T] batteries owned by this rank
+    size_t lmask;                      // [L*H] bytes (adjoint)
+    size_t total;
+};
+
+__host__ __device__ inline size_t crs_take(size_t& p, size_t bytes) {
+    const size_t r = p;
+    p += (bytes + 15) / 16 * 16;
+    return r;
+}
+
+__host__ __device__ inline CrsOff crs_offsets(int N, int G, int L, int B, int H, int nbo, int T) {
+    CrsOff o{};
+    size_t p = 0;
+    o.red = crs_take(p, sizeof(double) * kCrsMaxC * kCrsRed);
+    o.wred = crs_take(p, sizeof(float) * (kCrsThreads / 32) * kCrsRed);
+    o.flag = crs_take(p, 16);
+    const size_t nb = (size_t)N * H * 4, ng = (size_t)G * H * 4, nl = (size_t)L * H * 4;
+    o.pbar = crs_take(p, nb); o.u = crs_take(p, nb); o.thb = crs_take(p, nb);
+    o.xl = crs_take(p, nb); o.ld = crs_take(p, nb); o.aux = crs_take(p, nb);
+    o.xg = crs_take(p, ng); o.cap = crs_take(p, ng);
+    o.dl = crs_take(p, nl); o.sg = crs_take(p, nl); o.vf = crs_take(p, nl); o.vt = crs_take(p, nl);
+    o.xb = crs_take(p, (size_t)B * H * 4);
+    o.lcap = crs_take(p, (size_t)L * 4);
+    o.bst = crs_take(p, (size_t)nbo * kCrsBatState * T * 4);
+    o.lmask = crs_take(p, (size_t)L * H);
+    o.total = p;
+    return o;
+}
+
+// One per bus-kernel block (built at create).
+struct BusBlk {
+    long long e_bus, e_gen, e_line, e_bat;  // element offsets of the scenario's rows
+    int s, item0, n0, pool;   // scenario, first item (n * Tp + t) of the block, first bus, record offset (words)
+    int words, Tp, T, nitems; // record length (words), padded / true horizon, N * Tp
+};
+
 // Kernel modes.  FWD/ADJ advance the forward or adjoint message passing by one
 // iteration; RESET/INIT prepare a cold or user start; MASK records the active set.
 enum Mode : int { M_FWD = 0, M_ADJ = 1, M_RESET = 2, M_INIT = 3, M_MASK = 4 };
@@ -40,7 +108,8 @@ struct ScenDev {
     int eta0;                          // offset of the network's block in eta
     int gs0;                           // offset of this scenario's block in grad_s (FP64, K_net entries)
     long long e_bus, e_gen, e_line, e_bat;  // element offsets of the scenario's rows
-    int bus_blk0, bus_nblk, line_blk0, line_nblk, bat_w0;
+    int bus_blk0, bus_nblk, line_blk0, line_nblk, bat_w0;  // single-hour kernels (setup modes)
+    int bus4_blk0, bus4_nblk, line4_blk0, line4_nblk;     // hour-quad kernels (iterations)
     int cost_blk0;                     // first block of the cost reduction
     float weight;
     double load_norm;                  // sqrt(sum load^2), >= 1e-30
@@ -50,6 +119,7 @@ struct ScenDev {
 struct Ctx {
     // sizes
     int S, n_bus_blk, n_line_blk, n_bat_warps, n_cost_blk;
+    int n_bus4_blk, n_line4_blk;
     // options
     float rho, eps, voll, kappa, rho_in, rth_c;  // rth_c = rho * rho_theta_c
     float tol_act;
@@ -63,6 +133,12 @@ struct Ctx {
     // tables
     const ScenDev* scen;
     const int* bus_blk_scen;   // [n_bus_blk]
+    const BusBlk* bus_blk;     // [n_bus_blk]
+    const BusBlk* bus4_blk;    // [n_bus4_blk] hour-quad bus kernel
+    const int* line4_blk_scen; // [n_line4_blk]
+    int* pool;                 // bus-block pool records (generator plan values refreshed per call)
+    const int2* prep;          // [n_prep] (pool word, eta index) of every generator plan value
+    int n_prep;
     const int* line_blk_scen;  // [n_line_blk]
     const int* bat_warp_scen;  // [n_bat_warps]
     const int* cost_blk_scen;  // [n_cost_blk]
@@ -103,8 +179,8 @@ struct Ctx {
     double* hval;       // [S]
     double* grad_s;     // [sum_s K_net]
     float* out_flow; float* out_price; float* out_shed;
-    float* bus_part;    // [n_bus_blk * kBusPart]
-    float* line_part;   // [n_line_blk * kDevPart]
+    float* bus_part;    // [n_bus4_blk * kBusPart]
+    float* line_part;   // [n_line4_blk * kDevPart]
     float* bat_part;    // [n_bat_warps * kDevPart]
     double* cost_part;  // [n_cost_blk * 2]
     const float* warm;  // user warm start [prices | angles] over bus rows, or nullptr
@@ -116,6 +192,13 @@ int launch_dev(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st);
 int launch_line(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st);
 int launch_bat(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st);
 int launch_bus(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st);
+int launch_prep(const Ctx& c, cudaStream_t st);
+// Cluster-resident solver (gx_crs.cu): iterate the scenarios in `scen` (in_batch ones
+// only) to convergence, C CTAs per scenario, hpl hours per lane of a battery warp.
+cudaError_t crs_prepare(int adj, int hpl, int C, size_t smem);
+int crs_max_clusters(int adj, int hpl, int C, size_t smem);
+int launch_crs(const Ctx& c, int adj, const int* scen, int n, const int* in_batch, int C, int hpl, size_t smem,
+               double tol, cudaStream_t st);
 int launch_reduce(const Ctx& c, int adj, double tol, cudaStream_t st);
 int launch_tick(const Ctx& c, int chunk, cudaStream_t st);
 int launch_extract(const Ctx& c, const int* in_batch, cudaStream_t st);

@@ -278,35 +278,46 @@ __global__ void __launch_bounds__(kBatWarps * 32) k_bat(const Ctx c, int want_re
     float lo[3][kHpl], hi[3][kHpl], qc[kHpl], qd[kHpl];
     float idd[kHpl], iddp[kHpl];  // 1/dd_t and 1/dd_{t-1} (0 for t = 0)
     float xb_old[kHpl];
+    // Every load of the lane's hours is issued before any of them is used: hours past
+    // the horizon read hour T-1 (a valid row) and are zeroed afterwards.
 #pragma unroll
     for (int j = 0; j < kHpl; ++j) {
         const int t = t0 + j;
         const bool ok = (j < hpl) && (t < T);
-        v[j] = zc[j] = zd[j] = zs[j] = yc[j] = yd[j] = ys[j] = 0.f;
-        qc[j] = qd[j] = 0.f; idd[j] = iddp[j] = 0.f; xb_old[j] = 0.f;
-        lo[0][j] = lo[1][j] = lo[2][j] = 0.f;
-        hi[0][j] = hi[1][j] = hi[2][j] = 0.f;
-        if (ok) {
-            const long long r = row0 + t;
-            xb_old[j] = X.xb[r];
-            v[j] = xb_old[j] - X.pbar[brow0 + t] - X.u[brow0 + t];
-            zc[j] = X.zc[r]; zd[j] = X.zd[r]; zs[j] = X.zs[r];
-            yc[j] = X.yc[r]; yd[j] = X.yd[r]; ys[j] = X.ys[r];
-            idd[j] = 1.f / c.bat_dd[r];
-            iddp[j] = t > 0 ? 1.f / c.bat_dd[r - 1] : 0.f;
-            if (ADJ) {
-                const uint8_t m = c.m_bat[r];
+        const int tc = ok ? t : T - 1;
+        const long long r = row0 + tc;
+        xb_old[j] = X.xb[r];
+        v[j] = xb_old[j] - X.pbar[brow0 + tc] - X.u[brow0 + tc];
+        zc[j] = X.zc[r]; zd[j] = X.zd[r]; zs[j] = X.zs[r];
+        yc[j] = X.yc[r]; yd[j] = X.yd[r]; ys[j] = X.ys[r];
+        idd[j] = c.bat_dd[r];
+        iddp[j] = c.bat_dd[tc > 0 ? r - 1 : r];
+        if (ADJ) {
+            const uint8_t m = c.m_bat[r];
 #pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    const bool fixed = ((m >> (2 * q)) & 3) != A_FREE;
-                    lo[q][j] = fixed ? 0.f : -FLT_MAX;
-                    hi[q][j] = fixed ? 0.f : FLT_MAX;
-                }
-                qc[j] = -eps * c.zc[r];
-                qd[j] = -eps * c.zd[r];
-            } else {
-                hi[0][j] = P; hi[1][j] = P; hi[2][j] = E;
+            for (int q = 0; q < 3; ++q) {
+                const bool fixed = ((m >> (2 * q)) & 3) != A_FREE;
+                lo[q][j] = fixed ? 0.f : -FLT_MAX;
+                hi[q][j] = fixed ? 0.f : FLT_MAX;
             }
+            qc[j] = -eps * c.zc[r];
+            qd[j] = -eps * c.zd[r];
+        } else {
+            lo[0][j] = lo[1][j] = lo[2][j] = 0.f;
+            hi[0][j] = P; hi[1][j] = P; hi[2][j] = E;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < kHpl; ++j) {
+        const int t = t0 + j;
+        const bool ok = (j < hpl) && (t < T);
+        idd[j] = ok ? 1.f / idd[j] : 0.f;
+        iddp[j] = (ok && t > 0) ? 1.f / iddp[j] : 0.f;
+        if (!ok) {
+            v[j] = zc[j] = zd[j] = zs[j] = yc[j] = yd[j] = ys[j] = 0.f;
+            qc[j] = qd[j] = 0.f; xb_old[j] = 0.f;
+            lo[0][j] = lo[1][j] = lo[2][j] = 0.f;
+            hi[0][j] = hi[1][j] = hi[2][j] = 0.f;
         }
     }
 
@@ -436,82 +447,41 @@ __global__ void __launch_bounds__(kBatWarps * 32) k_bat(const Ctx c, int want_re
 // Bus kernel: generator and load proxes (closed-form clips), then the consensus step.
 //
 // A block covers 256 consecutive (bus, hour) items of one scenario, i.e. a few whole
-// buses.  It first stages those buses' device lists (generator rows with their cost,
-// plan value, emission rate and firm flag; line ends with beta and phase weight;
-// battery rows; bus constants) in shared memory, so each thread's per-hour loads no
-// longer wait on a chain of index lookups.  Blocks whose lists do not fit read them
-// from global memory instead (same arithmetic).
+// buses.  The static data of those buses (each bus's device lists, generator cost,
+// emission rate and firm flag, line-end codes with beta and phase weight, battery rows,
+// bus constants) is one contiguous pool record built at create and shared by every
+// scenario of the network with the same bus range; k_prep writes the generators' plan
+// values into it at the start of each call.  The block copies its record to shared
+// memory with 16-byte loads while each thread's own bus-state loads are in flight; then
+// each thread issues the loads of a first chunk of its device terminals before its first
+// store.  A record too long for shared memory is read from global memory in place.
 // ------------------------------------------------------------------------------------
-constexpr int kStGen = 512, kStEnd = 512, kStBat = 128, kStBus = 72;
-
-struct BusStage {
-    int ok, n0;
-    int gp[kStBus + 1], ep[kStBus + 1], bp[kStBus + 1];
-    float icnt[kStBus], iwsum[kStBus], dresw[kStBus];
-    int grow[kStGen];
-    float gcost[kStGen], geta[kStGen], gemis[kStGen];
-    unsigned char gfirm[kStGen];
-    int ecode[kStEnd];
-    float ebeta[kStEnd], ew[kStEnd];
-    int brow[kStBat];
+struct Pool {
+    const int* p;  // the record, in shared or global memory
+    __device__ __forceinline__ int at(int h, int k) const { return p[p[h] + k]; }
+    __device__ __forceinline__ float atf(int h, int k) const { return __int_as_float(p[p[h] + k]); }
 };
 
-// per-bus device lists, from shared memory (staged) or global memory
-struct SrcStaged {
-    const BusStage& S;
-    int nl;
-    __device__ int g0() const { return S.gp[nl]; }
-    __device__ int g1() const { return S.gp[nl + 1]; }
-    __device__ int grow(int q) const { return S.grow[q]; }
-    __device__ float gcost(int q) const { return S.gcost[q]; }
-    __device__ float geta(int q) const { return S.geta[q]; }
-    __device__ float gemis(int q) const { return S.gemis[q]; }
-    __device__ bool gfirm(int q) const { return S.gfirm[q]; }
-    __device__ int e0() const { return S.ep[nl]; }
-    __device__ int e1() const { return S.ep[nl + 1]; }
-    __device__ int ecode(int q) const { return S.ecode[q]; }
-    __device__ float ebeta(int q) const { return S.ebeta[q]; }
-    __device__ float ew(int q) const { return S.ew[q]; }
-    __device__ int b0() const { return S.bp[nl]; }
-    __device__ int b1() const { return S.bp[nl + 1]; }
-    __device__ int brow(int q) const { return S.brow[q]; }
-    __device__ float icnt() const { return S.icnt[nl]; }
-    __device__ float iwsum() const { return S.iwsum[nl]; }
-    __device__ float dresw() const { return S.dresw[nl]; }
+constexpr int kGC = 4;  // generators per load chunk
+constexpr int kEC = 4;  // line ends loaded ahead of the generator stores
+constexpr int kBC = 2;  // batteries loaded ahead of the generator stores
+
+// Per-item inputs read before the block's staging barrier.
+struct BusIn {
+    float pb, uu, thold, xl, Lnt, xlf;
+    int ml;
 };
 
-struct SrcGlobal {
-    const Ctx& c;
-    const ScenDev& sc;
-    int n;
-    __device__ int g0() const { return c.bus_gptr[sc.ptr0 + n]; }
-    __device__ int g1() const { return c.bus_gptr[sc.ptr0 + n + 1]; }
-    __device__ int grow(int q) const { return c.bus_gidx[sc.gen0 + q]; }
-    __device__ float gcost(int q) const { return c.g_cost[sc.gen0 + grow(q)]; }
-    __device__ float geta(int q) const { return fmaxf(c.eta[sc.eta0 + grow(q)], 0.f); }
-    __device__ float gemis(int q) const { return c.g_emis[sc.gen0 + grow(q)]; }
-    __device__ bool gfirm(int q) const { return c.g_firm[sc.gen0 + grow(q)]; }
-    __device__ int e0() const { return c.bus_eptr[sc.ptr0 + n]; }
-    __device__ int e1() const { return c.bus_eptr[sc.ptr0 + n + 1]; }
-    __device__ int ecode(int q) const { return c.bus_eidx[2 * sc.line0 + q]; }
-    __device__ float ebeta(int q) const { return c.l_beta[sc.line0 + (ecode(q) >> 1)]; }
-    __device__ float ew(int q) const { return c.l_w[sc.line0 + (ecode(q) >> 1)]; }
-    __device__ int b0() const { return c.bus_bptr[sc.ptr0 + n]; }
-    __device__ int b1() const { return c.bus_bptr[sc.ptr0 + n + 1]; }
-    __device__ int brow(int q) const { return c.bus_bidx[sc.bat0 + q]; }
-    __device__ float icnt() const { return c.bus_inv_cnt[sc.bus0 + n]; }
-    __device__ float iwsum() const { return c.bus_inv_wsum[sc.bus0 + n]; }
-    __device__ float dresw() const { return c.bus_dres_w[sc.bus0 + n]; }
-};
-
-template <int MODE, int ADJ, class Src>
-__device__ __forceinline__ void bus_item(const Ctx& c, const ScenDev& sc, const StatePtrs& X, const Src& B, int n,
-                                         int t, int want_res, float (&acc)[kBusPart]) {
-    const long long i = sc.e_bus + (long long)n * sc.Tp + t;
+template <int MODE, int ADJ>
+__device__ __forceinline__ void bus_item(const Ctx& c, const BusBlk& bb, const StatePtrs& X, const Pool P, int nl,
+                                         int t, long long i, const BusIn& in, int want_res,
+                                         float (&acc)[kBusPart]) {
     const float rho = c.rho, eps = c.eps;
     const float inv_re = 1.f / (rho + eps);
+    const int g0 = P.at(kPH_GP, nl), g1 = P.at(kPH_GP, nl + 1);
+    const long long gt = bb.e_gen + t;  // generator rows: gt + row * Tp
+    const float Lnt = in.Lnt;
     if (MODE == M_RESET) {
-        const float Lnt = c.load[i];
         X.xl[i] = ADJ ? 0.f : -Lnt;
         if (ADJ) X.u[i] = c.adj_from_fwd ? -c.rho_ratio * c.u[i] : 0.f;
         else X.u[i] = c.warm ? -c.warm[i] / rho : 0.f;
@@ -522,60 +492,102 @@ __device__ __forceinline__ void bus_item(const Ctx& c, const ScenDev& sc, const 
             const float lam = c.warm[i];
             const float shed = clampf((lam - c.voll) / eps, 0.f, Lnt);
             X.xl[i] = shed - Lnt;
-            for (int q = B.g0(); q < B.g1(); ++q) {
-                const long long r = sc.e_gen + (long long)B.grow(q) * sc.Tp + t;
-                const float cap = B.gfirm(q) ? B.geta(q) : c.cf[r] * B.geta(q);
-                X.xg[r] = clampf((lam - B.gcost(q)) / eps, 0.f, cap);
+            for (int q = g0; q < g1; ++q) {
+                const long long r = gt + (long long)P.at(kPH_GROW, q) * bb.Tp;
+                const float cap = P.at(kPH_GFIRM, q) ? P.atf(kPH_GETA, q) : c.cf[r] * P.atf(kPH_GETA, q);
+                X.xg[r] = clampf((lam - P.atf(kPH_GCOST, q)) / eps, 0.f, cap);
             }
         } else {
-            for (int q = B.g0(); q < B.g1(); ++q) X.xg[sc.e_gen + (long long)B.grow(q) * sc.Tp + t] = 0.f;
+            for (int q = g0; q < g1; ++q) X.xg[gt + (long long)P.at(kPH_GROW, q) * bb.Tp] = 0.f;
         }
         return;
     }
-    const float pb = X.pbar[i], uu = X.u[i], thold = X.thb[i];
+    const float pb = in.pb, uu = in.uu;
+    const int e0 = P.at(kPH_EP, nl), e1 = P.at(kPH_EP, nl + 1);
+    const int b0 = P.at(kPH_BP, nl), b1 = P.at(kPH_BP, nl + 1);
+    // first chunk of line ends and batteries: their loads are in flight during the
+    // generator proxes (they are only summed, after the generators and the load)
+    float ed[kEC], eq[kEC], bx[kBC];
+    if (MODE != M_MASK) {
+#pragma unroll
+        for (int k = 0; k < kEC; ++k) {
+            const int q = e0 + k;
+            ed[k] = eq[k] = 0.f;
+            if (q < e1) {
+                const int e = P.at(kPH_ECODE, q);
+                const long long r = bb.e_line + (long long)(e >> 1) * bb.Tp + t;
+                ed[k] = X.dl[r];
+                eq[k] = (e & 1) ? X.vt[r] : X.vf[r];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kBC; ++k) {
+            const int q = b0 + k;
+            bx[k] = q < b1 ? X.xb[bb.e_bat + (long long)P.at(kPH_BROW, q) * bb.Tp + t] : 0.f;
+        }
+    }
     float sum = 0.f, dx2 = 0.f, x2 = 0.f;
     float gscale = 0.f;  // adjoint: sum of (grad h / (rho + eps))^2 over free terminals
-    // generators
-    for (int q = B.g0(); q < B.g1(); ++q) {
-        const long long r = sc.e_gen + (long long)B.grow(q) * sc.Tp + t;
-        const float x = X.xg[r];
-        float xn = x;
-        if (MODE == M_FWD || MODE == M_ADJ || MODE == M_MASK) {
-            const float v = x - pb - uu;
-            if (ADJ) {
-                const float gh = B.gcost(q) + eps * c.xg[r] + c.kappa * B.gemis(q);
-                const bool fixed = c.m_gen[r] != 0;
-                xn = fixed ? 0.f : (rho * v + gh) * inv_re;
-                if (!fixed) gscale += (gh * inv_re) * (gh * inv_re);
-            } else {
-                const float etag = B.geta(q);
-                const float cap = B.gfirm(q) ? etag : c.cf[r] * etag;
-                const float pun = (rho * v - B.gcost(q)) * inv_re;
-                if (MODE == M_MASK) {
-                    uint8_t code = A_FREE;
-                    if (pun > cap && (rho + eps) * (pun - cap) > c.tol_act) code = A_UP;
-                    else if (pun < 0.f && -(rho + eps) * pun > c.tol_act) code = A_LO;
-                    c.m_gen[r] = code;
-                } else {
-                    xn = clampf(pun, 0.f, cap);
+    // generators, kGC at a time: all loads of a chunk before its stores
+    for (int q0 = g0; q0 < g1; q0 += kGC) {
+        float xv[kGC], av[kGC];
+        int ro[kGC], mv[kGC];
+#pragma unroll
+        for (int k = 0; k < kGC; ++k) {
+            const int q = q0 + k;
+            xv[k] = 0.f; av[k] = 1.f; ro[k] = 0; mv[k] = 0;
+            if (q < g1) {
+                ro[k] = P.at(kPH_GROW, q) * bb.Tp;
+                xv[k] = X.xg[gt + ro[k]];
+                if (ADJ) {
+                    av[k] = c.xg[gt + ro[k]];
+                    mv[k] = c.m_gen[gt + ro[k]];
+                } else if (MODE != M_INIT && !P.at(kPH_GFIRM, q)) {
+                    av[k] = c.cf[gt + ro[k]];
                 }
             }
-            if (MODE != M_MASK) X.xg[r] = xn;
         }
-        sum += xn;
-        dx2 += (xn - x) * (xn - x);
-        x2 += xn * xn;
+#pragma unroll
+        for (int k = 0; k < kGC; ++k) {
+            const int q = q0 + k;
+            if (q >= g1) break;
+            const float x = xv[k];
+            float xn = x;
+            if (MODE == M_FWD || MODE == M_ADJ || MODE == M_MASK) {
+                const float v = x - pb - uu;
+                if (ADJ) {
+                    const float gh = P.atf(kPH_GCOST, q) + eps * av[k] + c.kappa * P.atf(kPH_GEMIS, q);
+                    const bool fixed = mv[k] != 0;
+                    xn = fixed ? 0.f : (rho * v + gh) * inv_re;
+                    if (!fixed) gscale += (gh * inv_re) * (gh * inv_re);
+                } else {
+                    const float cap = av[k] * P.atf(kPH_GETA, q);
+                    const float pun = (rho * v - P.atf(kPH_GCOST, q)) * inv_re;
+                    if (MODE == M_MASK) {
+                        uint8_t code = A_FREE;
+                        if (pun > cap && (rho + eps) * (pun - cap) > c.tol_act) code = A_UP;
+                        else if (pun < 0.f && -(rho + eps) * pun > c.tol_act) code = A_LO;
+                        c.m_gen[gt + ro[k]] = code;
+                    } else {
+                        xn = clampf(pun, 0.f, cap);
+                    }
+                }
+                if (MODE != M_MASK) X.xg[gt + ro[k]] = xn;
+            }
+            sum += xn;
+            dx2 += (xn - x) * (xn - x);
+            x2 += xn * xn;
+        }
     }
     // load (shed variable; terminal injection shed - L)
     {
-        const float x = X.xl[i];
+        const float x = in.xl;
         float xn = x;
         if (MODE == M_FWD || MODE == M_ADJ || MODE == M_MASK) {
             const float v = x - pb - uu;
-            const float Lnt = c.load[i];
             if (ADJ) {
-                const float gsh = c.voll + eps * (c.xl[i] + Lnt);
-                const bool fixed = c.m_load[i] != 0;
+                const float gsh = c.voll + eps * (in.xlf + Lnt);
+                const bool fixed = in.ml != 0;
                 xn = fixed ? 0.f : (rho * v + gsh) * inv_re;
                 if (!fixed) gscale += (gsh * inv_re) * (gsh * inv_re);
             } else {
@@ -597,28 +609,45 @@ __device__ __forceinline__ void bus_item(const Ctx& c, const ScenDev& sc, const 
     }
     if (MODE == M_MASK) return;
     // batteries (their prox ran in k_bat this iteration)
-    for (int q = B.b0(); q < B.b1(); ++q) {
-        const float xb = X.xb[sc.e_bat + (long long)B.brow(q) * sc.Tp + t];
+#pragma unroll
+    for (int k = 0; k < kBC; ++k) {
+        if (b0 + k < b1) {
+            sum += bx[k];
+            x2 += bx[k] * bx[k];
+        }
+    }
+    for (int q = b0 + kBC; q < b1; ++q) {
+        const float xb = X.xb[bb.e_bat + (long long)P.at(kPH_BROW, q) * bb.Tp + t];
         sum += xb;
         x2 += xb * xb;
     }
     // line ends (their prox ran in k_line this iteration)
     float ths = 0.f;
-    for (int q = B.e0(); q < B.e1(); ++q) {
-        const int e = B.ecode(q);
-        const int side = e & 1;
-        const long long r = sc.e_line + (long long)(e >> 1) * sc.Tp + t;
+#pragma unroll
+    for (int k = 0; k < kEC; ++k) {
+        const int q = e0 + k;
+        if (q < e1) {
+            const float beta = P.atf(kPH_EBETA, q);
+            const float p = (P.at(kPH_ECODE, q) & 1) ? beta * ed[k] : -beta * ed[k];
+            sum += p;
+            x2 += p * p;
+            ths += P.atf(kPH_EW, q) * eq[k];
+        }
+    }
+    for (int q = e0 + kEC; q < e1; ++q) {
+        const int e = P.at(kPH_ECODE, q);
+        const long long r = bb.e_line + (long long)(e >> 1) * bb.Tp + t;
         const float d = X.dl[r];
-        const float qv = side ? X.vt[r] : X.vf[r];
-        const float beta = B.ebeta(q);
-        const float p = side ? beta * d : -beta * d;
+        const float qv = (e & 1) ? X.vt[r] : X.vf[r];
+        const float beta = P.atf(kPH_EBETA, q);
+        const float p = (e & 1) ? beta * d : -beta * d;
         sum += p;
         x2 += p * p;
-        ths += B.ew(q) * qv;
+        ths += P.atf(kPH_EW, q) * qv;
     }
-    const float icnt = B.icnt();
+    const float icnt = P.atf(kPH_IC, nl);
     const float pbn = sum * icnt;
-    const float thn = ths * B.iwsum();
+    const float thn = ths * P.atf(kPH_IW, nl);
     if (MODE == M_INIT) {
         X.pbar[i] = pbn;
         X.thb[i] = thn;
@@ -634,74 +663,298 @@ __device__ __forceinline__ void bus_item(const Ctx& c, const ScenDev& sc, const 
         acc[0] = cnt * pbn * pbn;
         acc[1] = gscale;
         acc[2] = dx2 - cnt * dpb * dpb;
-        acc[3] = (thn - thold) * (thn - thold) * B.dresw();
+        acc[3] = (thn - in.thold) * (thn - in.thold) * P.atf(kPH_DR, nl);
         acc[4] = cnt * (rho * un) * (rho * un);
         acc[5] = x2;
     }
 }
 
 template <int MODE, int ADJ>
-__global__ void __launch_bounds__(kBlock, 5) k_bus(const Ctx c, int want_res) {
-    __shared__ BusStage S;
-    const int blk = blockIdx.x;
-    const int s = c.bus_blk_scen[blk];
-    if (c.done[s]) return;  // block-uniform
-    const ScenDev sc = c.scen[s];
+__global__ void __launch_bounds__(kBlock, 4) k_bus(const Ctx c, int want_res) {
+    __shared__ __align__(16) int S[kPoolMax];
+    const BusBlk bb = c.bus_blk[blockIdx.x];
+    if (c.done[bb.s]) return;  // block-uniform
     const StatePtrs X = state<ADJ>(c);
-    const int item0 = (blk - sc.bus_blk0) * kBlock;
-    const int last = min(item0 + kBlock, sc.N * sc.Tp) - 1;
-    const int n0 = item0 / sc.Tp, n1 = last / sc.Tp;
-    const int nbus = n1 - n0 + 1;
-    // stage this block's buses
-    const int pb0 = sc.ptr0 + n0;
-    const int gb = c.bus_gptr[pb0], gcnt = c.bus_gptr[pb0 + nbus] - gb;
-    const int eb = c.bus_eptr[pb0], ecnt = c.bus_eptr[pb0 + nbus] - eb;
-    const int bb = c.bus_bptr[pb0], bcnt = c.bus_bptr[pb0 + nbus] - bb;
-    const bool ok = nbus <= kStBus && gcnt <= kStGen && ecnt <= kStEnd && bcnt <= kStBat;
-    if (ok) {
-        for (int k = threadIdx.x; k <= nbus; k += kBlock) {
-            S.gp[k] = c.bus_gptr[pb0 + k] - gb;
-            S.ep[k] = c.bus_eptr[pb0 + k] - eb;
-            S.bp[k] = c.bus_bptr[pb0 + k] - bb;
-            if (k < nbus) {
-                S.icnt[k] = c.bus_inv_cnt[sc.bus0 + n0 + k];
-                S.iwsum[k] = c.bus_inv_wsum[sc.bus0 + n0 + k];
-                S.dresw[k] = c.bus_dres_w[sc.bus0 + n0 + k];
-            }
+    const bool staged = bb.words <= kPoolMax;
+    if (staged) {
+        const int4* src = reinterpret_cast<const int4*>(c.pool + bb.pool);
+        int4* dst = reinterpret_cast<int4*>(S);
+        for (int k = threadIdx.x; k < (bb.words >> 2); k += kBlock) dst[k] = src[k];
+    }
+    const int local = bb.item0 + threadIdx.x;
+    const int n = local / bb.Tp;
+    const int t = local - n * bb.Tp;
+    const bool valid = (local < bb.nitems) && (t < bb.T);
+    const long long i = bb.e_bus + local;
+    BusIn in{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
+    if (valid) {
+        if (MODE != M_INIT) in.Lnt = c.load[i];
+        if (MODE == M_FWD || MODE == M_ADJ || MODE == M_MASK) {
+            in.pb = X.pbar[i]; in.uu = X.u[i]; in.thold = X.thb[i];
         }
-        for (int k = threadIdx.x; k < gcnt; k += kBlock) {
-            const int g = c.bus_gidx[sc.gen0 + gb + k];
-            S.grow[k] = g;
-            S.gcost[k] = c.g_cost[sc.gen0 + g];
-            S.geta[k] = fmaxf(c.eta[sc.eta0 + g], 0.f);
-            S.gemis[k] = c.g_emis[sc.gen0 + g];
-            S.gfirm[k] = c.g_firm[sc.gen0 + g];
-        }
-        for (int k = threadIdx.x; k < ecnt; k += kBlock) {
-            const int e = c.bus_eidx[2 * sc.line0 + eb + k];
-            S.ecode[k] = e;
-            S.ebeta[k] = c.l_beta[sc.line0 + (e >> 1)];
-            S.ew[k] = c.l_w[sc.line0 + (e >> 1)];
-        }
-        for (int k = threadIdx.x; k < bcnt; k += kBlock) S.brow[k] = c.bus_bidx[sc.bat0 + bb + k];
+        if (MODE != M_RESET) in.xl = X.xl[i];
+        if (ADJ && MODE == M_ADJ) { in.xlf = c.xl[i]; in.ml = c.m_load[i]; }
     }
     __syncthreads();
-    const int local = item0 + threadIdx.x;
-    const int n = local / sc.Tp;
-    const int t = local - n * sc.Tp;
-    const bool valid = (n < sc.N) && (t < sc.T);
     float acc[kBusPart] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (valid) {
-        if (ok) bus_item<MODE, ADJ>(c, sc, X, SrcStaged{S, n - n0}, n, t, want_res, acc);
-        else bus_item<MODE, ADJ>(c, sc, X, SrcGlobal{c, sc, n}, n, t, want_res, acc);
+        const Pool P{staged ? S : c.pool + bb.pool};
+        bus_item<MODE, ADJ>(c, bb, X, P, n - bb.n0, t, i, in, want_res, acc);
     }
     if ((MODE == M_FWD || MODE == M_ADJ) && want_res) {
         __shared__ float sh[kBusPart][kBlock / 32];
         block_sum<kBusPart>(acc, sh);
         if (threadIdx.x == 0) {
 #pragma unroll
-            for (int q = 0; q < kBusPart; ++q) c.bus_part[blk * kBusPart + q] = acc[q];
+            for (int q = 0; q < kBusPart; ++q) c.bus_part[blockIdx.x * kBusPart + q] = acc[q];
         }
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Iteration kernels over hour quads.  In the forward and adjoint iterations a thread of
+// the line or bus kernel handles four consecutive hours of one device row (rows are
+// padded to a multiple of 4 hours, so every quad is 16-byte aligned): one 128-bit load
+// or store per array instead of four, and the index arithmetic and device-list walk
+// paid once per four hours.  Each hour's arithmetic is that of the single-hour code
+// above, in the same order; hours past the horizon stay zero.
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ void ld4(const float* p, float (&v)[4]) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void st4(float* p, const float (&v)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void ldm4(const uint8_t* p, int (&v)[4]) {
+    const uchar4 q = *reinterpret_cast<const uchar4*>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+
+template <int ADJ>
+__global__ void __launch_bounds__(kBlock) k_line4(const Ctx c, int want_res) {
+    const int blk = blockIdx.x;
+    const int s = c.line4_blk_scen[blk];
+    if (c.done[s]) return;
+    const ScenDev sc = c.scen[s];
+    const StatePtrs X = state<ADJ>(c);
+    const int Tq = sc.Tp >> 2;
+    const int local = (blk - sc.line4_blk0) * kBlock + threadIdx.x;
+    const int l = local / Tq;
+    const int t = (local - l * Tq) * 4;
+    float dx2 = 0.f, x2 = 0.f, th2 = 0.f;
+    if (l < sc.L) {
+        const long long row = sc.e_line + (long long)l * sc.Tp + t;
+        const int lg = sc.line0 + l;
+        const long long bf = sc.e_bus + (long long)c.l_from[lg] * sc.Tp + t;
+        const long long bt = sc.e_bus + (long long)c.l_to[lg] * sc.Tp + t;
+        float d[4], g[4], qf[4], qt[4], pbf[4], uf[4], zf[4], pbt[4], ut[4], zt[4];
+        ld4(X.dl + row, d); ld4(X.sg + row, g); ld4(X.vf + row, qf); ld4(X.vt + row, qt);
+        ld4(X.pbar + bf, pbf); ld4(X.u + bf, uf); ld4(X.thb + bf, zf);
+        ld4(X.pbar + bt, pbt); ld4(X.u + bt, ut); ld4(X.thb + bt, zt);
+        int mk[4] = {0, 0, 0, 0};
+        if (ADJ) ldm4(c.m_line + row, mk);
+        const float beta = c.l_beta[lg];
+        const float rth = c.rth_c * c.l_w[lg];
+        const float capf = fmaxf(c.eta[sc.eta0 + sc.G + l], 0.f) / beta;
+        const float cap = fminf(capf, c.l_dth[lg]);
+        const float den = 2.f * c.rho * beta * beta + 0.5f * rth;
+        float dn[4], gn[4], nf[4], nt[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            dn[h] = gn[h] = nf[h] = nt[h] = 0.f;
+            if (t + h >= sc.T) continue;
+            const float vf = qf[h] - zf[h], vt = qt[h] - zt[h];
+            const float ef = 0.5f * (g[h] + d[h]) - zf[h], et = 0.5f * (g[h] - d[h]) - zt[h];
+            th2 += beta * beta * (ef * ef + et * et);
+            const float wf = zf[h] - vf, wt = zt[h] - vt;
+            const float tf = -beta * d[h] - pbf[h] - uf[h];
+            const float tt = beta * d[h] - pbt[h] - ut[h];
+            const float dun = (c.rho * beta * (tt - tf) + 0.5f * rth * (wf - wt)) / den;
+            if (ADJ) dn[h] = mk[h] ? 0.f : dun;
+            else dn[h] = clampf(dun, -cap, cap);
+            gn[h] = wf + wt;
+            nf[h] = 0.5f * (gn[h] + dn[h]) + vf;
+            nt[h] = 0.5f * (gn[h] - dn[h]) + vt;
+            const float dd = dn[h] - d[h];
+            dx2 += 2.f * beta * beta * dd * dd;
+            x2 += 2.f * beta * beta * dn[h] * dn[h];
+        }
+        st4(X.dl + row, dn); st4(X.sg + row, gn); st4(X.vf + row, nf); st4(X.vt + row, nt);
+    }
+    if (want_res) {
+        __shared__ float sh[3][kBlock / 32];
+        float v[3] = {dx2, x2, th2};
+        block_sum<3>(v, sh);
+        if (threadIdx.x == 0) {
+            c.line_part[blk * kDevPart + 0] = v[0];
+            c.line_part[blk * kDevPart + 1] = v[1];
+            c.line_part[blk * kDevPart + 2] = v[2];
+        }
+    }
+}
+
+template <int ADJ>
+__global__ void __launch_bounds__(kBlock) k_bus4(const Ctx c, int want_res) {
+    __shared__ __align__(16) int S[kPoolMax];
+    const BusBlk bb = c.bus4_blk[blockIdx.x];
+    if (c.done[bb.s]) return;  // block-uniform
+    const StatePtrs X = state<ADJ>(c);
+    const bool staged = bb.words <= kPoolMax;
+    if (staged) {
+        const int4* src = reinterpret_cast<const int4*>(c.pool + bb.pool);
+        int4* dst = reinterpret_cast<int4*>(S);
+        for (int k = threadIdx.x; k < (bb.words >> 2); k += kBlock) dst[k] = src[k];
+    }
+    const int Tq = bb.Tp >> 2;
+    const int local = bb.item0 + threadIdx.x;
+    const int n = local / Tq;
+    const int t = (local - n * Tq) * 4;
+    const bool valid = local < bb.nitems;
+    const long long i = bb.e_bus + (long long)n * bb.Tp + t;
+    float pb[4], uu[4], thold[4], xl[4], Ld[4], xlf[4];
+    int ml[4] = {0, 0, 0, 0};
+    if (valid) {
+        ld4(X.pbar + i, pb); ld4(X.u + i, uu); ld4(X.thb + i, thold);
+        ld4(X.xl + i, xl); ld4(c.load + i, Ld);
+        if (ADJ) { ld4(c.xl + i, xlf); ldm4(c.m_load + i, ml); }
+    }
+    __syncthreads();
+    float acc[kBusPart] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (valid) {
+        const Pool P{staged ? S : c.pool + bb.pool};
+        const int nl = n - bb.n0;
+        const float rho = c.rho, eps = c.eps;
+        const float inv_re = 1.f / (rho + eps);
+        bool hv[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) hv[h] = t + h < bb.T;
+        float sum[4] = {0.f, 0.f, 0.f, 0.f}, dx2[4] = {0.f, 0.f, 0.f, 0.f};
+        float x2 = 0.f, gscale = 0.f;
+        const long long gt = bb.e_gen + t;
+        const int g1 = P.at(kPH_GP, nl + 1);
+        for (int q = P.at(kPH_GP, nl); q < g1; ++q) {
+            const long long r = gt + (long long)P.at(kPH_GROW, q) * bb.Tp;
+            float x[4], a[4], xn[4];
+            int mg[4] = {0, 0, 0, 0};
+            ld4(X.xg + r, x);
+            if (ADJ) {
+                ld4(c.xg + r, a);
+                ldm4(c.m_gen + r, mg);
+            } else if (!P.at(kPH_GFIRM, q)) {
+                ld4(c.cf + r, a);
+            } else {
+                a[0] = a[1] = a[2] = a[3] = 1.f;
+            }
+            const float gcost = P.atf(kPH_GCOST, q);
+            const float etag = ADJ ? 0.f : P.atf(kPH_GETA, q);
+            const float gemis = ADJ ? P.atf(kPH_GEMIS, q) : 0.f;
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const float v = x[h] - pb[h] - uu[h];
+                if (ADJ) {
+                    const float gh = gcost + eps * a[h] + c.kappa * gemis;
+                    const bool fixed = mg[h] != 0;
+                    xn[h] = fixed ? 0.f : (rho * v + gh) * inv_re;
+                    if (!fixed && hv[h]) gscale += (gh * inv_re) * (gh * inv_re);
+                } else {
+                    const float cap = a[h] * etag;
+                    const float pun = (rho * v - gcost) * inv_re;
+                    xn[h] = clampf(pun, 0.f, cap);
+                }
+                if (!hv[h]) xn[h] = 0.f;
+                sum[h] += xn[h];
+                dx2[h] += (xn[h] - x[h]) * (xn[h] - x[h]);
+                x2 += xn[h] * xn[h];
+            }
+            st4(X.xg + r, xn);
+        }
+        {
+            float xn[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const float v = xl[h] - pb[h] - uu[h];
+                if (ADJ) {
+                    const float gsh = c.voll + eps * (xlf[h] + Ld[h]);
+                    const bool fixed = ml[h] != 0;
+                    xn[h] = fixed ? 0.f : (rho * v + gsh) * inv_re;
+                    if (!fixed && hv[h]) gscale += (gsh * inv_re) * (gsh * inv_re);
+                } else {
+                    const float sun = (rho * (v + Ld[h]) - c.voll) * inv_re;
+                    xn[h] = clampf(sun, 0.f, Ld[h]) - Ld[h];
+                }
+                if (!hv[h]) xn[h] = 0.f;
+                sum[h] += xn[h];
+                dx2[h] += (xn[h] - xl[h]) * (xn[h] - xl[h]);
+                x2 += xn[h] * xn[h];
+            }
+            st4(X.xl + i, xn);
+        }
+        const int b1 = P.at(kPH_BP, nl + 1);
+        for (int q = P.at(kPH_BP, nl); q < b1; ++q) {
+            float xb[4];
+            ld4(X.xb + bb.e_bat + (long long)P.at(kPH_BROW, q) * bb.Tp + t, xb);
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                sum[h] += xb[h];
+                x2 += xb[h] * xb[h];
+            }
+        }
+        float ths[4] = {0.f, 0.f, 0.f, 0.f};
+        const int e1 = P.at(kPH_EP, nl + 1);
+        for (int q = P.at(kPH_EP, nl); q < e1; ++q) {
+            const int e = P.at(kPH_ECODE, q);
+            const long long r = bb.e_line + (long long)(e >> 1) * bb.Tp + t;
+            float d[4], qv[4];
+            ld4(X.dl + r, d);
+            ld4((e & 1) ? X.vt + r : X.vf + r, qv);
+            const float beta = P.atf(kPH_EBETA, q), w = P.atf(kPH_EW, q);
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const float p = (e & 1) ? beta * d[h] : -beta * d[h];
+                sum[h] += p;
+                x2 += p * p;
+                ths[h] += w * qv[h];
+            }
+        }
+        const float icnt = P.atf(kPH_IC, nl), iws = P.atf(kPH_IW, nl), drw = P.atf(kPH_DR, nl);
+        const float cnt = 1.f / icnt;
+        float pbn[4], un[4], thn[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            pbn[h] = sum[h] * icnt;
+            thn[h] = ths[h] * iws;
+            un[h] = uu[h] + pbn[h];
+            if (hv[h]) {
+                const float dpb = pbn[h] - pb[h];
+                acc[0] += cnt * pbn[h] * pbn[h];
+                acc[2] += dx2[h] - cnt * dpb * dpb;
+                acc[3] += (thn[h] - thold[h]) * (thn[h] - thold[h]) * drw;
+                acc[4] += cnt * (rho * un[h]) * (rho * un[h]);
+            }
+        }
+        acc[1] = gscale;
+        acc[5] = x2;
+        st4(X.pbar + i, pbn);
+        st4(X.u + i, un);
+        st4(X.thb + i, thn);
+    }
+    if (want_res) {
+        __shared__ float sh[kBusPart][kBlock / 32];
+        block_sum<kBusPart>(acc, sh);
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int q = 0; q < kBusPart; ++q) c.bus_part[blockIdx.x * kBusPart + q] = acc[q];
+        }
+    }
+}
+
+// Write each generator's plan value max(eta_g, 0) into the pool records (once per call).
+__global__ void k_prep(const Ctx c) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < c.n_prep) {
+        const int2 e = c.prep[k];
+        c.pool[e.x] = __float_as_int(fmaxf(c.eta[e.y], 0.f));
     }
 }
 
@@ -723,13 +976,13 @@ __global__ void __launch_bounds__(kBlock) k_reduce(const Ctx c, int adj, double 
     const int final_ = it >= c.max_it;
     const ScenDev sc = c.scen[s];
     double a[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    for (int b = threadIdx.x; b < sc.bus_nblk; b += kBlock) {
+    for (int b = threadIdx.x; b < sc.bus4_nblk; b += kBlock) {
 #pragma unroll
-        for (int q = 0; q < kBusPart; ++q) a[q] += (double)c.bus_part[(sc.bus_blk0 + b) * kBusPart + q];
+        for (int q = 0; q < kBusPart; ++q) a[q] += (double)c.bus_part[(sc.bus4_blk0 + b) * kBusPart + q];
     }
-    for (int b = threadIdx.x; b < sc.line_nblk; b += kBlock) {
+    for (int b = threadIdx.x; b < sc.line4_nblk; b += kBlock) {
 #pragma unroll
-        for (int q = 0; q < kDevPart; ++q) a[6 + q] += (double)c.line_part[(sc.line_blk0 + b) * kDevPart + q];
+        for (int q = 0; q < kDevPart; ++q) a[6 + q] += (double)c.line_part[(sc.line4_blk0 + b) * kDevPart + q];
     }
     for (int b = threadIdx.x; b < sc.B; b += kBlock) {
 #pragma unroll
@@ -976,15 +1229,15 @@ __global__ void k_plan_step(float* eta, const float* grad, const float* gamma, c
 // ------------------------------------------------------------------------------------
 // launch wrappers
 // ------------------------------------------------------------------------------------
-#define GX_DISPATCH_MODE(KERNEL, GRID, ...)                                              \
+
+// Setup modes (reset, start, active set) of the single-hour kernels.
+#define GX_DISPATCH_MODE_SETUP(KERNEL, GRID, ...)                                        \
     do {                                                                                 \
         if (adj) {                                                                       \
-            if (mode == M_ADJ) KERNEL<M_ADJ, 1><<<GRID, kBlock, 0, st>>>(__VA_ARGS__);    \
-            else if (mode == M_RESET) KERNEL<M_RESET, 1><<<GRID, kBlock, 0, st>>>(__VA_ARGS__); \
+            if (mode == M_RESET) KERNEL<M_RESET, 1><<<GRID, kBlock, 0, st>>>(__VA_ARGS__);      \
             else if (mode == M_INIT) KERNEL<M_INIT, 1><<<GRID, kBlock, 0, st>>>(__VA_ARGS__);   \
         } else {                                                                         \
-            if (mode == M_FWD) KERNEL<M_FWD, 0><<<GRID, kBlock, 0, st>>>(__VA_ARGS__);    \
-            else if (mode == M_RESET) KERNEL<M_RESET, 0><<<GRID, kBlock, 0, st>>>(__VA_ARGS__); \
+            if (mode == M_RESET) KERNEL<M_RESET, 0><<<GRID, kBlock, 0, st>>>(__VA_ARGS__);      \
             else if (mode == M_INIT) KERNEL<M_INIT, 0><<<GRID, kBlock, 0, st>>>(__VA_ARGS__);   \
             else if (mode == M_MASK) KERNEL<M_MASK, 0><<<GRID, kBlock, 0, st>>>(__VA_ARGS__);   \
         }                                                                                \
@@ -992,7 +1245,12 @@ __global__ void k_plan_step(float* eta, const float* grad, const float* gamma, c
 
 int launch_line(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st) {
     if (mode == M_INIT || c.n_line_blk <= 0) return 0;
-    GX_DISPATCH_MODE(k_line, c.n_line_blk, c, want_res);
+    if (mode == M_FWD || mode == M_ADJ) {
+        if (adj) k_line4<1><<<c.n_line4_blk, kBlock, 0, st>>>(c, want_res);
+        else k_line4<0><<<c.n_line4_blk, kBlock, 0, st>>>(c, want_res);
+        return 1;
+    }
+    GX_DISPATCH_MODE_SETUP(k_line, c.n_line_blk, c, want_res);
     return 1;
 }
 
@@ -1040,7 +1298,18 @@ int launch_dev(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st) {
 
 int launch_bus(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st) {
     if (c.n_bus_blk <= 0) return 0;
-    GX_DISPATCH_MODE(k_bus, c.n_bus_blk, c, want_res);
+    if (mode == M_FWD || mode == M_ADJ) {
+        if (adj) k_bus4<1><<<c.n_bus4_blk, kBlock, 0, st>>>(c, want_res);
+        else k_bus4<0><<<c.n_bus4_blk, kBlock, 0, st>>>(c, want_res);
+        return 1;
+    }
+    GX_DISPATCH_MODE_SETUP(k_bus, c.n_bus_blk, c, want_res);
+    return 1;
+}
+
+int launch_prep(const Ctx& c, cudaStream_t st) {
+    if (c.n_prep <= 0) return 0;
+    k_prep<<<(c.n_prep + kBlock - 1) / kBlock, kBlock, 0, st>>>(c);
     return 1;
 }
 

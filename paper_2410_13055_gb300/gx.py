@@ -83,6 +83,8 @@ _SIGS = {
     "gx_plan_step": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, C.c_float, _vp]),
     "gx_profile_enable": (C.c_int, [_vp, C.c_int]),
     "gx_network_use_graphs": (C.c_int, [_vp, C.c_int]),
+    "gx_network_use_persistent": (C.c_int, [_vp, C.c_int]),
+    "gx_network_persistent_info": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int)]),
     "gx_profile_read": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
     "gx_dispatch_cost_noalloc": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp]),
     "gx_gnn_num_params": (_sz, []),
@@ -277,17 +279,32 @@ class Network:
         """Replay residual-check chunks as CUDA graphs (default) or launch kernel by kernel."""
         _check(_lib.gx_network_use_graphs(self._h, int(bool(on))), "gx_network_use_graphs", False)
 
+    def use_persistent(self, on=True):
+        """Cluster-resident persistent launches for the scenarios that fit (default) or the
+        per-iteration kernels for every scenario."""
+        _check(_lib.gx_network_use_persistent(self._h, int(bool(on))), "gx_network_use_persistent", False)
+
+    def persistent_info(self):
+        """Per scenario: CTAs of its resident cluster, 0 if it runs on the per-iteration kernels."""
+        out = []
+        for s in range(self.S):
+            v = C.c_int(0)
+            _check(_lib.gx_network_persistent_info(self._h, s, C.byref(v)), "gx_network_persistent_info", False)
+            out.append(v.value)
+        return out
+
     def profile(self, on=True):
-        """Sampled CUDA-event timing of the bus / line / battery kernels (see gx_profile_enable)."""
+        """Sampled CUDA-event timing of the bus / line / battery kernels and of the
+        cluster-resident launches (see gx_profile_enable)."""
         _check(_lib.gx_profile_enable(self._h, int(bool(on))), "gx_profile_enable", False)
 
     def profile_read(self):
-        ms = (C.c_double * 3)()
-        sm = (C.c_longlong * 3)()
-        ln = (C.c_longlong * 3)()
+        ms = (C.c_double * 4)()
+        sm = (C.c_longlong * 4)()
+        ln = (C.c_longlong * 4)()
         _check(_lib.gx_profile_read(self._h, ms, sm, ln), "gx_profile_read", False)
-        names = ["k_bus", "k_line", "k_bat"]
-        return {names[k]: {"ms": ms[k], "samples": sm[k], "launches": ln[k]} for k in range(3) if sm[k] > 0}
+        names = ["k_bus", "k_line", "k_bat", "k_crs"]
+        return {names[k]: {"ms": ms[k], "samples": sm[k], "launches": ln[k]} for k in range(4) if sm[k] > 0}
 
     def plan_step(self, eta, grad, gamma, eta_min, eta_max, alpha, stream=None):
         rc = _lib.gx_plan_step(self._h, _ptr(eta), _ptr(grad), _ptr(gamma), _ptr(eta_min), _ptr(eta_max),
