@@ -5,9 +5,11 @@ gradient, then `steps` previous-plan steps) for candidate settings, one paramete
 time from the defaults (coordinate descent), and keeps the fastest setting whose
 planner objective stays within `h_tol` of a tight reference solve at the same plan
 (equal residual tolerances do not give equal accuracy across penalties).  Parameters:
-residual-check chunk length (the CUDA-graph size), power penalty rho, phase penalty
-scale, adjoint penalty, battery inner iterations.  Results are cached as JSON, keyed by
-(buses, hours, scenarios) rounded to powers of two.
+the execution path (per-iteration kernels replayed as CUDA graphs, or one persistent
+cluster-resident launch per loop for the scenarios that fit), residual-check chunk
+length (the CUDA-graph size), power penalty rho, phase penalty scale, adjoint penalty,
+battery inner iterations.  Results are cached as JSON, keyed by (buses, hours,
+scenarios) rounded to powers of two.
 """
 from __future__ import annotations
 
@@ -22,6 +24,7 @@ import torch
 from . import gx
 
 SPACE = {
+    "persistent": [False, True],
     "check_every": [10, 20, 40],
     "rho": [0.2, 0.3, 0.5],
     "rho_theta_c": [0.03, 0.1],
@@ -65,14 +68,19 @@ def tune(net: gx.Network, nets, steps=3, h_tol=2e-3, cache=None, log=None, alpha
     eta_min = torch.tensor(np.concatenate([n["eta_min"] for n in nets]), dtype=torch.float32, device=dev)
     eta_max = torch.tensor(np.concatenate([n["eta_max"] for n in nets]), dtype=torch.float32, device=dev)
     gamma = torch.tensor(np.concatenate([n["gamma"] for n in nets]), dtype=torch.float32, device=dev)
-    base = {k: getattr(net.opts, k) for k in SPACE}
+    base = {k: getattr(net.opts, k) for k in SPACE if k != "persistent"}
+    base["persistent"] = False
     g0 = torch.zeros_like(eta_min)
     net.solve(eta_min, warm="cold")
     net.grad(eta_min, out=g0)
     alpha = alpha_frac * float(eta_min.median()) / max(float((gamma + g0).abs().max()), 1e-30)
 
+    def apply(opts):
+        net.set_opts(**{k: v for k, v in opts.items() if k != "persistent"})
+        net.use_persistent(opts["persistent"])
+
     def measure(opts):
-        net.set_opts(**opts)
+        apply(opts)
         return _run(net, eta_min, gamma, eta_min, eta_max, steps, alpha)
 
     t_best, eta_end, _ = measure(base)
@@ -100,7 +108,7 @@ def tune(net: gx.Network, nets, steps=3, h_tol=2e-3, cache=None, log=None, alpha
                 log(trials[-1])
             if ok and t < t_best:
                 best, t_best = cand, t
-    net.set_opts(**best)
+    apply(best)
     entry = dict(best=best, time_s=t_best, trials=trials)
     try:
         os.makedirs(os.path.dirname(cache), exist_ok=True)
@@ -120,6 +128,8 @@ def load(net: gx.Network, cache=None):
     db = json.load(open(cache))
     e = db.get(bucket(net))
     if e:
-        net.set_opts(**e["best"])
+        best = dict(e["best"])
+        net.use_persistent(bool(best.pop("persistent", False)))
+        net.set_opts(**best)
         return e["best"]
     return None
