@@ -586,12 +586,14 @@ void crs_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* at, int nclusters,
 
 }  // namespace
 
-cudaError_t crs_prepare(int adj, int hpl, int C, size_t smem) {
+// Several launch groups share one instantiation with different image sizes, so each
+// instantiation is opened to the largest image any group may use (smem_max) and to
+// non-portable cluster sizes; a launch still states its own size.
+cudaError_t crs_prepare(int adj, int hpl, size_t smem_max) {
     const void* f = crs_kernel(adj, hpl);
-    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
     if (e != cudaSuccess) return e;
-    if (C > 8) e = cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    return e;
+    return cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
 }
 
 int crs_max_clusters(int adj, int hpl, int C, size_t smem) {

@@ -761,7 +761,8 @@ gx_status gx_network_bind(gx_network* net, void* dev_mem, size_t bytes, void* st
     for (auto& g : net->crs_groups) {
         g.ok = true;
         for (int adj = 0; adj < 2 && g.ok; ++adj)
-            g.ok = crs_prepare(adj, g.hpl, g.C, g.smem) == cudaSuccess && crs_max_clusters(adj, g.hpl, g.C, g.smem) >= 1;
+            g.ok = crs_prepare(adj, g.hpl, kCrsSmemBudget) == cudaSuccess &&
+                   crs_max_clusters(adj, g.hpl, g.C, g.smem) >= 1;
         cudaGetLastError();
     }
     net->solved = false;

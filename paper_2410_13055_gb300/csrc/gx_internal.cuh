@@ -195,7 +195,7 @@ int launch_bus(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st);
 int launch_prep(const Ctx& c, cudaStream_t st);
 // Cluster-resident solver (gx_crs.cu): iterate the scenarios in `scen` (in_batch ones
 // only) to convergence, C CTAs per scenario, hpl hours per lane of a battery warp.
-cudaError_t crs_prepare(int adj, int hpl, int C, size_t smem);
+cudaError_t crs_prepare(int adj, int hpl, size_t smem_max);
 int crs_max_clusters(int adj, int hpl, int C, size_t smem);
 int launch_crs(const Ctx& c, int adj, const int* scen, int n, const int* in_batch, int C, int hpl, size_t smem,
                double tol, cudaStream_t st);

@@ -794,6 +794,26 @@ __global__ void __launch_bounds__(kBlock) k_line4(const Ctx c, int want_res) {
     }
 }
 
+constexpr int kEC4 = 4;  // line ends loaded ahead by the quad bus kernel
+constexpr int kBC4 = 2;  // batteries loaded ahead
+
+// One generator's quad: stored injection, then (adjoint) the forward dispatch and the
+// active set, or (forward) the capacity factor (1 for firm generators).
+template <int ADJ>
+__device__ __forceinline__ void gen_load4(const Ctx& c, const StatePtrs& X, const Pool& P, long long r, int q,
+                                          float (&x)[4], float (&a)[4], int (&m)[4]) {
+    ld4(X.xg + r, x);
+    m[0] = m[1] = m[2] = m[3] = 0;
+    if (ADJ) {
+        ld4(c.xg + r, a);
+        ldm4(c.m_gen + r, m);
+    } else if (!P.at(kPH_GFIRM, q)) {
+        ld4(c.cf + r, a);
+    } else {
+        a[0] = a[1] = a[2] = a[3] = 1.f;
+    }
+}
+
 template <int ADJ>
 __global__ void __launch_bounds__(kBlock) k_bus4(const Ctx c, int want_res) {
     __shared__ __align__(16) int S[kPoolMax];
@@ -832,20 +852,36 @@ __global__ void __launch_bounds__(kBlock) k_bus4(const Ctx c, int want_res) {
         float sum[4] = {0.f, 0.f, 0.f, 0.f}, dx2[4] = {0.f, 0.f, 0.f, 0.f};
         float x2 = 0.f, gscale = 0.f;
         const long long gt = bb.e_gen + t;
-        const int g1 = P.at(kPH_GP, nl + 1);
-        for (int q = P.at(kPH_GP, nl); q < g1; ++q) {
+        const int g0 = P.at(kPH_GP, nl), g1 = P.at(kPH_GP, nl + 1);
+        const int e0 = P.at(kPH_EP, nl), e1 = P.at(kPH_EP, nl + 1);
+        const int b0 = P.at(kPH_BP, nl), b1 = P.at(kPH_BP, nl + 1);
+        // Loads ahead of the first store: the first kEC4 line ends and kBC4 batteries
+        // (only summed at the end) and the first generator; each later generator is
+        // loaded before the previous one's store.
+        float ed[kEC4][4], eq[kEC4][4], bx[kBC4][4];
+#pragma unroll
+        for (int k = 0; k < kEC4; ++k) {
+            const int q = e0 + k;
+            if (q < e1) {
+                const int e = P.at(kPH_ECODE, q);
+                const long long r = bb.e_line + (long long)(e >> 1) * bb.Tp + t;
+                ld4(X.dl + r, ed[k]);
+                ld4((e & 1) ? X.vt + r : X.vf + r, eq[k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kBC4; ++k)
+            if (b0 + k < b1) ld4(X.xb + bb.e_bat + (long long)P.at(kPH_BROW, b0 + k) * bb.Tp + t, bx[k]);
+        float xc[4], ac[4];
+        int mc[4];
+        if (g0 < g1) gen_load4<ADJ>(c, X, P, gt + (long long)P.at(kPH_GROW, g0) * bb.Tp, g0, xc, ac, mc);
+        for (int q = g0; q < g1; ++q) {
             const long long r = gt + (long long)P.at(kPH_GROW, q) * bb.Tp;
             float x[4], a[4], xn[4];
-            int mg[4] = {0, 0, 0, 0};
-            ld4(X.xg + r, x);
-            if (ADJ) {
-                ld4(c.xg + r, a);
-                ldm4(c.m_gen + r, mg);
-            } else if (!P.at(kPH_GFIRM, q)) {
-                ld4(c.cf + r, a);
-            } else {
-                a[0] = a[1] = a[2] = a[3] = 1.f;
-            }
+            int mg[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) { x[h] = xc[h]; a[h] = ac[h]; mg[h] = mc[h]; }
+            if (q + 1 < g1) gen_load4<ADJ>(c, X, P, gt + (long long)P.at(kPH_GROW, q + 1) * bb.Tp, q + 1, xc, ac, mc);
             const float gcost = P.atf(kPH_GCOST, q);
             const float etag = ADJ ? 0.f : P.atf(kPH_GETA, q);
             const float gemis = ADJ ? P.atf(kPH_GEMIS, q) : 0.f;
@@ -890,8 +926,17 @@ __global__ void __launch_bounds__(kBlock) k_bus4(const Ctx c, int want_res) {
             }
             st4(X.xl + i, xn);
         }
-        const int b1 = P.at(kPH_BP, nl + 1);
-        for (int q = P.at(kPH_BP, nl); q < b1; ++q) {
+#pragma unroll
+        for (int k = 0; k < kBC4; ++k) {
+            if (b0 + k < b1) {
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    sum[h] += bx[k][h];
+                    x2 += bx[k][h] * bx[k][h];
+                }
+            }
+        }
+        for (int q = b0 + kBC4; q < b1; ++q) {
             float xb[4];
             ld4(X.xb + bb.e_bat + (long long)P.at(kPH_BROW, q) * bb.Tp + t, xb);
 #pragma unroll
@@ -901,8 +946,22 @@ __global__ void __launch_bounds__(kBlock) k_bus4(const Ctx c, int want_res) {
             }
         }
         float ths[4] = {0.f, 0.f, 0.f, 0.f};
-        const int e1 = P.at(kPH_EP, nl + 1);
-        for (int q = P.at(kPH_EP, nl); q < e1; ++q) {
+#pragma unroll
+        for (int k = 0; k < kEC4; ++k) {
+            const int q = e0 + k;
+            if (q < e1) {
+                const int e = P.at(kPH_ECODE, q);
+                const float beta = P.atf(kPH_EBETA, q), w = P.atf(kPH_EW, q);
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const float p = (e & 1) ? beta * ed[k][h] : -beta * ed[k][h];
+                    sum[h] += p;
+                    x2 += p * p;
+                    ths[h] += w * eq[k][h];
+                }
+            }
+        }
+        for (int q = e0 + kEC4; q < e1; ++q) {
             const int e = P.at(kPH_ECODE, q);
             const long long r = bb.e_line + (long long)(e >> 1) * bb.Tp + t;
             float d[4], qv[4];

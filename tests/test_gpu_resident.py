@@ -126,3 +126,23 @@ def test_mixed_resident_and_streaming_batch():
     e = torch.tensor(np.concatenate([n["eta_min"] for n in nets]), dtype=torch.float32, device="cuda")
     assert net2.solve(e, warm="cold", batch=[1, 2]) == 0
     assert torch.equal(net2.array("p", 0), p_big)
+
+
+def test_resident_groups_sharing_one_kernel():
+    """Networks of one horizon class but different sizes: their clusters differ in size
+    and shared-memory image yet share one kernel instantiation (launch groups of several
+    sizes in one call); results match the per-iteration kernels."""
+    nets, scens = [], []
+    for k, nb in enumerate([8, 60, 140, 260]):
+        n, sc = synth.custom(nb, int(1.5 * nb), 3 * nb, max(1, int(0.3 * nb)), 24, S=1, seed=90 + k, net_index=k)
+        sc[0]["weight"] = 0.25
+        nets.append(n)
+        scens.append(sc[0])
+    net1, a = _run(nets, scens, False, steps=2)
+    net2, b = _run(nets, scens, True, steps=2)
+    info = net2.persistent_info()
+    assert len(set(info)) >= 2 and all(c > 0 for c in info), info
+    for (f1, a1, h1, g1), (f2, a2, h2, g2) in zip(a, b):
+        assert (f1, a1) == (f2, a2)
+        assert np.max(np.abs(h1 - h2) / np.abs(h1)) <= 1e-5
+        assert rel(g2, g1) <= 1e-4
