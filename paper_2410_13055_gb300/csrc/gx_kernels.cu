@@ -218,11 +218,17 @@ __global__ void __launch_bounds__(kBlock) k_line(const Ctx c, int want_res) {
 // (pivots precomputed in bat_dd); its two Thomas sweeps are first-order linear
 // recurrences evaluated with warp-wide affine scans.
 // ------------------------------------------------------------------------------------
-template <int MODE, int ADJ, int kHpl>
+// kW warps per battery (1 or 2; a block of kBatWarps warps holds kBatWarps / kW
+// batteries).  With two warps the hours split over 64 lanes, halving each lane's serial
+// sweeps; the scans then combine the two warps' totals through shared memory.
+template <int MODE, int ADJ, int kHpl, int kW>
 __global__ void __launch_bounds__(kBatWarps * 32) k_bat(const Ctx c, int want_res) {
-    const int lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * kBatWarps + (threadIdx.x >> 5);
-    if (gw >= c.n_bat_warps) return;
+    static_assert(kW == 1 || kW == 2, "one or two warps per battery");
+    constexpr int NL = 32 * kW;  // lanes per battery
+    const int L = threadIdx.x & (NL - 1);  // lane within the battery
+    const int lane = L & 31, wb = L >> 5;  // lane within the warp, warp within the battery
+    const int gw = blockIdx.x * (kBatWarps / kW) + (int)(threadIdx.x / NL);
+    if (gw >= c.n_bat_warps) return;  // block-uniform when kW == 2 (one battery per block)
     const int s = c.bat_warp_scen[gw];
     if (c.done[s]) return;
     const ScenDev sc = c.scen[s];
@@ -230,14 +236,15 @@ __global__ void __launch_bounds__(kBatWarps * 32) k_bat(const Ctx c, int want_re
     const int b = gw - sc.bat_w0;
     const int bg = sc.bat0 + b;
     const int T = sc.T;
-    const int hpl = (T + 31) >> 5;
-    const int t0 = lane * hpl;
+    const int hpl = (T + NL - 1) / NL;
+    const int t0 = L * hpl;
+    __shared__ float xch[8];  // two-warp exchange: rs, forward (A, B), backward (A, B), partials
     const long long row0 = sc.e_bat + (long long)b * sc.Tp;
     const long long brow0 = sc.e_bus + (long long)c.b_bus[bg] * sc.Tp;
 
     if (MODE == M_RESET) {
         const bool neg = ADJ && c.adj_from_fwd;
-        for (int t = lane; t < sc.Tp; t += 32) {
+        for (int t = L; t < sc.Tp; t += NL) {
             const long long r = row0 + t;
             X.xb[r] = 0.f; X.zc[r] = 0.f; X.zd[r] = 0.f; X.zs[r] = 0.f;
             // h = c part of the adjoint: box multipliers are the negated forward ones
@@ -250,7 +257,7 @@ __global__ void __launch_bounds__(kBatWarps * 32) k_bat(const Ctx c, int want_re
     const float rho = c.rho, eps = c.eps, ri = c.rho_in, iri = 1.f / c.rho_in;
     if (MODE == M_MASK) {
         // active set from the inner box multipliers of the forward solution
-        for (int t = lane; t < T; t += 32) {
+        for (int t = L; t < T; t += NL) {
             const long long r = row0 + t;
             const float y3[3] = {c.yc[r], c.yd[r], c.ys[r]};
             uint8_t code = 0;
@@ -341,7 +348,11 @@ __global__ void __launch_bounds__(kBatWarps * 32) k_bat(const Ctx c, int want_re
 #pragma unroll
         for (int j = 0; j < kHpl; ++j) if (j == hpl - 1) rs_last = rs[j];
         float rs_prev = __shfl_up_sync(0xffffffffu, rs_last, 1);
-        if (lane == 0) rs_prev = 0.f;
+        if (kW == 2) {
+            if (L == 31) xch[0] = rs_last;
+            __syncthreads();
+        }
+        if (lane == 0) rs_prev = (kW == 2 && wb == 1) ? xch[0] : 0.f;
         // forward sweep y_t = rhs_t + y_{t-1} / dd_{t-1}
         float A = 1.f, Bv = 0.f;
 #pragma unroll
@@ -359,7 +370,19 @@ __global__ void __launch_bounds__(kBatWarps * 32) k_bat(const Ctx c, int want_re
             if (lane >= o) { Bv = A * Bo + Bv; A = A * Ao; }
         }
         float yin = __shfl_up_sync(0xffffffffu, Bv, 1);
-        if (lane == 0) yin = 0.f;
+        if (kW == 2) {
+            // the second warp's prefixes start from the first warp's total
+            if (L == 31) { xch[1] = A; xch[2] = Bv; }
+            __syncthreads();
+            if (wb == 1) {
+                const float A0 = xch[1], B0 = xch[2];
+                Bv = A * B0 + Bv;
+                A = A * A0;
+                const float yw = __shfl_up_sync(0xffffffffu, Bv, 1);
+                yin = lane == 0 ? B0 : yw;
+            }
+        }
+        if (lane == 0 && !(kW == 2 && wb == 1)) yin = 0.f;
         float yv[kHpl];
 #pragma unroll
         for (int j = 0; j < kHpl; ++j) {
@@ -383,7 +406,19 @@ __global__ void __launch_bounds__(kBatWarps * 32) k_bat(const Ctx c, int want_re
             if (lane + o < 32) { Bv = A * Bo + Bv; A = A * Ao; }
         }
         float min_ = __shfl_down_sync(0xffffffffu, Bv, 1);
-        if (lane == 31) min_ = 0.f;
+        if (kW == 2) {
+            // the first warp's suffixes continue into the second warp's total
+            if (L == 32) { xch[3] = A; xch[4] = Bv; }
+            __syncthreads();
+            if (wb == 0) {
+                const float B1 = xch[4];
+                Bv = A * B1 + Bv;
+                A = A * xch[3];
+                const float mw = __shfl_down_sync(0xffffffffu, Bv, 1);
+                min_ = lane == 31 ? B1 : mw;
+            }
+        }
+        if (lane == 31 && !(kW == 2 && wb == 0)) min_ = 0.f;
         float mu[kHpl];
         float mnext = min_;
 #pragma unroll
@@ -435,7 +470,12 @@ __global__ void __launch_bounds__(kBatWarps * 32) k_bat(const Ctx c, int want_re
     if (want_res) {
         dx2 = warp_sum(dx2);
         x2 = warp_sum(x2);
-        if (lane == 0) {
+        if (kW == 2) {
+            if (L == 32) { xch[5] = dx2; xch[6] = x2; }
+            __syncthreads();
+            if (L == 0) { dx2 += xch[5]; x2 += xch[6]; }
+        }
+        if (L == 0) {
             c.bat_part[gw * kDevPart + 0] = dx2;
             c.bat_part[gw * kDevPart + 1] = x2;
             c.bat_part[gw * kDevPart + 2] = 0.f;
@@ -1328,21 +1368,35 @@ int launch_line(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st) 
 #define GX_BAT_HPL(H)                                                                      \
     do {                                                                                   \
         if (adj) {                                                                         \
-            if (mode == M_ADJ) k_bat<M_ADJ, 1, H><<<grid, kBatWarps * 32, 0, st>>>(c, want_res);          \
-            else if (mode == M_RESET) k_bat<M_RESET, 1, H><<<grid, kBatWarps * 32, 0, st>>>(c, want_res); \
+            if (mode == M_ADJ) k_bat<M_ADJ, 1, H, 1><<<grid, kBatWarps * 32, 0, st>>>(c, want_res);          \
+            else if (mode == M_RESET) k_bat<M_RESET, 1, H, 1><<<grid, kBatWarps * 32, 0, st>>>(c, want_res); \
         } else {                                                                           \
-            if (mode == M_FWD) k_bat<M_FWD, 0, H><<<grid, kBatWarps * 32, 0, st>>>(c, want_res);          \
-            else if (mode == M_RESET) k_bat<M_RESET, 0, H><<<grid, kBatWarps * 32, 0, st>>>(c, want_res); \
-            else if (mode == M_MASK) k_bat<M_MASK, 0, H><<<grid, kBatWarps * 32, 0, st>>>(c, want_res);   \
+            if (mode == M_FWD) k_bat<M_FWD, 0, H, 1><<<grid, kBatWarps * 32, 0, st>>>(c, want_res);          \
+            else if (mode == M_RESET) k_bat<M_RESET, 0, H, 1><<<grid, kBatWarps * 32, 0, st>>>(c, want_res); \
+            else if (mode == M_MASK) k_bat<M_MASK, 0, H, 1><<<grid, kBatWarps * 32, 0, st>>>(c, want_res);   \
         }                                                                                  \
     } while (0)
 
-// Hours per lane: compiled for 1, 2, 3, 6 and 8 (T up to 32, 64, 96, 192, 256), chosen
-// from the longest horizon among the batch's batteries.
+// Hours per lane: compiled for 1, 2, 3 hours with one warp per battery (T up to 96) and
+// for 3 or 4 hours with two warps per battery in the iterations (T up to 192 or 256),
+// chosen from the longest horizon among the batch's batteries.  The setup modes use one
+// warp per battery (hour-strided loops).
 int launch_bat(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st) {
     if (mode == M_INIT || c.n_bat_warps <= 0) return 0;
     const int grid = (c.n_bat_warps + kBatWarps - 1) / kBatWarps;
     const int hpl = (c.max_bat_T + 31) / 32;
+    if ((mode == M_FWD || mode == M_ADJ) && hpl > 3) {
+        const int grid2 = c.n_bat_warps;  // one battery (two warps) per block
+        const int h2 = (c.max_bat_T + 63) / 64;
+        if (adj) {
+            if (h2 <= 3) k_bat<M_ADJ, 1, 3, 2><<<grid2, kBatWarps * 32, 0, st>>>(c, want_res);
+            else k_bat<M_ADJ, 1, 4, 2><<<grid2, kBatWarps * 32, 0, st>>>(c, want_res);
+        } else {
+            if (h2 <= 3) k_bat<M_FWD, 0, 3, 2><<<grid2, kBatWarps * 32, 0, st>>>(c, want_res);
+            else k_bat<M_FWD, 0, 4, 2><<<grid2, kBatWarps * 32, 0, st>>>(c, want_res);
+        }
+        return 1;
+    }
     if (hpl <= 1) GX_BAT_HPL(1);
     else if (hpl <= 2) GX_BAT_HPL(2);
     else if (hpl <= 3) GX_BAT_HPL(3);
