@@ -17,6 +17,7 @@ namespace gx {
 
 constexpr int kBlock = 256;        // threads per block of the bus / line / generic kernels
 constexpr int kLineItems = 2;     // line-hours per thread of the line kernel
+constexpr int kQBlock = 128;       // threads per block of the hour-quad line / bus kernels
 constexpr int kBatWarps = 2;       // batteries (warps) per block of the battery kernel
 constexpr int kMaxT = 256;         // hours per scenario handled by one warp (8 per lane)
 constexpr int kHplMax = kMaxT / 32;

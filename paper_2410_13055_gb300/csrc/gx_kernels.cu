@@ -37,9 +37,9 @@ __device__ __forceinline__ double warp_sum_d(double v) {
     return v;
 }
 
-// Sum NV values over a block of kBlock threads; thread 0 gets the totals in v[].
-template <int NV>
-__device__ __forceinline__ void block_sum(float (&v)[NV], float (*sh)[kBlock / 32]) {
+// Sum NV values over a block of NT threads; thread 0 gets the totals in v[].
+template <int NV, int NT = kBlock>
+__device__ __forceinline__ void block_sum(float (&v)[NV], float (*sh)[NT / 32]) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
@@ -50,7 +50,7 @@ __device__ __forceinline__ void block_sum(float (&v)[NV], float (*sh)[kBlock / 3
     if (w == 0) {
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
-            float s = lane < kBlock / 32 ? sh[k][lane] : 0.f;
+            float s = lane < NT / 32 ? sh[k][lane] : 0.f;
             v[k] = warp_sum(s);
         }
     }
@@ -772,14 +772,14 @@ __device__ __forceinline__ void ldm4(const uint8_t* p, int (&v)[4]) {
 }
 
 template <int ADJ>
-__global__ void __launch_bounds__(kBlock) k_line4(const Ctx c, int want_res) {
+__global__ void __launch_bounds__(kQBlock) k_line4(const Ctx c, int want_res) {
     const int blk = blockIdx.x;
     const int s = c.line4_blk_scen[blk];
     if (c.done[s]) return;
     const ScenDev sc = c.scen[s];
     const StatePtrs X = state<ADJ>(c);
     const int Tq = sc.Tp >> 2;
-    const int local = (blk - sc.line4_blk0) * kBlock + threadIdx.x;
+    const int local = (blk - sc.line4_blk0) * kQBlock + threadIdx.x;
     const int l = local / Tq;
     const int t = (local - l * Tq) * 4;
     float dx2 = 0.f, x2 = 0.f, th2 = 0.f;
@@ -823,9 +823,9 @@ __global__ void __launch_bounds__(kBlock) k_line4(const Ctx c, int want_res) {
         st4(X.dl + row, dn); st4(X.sg + row, gn); st4(X.vf + row, nf); st4(X.vt + row, nt);
     }
     if (want_res) {
-        __shared__ float sh[3][kBlock / 32];
+        __shared__ float sh[3][kQBlock / 32];
         float v[3] = {dx2, x2, th2};
-        block_sum<3>(v, sh);
+        block_sum<3, kQBlock>(v, sh);
         if (threadIdx.x == 0) {
             c.line_part[blk * kDevPart + 0] = v[0];
             c.line_part[blk * kDevPart + 1] = v[1];
@@ -855,7 +855,7 @@ __device__ __forceinline__ void gen_load4(const Ctx& c, const StatePtrs& X, cons
 }
 
 template <int ADJ>
-__global__ void __launch_bounds__(kBlock) k_bus4(const Ctx c, int want_res) {
+__global__ void __launch_bounds__(kQBlock) k_bus4(const Ctx c, int want_res) {
     __shared__ __align__(16) int S[kPoolMax];
     const BusBlk bb = c.bus4_blk[blockIdx.x];
     if (c.done[bb.s]) return;  // block-uniform
@@ -864,7 +864,7 @@ __global__ void __launch_bounds__(kBlock) k_bus4(const Ctx c, int want_res) {
     if (staged) {
         const int4* src = reinterpret_cast<const int4*>(c.pool + bb.pool);
         int4* dst = reinterpret_cast<int4*>(S);
-        for (int k = threadIdx.x; k < (bb.words >> 2); k += kBlock) dst[k] = src[k];
+        for (int k = threadIdx.x; k < (bb.words >> 2); k += kQBlock) dst[k] = src[k];
     }
     const int Tq = bb.Tp >> 2;
     const int local = bb.item0 + threadIdx.x;
@@ -1039,8 +1039,8 @@ __global__ void __launch_bounds__(kBlock) k_bus4(const Ctx c, int want_res) {
         st4(X.thb + i, thn);
     }
     if (want_res) {
-        __shared__ float sh[kBusPart][kBlock / 32];
-        block_sum<kBusPart>(acc, sh);
+        __shared__ float sh[kBusPart][kQBlock / 32];
+        block_sum<kBusPart, kQBlock>(acc, sh);
         if (threadIdx.x == 0) {
 #pragma unroll
             for (int q = 0; q < kBusPart; ++q) c.bus_part[blockIdx.x * kBusPart + q] = acc[q];
@@ -1345,8 +1345,8 @@ __global__ void k_plan_step(float* eta, const float* grad, const float* gamma, c
 int launch_line(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st) {
     if (mode == M_INIT || c.n_line_blk <= 0) return 0;
     if (mode == M_FWD || mode == M_ADJ) {
-        if (adj) k_line4<1><<<c.n_line4_blk, kBlock, 0, st>>>(c, want_res);
-        else k_line4<0><<<c.n_line4_blk, kBlock, 0, st>>>(c, want_res);
+        if (adj) k_line4<1><<<c.n_line4_blk, kQBlock, 0, st>>>(c, want_res);
+        else k_line4<0><<<c.n_line4_blk, kQBlock, 0, st>>>(c, want_res);
         return 1;
     }
     GX_DISPATCH_MODE_SETUP(k_line, c.n_line_blk, c, want_res);
@@ -1412,8 +1412,8 @@ int launch_dev(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st) {
 int launch_bus(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st) {
     if (c.n_bus_blk <= 0) return 0;
     if (mode == M_FWD || mode == M_ADJ) {
-        if (adj) k_bus4<1><<<c.n_bus4_blk, kBlock, 0, st>>>(c, want_res);
-        else k_bus4<0><<<c.n_bus4_blk, kBlock, 0, st>>>(c, want_res);
+        if (adj) k_bus4<1><<<c.n_bus4_blk, kQBlock, 0, st>>>(c, want_res);
+        else k_bus4<0><<<c.n_bus4_blk, kQBlock, 0, st>>>(c, want_res);
         return 1;
     }
     GX_DISPATCH_MODE_SETUP(k_bus, c.n_bus_blk, c, want_res);
