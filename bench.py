@@ -145,9 +145,9 @@ def algorithmic_bytes(nets, scens):
 # DRAM bytes (read + write) per launch from one ncu capture of the solver kernels on the
 # 100-bus network with 64 scenarios (profiles/solver_kernels_medium64_full.md); valid only
 # while gx_kernels.cu is the source that was profiled.
-PROFILED = {"sha256_prefix": "1774065c560ae1ef", "scenarios": 64, "config": "medium",
+PROFILED = {"sha256_prefix": "1939f5362321703d", "scenarios": 64, "config": "medium",
             "source": "profiles/solver_kernels_medium64_full.md",
-            "traffic": {"k_bus": 65.538304e6, "k_line": 38.744832e6, "k_bat": 21.120768e6}}
+            "traffic": {"k_bus": 65.450752e6, "k_line": 38.7456e6, "k_bat": 21.11488e6}}
 
 
 def profiled_traffic(config, n_scen, kernel):
