@@ -23,7 +23,8 @@ class Dispatch:
         v = qp.unpack(res.x)
         self.p, self.sh, self.th = v["p"], v["sh"], v["th"]
         self.ch, self.dis, self.soc = v["ch"], v["dis"], v["soc"]
-        self.flow = qp.flows(self.th)
+        self.fdc = v["fdc"]
+        self.flow = qp.flows(self.th, self.fdc)
         # nodal price lambda_nt = -y of the balance row
         self.price = -res.y[qp.row_bal:qp.row_bal + qp.N * qp.T].reshape(qp.N, qp.T)
         self.cost = qp.cost(res.x)

@@ -10,20 +10,30 @@ Variables, each a row of T hours, stacked in this order::
     ch   [B, T]   battery charging power, MW
     dis  [B, T]   battery discharging power, MW
     soc  [B, T]   battery state of charge at the end of hour t, MWh
+    fdc  [Ld, T]  flow on each HVDC (transport) line, MW, from -> to
 
 Objective c(x) = 1/2 x^T Q x + q^T x with
-    sum_gt (c_g p + eps/2 p^2) + sum_nt (VOLL sh + eps/2 sh^2) + sum_bt eps/2 (ch^2 + dis^2).
+    sum_gt (c_g p + eps/2 p^2) + sum_nt (VOLL sh + eps/2 sh^2) + sum_bt eps/2 (ch^2 + dis^2)
+    + sum_dc,t eps/2 fdc^2.
+
+HVDC lines (``net["line_dc"]`` = 1) are transport links (Sections 2.1 and 3 name HVDC
+among the planned assets): their flow is a free variable limited by eta_l, with no
+angle coupling and no angle-difference limit, regularised like the other free
+injections so the dispatch stays unique.
 
 Equalities A x = b:
     balance (n,t): sum_{g at n} p + sum_{b at n} (dis - ch) + sh
-                   - sum_{l from n} beta_l (th_f - th_t) + sum_{l to n} beta_l (th_f - th_t) = L_nt
+                   - sum_{l from n} f_l + sum_{l to n} f_l = L_nt,
+                   f_l = beta_l (th_f - th_t) for AC lines, fdc_l for HVDC lines
     dynamics (b,t): soc_t - soc_{t-1} - eff_c ch_t + dis_t / eff_d = 0,  soc_{-1} = 0
-    reference (component, t): th_ref = 0   (angles are fixed up to a constant per island)
+    reference (component, t): th_ref = 0   (angles are fixed up to a constant per island of
+                              the AC lines)
     pinned: p_gt = 0 where cf_gt eta_g = 0, sh_nt = 0 where L_nt = 0 (coinciding bounds)
 
 Inequalities G x <= h(eta) = h0 + D eta  (the capacity dependence b(eta) of Eq. 2):
     p <= cf eta_g,  -p <= 0,  sh <= L,  -sh <= 0,
-    +-beta (th_f - th_t) <= eta_l,  +-(th_f - th_t) <= dtheta_max,
+    +-beta (th_f - th_t) <= eta_l,  +-(th_f - th_t) <= dtheta_max   (AC lines),
+    +-fdc <= eta_l   (HVDC lines),
     ch <= eta_b, -ch <= 0, dis <= eta_b, -dis <= 0, soc <= dur eta_b, -soc <= 0.
 
 The nodal price is lambda_nt = -y_nt, y the multiplier of the balance row in
@@ -70,6 +80,12 @@ class DispatchQP:
         voll = float(opts["voll"])
         self.N, self.T, self.G, self.L, self.B = N, T, G, L, B
         self.K = G + L + B
+        dc = np.asarray(net.get("line_dc", np.zeros(L)), dtype=bool)
+        self.dc_lines = np.where(dc)[0]
+        self.ac_lines = np.where(~dc)[0]
+        Ld = self.dc_lines.size
+        self.Ld = Ld
+        dc_row = {int(l): j for j, l in enumerate(self.dc_lines)}
         eta = np.asarray(eta, dtype=np.float64)
         assert eta.shape == (self.K,)
         self.eta = eta.copy()
@@ -78,7 +94,7 @@ class DispatchQP:
         # --- variable offsets
         off = {}
         o = 0
-        for name, rows in (("p", G), ("sh", N), ("th", N), ("ch", B), ("dis", B), ("soc", B)):
+        for name, rows in (("p", G), ("sh", N), ("th", N), ("ch", B), ("dis", B), ("soc", B), ("fdc", Ld)):
             off[name] = o
             o += rows * T
         self.n = o
@@ -93,7 +109,7 @@ class DispatchQP:
         # --- objective
         Qd = np.zeros(self.n)
         q = np.zeros(self.n)
-        for name, rows in (("p", G), ("sh", N), ("ch", B), ("dis", B)):
+        for name, rows in (("p", G), ("sh", N), ("ch", B), ("dis", B), ("fdc", Ld)):
             Qd[off[name]:off[name] + rows * T] = eps
         q[off["p"]:off["p"] + G * T] = np.repeat(net["gen_cost"], T)
         q[off["sh"]:off["sh"] + N * T] = voll
@@ -131,6 +147,13 @@ class DispatchQP:
             vals += [-1.0] * T
         for l in range(L):
             f, to, beta = int(net["line_from"][l]), int(net["line_to"][l]), float(net["line_beta"][l])
+            if l in dc_row:
+                # HVDC: the flow variable leaves bus f and enters bus to
+                for t in range(T):
+                    rows += [r + f * T + t, r + to * T + t]
+                    cols += [vid("fdc", dc_row[l], t), vid("fdc", dc_row[l], t)]
+                    vals += [-1.0, 1.0]
+                continue
             # flow f_lt = beta (th_f - th_t) leaves bus f and enters bus to
             for t in range(T):
                 rows += [r + f * T + t, r + f * T + t, r + to * T + t, r + to * T + t]
@@ -149,7 +172,7 @@ class DispatchQP:
                 b.append(0.0)
         r += B * T
         self.row_ref = r
-        lab = components(N, net["line_from"], net["line_to"])
+        lab = components(N, np.asarray(net["line_from"])[self.ac_lines], np.asarray(net["line_to"])[self.ac_lines])
         self.comp = lab
         self.ref_bus = np.array([int(np.where(lab == c)[0][0]) for c in range(lab.max() + 1)])
         for rb in self.ref_bus:
@@ -209,6 +232,12 @@ class DispatchQP:
                 add_row([(vid("sh", n, t), -1.0)], 0.0, tag=("sh_lo", n, t))
         for l in range(L):
             f, to = int(net["line_from"][l]), int(net["line_to"][l])
+            if l in dc_row:
+                for t in range(T):
+                    v = vid("fdc", dc_row[l], t)
+                    add_row([(v, 1.0)], 0.0, G + l, 1.0, ("f_up", l, t))
+                    add_row([(v, -1.0)], 0.0, G + l, 1.0, ("f_lo", l, t))
+                continue
             beta = float(net["line_beta"][l])
             dth = float(net["line_dtheta"][l])
             for t in range(T):
@@ -246,10 +275,18 @@ class DispatchQP:
             ch=x[o["ch"]:o["ch"] + self.B * T].reshape(self.B, T),
             dis=x[o["dis"]:o["dis"] + self.B * T].reshape(self.B, T),
             soc=x[o["soc"]:o["soc"] + self.B * T].reshape(self.B, T),
+            fdc=x[o["fdc"]:o["fdc"] + self.Ld * T].reshape(self.Ld, T),
         )
 
-    def pack(self, p, sh, th, ch, dis, soc):
-        return np.concatenate([np.ravel(p), np.ravel(sh), np.ravel(th), np.ravel(ch), np.ravel(dis), np.ravel(soc)])
+    def pack(self, p, sh, th, ch, dis, soc, fdc=None):
+        """x from device arrays; `fdc` may be the flows of all L lines (the HVDC rows are taken)."""
+        if fdc is None:
+            fdc = np.zeros((self.Ld, self.T))
+        fdc = np.asarray(fdc, dtype=np.float64)
+        if fdc.shape[0] == self.L and self.L != self.Ld:
+            fdc = fdc[self.dc_lines]
+        return np.concatenate([np.ravel(p), np.ravel(sh), np.ravel(th), np.ravel(ch), np.ravel(dis), np.ravel(soc),
+                               np.ravel(fdc)])
 
     def cost(self, x):
         """Operating cost c(x) of Eq. 2 (with the eps regularisation), FP64."""
@@ -262,6 +299,11 @@ class DispatchQP:
     def planner_grad(self, x, kappa):
         return self.Qd * x + self.q + float(kappa) * self.emis_vec
 
-    def flows(self, th):
+    def flows(self, th, fdc=None):
+        """Flow of every line, from -> to: beta (th_f - th_t) on AC lines, the flow
+        variable on HVDC lines."""
         lf, lt = self.net["line_from"], self.net["line_to"]
-        return self.net["line_beta"][:, None] * (th[lf] - th[lt])
+        f = self.net["line_beta"][:, None] * (th[lf] - th[lt])
+        if self.Ld:
+            f[self.dc_lines] = fdc if fdc is not None else 0.0
+        return f

@@ -4,8 +4,9 @@ import math
 import numpy as np
 
 
-def network(n_bus, gens=(), lines=(), bats=(), gamma=None):
-    """gens: (bus, cost, cap[, emis]); lines: (from, to, beta, cap[, dtheta]); bats: (bus, P[, dur, eff])."""
+def network(n_bus, gens=(), lines=(), bats=(), gamma=None, dc=()):
+    """gens: (bus, cost, cap[, emis]); lines: (from, to, beta, cap[, dtheta]); bats: (bus, P[, dur, eff]);
+    dc: indices of the lines that are HVDC transport links (their beta and dtheta are unused)."""
     gb = np.array([g[0] for g in gens], dtype=np.int64)
     gc = np.array([g[1] for g in gens], dtype=float)
     gcap = np.array([g[2] for g in gens], dtype=float)
@@ -26,6 +27,8 @@ def network(n_bus, gens=(), lines=(), bats=(), gamma=None):
                bat_bus=bb, bat_dur=bdur, bat_eff_c=beff.copy(), bat_eff_d=beff.copy(),
                eta_min=0.5 * eta, eta_max=2.0 * eta + 1.0,
                gamma=np.zeros(K) if gamma is None else np.asarray(gamma, float), K=K)
+    if len(dc):
+        net["line_dc"] = np.isin(np.arange(lf.size), np.asarray(dc)).astype(np.uint8)
     return net, eta
 
 

@@ -133,6 +133,55 @@ def test_kvl_loop_flows():
     assert abs(f[0] / 1000.0 + f[1] / 1000.0 - f[2] / 500.0) < 1e-9
 
 
+# ---------------------------------------------------------------- HVDC transport links
+@pytest.mark.parametrize("F", [120.0, 1e4])
+def test_hvdc_link_closed_form(F):
+    """A transport link between a cheap and an expensive bus.  The KKT conditions of the
+    link's flow (eps f = lambda_to - lambda_from - mu) give the closed form: congested,
+    f = F, lambda_0 = c0 + eps F, lambda_1 = c1 + eps (L1 - F), d cost / dF = -mu;
+    uncongested, the cheap bus serves the whole load and the link's flow sets the price
+    difference, lambda_1 - lambda_0 = eps f."""
+    c0, c1, L1 = 10.0, 50.0, 200.0
+    net, eta = network(2, gens=[(0, c0, 1000.0), (1, c1, 1000.0)], lines=[(0, 1, 1.0, F)], dc=(0,))
+    sol = dispatch.solve(net, scenario([[0.0], [L1]], G=2), eta, opts())
+    if F < L1:
+        lam0, lam1 = c0 + EPS * F, c1 + EPS * (L1 - F)
+        assert abs(sol.flow[0, 0] - F) < 1e-6
+        mu = lam1 - lam0 - EPS * F
+        for g in (grad.envelope_grad(sol), grad.adjoint_grad(sol)):
+            assert abs(g[2] + mu) < 1e-6 * mu
+    else:
+        lam0, lam1 = c0 + EPS * L1, c0 + 2 * EPS * L1
+        assert abs(sol.flow[0, 0] - L1) < 1e-6 and abs(sol.p[1, 0]) < 1e-6
+        assert abs(grad.adjoint_grad(sol)[2]) < 1e-9
+    assert abs(sol.price[0, 0] - lam0) < 1e-6 and abs(sol.price[1, 0] - lam1) < 1e-6
+
+
+@pytest.mark.parametrize("kappa", [0.0, 50.0])
+def test_hvdc_joins_ac_islands(kappa):
+    """Two AC islands joined only by an HVDC link: one reference angle per island, the
+    link's flow decoupled from the angles, its capacity gradient equal to minus the sum
+    of the hourly price gaps net of the eps term, and the adjoint equal to the central
+    finite difference."""
+    net, eta = network(4, gens=[(0, 20.0, 300.0, 0.4), (1, 35.0, 300.0, 0.3), (2, 60.0, 300.0, 0.5),
+                                (3, 80.0, 300.0, 0.6)],
+                       lines=[(0, 1, 1000.0, 250.0), (2, 3, 800.0, 250.0), (1, 2, 1.0, 90.0)], dc=(2,))
+    sc = scenario([[20, 30], [40, 60], [120, 150], [90, 100]], G=4)
+    o = opts(kappa=kappa)
+    sol = dispatch.solve(net, sc, eta, o)
+    assert list(sol.qp.ref_bus) == [0, 2]
+    res = kkt.residuals(sol.qp, sol.x, sol.price)
+    assert res["primal"] < 1e-9 and res["dual"] < 1e-9
+    np.testing.assert_allclose(sol.flow[2], [90.0, 90.0], atol=1e-6)
+    g = grad.adjoint_grad(sol)
+    gf, ok = grad.fd_grad(net, sc, eta, o)
+    assert ok.all()
+    np.testing.assert_allclose(g, gf, atol=1e-6 * np.max(np.abs(gf)))
+    if kappa == 0.0:
+        mu = sol.price[2] - sol.price[1] - EPS * sol.flow[2]
+        assert abs(g[6] + mu.sum()) < 1e-6 * mu.sum()
+
+
 # ---------------------------------------------------------------- batteries
 @pytest.mark.parametrize("case", ["power", "spare", "energy"])
 def test_battery_arbitrage(case):
