@@ -80,12 +80,17 @@ typedef struct {
     const double* gen_emis;      /* [n_gen] t/MWh (planner's emission rate) */
     const int32_t* line_from;    /* [n_line] */
     const int32_t* line_to;      /* [n_line], != line_from */
-    const double* line_beta;     /* [n_line] MW/rad, > 0 */
-    const double* line_dtheta;   /* [n_line] rad, > 0 */
+    const double* line_beta;     /* [n_line] MW/rad, > 0 (AC lines) */
+    const double* line_dtheta;   /* [n_line] rad, > 0 (AC lines) */
     const int32_t* bat_bus;      /* [n_bat] */
     const double* bat_dur;       /* [n_bat] h, > 0 */
     const double* bat_eff_c;     /* [n_bat] in (0, 1] */
     const double* bat_eff_d;     /* [n_bat] in (0, 1] */
+    /* [n_line] or NULL (all AC): 1 marks an HVDC transport line (Sections 2.1 and 3 list
+     * HVDC among the planned assets).  Its flow f (MW, from -> to) is limited only by
+     * |f| <= eta_l, has no angle coupling, and carries eps/2 f^2 in the operating cost
+     * like the other free injections; line_beta and line_dtheta are ignored for it. */
+    const uint8_t* line_dc;
 } gx_network_desc;
 
 /* One scenario: a horizon of T hours on network `net` (Sec. 2.1: a scenario can

@@ -348,19 +348,22 @@ __global__ void __launch_bounds__(kCrsThreads, 1)
                 const int lg = sd.line0 + l;
                 const int bf = c.l_from[lg] * H + hl, bt = c.l_to[lg] * H + hl;
                 const float beta = c.l_beta[lg];
+                const float lw = c.l_w[lg];
+                const bool dc = lw == 0.f;  // HVDC transport line
                 const float d = m.dl[li], g = m.sg[li];
                 const float zf = m.thb[bf], zt = m.thb[bt];
                 const float vf = m.vf[li] - zf, vt = m.vt[li] - zt;
-                if (want) {
+                if (want && !dc) {
                     const float ef = 0.5f * (g + d) - zf, et = 0.5f * (g - d) - zt;
                     acc[8] += beta * beta * (ef * ef + et * et);
                 }
                 const float wf = zf - vf, wt = zt - vt;
                 const float tf = -beta * d - m.pbar[bf] - m.u[bf];
                 const float tt = beta * d - m.pbar[bt] - m.u[bt];
-                const float rth = c.rth_c * c.l_w[lg];
-                const float den = 2.f * rho * beta * beta + 0.5f * rth;
-                const float dun = (rho * beta * (tt - tf) + 0.5f * rth * (wf - wt)) / den;
+                const float rth = c.rth_c * lw;
+                const float den = 2.f * rho * beta * beta + 0.5f * rth + (dc ? eps : 0.f);
+                const float lin = (ADJ && dc) ? eps * c.dl[sd.e_line + (long long)l * sd.Tp + h0 + hl] : 0.f;
+                const float dun = (rho * beta * (tt - tf) + 0.5f * rth * (wf - wt) + lin) / den;
                 const float cap = fminf(m.lcap[l], c.l_dth[lg]);
                 float dn;
                 if (ADJ) dn = m.lmask[li] ? 0.f : dun;

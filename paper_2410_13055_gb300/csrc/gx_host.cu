@@ -32,6 +32,7 @@ gx_status fail(gx_status s, const std::string& msg) {
 struct NetH {
     int N = 0, G = 0, L = 0, B = 0;
     std::vector<int> gen_bus, line_from, line_to, bat_bus;
+    std::vector<uint8_t> line_dc;  // 1: HVDC transport line
     std::vector<double> gen_cost, gen_emis, line_beta, line_dth, bat_dur, bat_effc, bat_effd;
     std::vector<int> gptr, gidx, bptr, bidx, eptr, eidx;
     std::vector<float> inv_cnt, inv_wsum, dres_w, l_w;
@@ -329,12 +330,25 @@ static void derive_network(NetH& h, const gx_opts& o) {
         h.eidx[fe[h.line_from[l]]++] = 2 * l;
         h.eidx[fe[h.line_to[l]]++] = 2 * l + 1;
     }
+    // An HVDC line runs through the line kernels as a line of unit beta whose phase weight
+    // is 0 (no angle coupling: it drops out of every bus's phase average and of the phase
+    // residual) and whose angle limit never binds; the kernels read w_l = 0 as "transport
+    // line" and add its eps/2 f^2 term.
+    int n_ac = 0;
     double mb2 = 0;
-    for (int l = 0; l < h.L; ++l) mb2 += h.line_beta[l] * h.line_beta[l];
-    mb2 = h.L ? mb2 / h.L : 1.0;
+    for (int l = 0; l < h.L; ++l) {
+        if (h.line_dc[l]) {
+            h.line_beta[l] = 1.0;
+            h.line_dth[l] = 3.0e38;
+        } else {
+            mb2 += h.line_beta[l] * h.line_beta[l];
+            ++n_ac;
+        }
+    }
+    mb2 = n_ac ? mb2 / n_ac : 1.0;
     h.l_w.resize(h.L);
     for (int l = 0; l < h.L; ++l)
-        h.l_w[l] = (float)(o.theta_weight ? h.line_beta[l] * h.line_beta[l] : mb2);
+        h.l_w[l] = h.line_dc[l] ? 0.f : (float)(o.theta_weight ? h.line_beta[l] * h.line_beta[l] : mb2);
     h.inv_cnt.resize(N); h.inv_wsum.resize(N); h.dres_w.resize(N);
     for (int n = 0; n < N; ++n) {
         const int cnt = 1 + (h.gptr[n + 1] - h.gptr[n]) + (h.bptr[n + 1] - h.bptr[n]) + (h.eptr[n + 1] - h.eptr[n]);
@@ -520,6 +534,9 @@ gx_status gx_network_create(const gx_network_desc* nets, int n_nets, const gx_sc
         h.line_to.assign(d.line_to, d.line_to + h.L);
         h.line_beta.assign(d.line_beta, d.line_beta + h.L);
         h.line_dth.assign(d.line_dtheta, d.line_dtheta + h.L);
+        h.line_dc.assign(h.L, 0);
+        if (d.line_dc)
+            for (int l = 0; l < h.L; ++l) h.line_dc[l] = d.line_dc[l] != 0;
         h.bat_bus.assign(d.bat_bus, d.bat_bus + h.B);
         h.bat_dur.assign(d.bat_dur, d.bat_dur + h.B);
         h.bat_effc.assign(d.bat_eff_c, d.bat_eff_c + h.B);
@@ -532,6 +549,7 @@ gx_status gx_network_create(const gx_network_desc* nets, int n_nets, const gx_sc
             if (h.line_from[l] < 0 || h.line_from[l] >= h.N || h.line_to[l] < 0 || h.line_to[l] >= h.N)
                 return bad("line bus out of range");
             if (h.line_from[l] == h.line_to[l]) return bad("line with both ends on one bus");
+            if (h.line_dc[l]) continue;  // beta and dtheta unused
             if (!(h.line_beta[l] > 0 && isfin(h.line_beta[l]))) return bad("line_beta must be > 0");
             if (!(h.line_dth[l] > 0 && isfin(h.line_dth[l]))) return bad("line_dtheta must be > 0");
         }

@@ -120,13 +120,16 @@ __device__ __forceinline__ void line_compute(const Ctx& c, const StatePtrs& X, c
     const float beta = L.beta, d = L.d, g = L.g;
     const float vf = L.qf - L.zf, vt = L.qt - L.zt;
     const float ef = 0.5f * (g + d) - L.zf, et = 0.5f * (g - d) - L.zt;  // y - z of the last iteration
-    th2 += beta * beta * (ef * ef + et * et);
+    const bool dc = L.w == 0.f;  // HVDC transport line: no phase coupling, eps/2 f^2 cost
+    if (!dc) th2 += beta * beta * (ef * ef + et * et);
     const float wf = L.zf - vf, wt = L.zt - vt;
     const float tf = -beta * d - L.pbf - L.uf;  // power targets of the two terminals
     const float tt = beta * d - L.pbt - L.ut;
     const float rth = c.rth_c * L.w;
-    const float den = 2.f * c.rho * beta * beta + 0.5f * rth;
-    const float dun = (c.rho * beta * (tt - tf) + 0.5f * rth * (wf - wt)) / den;
+    const float den = 2.f * c.rho * beta * beta + 0.5f * rth + (dc ? c.eps : 0.f);
+    // adjoint of a transport line: the linear term eps f* of grad h at the solved flow
+    const float lin = (ADJ && dc) ? c.eps * c.dl[L.row] : 0.f;
+    const float dun = (c.rho * beta * (tt - tf) + 0.5f * rth * (wf - wt) + lin) / den;
     const float cap = fminf(L.capf, L.dth);
     if (MODE == M_MASK) {
         uint8_t code = AL_FREE;
@@ -173,7 +176,7 @@ __global__ void __launch_bounds__(kBlock) k_line(const Ctx c, int want_res) {
             line_index<MODE, ADJ>(c, sc, base + r * kBlock, L);
             if (!L.valid) continue;
             float d0 = 0.f, g0 = 0.f, q0f = 0.f, q0t = 0.f;
-            if (!ADJ && c.warm) {
+            if (!ADJ && c.warm && c.l_w[L.lg] != 0.f) {  // (a transport line's flow starts at 0)
                 const float* th = c.warm + c.warm_half;
                 d0 = th[L.bf] - th[L.bt];
                 g0 = th[L.bf] + th[L.bt];
@@ -795,10 +798,14 @@ __global__ void __launch_bounds__(kQBlock) k_line4(const Ctx c, int want_res) {
         int mk[4] = {0, 0, 0, 0};
         if (ADJ) ldm4(c.m_line + row, mk);
         const float beta = c.l_beta[lg];
-        const float rth = c.rth_c * c.l_w[lg];
+        const float w = c.l_w[lg];
+        const bool dc = w == 0.f;  // HVDC transport line: no phase coupling, eps/2 f^2 cost
+        const float rth = c.rth_c * w;
         const float capf = fmaxf(c.eta[sc.eta0 + sc.G + l], 0.f) / beta;
         const float cap = fminf(capf, c.l_dth[lg]);
-        const float den = 2.f * c.rho * beta * beta + 0.5f * rth;
+        const float den = 2.f * c.rho * beta * beta + 0.5f * rth + (dc ? c.eps : 0.f);
+        float fs[4] = {0.f, 0.f, 0.f, 0.f};  // adjoint of a transport line: eps f* of grad h
+        if (ADJ && dc) ld4(c.dl + row, fs);
         float dn[4], gn[4], nf[4], nt[4];
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
@@ -806,11 +813,11 @@ __global__ void __launch_bounds__(kQBlock) k_line4(const Ctx c, int want_res) {
             if (t + h >= sc.T) continue;
             const float vf = qf[h] - zf[h], vt = qt[h] - zt[h];
             const float ef = 0.5f * (g[h] + d[h]) - zf[h], et = 0.5f * (g[h] - d[h]) - zt[h];
-            th2 += beta * beta * (ef * ef + et * et);
+            if (!dc) th2 += beta * beta * (ef * ef + et * et);
             const float wf = zf[h] - vf, wt = zt[h] - vt;
             const float tf = -beta * d[h] - pbf[h] - uf[h];
             const float tt = beta * d[h] - pbt[h] - ut[h];
-            const float dun = (c.rho * beta * (tt - tf) + 0.5f * rth * (wf - wt)) / den;
+            const float dun = (c.rho * beta * (tt - tf) + 0.5f * rth * (wf - wt) + c.eps * fs[h]) / den;
             if (ADJ) dn[h] = mk[h] ? 0.f : dun;
             else dn[h] = clampf(dun, -cap, cap);
             gn[h] = wf + wt;
@@ -1190,6 +1197,14 @@ __global__ void __launch_bounds__(kBlock) k_cost(const Ctx c, const int* in_batc
             const double ch = c.zc[sc.e_bat + i], di = c.zd[sc.e_bat + i];
             cs += 0.5 * eps * (ch * ch + di * di);
         }
+        // HVDC transport lines (phase weight 0, unit beta): eps/2 f^2
+        const long long nl = (long long)sc.L * sc.Tp;
+        for (long long i = (long long)nb * kBlock + threadIdx.x; i < nl; i += stride) {
+            const int l = (int)(i / sc.Tp), t = (int)(i - (long long)l * sc.Tp);
+            if (t >= sc.T || c.l_w[sc.line0 + l] != 0.f) continue;
+            const double f = c.dl[sc.e_line + i];
+            cs += 0.5 * eps * f * f;
+        }
     }
     cs = warp_sum_d(cs);
     em = warp_sum_d(em);
@@ -1276,10 +1291,13 @@ __global__ void __launch_bounds__(kBlock) k_grad(const Ctx c, int envelope, cons
             const float wf = th[bf] - vf, wt = th[bt] - vt;
             const float tf = -beta * d - pb[bf] - uu[bf];
             const float tt = beta * d - pb[bt] - uu[bt];
-            // derivative of the line prox objective in delta at the frozen delta
+            // derivative of the line prox objective in delta at the frozen delta (a transport
+            // line adds eps/2 f^2, and in the adjoint the linear term -eps f*)
             const float dstar = envelope ? d : 0.f;
+            const bool dc = c.l_w[sc.line0 + l] == 0.f;
+            const float Fdc = dc ? c.eps * (envelope ? dstar : -c.dl[rr]) : 0.f;
             const float Fp = rho * beta * (beta * dstar + tf) + rho * beta * (beta * dstar - tt) +
-                             0.5f * rth * (dstar - (wf - wt));
+                             0.5f * rth * (dstar - (wf - wt)) + Fdc;
             float xi;
             if (envelope) xi = (m == AL_FUP) ? Fp / beta : -Fp / beta;
             else xi = (m == AL_FUP) ? -Fp / beta : Fp / beta;

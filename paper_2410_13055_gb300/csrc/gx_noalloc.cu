@@ -36,8 +36,8 @@ __device__ __forceinline__ double warp_sum_nd(double v) {
 }
 
 // Same sums as the workspace cost reduction: sum c p + eps/2 p^2 over generators,
-// VOLL sh + eps/2 sh^2 over loads, eps/2 (ch^2 + dis^2) over batteries; plus the
-// emission total e p.  Block b of `nblk` takes a strided share of scenario s.
+// VOLL sh + eps/2 sh^2 over loads, eps/2 (ch^2 + dis^2) over batteries, eps/2 f^2 over
+// HVDC lines; plus the emission total e p.  Block b of `nblk` takes a strided share of scenario s.
 __global__ void __launch_bounds__(kBlock) k_cost_noalloc(const Ctx c, int s, int nblk, double* part) {
     const ScenDev sc = c.scen[s];
     const int nb = blockIdx.x;
@@ -61,6 +61,13 @@ __global__ void __launch_bounds__(kBlock) k_cost_noalloc(const Ctx c, int s, int
         if ((int)(i % sc.Tp) >= sc.T) continue;
         const double ch = c.zc[sc.e_bat + i], di = c.zd[sc.e_bat + i];
         cs += 0.5 * eps * (ch * ch + di * di);
+    }
+    const long long nl = (long long)sc.L * sc.Tp;
+    for (long long i = (long long)nb * kBlock + threadIdx.x; i < nl; i += stride) {
+        const int l = (int)(i / sc.Tp);
+        if ((int)(i - (long long)l * sc.Tp) >= sc.T || c.l_w[sc.line0 + l] != 0.f) continue;
+        const double f = c.dl[sc.e_line + i];
+        cs += 0.5 * eps * f * f;
     }
     cs = warp_sum_nd(cs);
     em = warp_sum_nd(em);

@@ -37,7 +37,8 @@ class NetworkDesc(C.Structure):
     _fields_ = [("n_bus", C.c_int), ("n_gen", C.c_int), ("n_line", C.c_int), ("n_bat", C.c_int),
                 ("gen_bus", _i32p), ("gen_cost", _f64p), ("gen_emis", _f64p),
                 ("line_from", _i32p), ("line_to", _i32p), ("line_beta", _f64p), ("line_dtheta", _f64p),
-                ("bat_bus", _i32p), ("bat_dur", _f64p), ("bat_eff_c", _f64p), ("bat_eff_d", _f64p)]
+                ("bat_bus", _i32p), ("bat_dur", _f64p), ("bat_eff_c", _f64p), ("bat_eff_d", _f64p),
+                ("line_dc", C.POINTER(C.c_uint8))]
 
 
 class ScenarioDesc(C.Structure):
@@ -171,6 +172,10 @@ class Network:
             for name, a in arrs.items():
                 ct = _i32p if a.dtype == np.int32 else _f64p
                 setattr(d, name, a.ctypes.data_as(ct))
+            if "line_dc" in n and np.any(n["line_dc"]):
+                dc = np.ascontiguousarray(n["line_dc"], np.uint8)
+                arrs["line_dc"] = dc
+                d.line_dc = dc.ctypes.data_as(C.POINTER(C.c_uint8))
         sd = (ScenarioDesc * len(scens))()
         for s, sc in enumerate(scens):
             load = np.ascontiguousarray(sc["load"], np.float64)

@@ -257,6 +257,39 @@ def custom(n_bus, n_lines, n_gen, n_bat, T, S=1, seed=0, net_index=0):
     return net, scens
 
 
+def add_hvdc(net, n_dc, seed=0, cap=(200.0, 600.0)):
+    """Append `n_dc` HVDC transport lines between random bus pairs not already joined
+    (the paper's WECC case plans 3 HVDC lines next to 1191 AC lines).  Their plan entries
+    go at the end of the line block: eta_min = U[cap], eta_max = 2 eta_min, gamma = the
+    line rate.  Returns a new network dict (inputs only)."""
+    rng = _rng(seed)
+    N = int(net["n_bus"])
+    G, L = net["gen_bus"].size, net["line_from"].size
+    have = set(zip(net["line_from"].tolist(), net["line_to"].tolist()))
+    pairs = []
+    while len(pairs) < n_dc:
+        a, b = (int(x) for x in rng.choice(N, size=2, replace=False))
+        if (a, b) not in have and (b, a) not in have:
+            have.add((a, b))
+            pairs.append((a, b))
+    out = dict(net)
+    fa = np.array([p[0] for p in pairs], dtype=np.int64)
+    ta = np.array([p[1] for p in pairs], dtype=np.int64)
+    c = rng.uniform(cap[0], cap[1], size=n_dc)
+    out["line_from"] = np.concatenate([net["line_from"], fa])
+    out["line_to"] = np.concatenate([net["line_to"], ta])
+    out["line_beta"] = np.concatenate([net["line_beta"], np.ones(n_dc)])
+    out["line_dtheta"] = np.concatenate([net["line_dtheta"], np.full(n_dc, math.pi / 6)])
+    out["line_dc"] = np.concatenate([np.asarray(net.get("line_dc", np.zeros(L)), np.uint8), np.ones(n_dc, np.uint8)])
+    rate = net["gamma"][G] if L else GAMMA_LINE_ANNUAL / 8760.0
+    ins = lambda v, new: np.concatenate([v[:G + L], new, v[G + L:]])
+    out["eta_min"] = ins(net["eta_min"], c)
+    out["eta_max"] = ins(net["eta_max"], 2.0 * c)
+    out["gamma"] = ins(net["gamma"], np.full(n_dc, rate))
+    out["K"] = int(net["K"]) + n_dc
+    return out
+
+
 CONFIGS = {"tiny": tiny, "medium": medium, "batching": batching, "scale": scale}
 
 

@@ -40,7 +40,7 @@ def ref_groups(qp):
 
 
 def pack_x(qp, g):
-    return qp.pack(g["p"], g["shed"], g["theta"], g["ch"], g["dis"], g["soc"])
+    return qp.pack(g["p"], g["shed"], g["theta"], g["ch"], g["dis"], g["soc"], fdc=g["flow"])
 
 
 def rel(a, b):
