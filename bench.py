@@ -110,7 +110,7 @@ def build_workload(config, rank=0, scenarios=None):
         # one network; rank r > 0 draws its own scenarios (weak scaling: 16 per GPU)
         nets, scens = synth.medium(seed=1, S=scenarios or 16, scen_seed=None if rank == 0 else 1000 + rank)
     elif config == "scale":
-        nets, scens = synth.scale(seed=3 + seed_shift)
+        nets, scens = synth.scale(seed=3 + seed_shift, S=scenarios or 52)
     elif config == "batching":
         nets, scens = synth.batching(seed=2 + seed_shift)
     elif config == "tiny":
@@ -145,18 +145,26 @@ def algorithmic_bytes(nets, scens):
 # DRAM bytes (read + write) per launch from one ncu capture of the solver kernels on the
 # 100-bus network with 64 scenarios (profiles/solver_kernels_medium64_full.md); valid only
 # while gx_kernels.cu is the source that was profiled.
-PROFILED = {"sha256_prefix": "1939f5362321703d", "scenarios": 64, "config": "medium",
-            "source": "profiles/solver_kernels_medium64_full.md",
-            "traffic": {"k_bus": 65.450752e6, "k_line": 38.7456e6, "k_bat": 21.11488e6}}
+PROFILED = {
+    "sha256_prefix": "82e7622b4dfb56d3",
+    "medium": {"scenarios": 64, "source": "profiles/solver_kernels_medium64_full.md",
+               "traffic": {"k_bus": 65.426176e6, "k_line": 38.745344e6, "k_bat": 21.115136e6}},
+    "scale": {"scenarios": 13, "source": "profiles/solver_kernels_scale13.md",
+              "traffic": {"k_bus": 388.552448e6, "k_line": 207.390464e6, "k_bat": 43.613952e6}},
+}
 
 
 def profiled_traffic(config, n_scen, kernel):
+    """DRAM bytes per launch from the capture of this workload, scaled by scenarios (both
+    captures are above L2, where traffic grows in proportion to the scenarios); None if
+    the kernels changed since, or the workload has no capture."""
     import hashlib
     src = os.path.join(ROOT, "paper_2410_13055_gb300", "csrc", "gx_kernels.cu")
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if sha != PROFILED["sha256_prefix"] or config != PROFILED["config"] or kernel not in PROFILED["traffic"]:
+    cap = PROFILED.get(config)
+    if sha != PROFILED["sha256_prefix"] or cap is None or kernel not in cap["traffic"]:
         return None
-    return PROFILED["traffic"][kernel] * n_scen / PROFILED["scenarios"]
+    return cap["traffic"][kernel] * n_scen / cap["scenarios"]
 
 
 def run_gx(args):
@@ -352,7 +360,8 @@ def run_gx(args):
             tr = profiled_traffic(args.config, len(scens), dom)
             roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                     "frac": round(achieved / peak, 4), "traffic": tr,
-                    "traffic_note": (f"ncu dram read+write per launch, scaled by scenarios from {PROFILED['source']}"
+                    "traffic_note": (f"ncu dram read+write per launch, scaled by scenarios from "
+                                     f"{PROFILED[args.config]['source']}"
                                      if tr is not None else "kernel changed since the ncu capture"),
                     "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
                     "bytes_per_launch": ab[dom], "avg_launch_us": round(avg_ms * 1e3, 2),
@@ -472,7 +481,8 @@ def main():
     ap.add_argument("--impl", default="gx", choices=["gx", "reference"])
     ap.add_argument("--check-every", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--scenarios", type=int, default=None, help="scenario count of the medium workload (default 16)")
+    ap.add_argument("--scenarios", type=int, default=None,
+                    help="scenario count of the medium (default 16) or scale (default 52) workload")
     ap.add_argument("--quick", action="store_true", help="timed previous-plan steps only (profiling runs)")
     ap.add_argument("--persistent", action="store_true",
                     help="cluster-resident persistent launches for the scenarios that fit shared memory")
