@@ -207,8 +207,13 @@ gx_status gx_dispatch_grad_batch(gx_network* net, const float* eta_dev, int warm
 gx_status gx_plan_step(gx_network* net, float* eta_dev, const float* grad_dev, const float* gamma_dev,
                        const float* eta_min_dev, const float* eta_max_dev, float alpha, void* stream);
 
-/* Replay each residual-check chunk as one CUDA graph (default on) or launch its kernels
- * one by one (off).  Results are identical; graphs cut the host launch cost. */
+/* How the per-iteration kernels are launched.  2 (default): the whole loop is one CUDA
+ * graph; a conditional WHILE node repeats one residual-check chunk and the convergence
+ * test on the device, so the host launches once and synchronises once per loop (used
+ * when max_iter is a multiple of check_every and sampled timing is off; otherwise mode 1).
+ * 1: one graph per residual-check chunk, the host reading the active-scenario count after
+ * each.  0: kernel-by-kernel launches.  All modes run the same kernels in the same order:
+ * results are bitwise identical.  Other values: GX_ERR_INVALID_ARG. */
 gx_status gx_network_use_graphs(gx_network* net, int on);
 
 /* Cluster-resident solver (default off).  A scenario whose state fits the shared memory

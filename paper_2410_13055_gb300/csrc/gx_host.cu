@@ -110,15 +110,15 @@ struct gx_network {
     // CUDA graphs of one residual-check chunk, keyed by what their captured parameters depend on
     struct ChunkGraph {
         bool valid = false;
-        int adj = 0, chunk = 0, prof = 0;
+        int adj = 0, chunk = 0, prof = 0, loop = 0;  // loop: the whole loop (conditional WHILE node)
         const float* eta = nullptr;
         cudaGraphExec_t exec = nullptr;
     } graphs[4];
     int graph_next = 0;
     cudaStream_t cap_stream = nullptr, cap_stream2 = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-    int* h_nact = nullptr;  // pinned host copy of the active-scenario count
-    bool use_graphs = true;
+    int* h_nact = nullptr;  // pinned host copies: [0] active-scenario count, [1] iteration counter
+    int use_graphs = 2;     // 0 eager launches, 1 one graph per chunk, 2 the whole loop as one graph
     void drop_graphs() {
         for (auto& g : graphs) {
             if (g.exec) cudaGraphExecDestroy(g.exec);
@@ -253,6 +253,19 @@ static void make_ctx(gx_network* net) {
 }
 
 namespace gx {
+// Condition of the device-side loop (a conditional WHILE node around one residual-check
+// chunk): run another chunk while a scenario is still iterating and the cap is not reached.
+// The reduction marks every scenario done once the counter reaches the cap, so the loop
+// ends after at most cap / chunk bodies.
+__global__ void k_loop_cond(const int* n_active, const int* iter_ctr, int max_it, cudaGraphConditionalHandle h) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(h, (*n_active > 0 && *iter_ctr < max_it) ? 1u : 0u);
+}
+
+int launch_loop_cond(const Ctx& c, int max_it, cudaGraphConditionalHandle h, cudaStream_t st) {
+    k_loop_cond<<<1, 32, 0, st>>>(c.n_active, c.iter_ctr, max_it, h);
+    return 1;
+}
+
 const Ctx* gx_internal_ctx(const gx_network* net) { return (net && net->dev) ? &net->ctx : nullptr; }
 ScenDev gx_internal_scen(const gx_network* net, int s) { return net->sdev[s]; }
 gx_status gx_internal_fail(gx_status s, const std::string& msg) { return fail(s, msg); }
@@ -771,7 +784,7 @@ gx_status gx_network_bind(gx_network* net, void* dev_mem, size_t bytes, void* st
     GX_CUDA(cudaMemsetAsync(net->dev + net->static_end, 0, net->lay.total - net->static_end, st));
     GX_CUDA(cudaStreamSynchronize(st));
     net->dd_dirty = false;
-    if (!net->h_nact) GX_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&net->h_nact), sizeof(int), cudaHostAllocDefault));
+    if (!net->h_nact) GX_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&net->h_nact), 2 * sizeof(int), cudaHostAllocDefault));
     if (!net->cap_stream) GX_CUDA(cudaStreamCreateWithFlags(&net->cap_stream, cudaStreamNonBlocking));
     if (!net->cap_stream2) GX_CUDA(cudaStreamCreateWithFlags(&net->cap_stream2, cudaStreamNonBlocking));
     if (!net->ev_fork) GX_CUDA(cudaEventCreateWithFlags(&net->ev_fork, cudaEventDisableTiming));
@@ -852,7 +865,7 @@ gx_status gx_network_scenario_info(const gx_network* net, int s, int* T, int* Tp
 // per-scenario reduction and the copy of the active count to the host.  With `prof` the
 // chunk's last iteration is bracketed by timing events (eager launches only).
 static gx_status enqueue_iters(gx_network* net, const Ctx& c, int adj, int chunk, int j0, int j1, bool tick,
-                               bool reduce, bool prof, cudaStream_t st, int* launches) {
+                               bool reduce, bool prof, cudaStream_t st, int* launches, bool to_host = true) {
     const int mode = adj ? M_ADJ : M_FWD;
     const double tol = adj ? net->opts.adj_tol : net->opts.tol;
     if (tick) *launches += launch_tick(c, chunk, st);
@@ -884,7 +897,7 @@ static gx_status enqueue_iters(gx_network* net, const Ctx& c, int adj, int chunk
     if (reduce) {
         GX_CUDA(cudaMemsetAsync(c.n_active, 0, sizeof(int), st));
         *launches += launch_reduce(c, adj, tol, st);
-        GX_CUDA(cudaMemcpyAsync(net->h_nact, c.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+        if (to_host) GX_CUDA(cudaMemcpyAsync(net->h_nact, c.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
     }
     return GX_OK;
 }
@@ -894,7 +907,7 @@ static gx_status enqueue_iters(gx_network* net, const Ctx& c, int adj, int chunk
 // on the legacy default stream).  Cached by everything its parameters depend on.
 static gx_status chunk_graph(gx_network* net, const Ctx& c, int adj, int chunk, bool prof, cudaGraphExec_t* out) {
     for (auto& g : net->graphs)
-        if (g.valid && g.adj == adj && g.chunk == chunk && g.prof == (int)prof && g.eta == c.eta) {
+        if (g.valid && !g.loop && g.adj == adj && g.chunk == chunk && g.prof == (int)prof && g.eta == c.eta) {
             *out = g.exec;
             return GX_OK;
         }
@@ -915,6 +928,57 @@ static gx_status chunk_graph(gx_network* net, const Ctx& c, int adj, int chunk, 
     if (ce != cudaSuccess) return fail(GX_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ce));
     g.valid = true;
     g.adj = adj; g.chunk = chunk; g.prof = prof; g.eta = c.eta;
+    *out = g.exec;
+    return GX_OK;
+}
+
+// The whole iteration loop as one graph: a conditional WHILE node whose body is one
+// residual-check chunk (tick, check_every iterations, reduction) followed by k_loop_cond,
+// which sets the node's condition on the device.  The host launches it once per solve and
+// synchronises once, instead of once per chunk.
+static gx_status loop_graph(gx_network* net, const Ctx& c, int adj, int every, int max_it, cudaGraphExec_t* out) {
+    for (auto& g : net->graphs)
+        if (g.valid && g.loop && g.adj == adj && g.chunk == every && g.eta == c.eta) {
+            *out = g.exec;
+            return GX_OK;
+        }
+    auto& g = net->graphs[net->graph_next];
+    net->graph_next = (net->graph_next + 1) % 4;
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g = gx_network::ChunkGraph{};
+    cudaGraph_t graph = nullptr;
+    GX_CUDA(cudaGraphCreate(&graph, 0));
+    auto bail = [&](cudaError_t ce, const char* what) {
+        cudaGraphDestroy(graph);
+        return fail(GX_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(ce));
+    };
+    cudaGraphConditionalHandle h;
+    cudaError_t ce = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
+    if (ce != cudaSuccess) return bail(ce, "cudaGraphConditionalHandleCreate");
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    ce = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &p);
+    if (ce != cudaSuccess) return bail(ce, "cudaGraphAddNode");
+    cudaGraph_t body = p.conditional.phGraph_out[0];
+    ce = cudaStreamBeginCaptureToGraph(net->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (ce != cudaSuccess) return bail(ce, "cudaStreamBeginCaptureToGraph");
+    int dummy = 0;
+    gx_status e = enqueue_iters(net, c, adj, every, 0, every, true, true, false, net->cap_stream, &dummy, false);
+    if (!e) launch_loop_cond(c, max_it, h, net->cap_stream);
+    cudaGraph_t captured = nullptr;
+    ce = cudaStreamEndCapture(net->cap_stream, &captured);
+    if (e) { cudaGraphDestroy(graph); return e; }
+    if (ce != cudaSuccess) return bail(ce, "cudaStreamEndCapture");
+    ce = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return fail(GX_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ce));
+    g.valid = true;
+    g.loop = 1;
+    g.adj = adj; g.chunk = every; g.eta = c.eta;
     *out = g.exec;
     return GX_OK;
 }
@@ -968,11 +1032,14 @@ static gx_status run_crs(gx_network* net, int adj, cudaStream_t st, int* launche
 }
 
 // Iterate the forward (adj = 0) or adjoint (adj = 1) message passing until every
-// scenario of the batch meets its tolerance or the cap is reached.  Each chunk of
-// check_every iterations is replayed as one CUDA graph; the stream is synchronised
-// once per chunk to read the number of scenarios still iterating.  While kernels are
-// being timed, a chunk's last iteration and its reduction run as eager launches
-// bracketed by events (event times cannot be read from graph-recorded events).
+// scenario of the batch meets its tolerance or the cap is reached.  Graph mode 2 (the
+// default, when the cap is a multiple of check_every and kernels are not being timed)
+// replays the whole loop as one graph whose conditional node tests convergence on the
+// device.  Otherwise each chunk of check_every iterations is one graph (mode 1) or eager
+// launches (mode 0), and the stream is synchronised once per chunk to read the number of
+// scenarios still iterating.  While kernels are being timed, a chunk's last iteration
+// and its reduction run as eager launches bracketed by events (event times cannot be read
+// from graph-recorded events).
 static gx_status run_loop(gx_network* net, int adj, cudaStream_t st, int* launches, int* iters_out) {
     const Ctx& c = adj ? net->actx : net->ctx;
     const int max_it = adj ? net->opts.adj_max_iter : net->opts.max_iter;
@@ -981,6 +1048,19 @@ static gx_status run_loop(gx_network* net, int adj, cudaStream_t st, int* launch
     const int per_it = (c.n_line_blk > 0) + (c.n_bat_warps > 0) + (c.n_bus_blk > 0);
     int it = 0;
     GX_CUDA(cudaMemsetAsync(c.iter_ctr, 0, sizeof(int), st));
+    if (net->use_graphs == 2 && !prof && max_it % every == 0) {
+        cudaGraphExec_t exec = nullptr;
+        if (gx_status e = loop_graph(net, c, adj, every, max_it, &exec)) return e;
+        GX_CUDA(cudaGraphLaunch(exec, st));
+        GX_CUDA(cudaMemcpyAsync(net->h_nact + 1, c.iter_ctr, sizeof(int), cudaMemcpyDeviceToHost, st));
+        GX_CUDA(cudaGetLastError());
+        GX_CUDA(cudaStreamSynchronize(st));
+        it = net->h_nact[1];
+        // per body: tick, the iterations, the reduction and the condition kernel
+        *launches += (it / every) * (3 + every * per_it);
+        *iters_out = it;
+        return GX_OK;
+    }
     while (it < max_it) {
         const int chunk = std::min(every, max_it - it);
         int nk = 0;
@@ -1177,7 +1257,8 @@ gx_status gx_plan_step(gx_network* net, float* eta_dev, const float* grad_dev, c
 
 gx_status gx_network_use_graphs(gx_network* net, int on) {
     if (!net) return fail(GX_ERR_INVALID_ARG, "net is NULL");
-    net->use_graphs = on != 0;
+    if (on < 0 || on > 2) return fail(GX_ERR_INVALID_ARG, "graph mode must be 0, 1 or 2");
+    net->use_graphs = on;
     return GX_OK;
 }
 

@@ -194,6 +194,7 @@ int launch_line(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st);
 int launch_bat(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st);
 int launch_bus(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st);
 int launch_prep(const Ctx& c, cudaStream_t st);
+int launch_loop_cond(const Ctx& c, int max_it, cudaGraphConditionalHandle h, cudaStream_t st);
 // Cluster-resident solver (gx_crs.cu): iterate the scenarios in `scen` (in_batch ones
 // only) to convergence, C CTAs per scenario, hpl hours per lane of a battery warp.
 cudaError_t crs_prepare(int adj, int hpl, size_t smem_max);

@@ -280,9 +280,12 @@ class Network:
         self.last_grad_status = rc
         return out
 
-    def use_graphs(self, on=True):
-        """Replay residual-check chunks as CUDA graphs (default) or launch kernel by kernel."""
-        _check(_lib.gx_network_use_graphs(self._h, int(bool(on))), "gx_network_use_graphs", False)
+    def use_graphs(self, on=True, device_loop=True):
+        """Launch mode of the per-iteration kernels (gx_network_use_graphs): the whole loop
+        as one graph with a device-side convergence test (default), one graph per
+        residual-check chunk (device_loop=False), or kernel by kernel (on=False)."""
+        mode = 0 if not on else (2 if device_loop else 1)
+        _check(_lib.gx_network_use_graphs(self._h, mode), "gx_network_use_graphs", False)
 
     def use_persistent(self, on=True):
         """Cluster-resident persistent launches for the scenarios that fit (default) or the

@@ -138,17 +138,41 @@ def test_medium_full_size_properties():
     assert abs(fd - lin) <= 2e-2 * abs(fd), (fd, lin)
 
 
-def test_graph_replay_matches_eager_launches_bitwise():
-    """Chunks replayed as CUDA graphs run the same kernels in the same order."""
+@pytest.mark.parametrize("case", ["tiny", "medium4"])
+def test_graph_modes_match_eager_launches_bitwise(case):
+    """The device-side loop (one graph with a conditional WHILE node), one graph per chunk
+    and kernel-by-kernel launches run the same kernels in the same order: identical
+    iteration counts and bitwise-identical dispatch and gradient, forward and adjoint,
+    over two plan steps (the second from the previous plan's state)."""
+    nets, scens = synth.tiny() if case == "tiny" else synth.medium(S=4, T=48)
+    e0 = eta_tensor(np.concatenate([n["eta_min"] for n in nets]))
+    out = []
+    for mode in ((True, True), (True, False), (False, True)):
+        net = gpu_net(nets, scens, kappa=50.0, tol=1e-5, adj_tol=1e-4, max_iter=50000, adj_max_iter=50000)
+        net.use_graphs(*mode)
+        e = e0.clone()
+        res = []
+        for k in range(2):
+            assert net.solve(e, warm="cold" if k == 0 else "prev") == 0
+            f_it = net.last_stats["iters_max"]
+            g = net.grad(e, warm="cold" if k == 0 else "prev").cpu().numpy().copy()
+            res.append((net.array("p").cpu().numpy().copy(), g, f_it, net.last_grad_stats["iters_max"]))
+            e = (e * 1.01).contiguous()
+        out.append(res)
+    for other in out[1:]:
+        for a, b in zip(out[0], other):
+            assert a[2] == b[2] and a[3] == b[3]
+            assert np.array_equal(a[0], b[0])
+            assert np.array_equal(a[1], b[1])
+
+
+def test_device_loop_respects_the_iteration_cap():
+    """With a cap below the iterations needed, the device-side loop stops at the cap and
+    reports GX_NOT_CONVERGED, like the host-checked loop."""
     nets, scens = synth.tiny()
     e = eta_tensor(nets[0]["eta_min"])
-    out = []
-    for graphs in (True, False):
-        net = gpu_net(nets, scens, kappa=50.0, tol=1e-5, adj_tol=1e-4, max_iter=50000, adj_max_iter=50000)
-        net.use_graphs(graphs)
-        assert net.solve(e) == 0
-        g = net.grad(e).cpu().numpy().copy()
-        out.append((net.array("p", 0).cpu().numpy().copy(), g, net.last_stats["iters_max"]))
-    assert out[0][2] == out[1][2]
-    assert np.array_equal(out[0][0], out[1][0])
-    assert np.array_equal(out[0][1], out[1][1])
+    for mode in ((True, True), (True, False)):
+        net = gpu_net(nets, scens, kappa=50.0, tol=1e-9, max_iter=60, check_every=20)
+        net.use_graphs(*mode)
+        assert net.solve(e) == 1
+        assert net.last_stats["iters_max"] == 60 and net.last_stats["n_converged"] == 0
