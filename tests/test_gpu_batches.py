@@ -176,3 +176,51 @@ def test_device_loop_respects_the_iteration_cap():
         net.use_graphs(*mode)
         assert net.solve(e) == 1
         assert net.last_stats["iters_max"] == 60 and net.last_stats["n_converged"] == 0
+
+
+def test_scale_full_size_properties():
+    """The full Scale workload (2000 buses, 52 x 168 h) at the bench's 1e-3 tolerance,
+    checked through properties that hold at any size (the dense oracle cannot hold it):
+    every scenario converges; on sampled scenarios bounds hold, every bus-hour's power
+    balance computed from the reported injections, flows and battery powers is within
+    the residual tolerance, flows respect their limits, and prices satisfy the generator
+    optimality condition lambda = c + eps p at generators strictly inside their bounds;
+    with kappa = 0 (h = cost) every capacity gradient entry is <= 0."""
+    nets, scens = synth.scale()
+    n = nets[0]
+    G, L = n["gen_bus"].size, n["line_from"].size
+    eta = n["eta_min"] * 1.05
+    eps = synth.default_opts()["eps"]
+    net = gpu_net(nets, scens, kappa=0.0, tol=1e-3, adj_tol=1e-3, max_iter=50000, adj_max_iter=50000)
+    e = eta_tensor(eta)
+    assert net.solve(e) == 0
+    assert net.last_stats["n_converged"] == 52
+    for s in (0, 25, 51):
+        sc = scens[s]
+        p = net.array("p", s).double().cpu().numpy()
+        cap = eta[:G][:, None] * sc["cf"]
+        assert np.all(p >= -1e-4) and np.all(p <= cap * (1 + 1e-5) + 1e-3)
+        sh = net.array("shed", s).double().cpu().numpy()
+        assert np.all(sh >= -1e-3) and np.all(sh <= sc["load"] + 1e-3)
+        f = net.array("flow", s).double().cpu().numpy()
+        assert np.all(np.abs(f) <= eta[G:G + L][:, None] * (1 + 1e-5) + 1e-3)
+        ch = net.array("ch", s).double().cpu().numpy()
+        dis = net.array("dis", s).double().cpu().numpy()
+        inj = np.zeros_like(sc["load"])
+        np.add.at(inj, n["gen_bus"], p)
+        np.add.at(inj, n["bat_bus"], dis - ch)
+        inj += sh - sc["load"]
+        np.add.at(inj, n["line_from"], -f)
+        np.add.at(inj, n["line_to"], f)
+        # the primal residual bounds |imbalance| / |load| by the tolerance; the reported
+        # battery powers are the inner box copies, within the inner residual of the x-step
+        assert np.linalg.norm(inj) <= 5e-3 * np.linalg.norm(sc["load"]), np.linalg.norm(inj) / np.linalg.norm(sc["load"])
+        lam = net.array("price", s).double().cpu().numpy()
+        interior = (p > 1.0) & (p < cap - 1.0)
+        lam_g = lam[n["gen_bus"]]
+        stat = np.abs(lam_g - (n["gen_cost"][:, None] + eps * p))[interior]
+        # a 1e-3 relative dual residual on prices of tens of $/MWh
+        assert np.median(stat) <= 0.05 and np.quantile(stat, 0.99) <= 0.5, (np.median(stat), np.quantile(stat, 0.99))
+    g = net.grad(e).double().cpu().numpy()
+    assert net.last_grad_status == 0
+    assert np.max(g) <= 1e-3 * np.max(np.abs(g)), np.max(g)
