@@ -34,6 +34,8 @@ Inequalities G x <= h(eta) = h0 + D eta  (the capacity dependence b(eta) of Eq. 
     p <= cf eta_g,  -p <= 0,  sh <= L,  -sh <= 0,
     +-beta (th_f - th_t) <= eta_l,  +-(th_f - th_t) <= dtheta_max   (AC lines),
     +-fdc <= eta_l   (HVDC lines),
+    +-(p_t - p_{t-1}) <= r_g eta_g, t >= 1   (ramping generators: 0 < r_g < 1, the hourly
+                                             ramp limit as a fraction of capacity),
     ch <= eta_b, -ch <= 0, dis <= eta_b, -dis <= 0, soc <= dur eta_b, -soc <= 0.
 
 The nodal price is lambda_nt = -y_nt, y the multiplier of the balance row in
@@ -224,6 +226,14 @@ class DispatchQP:
                     continue
                 add_row([(vid("p", g, t), 1.0)], 0.0, g, cf[g, t], ("p_up", g, t))
                 add_row([(vid("p", g, t), -1.0)], 0.0, tag=("p_lo", g, t))
+        ramp = np.asarray(net.get("gen_ramp", np.zeros(G)), dtype=np.float64)
+        self.ramp_gens = np.where((ramp > 0.0) & (ramp < 1.0))[0]
+        for g in self.ramp_gens:
+            r = float(ramp[g])
+            for t in range(1, T):
+                a, b0 = vid("p", g, t), vid("p", g, t - 1)
+                add_row([(a, 1.0), (b0, -1.0)], 0.0, int(g), r, ("r_up", int(g), t))
+                add_row([(a, -1.0), (b0, 1.0)], 0.0, int(g), r, ("r_lo", int(g), t))
         for n in range(N):
             for t in range(T):
                 if ("sh", n, t) in self.pinned:

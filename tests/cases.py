@@ -4,9 +4,10 @@ import math
 import numpy as np
 
 
-def network(n_bus, gens=(), lines=(), bats=(), gamma=None, dc=()):
+def network(n_bus, gens=(), lines=(), bats=(), gamma=None, dc=(), ramp=None):
     """gens: (bus, cost, cap[, emis]); lines: (from, to, beta, cap[, dtheta]); bats: (bus, P[, dur, eff]);
-    dc: indices of the lines that are HVDC transport links (their beta and dtheta are unused)."""
+    dc: indices of the lines that are HVDC transport links (their beta and dtheta are unused);
+    ramp: {generator index: hourly ramp limit as a fraction of its capacity}."""
     gb = np.array([g[0] for g in gens], dtype=np.int64)
     gc = np.array([g[1] for g in gens], dtype=float)
     gcap = np.array([g[2] for g in gens], dtype=float)
@@ -29,6 +30,10 @@ def network(n_bus, gens=(), lines=(), bats=(), gamma=None, dc=()):
                gamma=np.zeros(K) if gamma is None else np.asarray(gamma, float), K=K)
     if len(dc):
         net["line_dc"] = np.isin(np.arange(lf.size), np.asarray(dc)).astype(np.uint8)
+    if ramp:
+        net["gen_ramp"] = np.zeros(gb.size)
+        for g, r in ramp.items():
+            net["gen_ramp"][g] = r
     return net, eta
 
 

@@ -182,6 +182,43 @@ def test_hvdc_joins_ac_islands(kappa):
         assert abs(g[6] + mu.sum()) < 1e-6 * mu.sum()
 
 
+# ---------------------------------------------------------------- ramping generators
+def test_ramp_limit_closed_form():
+    """A cheap generator limited to ramping 0.2 of its 500 MW per hour while the load
+    jumps from 100 to 300 MW: it serves 100 then 200 MW and the expensive unit covers the
+    rest.  The KKT conditions give lambda_1 = 60 + eps 100, the ramp multiplier
+    mu = lambda_1 - 10 - eps 200 and lambda_0 = 10 + eps 100 - mu (negative: load in the
+    first hour would buy ramp headroom); dc/deta_A = -0.2 mu through R = 0.2 eta_A."""
+    net, eta = network(1, gens=[(0, 10.0, 500.0), (0, 60.0, 500.0)], ramp={0: 0.2})
+    sol = dispatch.solve(net, scenario([[100.0, 300.0]], G=2), eta, opts())
+    np.testing.assert_allclose(sol.p[0], [100.0, 200.0], atol=1e-6)
+    np.testing.assert_allclose(sol.p[1], [0.0, 100.0], atol=1e-6)
+    lam1 = 60.0 + EPS * 100.0
+    mu = lam1 - 10.0 - EPS * 200.0
+    np.testing.assert_allclose(sol.price[0], [10.0 + EPS * 100.0 - mu, lam1], atol=1e-6)
+    for g in (grad.envelope_grad(sol), grad.adjoint_grad(sol)):
+        assert abs(g[0] + 0.2 * mu) < 1e-6 * mu and abs(g[1]) < 1e-6
+
+
+@pytest.mark.parametrize("kappa", [0.0, 50.0])
+def test_ramp_limits_gradient_routes(kappa):
+    """Three buses, six hours, two ramping generators whose limits bind on the load's
+    rise and fall: the adjoint gradient equals the central finite difference."""
+    net, eta = network(3, gens=[(0, 12.0, 300.0, 0.5), (1, 25.0, 250.0, 0.4), (2, 70.0, 400.0, 0.3)],
+                       lines=[(0, 1, 800.0, 400.0), (1, 2, 600.0, 400.0), (0, 2, 500.0, 400.0)],
+                       ramp={0: 0.25, 1: 0.3})
+    load = np.array([[30, 60, 120, 150, 90, 40], [40, 70, 110, 160, 80, 50], [20, 50, 90, 120, 70, 30]], float)
+    sc = scenario(load, G=3)
+    o = opts(kappa=kappa)
+    sol = dispatch.solve(net, sc, eta, o)
+    dp = np.abs(np.diff(sol.p[:2], axis=1))
+    assert np.any(np.isclose(dp[0], 0.25 * eta[0], atol=1e-6)) and np.any(np.isclose(dp[1], 0.3 * eta[1], atol=1e-6))
+    g = grad.adjoint_grad(sol)
+    gf, ok = grad.fd_grad(net, sc, eta, o)
+    assert ok.all()
+    np.testing.assert_allclose(g, gf, atol=1e-6 * np.max(np.abs(gf)))
+
+
 # ---------------------------------------------------------------- batteries
 @pytest.mark.parametrize("case", ["power", "spare", "energy"])
 def test_battery_arbitrage(case):
