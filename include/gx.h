@@ -91,6 +91,12 @@ typedef struct {
      * |f| <= eta_l, has no angle coupling, and carries eps/2 f^2 in the operating cost
      * like the other free injections; line_beta and line_dtheta are ignored for it. */
     const uint8_t* line_dc;
+    /* [n_gen] or NULL (no ramp limits): hourly ramp limit as a fraction of the planned
+     * capacity, |p_t - p_{t-1}| <= gen_ramp[g] * eta_g for t >= 1 (Section 2.1's
+     * operating constraints; the paper's "generator ramping limits").  Only values in
+     * (0, 1) constrain; 0 or >= 1 means unlimited.  A scenario with ramping generators
+     * runs on the per-iteration kernels, not the cluster-resident path. */
+    const double* gen_ramp;
 } gx_network_desc;
 
 /* One scenario: a horizon of T hours on network `net` (Sec. 2.1: a scenario can

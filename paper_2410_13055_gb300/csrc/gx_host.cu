@@ -33,6 +33,10 @@ struct NetH {
     int N = 0, G = 0, L = 0, B = 0;
     std::vector<int> gen_bus, line_from, line_to, bat_bus;
     std::vector<uint8_t> line_dc;  // 1: HVDC transport line
+    std::vector<double> gen_ramp;   // ramp limit / capacity per hour (0: none)
+    std::vector<int> ramp_gens;     // generators with a ramp limit in (0, 1)
+    std::vector<int> g_ramp;        // per generator: its index in ramp_gens, -1 if none
+    int ramp0 = 0;                  // offset of ramp_gens in the concatenated static arrays
     std::vector<double> gen_cost, gen_emis, line_beta, line_dth, bat_dur, bat_effc, bat_effd;
     std::vector<int> gptr, gidx, bptr, bidx, eptr, eidx;
     std::vector<float> inv_cnt, inv_wsum, dres_w, l_w;
@@ -87,10 +91,15 @@ struct gx_network {
     bool use_crs = false;
     long long bus_el = 0, gen_el = 0, line_el = 0, bat_el = 0;
     int n_bus_blk = 0, n_line_blk = 0, n_bat_warps = 0, n_cost_blk = 0, n_gwarps = 0, gs_total = 0;
-    int tot_gen = 0, tot_line = 0, tot_bat = 0, tot_bus = 0, tot_ptr = 0;
+    int tot_gen = 0, tot_line = 0, tot_bat = 0, tot_bus = 0, tot_ptr = 0, tot_ramp = 0;
+    std::vector<int> ramp_warp_scen;   // scenario of each ramp-kernel warp
+    int n_ramp_warps = 0;
+    long long ramp_el = 0;             // ramp state rows x Tp over all scenarios
+    int max_ramp_T = 1;
     // workspace offsets
     size_t o_scen, o_bbs, o_lbs, o_bws, o_cbs, o_gwarp, o_knet, o_busblk, o_pool, o_prep, o_crs;
     size_t o_bus4blk, o_l4bs;
+    size_t o_rgen, o_rrate, o_gramp, o_rws, o_rdd, o_ardd, o_rf[4], o_ra[4], o_rpart;
     size_t o_gbus, o_gcost, o_gemis, o_gfirm, o_lfrom, o_lto, o_lbeta, o_ldth, o_lw, o_bbus, o_bdur, o_beffc, o_beffd;
     size_t o_gptr, o_gidx, o_bptr, o_bidx, o_eptr, o_eidx, o_icnt, o_iwsum, o_dresw;
     size_t o_load, o_cf, o_dd, o_add;
@@ -105,7 +114,7 @@ struct gx_network {
     bool solved = false, adj_ready = false, dd_dirty = true;
     std::vector<int> in_batch, done_init;
     std::vector<double> wprime;
-    std::vector<float> dd_host, add_host;
+    std::vector<float> dd_host, add_host, rdd_host, ardd_host;
     Ctx ctx{}, actx{};
     // CUDA graphs of one residual-check chunk, keyed by what their captured parameters depend on
     struct ChunkGraph {
@@ -167,9 +176,33 @@ static void fill_dd_for(gx_network* net, double rho, std::vector<float>& out) {
     }
 }
 
+// Thomas pivots of the ramp prox's x-step (one row per ramping generator and scenario):
+// (eps + rho + rho_in) I + rho_in D^T D, D the first difference over T hours, so the
+// diagonal is a + rho_in [1, 2, ..., 2, 1] (a alone for T = 1) and the off-diagonal -rho_in.
+// Stored as 1 / m_t for m_0 = diag_0, m_t = diag_t - rho_in^2 / m_{t-1}.
+static void fill_ramp_dd_for(gx_network* net, double rho, std::vector<float>& out) {
+    const double eps = net->opts.eps, ri = rho * net->opts.rho_inner_c, a = eps + rho + ri;
+    out.assign((size_t)std::max<long long>(net->ramp_el, 1), 1.0f);
+    for (int s = 0; s < net->S; ++s) {
+        const ScenDev& sd = net->sdev[s];
+        for (int r = 0; r < sd.R; ++r) {
+            float* o = out.data() + sd.e_ramp + (size_t)r * sd.Tp;
+            double m = 0;
+            for (int t = 0; t < sd.T; ++t) {
+                const double dg = sd.T == 1 ? 0.0 : ((t == 0 || t == sd.T - 1) ? 1.0 : 2.0);
+                const double diag = a + ri * dg;
+                m = t == 0 ? diag : diag - ri * ri / m;
+                o[t] = (float)(1.0 / m);
+            }
+        }
+    }
+}
+
 static void fill_dd(gx_network* net) {
     fill_dd_for(net, net->opts.rho, net->dd_host);
     fill_dd_for(net, net->opts.adj_rho, net->add_host);
+    fill_ramp_dd_for(net, net->opts.rho, net->rdd_host);
+    fill_ramp_dd_for(net, net->opts.adj_rho, net->ardd_host);
     net->dd_dirty = true;
 }
 
@@ -199,6 +232,17 @@ static void make_ctx(gx_network* net) {
     c.bus_blk_scen = I(net->o_bbs);
     c.bus_blk = reinterpret_cast<const BusBlk*>(d + net->o_busblk);
     c.bus4_blk = reinterpret_cast<const BusBlk*>(d + net->o_bus4blk);
+    c.n_ramp_warps = net->n_ramp_warps;
+    c.ramp_warp_scen = I(net->o_rws);
+    c.r_gen = I(net->o_rgen);
+    c.r_rate = F(net->o_rrate);
+    c.g_ramp = I(net->o_gramp);
+    c.ramp_dd = F(net->o_rdd);
+    c.max_ramp_T = net->max_ramp_T;
+    float** rfs[4] = {&c.rz, &c.rw, &c.ry, &c.rq};
+    float** ras[4] = {&c.a_rz, &c.a_rw, &c.a_ry, &c.a_rq};
+    for (int k = 0; k < 4; ++k) { *rfs[k] = F(net->o_rf[k]); *ras[k] = F(net->o_ra[k]); }
+    c.ramp_part = F(net->o_rpart);
     c.line4_blk_scen = I(net->o_l4bs);
     c.n_bus4_blk = net->n_bus4_blk;
     c.n_line4_blk = net->n_line4_blk;
@@ -244,6 +288,7 @@ static void make_ctx(gx_network* net) {
     a.rho_in = (float)(o.adj_rho * o.rho_inner_c);
     a.rth_c = (float)(o.adj_rho * o.rho_theta_c);
     a.bat_dd = F(net->o_add);
+    a.ramp_dd = F(net->o_ardd);
     a.max_it = o.adj_max_iter;
     a.rho_ratio = (float)(o.rho / o.adj_rho);
     a.adj_from_fwd = 1;
@@ -396,6 +441,7 @@ static void build_crs_groups(gx_network* net) {
     std::map<std::pair<int, int>, size_t> smem;
     for (int s = 0; s < net->S; ++s) {
         const ScenDev& sd = net->sdev[s];
+        if (sd.R > 0) continue;  // ramping generators: per-iteration kernels only
         for (int C = 1; C <= kCrsMaxC; C *= 2) {
             const int H = (sd.T + C - 1) / C, nbo = (sd.B + C - 1) / C;
             const size_t bytes = crs_offsets(sd.N, sd.G, sd.L, sd.B, H, nbo, sd.T).total;
@@ -493,7 +539,9 @@ static void build_bus_blocks(gx_network* net) {
                     p[o[kPH_GROW] + k] = g;
                     p[o[kPH_GCOST] + k] = fbits((float)h.gen_cost[g]);
                     p[o[kPH_GEMIS] + k] = fbits((float)h.gen_emis[g]);
-                    p[o[kPH_GFIRM] + k] = net->firm[h.gen0 + g];
+                    // bit 0: capacity factor 1 throughout; bit 1: ramp-limited (its prox runs
+                    // in the ramp kernel, the bus kernels only sum its injection)
+                    p[o[kPH_GFIRM] + k] = net->firm[h.gen0 + g] | (h.g_ramp[g] >= 0 ? 2 : 0);
                     net->prep.push_back(int2{off + o[kPH_GETA] + k, h.eta0 + g});
                 }
                 for (int k = 0; k < ecnt; ++k) {
@@ -550,6 +598,18 @@ gx_status gx_network_create(const gx_network_desc* nets, int n_nets, const gx_sc
         h.line_dc.assign(h.L, 0);
         if (d.line_dc)
             for (int l = 0; l < h.L; ++l) h.line_dc[l] = d.line_dc[l] != 0;
+        h.gen_ramp.assign(h.G, 0.0);
+        if (d.gen_ramp)
+            for (int g = 0; g < h.G; ++g) {
+                if (!(d.gen_ramp[g] >= 0 && isfin(d.gen_ramp[g]))) return bad("gen_ramp must be finite and >= 0");
+                h.gen_ramp[g] = d.gen_ramp[g];
+            }
+        h.g_ramp.assign(h.G, -1);
+        for (int g = 0; g < h.G; ++g)
+            if (h.gen_ramp[g] > 0 && h.gen_ramp[g] < 1) {
+                h.g_ramp[g] = (int)h.ramp_gens.size();
+                h.ramp_gens.push_back(g);
+            }
         h.bat_bus.assign(d.bat_bus, d.bat_bus + h.B);
         h.bat_dur.assign(d.bat_dur, d.bat_dur + h.B);
         h.bat_effc.assign(d.bat_eff_c, d.bat_eff_c + h.B);
@@ -574,7 +634,9 @@ gx_status gx_network_create(const gx_network_desc* nets, int n_nets, const gx_sc
         }
         derive_network(h, o);
         h.gen0 = gen0; h.line0 = line0; h.bat0 = bat0; h.bus0 = bus0; h.ptr0 = ptr0; h.eta0 = K;
+        h.ramp0 = net->tot_ramp;
         gen0 += h.G; line0 += h.L; bat0 += h.B; bus0 += h.N; ptr0 += h.N + 1; K += h.G + h.L + h.B;
+        net->tot_ramp += (int)h.ramp_gens.size();
     }
     net->K = K;
     net->tot_gen = gen0; net->tot_line = line0; net->tot_bat = bat0; net->tot_bus = bus0; net->tot_ptr = ptr0;
@@ -620,6 +682,14 @@ gx_status gx_network_create(const gx_network_desc* nets, int n_nets, const gx_sc
         sd.e_bus = eb; sd.e_gen = eg; sd.e_line = el; sd.e_bat = ebt;
         eb += (long long)h.N * sh.Tp; eg += (long long)h.G * sh.Tp; el += (long long)h.L * sh.Tp;
         ebt += (long long)h.B * sh.Tp;
+        sd.R = (int)h.ramp_gens.size();
+        sd.ramp0 = h.ramp0;
+        sd.e_ramp = net->ramp_el;
+        net->ramp_el += (long long)sd.R * sh.Tp;
+        sd.ramp_w0 = net->n_ramp_warps;
+        for (int r = 0; r < sd.R; ++r) net->ramp_warp_scen.push_back(s);
+        net->n_ramp_warps += sd.R;
+        if (sd.R > 0) net->max_ramp_T = std::max(net->max_ramp_T, sh.T);
         sd.weight = (float)d.weight;
         sd.load_norm = std::max(std::sqrt(ln2), 1e-30);
         // block tables
@@ -697,6 +767,12 @@ gx_status gx_network_create(const gx_network_desc* nets, int n_nets, const gx_sc
     net->o_icnt = L.add(F4(bus0)); net->o_iwsum = L.add(F4(bus0)); net->o_dresw = L.add(F4(bus0));
     net->o_load = L.add(F4(eb)); net->o_cf = L.add(F4(eg)); net->o_dd = L.add(F4(ebt));
     net->o_add = L.add(F4(ebt));
+    net->o_rgen = L.add(I4(net->tot_ramp));
+    net->o_rrate = L.add(F4(net->tot_ramp));
+    net->o_gramp = L.add(I4(gen0));
+    net->o_rws = L.add(I4(net->n_ramp_warps));
+    net->o_rdd = L.add(F4(net->ramp_el));
+    net->o_ardd = L.add(F4(net->ramp_el));
     net->static_end = L.total;
     const long long rows[16] = {eg, eb, el, el, el, el, ebt, ebt, ebt, ebt, ebt, ebt, ebt, eb, eb, eb};
     for (int k = 0; k < 16; ++k) net->o_f[k] = L.add(F4(rows[k]));
@@ -710,6 +786,9 @@ gx_status gx_network_create(const gx_network_desc* nets, int n_nets, const gx_sc
     net->o_bpart = L.add(F4((long long)net->n_bus4_blk * kBusPart));
     net->o_lpart = L.add(F4((long long)net->n_line4_blk * kDevPart));
     net->o_btpart = L.add(F4((long long)net->n_bat_warps * kDevPart));
+    for (int k = 0; k < 4; ++k) net->o_rf[k] = L.add(F4(net->ramp_el));
+    for (int k = 0; k < 4; ++k) net->o_ra[k] = L.add(F4(net->ramp_el));
+    net->o_rpart = L.add(F4((long long)net->n_ramp_warps * kDevPart));
     net->o_cpart = L.add(D8(2LL * net->n_cost_blk));
     net->in_batch.assign(S, 0);
     net->done_init.assign(S, 1);
@@ -780,6 +859,23 @@ gx_status gx_network_bind(gx_network* net, void* dev_mem, size_t bytes, void* st
     put(net->o_gfirm, net->firm.data(), net->tot_gen);
     put_v(net->o_dd, net->dd_host, 0);
     put_v(net->o_add, net->add_host, 0);
+    put_v(net->o_rdd, net->rdd_host, 0);
+    put_v(net->o_ardd, net->ardd_host, 0);
+    {
+        std::vector<int> rgen, gramp(std::max(net->tot_gen, 1), -1);
+        std::vector<float> rrate;
+        for (const NetH& n : net->nets) {
+            for (int r = 0; r < (int)n.ramp_gens.size(); ++r) {
+                rgen.push_back(n.ramp_gens[r]);
+                rrate.push_back((float)n.gen_ramp[n.ramp_gens[r]]);
+            }
+            for (int g = 0; g < n.G; ++g) gramp[n.gen0 + g] = n.g_ramp[g];
+        }
+        put(net->o_rgen, rgen.data(), 4 * rgen.size());
+        put(net->o_rrate, rrate.data(), 4 * rrate.size());
+        put(net->o_gramp, gramp.data(), 4 * (size_t)net->tot_gen);
+        put(net->o_rws, net->ramp_warp_scen.data(), 4 * net->ramp_warp_scen.size());
+    }
     GX_CUDA(cudaMemcpyAsync(net->dev, h.data(), net->static_end, cudaMemcpyHostToDevice, st));
     GX_CUDA(cudaMemsetAsync(net->dev + net->static_end, 0, net->lay.total - net->static_end, st));
     GX_CUDA(cudaStreamSynchronize(st));
@@ -871,7 +967,7 @@ static gx_status enqueue_iters(gx_network* net, const Ctx& c, int adj, int chunk
     if (tick) *launches += launch_tick(c, chunk, st);
     // While capturing, the line and battery proxes are two branches of the graph: they
     // are independent and both feed the bus kernel.
-    const bool fork = (st == net->cap_stream) && c.n_bat_warps > 0 && c.n_line_blk > 0;
+    const bool fork = (st == net->cap_stream) && (c.n_bat_warps > 0 || c.n_ramp_warps > 0) && c.n_line_blk > 0;
     for (int j = j0; j < j1; ++j) {
         const int want = j == chunk - 1;
         const bool samp = prof && want;
@@ -880,6 +976,7 @@ static gx_status enqueue_iters(gx_network* net, const Ctx& c, int adj, int chunk
             GX_CUDA(cudaEventRecord(net->ev_fork, st));
             GX_CUDA(cudaStreamWaitEvent(net->cap_stream2, net->ev_fork, 0));
             nb = launch_bat(c, mode, adj, want, net->cap_stream2);
+            nb += launch_ramp(c, mode, adj, want, net->cap_stream2);
             GX_CUDA(cudaEventRecord(net->ev_join, net->cap_stream2));
             nl = launch_line(c, mode, adj, want, st);
             GX_CUDA(cudaStreamWaitEvent(st, net->ev_join, 0));
@@ -888,6 +985,7 @@ static gx_status enqueue_iters(gx_network* net, const Ctx& c, int adj, int chunk
             nl = launch_line(c, mode, adj, want, st);
             if (samp) GX_CUDA(cudaEventRecord(net->ev[1], st));
             nb = launch_bat(c, mode, adj, want, st);
+            nb += launch_ramp(c, mode, adj, want, st);
             if (samp) GX_CUDA(cudaEventRecord(net->ev[2], st));
         }
         const int nu = launch_bus(c, mode, adj, want, st);
@@ -1045,7 +1143,7 @@ static gx_status run_loop(gx_network* net, int adj, cudaStream_t st, int* launch
     const int max_it = adj ? net->opts.adj_max_iter : net->opts.max_iter;
     const int every = net->opts.check_every;
     const bool prof = net->prof;
-    const int per_it = (c.n_line_blk > 0) + (c.n_bat_warps > 0) + (c.n_bus_blk > 0);
+    const int per_it = (c.n_line_blk > 0) + (c.n_bat_warps > 0) + (c.n_ramp_warps > 0) + (c.n_bus_blk > 0);
     int it = 0;
     GX_CUDA(cudaMemsetAsync(c.iter_ctr, 0, sizeof(int), st));
     if (net->use_graphs == 2 && !prof && max_it % every == 0) {
@@ -1161,6 +1259,10 @@ gx_status gx_dispatch_solve_batch(gx_network* net, const float* eta_dev, const i
         GX_CUDA(cudaMemcpyAsync(net->dev + net->o_dd, net->dd_host.data(), 4 * net->dd_host.size(),
                                 cudaMemcpyHostToDevice, st));
         GX_CUDA(cudaMemcpyAsync(net->dev + net->o_add, net->add_host.data(), 4 * net->add_host.size(),
+                                cudaMemcpyHostToDevice, st));
+        GX_CUDA(cudaMemcpyAsync(net->dev + net->o_rdd, net->rdd_host.data(), 4 * net->rdd_host.size(),
+                                cudaMemcpyHostToDevice, st));
+        GX_CUDA(cudaMemcpyAsync(net->dev + net->o_ardd, net->ardd_host.data(), 4 * net->ardd_host.size(),
                                 cudaMemcpyHostToDevice, st));
         GX_CUDA(cudaStreamSynchronize(st));
         net->dd_dirty = false;

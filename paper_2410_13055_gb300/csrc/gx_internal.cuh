@@ -111,6 +111,9 @@ struct ScenDev {
     long long e_bus, e_gen, e_line, e_bat;  // element offsets of the scenario's rows
     int bus_blk0, bus_nblk, line_blk0, line_nblk, bat_w0;  // single-hour kernels (setup modes)
     int bus4_blk0, bus4_nblk, line4_blk0, line4_nblk;     // hour-quad kernels (iterations)
+    int R, ramp0, ramp_w0;             // ramping generators: count, offset in the static ramp
+                                       // arrays, first warp of the ramp kernel
+    long long e_ramp;                  // element offset of the scenario's ramp state rows
     int cost_blk0;                     // first block of the cost reduction
     float weight;
     double load_norm;                  // sqrt(sum load^2), >= 1e-30
@@ -121,6 +124,7 @@ struct Ctx {
     // sizes
     int S, n_bus_blk, n_line_blk, n_bat_warps, n_cost_blk;
     int n_bus4_blk, n_line4_blk;
+    int n_ramp_warps;
     // options
     float rho, eps, voll, kappa, rho_in, rth_c;  // rth_c = rho * rho_theta_c
     float tol_act;
@@ -130,6 +134,7 @@ struct Ctx {
     int check_every;
     int max_it;          // iteration cap of the loop this context drives
     int max_bat_T;       // longest horizon among scenarios that have batteries
+    int max_ramp_T;      // longest horizon among scenarios that have ramping generators
     int* iter_ctr;       // device iteration counter of the current loop
     // tables
     const ScenDev* scen;
@@ -137,6 +142,10 @@ struct Ctx {
     const BusBlk* bus_blk;     // [n_bus_blk]
     const BusBlk* bus4_blk;    // [n_bus4_blk] hour-quad bus kernel
     const int* line4_blk_scen; // [n_line4_blk]
+    const int* ramp_warp_scen; // [n_ramp_warps]
+    const int* r_gen;          // [ramping generators] generator index within its network
+    const float* r_rate;       // [ramping generators] ramp limit / capacity per hour
+    const int* g_ramp;         // [generators] index among its network's ramping generators, -1 if none
     int* pool;                 // bus-block pool records (generator plan values refreshed per call)
     const int2* prep;          // [n_prep] (pool word, eta index) of every generator plan value
     int n_prep;
@@ -166,6 +175,10 @@ struct Ctx {
     float* a_xg; float* a_xl; float* a_dl; float* a_sg; float* a_vf; float* a_vt;
     float* a_xb; float* a_zc; float* a_zd; float* a_zs; float* a_yc; float* a_yd; float* a_ys;
     float* a_u; float* a_pbar; float* a_thb;
+    // ramping generators, [ramp rows]: box copy z, ramp copy w (hour t: p_t - p_{t-1}),
+    // their scaled duals y, q; forward and adjoint; Thomas pivots 1/m_t of the x-step
+    float *rz, *rw, *ry, *rq, *a_rz, *a_rw, *a_ry, *a_rq;
+    const float* ramp_dd;
     // active set
     uint8_t* m_gen; uint8_t* m_load; uint8_t* m_line; uint8_t* m_bat;
     // flags, outputs and partials
@@ -183,6 +196,7 @@ struct Ctx {
     float* bus_part;    // [n_bus4_blk * kBusPart]
     float* line_part;   // [n_line4_blk * kDevPart]
     float* bat_part;    // [n_bat_warps * kDevPart]
+    float* ramp_part;   // [n_ramp_warps * kDevPart] (dx^2, x^2, adjoint scale)
     double* cost_part;  // [n_cost_blk * 2]
     const float* warm;  // user warm start [prices | angles] over bus rows, or nullptr
     long long warm_half; // element count of the prices half of `warm` (= all bus rows)
@@ -192,6 +206,7 @@ struct Ctx {
 int launch_dev(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st);
 int launch_line(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st);
 int launch_bat(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st);
+int launch_ramp(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st);
 int launch_bus(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st);
 int launch_prep(const Ctx& c, cudaStream_t st);
 int launch_loop_cond(const Ctx& c, int max_it, cudaGraphConditionalHandle h, cudaStream_t st);

@@ -537,7 +537,7 @@ __device__ __forceinline__ void bus_item(const Ctx& c, const BusBlk& bb, const S
             X.xl[i] = shed - Lnt;
             for (int q = g0; q < g1; ++q) {
                 const long long r = gt + (long long)P.at(kPH_GROW, q) * bb.Tp;
-                const float cap = P.at(kPH_GFIRM, q) ? P.atf(kPH_GETA, q) : c.cf[r] * P.atf(kPH_GETA, q);
+                const float cap = (P.at(kPH_GFIRM, q) & 1) ? P.atf(kPH_GETA, q) : c.cf[r] * P.atf(kPH_GETA, q);
                 X.xg[r] = clampf((lam - P.atf(kPH_GCOST, q)) / eps, 0.f, cap);
             }
         } else {
@@ -585,7 +585,7 @@ __device__ __forceinline__ void bus_item(const Ctx& c, const BusBlk& bb, const S
                 if (ADJ) {
                     av[k] = c.xg[gt + ro[k]];
                     mv[k] = c.m_gen[gt + ro[k]];
-                } else if (MODE != M_INIT && !P.at(kPH_GFIRM, q)) {
+                } else if (MODE != M_INIT && !(P.at(kPH_GFIRM, q) & 1)) {
                     av[k] = c.cf[gt + ro[k]];
                 }
             }
@@ -594,9 +594,12 @@ __device__ __forceinline__ void bus_item(const Ctx& c, const BusBlk& bb, const S
         for (int k = 0; k < kGC; ++k) {
             const int q = q0 + k;
             if (q >= g1) break;
+            // a ramp-limited generator's prox and active set come from the ramp kernel
+            const bool rampg = (P.at(kPH_GFIRM, q) & 2) != 0;
+            if (MODE == M_MASK && rampg) continue;
             const float x = xv[k];
             float xn = x;
-            if (MODE == M_FWD || MODE == M_ADJ || MODE == M_MASK) {
+            if ((MODE == M_FWD || MODE == M_ADJ || MODE == M_MASK) && !rampg) {
                 const float v = x - pb - uu;
                 if (ADJ) {
                     const float gh = P.atf(kPH_GCOST, q) + eps * av[k] + c.kappa * P.atf(kPH_GEMIS, q);
@@ -854,14 +857,16 @@ __device__ __forceinline__ void gen_load4(const Ctx& c, const StatePtrs& X, cons
     if (ADJ) {
         ld4(c.xg + r, a);
         ldm4(c.m_gen + r, m);
-    } else if (!P.at(kPH_GFIRM, q)) {
+    } else if (!(P.at(kPH_GFIRM, q) & 1)) {
         ld4(c.cf + r, a);
     } else {
         a[0] = a[1] = a[2] = a[3] = 1.f;
     }
 }
 
-template <int ADJ>
+// RAMP: the batch has ramp-limited generators (whose injections are only summed here);
+// without them the flag test is compiled out.
+template <int ADJ, int RAMP>
 __global__ void __launch_bounds__(kQBlock) k_bus4(const Ctx c, int want_res) {
     __shared__ __align__(16) int S[kPoolMax];
     const BusBlk bb = c.bus4_blk[blockIdx.x];
@@ -929,6 +934,16 @@ __global__ void __launch_bounds__(kQBlock) k_bus4(const Ctx c, int want_res) {
 #pragma unroll
             for (int h = 0; h < 4; ++h) { x[h] = xc[h]; a[h] = ac[h]; mg[h] = mc[h]; }
             if (q + 1 < g1) gen_load4<ADJ>(c, X, P, gt + (long long)P.at(kPH_GROW, q + 1) * bb.Tp, q + 1, xc, ac, mc);
+            if (RAMP && (P.at(kPH_GFIRM, q) & 2)) {
+                // ramp-limited: the ramp kernel wrote this iteration's injection (and keeps
+                // its own residual terms); the bus only sums it
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    sum[h] += x[h];
+                    x2 += x[h] * x[h];
+                }
+                continue;
+            }
             const float gcost = P.atf(kPH_GCOST, q);
             const float etag = ADJ ? 0.f : P.atf(kPH_GETA, q);
             const float gemis = ADJ ? P.atf(kPH_GEMIS, q) : 0.f;
@@ -1094,6 +1109,12 @@ __global__ void __launch_bounds__(kBlock) k_reduce(const Ctx c, int adj, double 
 #pragma unroll
         for (int q = 0; q < kDevPart; ++q) a[6 + q] += (double)c.bat_part[(sc.bat_w0 + b) * kDevPart + q];
     }
+    for (int b = threadIdx.x; b < sc.R; b += kBlock) {  // ramping generators: dx^2, x^2, adjoint scale
+        const float* rp = c.ramp_part + (long long)(sc.ramp_w0 + b) * kDevPart;
+        a[6] += (double)rp[0];
+        a[7] += (double)rp[1];
+        a[1] += (double)rp[2];
+    }
     __shared__ double sh[9][kBlock / 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
@@ -1248,7 +1269,25 @@ __global__ void __launch_bounds__(kBlock) k_grad(const Ctx c, int envelope, cons
     const ScenDev sc = c.scen[s];
     const float rho = c.rho, eps = c.eps;
     double acc = 0.0;
-    if (r < sc.G) {
+    if (r < sc.G && c.g_ramp[sc.gen0 + r] >= 0) {
+        // ramp-limited generator: multipliers of its inner box copy (capacity, dcap/deta =
+        // cf) and ramp copy (+-(p_t - p_{t-1}) <= rate eta, both bounds move with eta)
+        const int g = r, gg = sc.gen0 + g;
+        const int rk = c.g_ramp[gg];
+        const float rate = c.r_rate[sc.ramp0 + rk];
+        const long long row0 = sc.e_ramp + (long long)rk * sc.Tp;
+        for (int t = lane; t < sc.T; t += 32) {
+            const long long rr = sc.e_gen + (long long)g * sc.Tp + t;
+            const uint8_t m = c.m_gen[rr];
+            const float yv = envelope ? -c.ry[row0 + t] : c.a_ry[row0 + t];
+            const float qv = envelope ? -c.rq[row0 + t] : c.a_rq[row0 + t];
+            const float cf = c.g_firm[gg] ? 1.f : c.cf[rr];
+            if ((m & 3) == A_UP) acc += (double)yv * (double)cf;
+            const int rm = (m >> 2) & 3;
+            if (rm == A_UP) acc += (double)qv * (double)rate;
+            else if (rm == A_LO) acc -= (double)qv * (double)rate;
+        }
+    } else if (r < sc.G) {
         const int g = r, gg = sc.gen0 + g;
         const int bus = c.g_bus[gg];
         const float cost = c.g_cost[gg];
@@ -1424,14 +1463,20 @@ int launch_bat(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st) {
 }
 
 int launch_dev(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st) {
-    return launch_line(c, mode, adj, want_res, st) + launch_bat(c, mode, adj, want_res, st);
+    return launch_line(c, mode, adj, want_res, st) + launch_bat(c, mode, adj, want_res, st) +
+           launch_ramp(c, mode, adj, want_res, st);
 }
 
 int launch_bus(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st) {
     if (c.n_bus_blk <= 0) return 0;
     if (mode == M_FWD || mode == M_ADJ) {
-        if (adj) k_bus4<1><<<c.n_bus4_blk, kQBlock, 0, st>>>(c, want_res);
-        else k_bus4<0><<<c.n_bus4_blk, kQBlock, 0, st>>>(c, want_res);
+        if (c.n_ramp_warps > 0) {
+            if (adj) k_bus4<1, 1><<<c.n_bus4_blk, kQBlock, 0, st>>>(c, want_res);
+            else k_bus4<0, 1><<<c.n_bus4_blk, kQBlock, 0, st>>>(c, want_res);
+        } else {
+            if (adj) k_bus4<1, 0><<<c.n_bus4_blk, kQBlock, 0, st>>>(c, want_res);
+            else k_bus4<0, 0><<<c.n_bus4_blk, kQBlock, 0, st>>>(c, want_res);
+        }
         return 1;
     }
     GX_DISPATCH_MODE_SETUP(k_bus, c.n_bus_blk, c, want_res);

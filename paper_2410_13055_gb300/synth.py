@@ -290,6 +290,21 @@ def add_hvdc(net, n_dc, seed=0, cap=(200.0, 600.0)):
     return out
 
 
+def add_ramps(net, rate=(0.1, 0.3), share=1.0, seed=0):
+    """Give a share of the gas generators an hourly ramp limit drawn from U[rate] as a
+    fraction of their capacity (``gen_ramp``; renewables stay unlimited).  Returns a new
+    network dict (inputs only)."""
+    rng = _rng(seed)
+    G = net["gen_bus"].size
+    out = dict(net)
+    ramp = np.zeros(G)
+    gas = np.where(np.asarray(net.get("gen_kind", np.zeros(G))) == GAS)[0]
+    pick = gas[rng.random(gas.size) < share]
+    ramp[pick] = rng.uniform(rate[0], rate[1], size=pick.size)
+    out["gen_ramp"] = ramp
+    return out
+
+
 CONFIGS = {"tiny": tiny, "medium": medium, "batching": batching, "scale": scale}
 
 
