@@ -26,7 +26,13 @@ from .dispatch import solve, net_slices
 
 
 def envelope_grad(sol) -> np.ndarray:
-    return -(sol.qp.D.T @ sol.z)
+    """-D^T z, plus y^T dA_k x + z^T dG_k x for plan entries that enter the constraint
+    matrix (lines whose susceptance scales with capacity)."""
+    qp = sol.qp
+    g = -(qp.D.T @ sol.z)
+    for k, dA in qp.dA.items():
+        g[k] += float(sol.y @ (dA @ sol.x)) + float(sol.z @ (qp.dG[k] @ sol.x))
+    return g
 
 
 def active_set(sol, ratio=1.0):
@@ -98,7 +104,16 @@ def adjoint_grad(sol, kappa=None, act=None) -> np.ndarray:
     if not np.all(np.isfinite(sol_vec)) or np.linalg.norm(K @ sol_vec - rhs) > 1e-8 * max(1.0, np.linalg.norm(rhs)):
         raise np.linalg.LinAlgError("active-set KKT system is inconsistent")
     xi = sol_vec[n + me:]
-    return qp.D[act].T @ xi
+    out = qp.D[act].T @ xi
+    # plan entries inside the constraint matrix: -[w^T (dA^T y + dG_A^T z_A) + zeta^T dA x
+    # + xi^T dG_A x], from differentiating the KKT residual in eta
+    if qp.dA:
+        w, zeta = sol_vec[:n], sol_vec[n:n + me]
+        zA = sol.z[act]
+        for k, dA in qp.dA.items():
+            dGA = qp.dG[k][act]
+            out[k] -= float(w @ (dA.T @ sol.y + dGA.T @ zA)) + float(zeta @ (dA @ sol.x)) + float(xi @ (dGA @ sol.x))
+    return out
 
 
 def fd_grad(net, scen, eta, opts, idx=None, rel_step=1e-4, tol=1e-12):

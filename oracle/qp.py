@@ -16,6 +16,11 @@ Objective c(x) = 1/2 x^T Q x + q^T x with
     sum_gt (c_g p + eps/2 p^2) + sum_nt (VOLL sh + eps/2 sh^2) + sum_bt eps/2 (ch^2 + dis^2)
     + sum_dc,t eps/2 fdc^2.
 
+Capacity-dependent susceptance (``net["line_beta_ref"]`` > 0 for an AC line): the line's
+susceptance scales with its planned capacity, beta_l(eta) = line_beta_l eta_l / ref_l, as when
+capacity is added by parallel circuits.  The constraint matrix then depends on eta (the A(eta)
+of Eq. 2); ``dA[k]`` and ``dG[k]`` hold its derivatives for such a line's plan entry k.
+
 HVDC lines (``net["line_dc"]`` = 1) are transport links (Sections 2.1 and 3 name HVDC
 among the planned assets): their flow is a free variable limited by eta_l, with no
 angle coupling and no angle-difference limit, regularised like the other free
@@ -88,6 +93,14 @@ class DispatchQP:
         Ld = self.dc_lines.size
         self.Ld = Ld
         dc_row = {int(l): j for j, l in enumerate(self.dc_lines)}
+        # effective susceptances: fixed, or scaling with the line's capacity
+        bref = np.asarray(net.get("line_beta_ref", np.zeros(L)), dtype=np.float64)
+        beta0 = np.asarray(net["line_beta"], dtype=np.float64)
+        self.scaling = np.where((bref > 0) & ~dc)[0]
+        self.beta = beta0.copy()
+        self.beta[self.scaling] = beta0[self.scaling] * eta[G + self.scaling] / bref[self.scaling]
+        dA_entries = {int(G + l): ([], [], []) for l in self.scaling}  # rows, cols, vals of dA / deta_k
+        dG_entries = {int(G + l): ([], [], []) for l in self.scaling}
         eta = np.asarray(eta, dtype=np.float64)
         assert eta.shape == (self.K,)
         self.eta = eta.copy()
@@ -148,7 +161,7 @@ class DispatchQP:
             cols += [vid("ch", bb, t) for t in range(T)]
             vals += [-1.0] * T
         for l in range(L):
-            f, to, beta = int(net["line_from"][l]), int(net["line_to"][l]), float(net["line_beta"][l])
+            f, to, beta = int(net["line_from"][l]), int(net["line_to"][l]), float(self.beta[l])
             if l in dc_row:
                 # HVDC: the flow variable leaves bus f and enters bus to
                 for t in range(T):
@@ -161,6 +174,12 @@ class DispatchQP:
                 rows += [r + f * T + t, r + f * T + t, r + to * T + t, r + to * T + t]
                 cols += [vid("th", f, t), vid("th", to, t), vid("th", f, t), vid("th", to, t)]
                 vals += [-beta, beta, beta, -beta]
+                if G + l in dA_entries:  # d beta / d eta_l = beta / eta_l
+                    db = beta / float(eta[G + l])
+                    e = dA_entries[G + l]
+                    e[0].extend([r + f * T + t, r + f * T + t, r + to * T + t, r + to * T + t])
+                    e[1].extend([vid("th", f, t), vid("th", to, t), vid("th", f, t), vid("th", to, t)])
+                    e[2].extend([-db, db, db, -db])
         r += N * T
         self.row_dyn = r
         for bb in range(B):
@@ -248,10 +267,16 @@ class DispatchQP:
                     add_row([(v, 1.0)], 0.0, G + l, 1.0, ("f_up", l, t))
                     add_row([(v, -1.0)], 0.0, G + l, 1.0, ("f_lo", l, t))
                 continue
-            beta = float(net["line_beta"][l])
+            beta = float(self.beta[l])
             dth = float(net["line_dtheta"][l])
             for t in range(T):
                 a, c = vid("th", f, t), vid("th", to, t)
+                if G + l in dG_entries:
+                    db = beta / float(eta[G + l])
+                    e = dG_entries[G + l]
+                    e[0].extend([m, m, m + 1, m + 1])
+                    e[1].extend([a, c, a, c])
+                    e[2].extend([db, -db, -db, db])
                 add_row([(a, beta), (c, -beta)], 0.0, G + l, 1.0, ("f_up", l, t))
                 add_row([(a, -beta), (c, beta)], 0.0, G + l, 1.0, ("f_lo", l, t))
                 add_row([(a, 1.0), (c, -1.0)], dth, tag=("a_up", l, t))
@@ -267,6 +292,8 @@ class DispatchQP:
                 add_row([(vid("soc", bb, t), -1.0)], 0.0, tag=("soc_lo", bb, t))
         self.m_in = m
         self.Gm = sp.csr_matrix((gvals, (grows, gcols)), shape=(m, self.n))
+        self.dA = {k: sp.csr_matrix((v, (r_, c_)), shape=(self.m_eq, self.n)) for k, (r_, c_, v) in dA_entries.items()}
+        self.dG = {k: sp.csr_matrix((v, (r_, c_)), shape=(m, self.n)) for k, (r_, c_, v) in dG_entries.items()}
         self.h0 = np.array(h0)
         self.D = sp.csr_matrix((dvals, (drows, dcols)), shape=(m, self.K))
         self.h = self.h0 + self.D @ eta
@@ -313,7 +340,7 @@ class DispatchQP:
         """Flow of every line, from -> to: beta (th_f - th_t) on AC lines, the flow
         variable on HVDC lines."""
         lf, lt = self.net["line_from"], self.net["line_to"]
-        f = self.net["line_beta"][:, None] * (th[lf] - th[lt])
+        f = self.beta[:, None] * (th[lf] - th[lt])
         if self.Ld:
             f[self.dc_lines] = fdc if fdc is not None else 0.0
         return f

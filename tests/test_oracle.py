@@ -182,6 +182,51 @@ def test_hvdc_joins_ac_islands(kappa):
         assert abs(g[6] + mu.sum()) < 1e-6 * mu.sum()
 
 
+# ---------------------------------------------------------------- capacity-dependent susceptance
+def _scaling_triangle():
+    net, eta = network(3, gens=[(0, 10.0, 600.0, 0.5), (1, 30.0, 300.0, 0.3), (2, 80.0, 300.0, 0.6)],
+                       lines=[(0, 1, 1000.0, 500.0), (1, 2, 800.0, 70.0), (0, 2, 500.0, 400.0)])
+    load = np.array([[20, 40, 30], [30, 50, 40], [200, 260, 230]], float)
+    return net, eta * 1.02, scenario(load, G=3)
+
+
+@pytest.mark.parametrize("kappa", [0.0, 50.0])
+def test_scaling_susceptance_gradient_routes(kappa):
+    """A meshed triangle whose line 0-2 gains susceptance with capacity (beta eta / ref):
+    below its own limit, more capacity still pays by drawing loop flow off the congested
+    line 1-2 (the A(eta) term of Eq. 2).  Adjoint, envelope (kappa = 0) and central finite
+    differences agree; with the susceptance fixed the same line's gradient is zero."""
+    net, eta, sc = _scaling_triangle()
+    o = opts(kappa=kappa)
+    fixed = dispatch.solve(net, sc, eta, o)
+    assert abs(grad.adjoint_grad(fixed)[5]) < 1e-9
+    net["line_beta_ref"] = np.array([0.0, 0.0, eta[5]])
+    sol = dispatch.solve(net, sc, eta, o)
+    assert np.all(np.abs(sol.flow[2]) < eta[5] - 1.0)            # the scaling line is not at its limit
+    g = grad.adjoint_grad(sol)
+    gf, ok = grad.fd_grad(net, sc, eta, o)
+    assert ok.all()
+    np.testing.assert_allclose(g, gf, atol=1e-6 * np.max(np.abs(gf)))
+    assert g[5] < -1.0
+    if kappa == 0.0:
+        np.testing.assert_allclose(grad.envelope_grad(sol), gf, atol=1e-6 * np.max(np.abs(gf)))
+
+
+def test_scaling_susceptance_radial_line_at_limit():
+    """A radial line at its flow limit: scaling its susceptance with capacity leaves the
+    capacity gradient unchanged (the flow is fixed by balance and its MW limit is eta
+    either way), which pins the cancellation between the limit row's eta-derivatives."""
+    net, eta = network(2, gens=[(0, 10.0, 1000.0), (1, 60.0, 1000.0)], lines=[(0, 1, 1000.0, 150.0)])
+    sc = scenario([[20.0, 30.0], [300.0, 260.0]], G=2)
+    g_fixed = grad.adjoint_grad(dispatch.solve(net, sc, eta, opts()))
+    assert g_fixed[2] < -1.0  # the flow limit binds (beta dtheta_max = 524 MW > 150 MW)
+    net["line_beta_ref"] = np.array([0.5 * eta[2]])
+    sol = dispatch.solve(net, sc, eta, opts())
+    np.testing.assert_allclose(sol.flow[0], [eta[2], eta[2]], atol=1e-6)
+    for g in (grad.adjoint_grad(sol), grad.envelope_grad(sol)):
+        np.testing.assert_allclose(g, g_fixed, atol=1e-6 * np.max(np.abs(g_fixed)))
+
+
 # ---------------------------------------------------------------- ramping generators
 def test_ramp_limit_closed_form():
     """A cheap generator limited to ramping 0.2 of its 500 MW per hour while the load
