@@ -97,6 +97,11 @@ typedef struct {
      * (0, 1) constrain; 0 or >= 1 means unlimited.  A scenario with ramping generators
      * runs on the per-iteration kernels, not the cluster-resident path. */
     const double* gen_ramp;
+    /* [n_line] or NULL (fixed susceptances): a value > 0 makes an AC line's susceptance
+     * scale with its planned capacity, beta_l(eta) = line_beta[l] * eta_l / line_beta_ref[l]
+     * (capacity added by parallel circuits): the constraint matrix then depends on eta
+     * (the A(eta) of Eq. 2) and the gradient includes that dependence.  0 keeps beta fixed. */
+    const double* line_beta_ref;
 } gx_network_desc;
 
 /* One scenario: a horizon of T hours on network `net` (Sec. 2.1: a scenario can

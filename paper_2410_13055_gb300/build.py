@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgx.so")
-SOURCES = ["gx_host.cu", "gx_kernels.cu", "gx_crs.cu", "gx_ramp.cu", "gx_noalloc.cu", "gx_gnn.cu"]
+SOURCES = ["gx_host.cu", "gx_kernels.cu", "gx_crs.cu", "gx_ramp.cu", "gx_scale.cu", "gx_noalloc.cu", "gx_gnn.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "--expt-relaxed-constexpr"]
 

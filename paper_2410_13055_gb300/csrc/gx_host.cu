@@ -42,6 +42,9 @@ struct NetH {
     std::vector<float> inv_cnt, inv_wsum, dres_w, l_w;
     std::vector<uint8_t> firm;
     int gen0 = 0, line0 = 0, bat0 = 0, bus0 = 0, ptr0 = 0, eta0 = 0;
+    std::vector<double> line_bref;  // reference capacity of a scaling susceptance (0: fixed beta)
+    std::vector<int> l_scale;       // per line: its scaling index, -1 if beta is fixed
+    std::vector<int> bus_sdres;     // per bus: its dual-residual record among the scaling ones, -1 if none
 };
 
 struct ScenH {
@@ -78,6 +81,11 @@ struct gx_network {
     std::vector<int> pool;             // their pool records (words)
     std::vector<int2> prep;            // (pool word, eta index) of each generator plan value
     std::vector<uint8_t> firm;         // generator has capacity factor 1 in every hour of every scenario
+    // lines whose susceptance scales with capacity (gx_scale.cu)
+    std::vector<int> sc_line, sc_eta, sc_gwarp;
+    std::vector<double> sc_b, sc_bmin;
+    std::vector<int2> sc_pool, sc_dres_l;
+    std::vector<ScaleDres> sc_dres, sc_dres_pool;  // bus_dres_w targets; pool-word targets
     // cluster-resident solver: scenarios grouped by (cluster size, hours per battery lane)
     struct CrsGroup {
         int C = 0, hpl = 0, first = 0, n = 0;
@@ -99,6 +107,7 @@ struct gx_network {
     // workspace offsets
     size_t o_scen, o_bbs, o_lbs, o_bws, o_cbs, o_gwarp, o_knet, o_busblk, o_pool, o_prep, o_crs;
     size_t o_bus4blk, o_l4bs;
+    size_t o_scl, o_sce, o_scb, o_scbm, o_scp, o_scd, o_scdl, o_scgw;
     size_t o_rgen, o_rrate, o_gramp, o_rws, o_rdd, o_ardd, o_rf[4], o_ra[4], o_rpart;
     size_t o_gbus, o_gcost, o_gemis, o_gfirm, o_lfrom, o_lto, o_lbeta, o_ldth, o_lw, o_bbus, o_bdur, o_beffc, o_beffd;
     size_t o_gptr, o_gidx, o_bptr, o_bidx, o_eptr, o_eidx, o_icnt, o_iwsum, o_dresw;
@@ -249,6 +258,20 @@ static void make_ctx(gx_network* net) {
     c.pool = I(net->o_pool);
     c.prep = reinterpret_cast<const int2*>(d + net->o_prep);
     c.n_prep = (int)net->prep.size();
+    c.sc_line = I(net->o_scl);
+    c.sc_eta = I(net->o_sce);
+    c.sc_b = D(net->o_scb);
+    c.sc_bmin = D(net->o_scbm);
+    c.sc_pool = reinterpret_cast<const int2*>(d + net->o_scp);
+    c.sc_dres = reinterpret_cast<const ScaleDres*>(d + net->o_scd);
+    c.sc_dres_l = reinterpret_cast<const int2*>(d + net->o_scdl);
+    c.sc_gwarp = I(net->o_scgw);
+    c.l_beta_w = F(net->o_lbeta);
+    c.dres_w_w = F(net->o_dresw);
+    c.n_scale = (int)net->sc_line.size();
+    c.n_sc_pool = (int)net->sc_pool.size();
+    c.n_sc_dres = (int)net->sc_dres.size();
+    c.n_sc_gwarps = (int)net->sc_gwarp.size() / 2;
     c.line_blk_scen = I(net->o_lbs);
     c.bat_warp_scen = I(net->o_bws);
     c.cost_blk_scen = I(net->o_cbs);
@@ -477,6 +500,8 @@ static void build_bus_blocks(gx_network* net) {
     net->bus4_blk.clear();
     net->pool.clear();
     net->prep.clear();
+    net->sc_pool.clear();
+    net->sc_dres_pool.clear();
     for (int quad = 0; quad < 2; ++quad)
     for (int s = 0; s < net->S; ++s) {
         const ScenDev& sd = net->sdev[s];
@@ -533,6 +558,11 @@ static void build_bus_blocks(gx_network* net) {
                     p[o[kPH_IC] + k] = fbits(h.inv_cnt[r.n0 + k]);
                     p[o[kPH_IW] + k] = fbits(h.inv_wsum[r.n0 + k]);
                     p[o[kPH_DR] + k] = fbits(h.dres_w[r.n0 + k]);
+                    if (h.bus_sdres[r.n0 + k] >= 0) {
+                        ScaleDres rec = net->sc_dres[h.bus_sdres[r.n0 + k]];
+                        rec.target = off + o[kPH_DR] + k;
+                        net->sc_dres_pool.push_back(rec);
+                    }
                 }
                 for (int k = 0; k < gcnt; ++k) {
                     const int g = h.gidx[gb + k];
@@ -548,6 +578,7 @@ static void build_bus_blocks(gx_network* net) {
                     const int e = h.eidx[eb + k];
                     p[o[kPH_ECODE] + k] = e;
                     p[o[kPH_EBETA] + k] = fbits((float)h.line_beta[e >> 1]);
+                    if (h.l_scale[e >> 1] >= 0) net->sc_pool.push_back(int2{off + o[kPH_EBETA] + k, h.l_scale[e >> 1]});
                     p[o[kPH_EW] + k] = fbits(h.l_w[e >> 1]);
                 }
                 for (int k = 0; k < bcnt; ++k) p[o[kPH_BROW] + k] = h.bidx[bb + k];
@@ -598,6 +629,13 @@ gx_status gx_network_create(const gx_network_desc* nets, int n_nets, const gx_sc
         h.line_dc.assign(h.L, 0);
         if (d.line_dc)
             for (int l = 0; l < h.L; ++l) h.line_dc[l] = d.line_dc[l] != 0;
+        h.line_bref.assign(h.L, 0.0);
+        if (d.line_beta_ref)
+            for (int l = 0; l < h.L; ++l) {
+                if (!(d.line_beta_ref[l] >= 0 && isfin(d.line_beta_ref[l])))
+                    return bad("line_beta_ref must be finite and >= 0");
+                if (!h.line_dc[l]) h.line_bref[l] = d.line_beta_ref[l];  // HVDC: no susceptance
+            }
         h.gen_ramp.assign(h.G, 0.0);
         if (d.gen_ramp)
             for (int g = 0; g < h.G; ++g) {
@@ -635,6 +673,39 @@ gx_status gx_network_create(const gx_network_desc* nets, int n_nets, const gx_sc
         derive_network(h, o);
         h.gen0 = gen0; h.line0 = line0; h.bat0 = bat0; h.bus0 = bus0; h.ptr0 = ptr0; h.eta0 = K;
         h.ramp0 = net->tot_ramp;
+        // scaling susceptances: beta = (beta0 / ref) eta, and the dual-residual weights of
+        // the buses they touch, split into the fixed lines' part and the scaling ends
+        h.l_scale.assign(h.L, -1);
+        for (int l = 0; l < h.L; ++l)
+            if (h.line_bref[l] > 0) {
+                h.l_scale[l] = (int)net->sc_line.size();
+                net->sc_line.push_back(h.line0 + l);
+                net->sc_eta.push_back(h.eta0 + h.G + l);
+                net->sc_b.push_back(h.line_beta[l] / h.line_bref[l]);
+                net->sc_bmin.push_back(1e-6 * h.line_beta[l]);
+            }
+        h.bus_sdres.assign(h.N, -1);
+        for (int n = 0; n < h.N; ++n) {
+            ScaleDres rec{};
+            rec.first = (int)net->sc_dres_l.size();
+            for (int q = h.eptr[n]; q < h.eptr[n + 1]; ++q) {
+                const int l = h.eidx[q] >> 1;
+                if (h.l_scale[l] >= 0) {
+                    int wb;
+                    std::memcpy(&wb, &h.l_w[l], 4);
+                    net->sc_dres_l.push_back(int2{h.l_scale[l], wb});
+                    ++rec.count;
+                } else {
+                    const double q2 = h.l_w[l] / h.line_beta[l];
+                    rec.d0 += q2 * q2;
+                }
+            }
+            if (rec.count) {
+                rec.target = -1 - (h.bus0 + n);
+                h.bus_sdres[n] = (int)net->sc_dres.size();
+                net->sc_dres.push_back(rec);
+            }
+        }
         gen0 += h.G; line0 += h.L; bat0 += h.B; bus0 += h.N; ptr0 += h.N + 1; K += h.G + h.L + h.B;
         net->tot_ramp += (int)h.ramp_gens.size();
     }
@@ -718,6 +789,8 @@ gx_status gx_network_create(const gx_network_desc* nets, int n_nets, const gx_sc
         net->n_cost_blk += ncb;
         for (int r = 0; r < h.G + h.L + h.B; ++r) { net->gwarp.push_back(s); net->gwarp.push_back(r); }
         net->n_gwarps += h.G + h.L + h.B;
+        for (int l = 0; l < h.L; ++l)
+            if (h.l_scale[l] >= 0) { net->sc_gwarp.push_back(s); net->sc_gwarp.push_back(h.l_scale[l]); }
     }
     net->gs_total = gs;
     net->bus_el = eb; net->gen_el = eg; net->line_el = el; net->bat_el = ebt;
@@ -731,6 +804,7 @@ gx_status gx_network_create(const gx_network_desc* nets, int n_nets, const gx_sc
                 if (sc.cf[(size_t)g * sc.Tp + t] != 1.0f) { net->firm[n.gen0 + g] = 0; break; }
     }
     build_bus_blocks(net);
+    net->sc_dres.insert(net->sc_dres.end(), net->sc_dres_pool.begin(), net->sc_dres_pool.end());
     build_crs_groups(net);
     net->k_net.resize(K);
     for (int k = 0; k < n_nets; ++k)
@@ -773,6 +847,14 @@ gx_status gx_network_create(const gx_network_desc* nets, int n_nets, const gx_sc
     net->o_rws = L.add(I4(net->n_ramp_warps));
     net->o_rdd = L.add(F4(net->ramp_el));
     net->o_ardd = L.add(F4(net->ramp_el));
+    net->o_scl = L.add(I4((long long)net->sc_line.size()));
+    net->o_sce = L.add(I4((long long)net->sc_eta.size()));
+    net->o_scb = L.add(D8((long long)net->sc_b.size()));
+    net->o_scbm = L.add(D8((long long)net->sc_bmin.size()));
+    net->o_scp = L.add(8 * std::max<size_t>(net->sc_pool.size(), 1));
+    net->o_scd = L.add(sizeof(ScaleDres) * std::max<size_t>(net->sc_dres.size(), 1));
+    net->o_scdl = L.add(8 * std::max<size_t>(net->sc_dres_l.size(), 1));
+    net->o_scgw = L.add(I4((long long)net->sc_gwarp.size()));
     net->static_end = L.total;
     const long long rows[16] = {eg, eb, el, el, el, el, ebt, ebt, ebt, ebt, ebt, ebt, ebt, eb, eb, eb};
     for (int k = 0; k < 16; ++k) net->o_f[k] = L.add(F4(rows[k]));
@@ -830,6 +912,14 @@ gx_status gx_network_bind(gx_network* net, void* dev_mem, size_t bytes, void* st
     put(net->o_crs, net->crs_list.data(), 4 * net->crs_list.size());
     put(net->o_bus4blk, net->bus4_blk.data(), sizeof(BusBlk) * net->bus4_blk.size());
     put(net->o_l4bs, net->line4_blk_scen.data(), 4 * net->line4_blk_scen.size());
+    put(net->o_scl, net->sc_line.data(), 4 * net->sc_line.size());
+    put(net->o_sce, net->sc_eta.data(), 4 * net->sc_eta.size());
+    put(net->o_scb, net->sc_b.data(), 8 * net->sc_b.size());
+    put(net->o_scbm, net->sc_bmin.data(), 8 * net->sc_bmin.size());
+    put(net->o_scp, net->sc_pool.data(), 8 * net->sc_pool.size());
+    put(net->o_scd, net->sc_dres.data(), sizeof(ScaleDres) * net->sc_dres.size());
+    put(net->o_scdl, net->sc_dres_l.data(), 8 * net->sc_dres_l.size());
+    put(net->o_scgw, net->sc_gwarp.data(), 4 * net->sc_gwarp.size());
     auto put_f = [&](size_t off, const std::vector<double>& v, size_t base) {
         float* p = reinterpret_cast<float*>(h.data() + off) + base;
         for (size_t i = 0; i < v.size(); ++i) p[i] = (float)v[i];
@@ -1271,6 +1361,7 @@ gx_status gx_dispatch_solve_batch(gx_network* net, const float* eta_dev, const i
     c.eta = eta_dev;
     c.warm = warm == GX_WARM_USER ? warm_dev : nullptr;
     int launches = launch_prep(c, st);
+    launches += launch_scale_prep(c, st);
     if (warm != GX_WARM_PREV || !net->solved) {
         launches += launch_dev(c, M_RESET, 0, 0, st);
         launches += launch_bus(c, M_RESET, 0, 0, st);
@@ -1312,6 +1403,7 @@ gx_status gx_dispatch_grad_batch(gx_network* net, const float* eta_dev, int warm
     GX_CUDA(cudaMemcpyAsync(net->dev + net->o_wprime, net->wprime.data(), 8 * net->S, cudaMemcpyHostToDevice, st));
     GX_CUDA(cudaMemcpyAsync(net->dev + net->o_done, net->done_init.data(), 4 * net->S, cudaMemcpyHostToDevice, st));
     int launches = launch_prep(c, st);
+    launches += launch_scale_prep(c, st);
     launches += launch_dev(c, M_MASK, 0, 0, st);
     launches += launch_bus(c, M_MASK, 0, 0, st);
     const bool envelope = net->opts.grad_envelope && net->opts.kappa == 0.0;
@@ -1332,6 +1424,7 @@ gx_status gx_dispatch_grad_batch(gx_network* net, const float* eta_dev, int warm
     const int* inb = reinterpret_cast<const int*>(net->dev + net->o_inb);
     launches += launch_grad(envelope ? c : ac, envelope ? 1 : 0,
                             reinterpret_cast<const int*>(net->dev + net->o_gwarp), net->n_gwarps, inb, st);
+    launches += launch_scale_grad(envelope ? c : ac, envelope ? 1 : 0, inb, st);
     launches += launch_grad_combine(c, reinterpret_cast<const double*>(net->dev + net->o_wprime),
                                     reinterpret_cast<const int*>(net->dev + net->o_knet), grad_dev, net->K, st);
     GX_CUDA(cudaGetLastError());

@@ -120,6 +120,14 @@ struct ScenDev {
 };
 
 // Device pointers + scalars handed to every kernel by value.
+// A dual-residual weight sum_{line ends at the bus} (w_l / beta_l)^2 that depends on
+// scaling susceptances: d0 holds the fixed lines' part, [first, first + count) of
+// sc_dres_l the scaling ones.  target >= 0: pool word; < 0: bus_dres_w[-1 - target].
+struct ScaleDres {
+    double d0;
+    int target, first, count, pad;
+};
+
 struct Ctx {
     // sizes
     int S, n_bus_blk, n_line_blk, n_bat_warps, n_cost_blk;
@@ -149,6 +157,20 @@ struct Ctx {
     int* pool;                 // bus-block pool records (generator plan values refreshed per call)
     const int2* prep;          // [n_prep] (pool word, eta index) of every generator plan value
     int n_prep;
+    // Lines whose susceptance scales with capacity, beta_l = (beta0_l / ref_l) eta_l: once per
+    // call k_scale_prep writes the effective beta into the line table and the bus pool
+    // records, and the dual-residual weights of the buses they touch.
+    const int* sc_line;        // [n_scale] global line index
+    const int* sc_eta;         // [n_scale] its plan entry
+    const double* sc_b;        // [n_scale] beta0_l / ref_l  (= d beta_l / d eta_l)
+    const double* sc_bmin;     // [n_scale] floor of beta_l (1e-6 beta0_l, for eta_l -> 0)
+    const int2* sc_pool;       // [n_sc_pool] (pool word of a line end's beta, scaling index)
+    const ScaleDres* sc_dres;  // [n_sc_dres] dual-residual weights to rewrite
+    const int2* sc_dres_l;     // (scaling index, float bits of w_l) of the scaling line ends
+    const int* sc_gwarp;       // [2 n_sc_gwarps] (scenario, scaling index) gradient warps
+    float* l_beta_w;           // the line table (l_beta) and ...
+    float* dres_w_w;           // ... the bus dual-residual weights (bus_dres_w), writable
+    int n_scale, n_sc_pool, n_sc_dres, n_sc_gwarps;
     const int* line_blk_scen;  // [n_line_blk]
     const int* bat_warp_scen;  // [n_bat_warps]
     const int* cost_blk_scen;  // [n_cost_blk]
@@ -223,6 +245,9 @@ int launch_grad(const Ctx& c, int envelope, const int* gwarp_scen, int n_gwarps,
                 cudaStream_t st);
 int launch_grad_combine(const Ctx& c, const double* wprime, const int* k_net, float* grad_out, int K,
                         cudaStream_t st);
+// capacity-dependent susceptance (gx_scale.cu)
+int launch_scale_prep(const Ctx& c, cudaStream_t st);
+int launch_scale_grad(const Ctx& c, int envelope, const int* in_batch, cudaStream_t st);
 int launch_plan_step(float* eta, const float* grad, const float* gamma, const float* lo, const float* hi, float alpha,
                      int K, cudaStream_t st);
 

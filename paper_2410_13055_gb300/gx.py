@@ -38,7 +38,8 @@ class NetworkDesc(C.Structure):
                 ("gen_bus", _i32p), ("gen_cost", _f64p), ("gen_emis", _f64p),
                 ("line_from", _i32p), ("line_to", _i32p), ("line_beta", _f64p), ("line_dtheta", _f64p),
                 ("bat_bus", _i32p), ("bat_dur", _f64p), ("bat_eff_c", _f64p), ("bat_eff_d", _f64p),
-                ("line_dc", C.POINTER(C.c_uint8)), ("gen_ramp", _f64p)]
+                ("line_dc", C.POINTER(C.c_uint8)), ("gen_ramp", _f64p),
+                ("line_beta_ref", _f64p)]
 
 
 class ScenarioDesc(C.Structure):
@@ -180,6 +181,10 @@ class Network:
                 rp = np.ascontiguousarray(n["gen_ramp"], np.float64)
                 arrs["gen_ramp"] = rp
                 d.gen_ramp = rp.ctypes.data_as(_f64p)
+            if "line_beta_ref" in n and np.any(np.asarray(n["line_beta_ref"]) > 0):
+                br = np.ascontiguousarray(n["line_beta_ref"], np.float64)
+                arrs["line_beta_ref"] = br
+                d.line_beta_ref = br.ctypes.data_as(_f64p)
         sd = (ScenarioDesc * len(scens))()
         for s, sc in enumerate(scens):
             load = np.ascontiguousarray(sc["load"], np.float64)

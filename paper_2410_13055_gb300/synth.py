@@ -305,6 +305,19 @@ def add_ramps(net, rate=(0.1, 0.3), share=1.0, seed=0):
     return out
 
 
+def add_scaling(net, share=0.3, seed=0):
+    """Let a share of the AC lines gain susceptance with capacity (``line_beta_ref`` = their
+    existing capacity eta_min, so beta is the given one at eta_min and grows in proportion
+    as circuits are added).  Returns a new network dict (inputs only)."""
+    rng = _rng(seed)
+    G, L = net["gen_bus"].size, net["line_from"].size
+    out = dict(net)
+    dc = np.asarray(net.get("line_dc", np.zeros(L)), bool)
+    pick = (rng.random(L) < share) & ~dc
+    out["line_beta_ref"] = np.where(pick, np.asarray(net["eta_min"][G:G + L], float), 0.0)
+    return out
+
+
 CONFIGS = {"tiny": tiny, "medium": medium, "batching": batching, "scale": scale}
 
 

@@ -63,6 +63,27 @@ def test_create_validates_on_host(gx):
     gx._lib.gx_network_destroy(h)
 
 
+def test_scaling_susceptance_validated_on_host(gx):
+    """line_beta_ref must be finite and >= 0; a valid one adds the per-call tables of the
+    scaling lines to the workspace."""
+    from paper_2410_13055_gb300 import synth
+    nets, scens = synth.tiny()
+    L = nets[0]["line_from"].size
+    bad = dict(nets[0]); bad["line_beta_ref"] = np.full(L, -1.0)
+    with pytest.raises(gx.GxError) as e:
+        gx_create(gx, [bad], scens)
+    assert "line_beta_ref" in str(e.value)
+    bad["line_beta_ref"] = np.full(L, np.nan)
+    with pytest.raises(gx.GxError):
+        gx_create(gx, [bad], scens)
+    h0, _, b0 = gx_create(gx, nets, scens)
+    ok = dict(nets[0]); ok["line_beta_ref"] = np.where(np.arange(L) % 2 == 0, 100.0, 0.0)
+    h1, K, b1 = gx_create(gx, [ok], scens)
+    assert K == nets[0]["K"] and b1 >= b0
+    gx._lib.gx_network_destroy(h0)
+    gx._lib.gx_network_destroy(h1)
+
+
 def test_opts_validation(gx):
     o = gx.default_opts()
     assert o.eps > 0 and o.rho > 0 and o.inner_iters >= 1
@@ -97,6 +118,10 @@ def gx_create(gx, nets, scens, opts=None):
             arrs["bat_bus"].size
         for name, a in arrs.items():
             setattr(d, name, a.ctypes.data_as(gx._i32p if a.dtype == np.int32 else gx._f64p))
+        if "line_beta_ref" in n:
+            br = np.ascontiguousarray(n["line_beta_ref"], np.float64)
+            keep.append(br)
+            d.line_beta_ref = br.ctypes.data_as(gx._f64p)
     sd = (gx.ScenarioDesc * len(scens))()
     for s, sc in enumerate(scens):
         load = np.ascontiguousarray(sc["load"], np.float64)
