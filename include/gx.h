@@ -137,6 +137,9 @@ typedef struct {
                             penalties scale with it as in the forward); the adjoint's free
                             devices have curvature eps only, so a penalty near eps converges
                             far faster than the forward's rho */
+    double adj_rho_theta_c;  /* phase penalty scale of the adjoint iteration (rho_theta_l =
+                                adj_rho * adj_rho_theta_c * w_l); 0: rho_theta_c */
+    double adj_rho_inner_c;  /* battery and ramp inner penalty scale of the adjoint; 0: rho_inner_c */
 } gx_opts;
 
 enum { GX_WARM_COLD = 0, GX_WARM_PREV = 1, GX_WARM_USER = 2, GX_WARM_LEARNED = 3 };
@@ -190,6 +193,14 @@ gx_status gx_network_set_opts(gx_network* net, const gx_opts* opts);
 /* Byte offset (from dev_mem) and element count of array `which` for scenario
  * `scen` (scen = -1: the whole array over all scenarios). */
 gx_status gx_network_array(const gx_network* net, int which, int scen, size_t* offset_bytes, size_t* count);
+/* Byte range [offset, offset + bytes) of the message passing's iteration state inside the
+ * workspace: which = 0 the forward solve's, 1 the adjoint's.  The state is every FP32 array
+ * the iteration carries from one step to the next (device outputs, line phase copies,
+ * battery and ramp inner copies and multipliers, bus duals and averages), contiguous in
+ * that order; alignment gaps between arrays stay zero.  Saving it after a call and writing
+ * it back before a GX_WARM_PREV call restores that warm start exactly (checkpointing).
+ * Errors: GX_ERR_INVALID_ARG for a NULL argument or another `which`. */
+gx_status gx_network_state_range(const gx_network* net, int which, size_t* offset_bytes, size_t* bytes);
 /* Row stride Tp and device counts of scenario s. */
 gx_status gx_network_scenario_info(const gx_network* net, int s, int* T, int* Tp, int* N, int* G, int* L, int* B,
                                    int* eta_offset);

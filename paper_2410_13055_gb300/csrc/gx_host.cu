@@ -114,6 +114,7 @@ struct gx_network {
     size_t o_load, o_cf, o_dd, o_add;
     size_t static_end;
     size_t o_f[16], o_a[16];  // forward / adjoint state arrays, order of StatePtrs
+    size_t o_fend, o_aend;    // end of the forward / adjoint state range (ramp arrays included)
     size_t o_mgen, o_mload, o_mline, o_mbat;
     size_t o_done, o_iters, o_status, o_adjit, o_nact, o_ctr, o_inb, o_resid, o_rbest, o_cost, o_h, o_grads, o_wprime;
     size_t o_flow, o_price, o_shed, o_bpart, o_lpart, o_btpart, o_cpart;
@@ -160,11 +161,14 @@ struct gx_network {
     }
 };
 
-static void fill_dd_for(gx_network* net, double rho, std::vector<float>& out) {
+static double adj_theta_c(const gx_opts& o) { return o.adj_rho_theta_c > 0 ? o.adj_rho_theta_c : o.rho_theta_c; }
+static double adj_inner_c(const gx_opts& o) { return o.adj_rho_inner_c > 0 ? o.adj_rho_inner_c : o.rho_inner_c; }
+
+static void fill_dd_for(gx_network* net, double rho, double inner_c, std::vector<float>& out) {
     // Thomas pivots of the battery tridiagonal system (one row per battery and scenario):
     // diag = [1 + g rho_in, 2 + g rho_in, ...], off-diagonal -1, with
     // g = [a, -k] H^{-1} [a, -k]^T and H = [[eps+rho_in+rho, -rho], [-rho, eps+rho_in+rho]].
-    const double eps = net->opts.eps, ri = rho * net->opts.rho_inner_c;
+    const double eps = net->opts.eps, ri = rho * inner_c;
     out.assign((size_t)net->bat_el, 1.0f);
     for (int s = 0; s < net->S; ++s) {
         const ScenH& sc = net->scens[s];
@@ -189,8 +193,8 @@ static void fill_dd_for(gx_network* net, double rho, std::vector<float>& out) {
 // (eps + rho + rho_in) I + rho_in D^T D, D the first difference over T hours, so the
 // diagonal is a + rho_in [1, 2, ..., 2, 1] (a alone for T = 1) and the off-diagonal -rho_in.
 // Stored as 1 / m_t for m_0 = diag_0, m_t = diag_t - rho_in^2 / m_{t-1}.
-static void fill_ramp_dd_for(gx_network* net, double rho, std::vector<float>& out) {
-    const double eps = net->opts.eps, ri = rho * net->opts.rho_inner_c, a = eps + rho + ri;
+static void fill_ramp_dd_for(gx_network* net, double rho, double inner_c, std::vector<float>& out) {
+    const double eps = net->opts.eps, ri = rho * inner_c, a = eps + rho + ri;
     out.assign((size_t)std::max<long long>(net->ramp_el, 1), 1.0f);
     for (int s = 0; s < net->S; ++s) {
         const ScenDev& sd = net->sdev[s];
@@ -208,10 +212,11 @@ static void fill_ramp_dd_for(gx_network* net, double rho, std::vector<float>& ou
 }
 
 static void fill_dd(gx_network* net) {
-    fill_dd_for(net, net->opts.rho, net->dd_host);
-    fill_dd_for(net, net->opts.adj_rho, net->add_host);
-    fill_ramp_dd_for(net, net->opts.rho, net->rdd_host);
-    fill_ramp_dd_for(net, net->opts.adj_rho, net->ardd_host);
+    const gx_opts& o = net->opts;
+    fill_dd_for(net, o.rho, o.rho_inner_c, net->dd_host);
+    fill_dd_for(net, o.adj_rho, adj_inner_c(o), net->add_host);
+    fill_ramp_dd_for(net, o.rho, o.rho_inner_c, net->rdd_host);
+    fill_ramp_dd_for(net, o.adj_rho, adj_inner_c(o), net->ardd_host);
     net->dd_dirty = true;
 }
 
@@ -308,8 +313,8 @@ static void make_ctx(gx_network* net) {
     Ctx& a = net->actx;
     a = c;
     a.rho = (float)o.adj_rho;
-    a.rho_in = (float)(o.adj_rho * o.rho_inner_c);
-    a.rth_c = (float)(o.adj_rho * o.rho_theta_c);
+    a.rho_in = (float)(o.adj_rho * adj_inner_c(o));
+    a.rth_c = (float)(o.adj_rho * adj_theta_c(o));
     a.bat_dd = F(net->o_add);
     a.ramp_dd = F(net->o_ardd);
     a.max_it = o.adj_max_iter;
@@ -359,6 +364,8 @@ gx_status gx_opts_default(gx_opts* o) {
     o->adj_max_iter = 20000;
     o->grad_envelope = 0;
     o->adj_rho = 0.002;
+    o->adj_rho_theta_c = 0.0;
+    o->adj_rho_inner_c = 0.0;
     return GX_OK;
 }
 
@@ -392,6 +399,8 @@ static gx_status check_opts(const gx_opts* o) {
     if (o->check_every < 1) return fail(GX_ERR_INVALID_ARG, "check_every must be >= 1");
     if (!(o->tol_active >= 0)) return fail(GX_ERR_INVALID_ARG, "tol_active must be >= 0");
     if (o->theta_weight != 0 && o->theta_weight != 1) return fail(GX_ERR_INVALID_ARG, "theta_weight is 0 or 1");
+    if (!(o->adj_rho_theta_c >= 0 && isfin(o->adj_rho_theta_c)) || !(o->adj_rho_inner_c >= 0 && isfin(o->adj_rho_inner_c)))
+        return fail(GX_ERR_INVALID_ARG, "opts.adj_rho_theta_c and adj_rho_inner_c must be >= 0 (0: the forward's)");
     return GX_OK;
 }
 
@@ -857,8 +866,13 @@ gx_status gx_network_create(const gx_network_desc* nets, int n_nets, const gx_sc
     net->o_scgw = L.add(I4((long long)net->sc_gwarp.size()));
     net->static_end = L.total;
     const long long rows[16] = {eg, eb, el, el, el, el, ebt, ebt, ebt, ebt, ebt, ebt, ebt, eb, eb, eb};
+    // forward state, then adjoint state, each one contiguous range (gx_network_state_range)
     for (int k = 0; k < 16; ++k) net->o_f[k] = L.add(F4(rows[k]));
+    for (int k = 0; k < 4; ++k) net->o_rf[k] = L.add(F4(net->ramp_el));
+    net->o_fend = L.total;
     for (int k = 0; k < 16; ++k) net->o_a[k] = L.add(F4(rows[k]));
+    for (int k = 0; k < 4; ++k) net->o_ra[k] = L.add(F4(net->ramp_el));
+    net->o_aend = L.total;
     net->o_mgen = L.add(B1(eg)); net->o_mload = L.add(B1(eb)); net->o_mline = L.add(B1(el)); net->o_mbat = L.add(B1(ebt));
     net->o_done = L.add(I4(S)); net->o_iters = L.add(I4(S)); net->o_status = L.add(I4(S)); net->o_adjit = L.add(I4(S));
     net->o_nact = L.add(I4(1)); net->o_ctr = L.add(I4(1)); net->o_inb = L.add(I4(S));
@@ -868,8 +882,6 @@ gx_status gx_network_create(const gx_network_desc* nets, int n_nets, const gx_sc
     net->o_bpart = L.add(F4((long long)net->n_bus4_blk * kBusPart));
     net->o_lpart = L.add(F4((long long)net->n_line4_blk * kDevPart));
     net->o_btpart = L.add(F4((long long)net->n_bat_warps * kDevPart));
-    for (int k = 0; k < 4; ++k) net->o_rf[k] = L.add(F4(net->ramp_el));
-    for (int k = 0; k < 4; ++k) net->o_ra[k] = L.add(F4(net->ramp_el));
     net->o_rpart = L.add(F4((long long)net->n_ramp_warps * kDevPart));
     net->o_cpart = L.add(D8(2LL * net->n_cost_blk));
     net->in_batch.assign(S, 0);
@@ -996,6 +1008,14 @@ gx_status gx_network_set_opts(gx_network* net, const gx_opts* opts) {
     net->opts = *opts;
     fill_dd(net);
     if (net->dev) make_ctx(net);
+    return GX_OK;
+}
+
+gx_status gx_network_state_range(const gx_network* net, int which, size_t* offset, size_t* bytes) {
+    if (!net || !offset || !bytes) return fail(GX_ERR_INVALID_ARG, "NULL argument");
+    if (which != 0 && which != 1) return fail(GX_ERR_INVALID_ARG, "which must be 0 (forward) or 1 (adjoint)");
+    *offset = which ? net->o_a[0] : net->o_f[0];
+    *bytes = (which ? net->o_aend : net->o_fend) - *offset;
     return GX_OK;
 }
 

@@ -52,7 +52,8 @@ class Opts(C.Structure):
                 ("rho_inner_c", C.c_double), ("inner_iters", C.c_int),
                 ("tol", C.c_double), ("max_iter", C.c_int), ("check_every", C.c_int),
                 ("tol_active", C.c_double), ("adj_tol", C.c_double), ("adj_max_iter", C.c_int),
-                ("grad_envelope", C.c_int), ("adj_rho", C.c_double)]
+                ("grad_envelope", C.c_int), ("adj_rho", C.c_double),
+                ("adj_rho_theta_c", C.c_double), ("adj_rho_inner_c", C.c_double)]
 
 
 class Stats(C.Structure):
@@ -78,6 +79,7 @@ _SIGS = {
     "gx_network_bind": (C.c_int, [_vp, _vp, _sz, _vp]),
     "gx_network_set_opts": (C.c_int, [_vp, C.POINTER(Opts)]),
     "gx_network_array": (C.c_int, [_vp, C.c_int, C.c_int, C.POINTER(_sz), C.POINTER(_sz)]),
+    "gx_network_state_range": (C.c_int, [_vp, C.c_int, C.POINTER(_sz), C.POINTER(_sz)]),
     "gx_network_scenario_info": (C.c_int, [_vp, C.c_int] + [C.POINTER(C.c_int)] * 7),
     "gx_dispatch_solve_batch": (C.c_int, [_vp, _vp, C.POINTER(C.c_int), C.c_int, C.c_int, _vp,
                                           C.POINTER(Stats), _vp]),
@@ -238,6 +240,16 @@ class Network:
                 setattr(opts, k, v)
         _check(_lib.gx_network_set_opts(self._h, C.byref(opts)), "gx_network_set_opts", False)
         self.opts = opts
+
+    def state(self, adjoint=False):
+        """A float32 torch view (no copy) of the forward or adjoint iteration state; clone it
+        to checkpoint a warm start, copy it back before a warm="prev" call to restore it."""
+        import torch
+        off, nb = C.c_size_t(), C.c_size_t()
+        _check(_lib.gx_network_state_range(self._h, 1 if adjoint else 0, C.byref(off), C.byref(nb)),
+               "gx_network_state_range", False)
+        start = self._off0 + off.value
+        return self.ws[start:start + nb.value].view(torch.float32)
 
     def array(self, which, scen=-1):
         """A torch view (no copy) of an output array inside the workspace."""
