@@ -1311,6 +1311,23 @@ static gx_status run_loop(gx_network* net, int adj, cudaStream_t st, int* launch
     return GX_OK;
 }
 
+// Battery and ramp pivot tables after gx_network_set_opts changed a penalty: both the
+// solve and the gradient entry points upload them before their first iteration.
+static gx_status upload_pivots(gx_network* net, cudaStream_t st) {
+    if (!net->dd_dirty) return GX_OK;
+    GX_CUDA(cudaMemcpyAsync(net->dev + net->o_dd, net->dd_host.data(), 4 * net->dd_host.size(),
+                            cudaMemcpyHostToDevice, st));
+    GX_CUDA(cudaMemcpyAsync(net->dev + net->o_add, net->add_host.data(), 4 * net->add_host.size(),
+                            cudaMemcpyHostToDevice, st));
+    GX_CUDA(cudaMemcpyAsync(net->dev + net->o_rdd, net->rdd_host.data(), 4 * net->rdd_host.size(),
+                            cudaMemcpyHostToDevice, st));
+    GX_CUDA(cudaMemcpyAsync(net->dev + net->o_ardd, net->ardd_host.data(), 4 * net->ardd_host.size(),
+                            cudaMemcpyHostToDevice, st));
+    GX_CUDA(cudaStreamSynchronize(st));
+    net->dd_dirty = false;
+    return GX_OK;
+}
+
 static gx_status upload_batch(gx_network* net, const int* scen_idx, int B, cudaStream_t st) {
     std::vector<int>& inb = net->in_batch;
     if (scen_idx) {
@@ -1365,18 +1382,7 @@ gx_status gx_dispatch_solve_batch(gx_network* net, const float* eta_dev, const i
     if (warm == GX_WARM_USER && !warm_dev) return fail(GX_ERR_INVALID_ARG, "GX_WARM_USER needs warm_dev");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (gx_status e = upload_batch(net, scen_idx, B, st)) return e;
-    if (net->dd_dirty) {
-        GX_CUDA(cudaMemcpyAsync(net->dev + net->o_dd, net->dd_host.data(), 4 * net->dd_host.size(),
-                                cudaMemcpyHostToDevice, st));
-        GX_CUDA(cudaMemcpyAsync(net->dev + net->o_add, net->add_host.data(), 4 * net->add_host.size(),
-                                cudaMemcpyHostToDevice, st));
-        GX_CUDA(cudaMemcpyAsync(net->dev + net->o_rdd, net->rdd_host.data(), 4 * net->rdd_host.size(),
-                                cudaMemcpyHostToDevice, st));
-        GX_CUDA(cudaMemcpyAsync(net->dev + net->o_ardd, net->ardd_host.data(), 4 * net->ardd_host.size(),
-                                cudaMemcpyHostToDevice, st));
-        GX_CUDA(cudaStreamSynchronize(st));
-        net->dd_dirty = false;
-    }
+    if (gx_status e = upload_pivots(net, st)) return e;
     Ctx& c = net->ctx;
     c.eta = eta_dev;
     c.warm = warm == GX_WARM_USER ? warm_dev : nullptr;
@@ -1422,6 +1428,7 @@ gx_status gx_dispatch_grad_batch(gx_network* net, const float* eta_dev, int warm
     for (int s = 0; s < net->S; ++s) net->wprime[s] = net->in_batch[s] ? net->scens[s].weight * wall / wb : 0.0;
     GX_CUDA(cudaMemcpyAsync(net->dev + net->o_wprime, net->wprime.data(), 8 * net->S, cudaMemcpyHostToDevice, st));
     GX_CUDA(cudaMemcpyAsync(net->dev + net->o_done, net->done_init.data(), 4 * net->S, cudaMemcpyHostToDevice, st));
+    if (gx_status e = upload_pivots(net, st)) return e;
     int launches = launch_prep(c, st);
     launches += launch_scale_prep(c, st);
     launches += launch_dev(c, M_MASK, 0, 0, st);

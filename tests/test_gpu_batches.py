@@ -224,3 +224,25 @@ def test_scale_full_size_properties():
     g = net.grad(e).double().cpu().numpy()
     assert net.last_grad_status == 0
     assert np.max(g) <= 1e-3 * np.max(np.abs(g)), np.max(g)
+
+
+def test_set_opts_between_solve_and_grad():
+    """Changing the adjoint penalty after a solve takes effect in the next gradient call
+    (its battery pivots are refreshed there too): the gradient equals that of a network
+    created with the new penalty, bit for bit."""
+    import torch
+    nets, scens = synth.medium(S=2, T=48)
+    e = eta_tensor(nets[0]["eta_min"] * 1.05)
+    kw = dict(kappa=50.0, tol=1e-4, adj_tol=1e-4, max_iter=50000, adj_max_iter=50000)
+    a = gpu_net(nets, scens, adj_rho=0.002, **kw)
+    assert a.solve(e) == 0
+    a.grad(e)
+    a.set_opts(adj_rho=0.004)
+    g_a = a.grad(e, warm="cold").clone()
+    it_a = a.last_grad_stats["iters_max"]
+    b = gpu_net(nets, scens, adj_rho=0.004, **kw)
+    assert b.solve(e) == 0
+    g_b = b.grad(e, warm="cold").clone()
+    assert a.last_grad_status == 0 and b.last_grad_status == 0
+    assert it_a == b.last_grad_stats["iters_max"]
+    assert torch.equal(g_a, g_b)
