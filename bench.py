@@ -183,6 +183,7 @@ def run_gx(args):
     net = gx.Network(nets, scens, kappa=KAPPA, tol=1e-3, adj_tol=1e-3, max_iter=50000, adj_max_iter=50000,
                      check_every=args.check_every)
     net.use_persistent(args.persistent)
+    net.use_graphs(args.graphs != "eager", args.graphs == "loop")
     resident = sum(1 for c in net.persistent_info() if c > 0)
     dev = torch.device("cuda", local)
     eta_min = torch.tensor(np.concatenate([n["eta_min"] for n in nets]), dtype=torch.float32, device=dev)
@@ -397,7 +398,10 @@ def run_gx(args):
                    "parallelism": f"replicas x{ws} (independent scenario shards)",
                    "path": (f"cluster-resident persistent launches for {resident} of {len(scens)} scenarios, "
                             "per-iteration kernels (CUDA graphs) for the rest") if args.persistent
-                           else "per-iteration kernels replayed as CUDA graphs"},
+                           else {"loop": "per-iteration kernels, the whole loop one CUDA graph (device-side "
+                                          "convergence test)",
+                                 "chunk": "per-iteration kernels, one CUDA graph per residual-check chunk",
+                                 "eager": "per-iteration kernels launched one by one"}[args.graphs]},
         "iterations": {"prev_fwd_median": float(np.median(it_prev)), "prev_adj_median": float(np.median(ait_prev)),
                        "cold_fwd_median": float(np.median(it_cold)), "cold_adj_median": float(np.median(ait_cold))},
         "modes": {"prev": round(value, 1), "cold": round(ws * dh / (ms_cold / 1e3), 1),
@@ -487,6 +491,10 @@ def main():
     ap.add_argument("--quick", action="store_true", help="timed previous-plan steps only (profiling runs)")
     ap.add_argument("--persistent", action="store_true",
                     help="cluster-resident persistent launches for the scenarios that fit shared memory")
+    ap.add_argument("--graphs", default="loop", choices=["loop", "chunk", "eager"],
+                    help="launch mode of the iteration kernels: the whole loop as one graph with a device-side "
+                         "convergence test (default), one graph per residual-check chunk (ncu cannot profile the "
+                         "kernel nodes of a graph with conditional nodes), or kernel by kernel")
     ap.add_argument("--per-scenario", action="store_true",
                     help="batching config: also time one network and launch sequence per scenario")
     args = ap.parse_args()
