@@ -1,6 +1,6 @@
 """Compile the CUDA library libgx.so in-tree for sm_103a (GB300).
 
-Two translation units are compiled in parallel with nvcc and linked into a shared
+The CUDA sources are compiled in parallel with nvcc and linked into one shared
 library next to this file.  Run ``python -m paper_2410_13055_gb300.build``.
 """
 import os
