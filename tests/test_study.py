@@ -29,6 +29,18 @@ def test_within_two_percent_rule():
     assert study.within(neg, -100.0) == 10           # -98.5 <= -100 + 2, -97 is not
 
 
+def test_within_gap_rule():
+    hist = [(0, 200.0), (5, 130.0), (10, 103.0), (15, 101.5), (20, 100.0)]
+    # gap 100: within 2 of the target
+    assert study.within_gap(hist, 200.0, 100.0) == 15
+    assert study.within_gap(hist, 200.0, 100.0, frac=0.05) == 10
+    assert study.within_gap(hist, 200.0, 97.0) is None  # needs J <= 99.06
+    # a warm history measured against the cold run's start and best
+    warm = [(0, 100.8), (5, 100.1)]
+    assert study.within_gap(warm, 200.0, 100.0) == 0
+    assert study.within_gap(warm, 200.0, 100.0, frac=0.005) == 5
+
+
 def test_asset_classes_partition_the_plan():
     nets, _ = synth.medium(S=1, T=24)
     g = study.asset_classes(nets[0])
