@@ -181,7 +181,7 @@ def run_gx(args):
     nets, scens = build_workload(args.config, rank, args.scenarios)
     dh = synth.device_hours(nets, scens)
     net = gx.Network(nets, scens, kappa=KAPPA, tol=1e-3, adj_tol=1e-3, max_iter=50000, adj_max_iter=50000,
-                     check_every=args.check_every)
+                     check_every=args.check_every, rho=args.rho)
     net.use_persistent(args.persistent)
     net.use_graphs(args.graphs != "eager", args.graphs == "loop")
     resident = sum(1 for c in net.persistent_info() if c > 0)
@@ -327,7 +327,7 @@ def run_gx(args):
             k = sc["net"]
             one = dict(sc, net=0, weight=1.0)
             nt = gx.Network([nets[k]], [one], kappa=KAPPA, tol=1e-3, adj_tol=1e-3, max_iter=50000,
-                            adj_max_iter=50000, check_every=args.check_every)
+                            adj_max_iter=50000, check_every=args.check_every, rho=args.rho)
             nt.use_persistent(args.persistent)
             singles.append((nt, slice(offs[k], offs[k + 1])))
         e_s = [eta[sl].clone().contiguous() for _, sl in singles]
@@ -403,7 +403,7 @@ def run_gx(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.config, "scenarios": len(scens), "device_hours_per_step": dh,
                    "start": "prev (previous plan's dispatch and adjoint state)",
-                   "kappa": KAPPA,
+                   "kappa": KAPPA, "rho": args.rho,
                    "tol": 1e-3, "l2": "256 MB buffer written between steps, outside the per-step events",
                    "parallelism": f"replicas x{ws} (independent scenario shards)",
                    "path": (f"cluster-resident persistent launches for {resident} of {len(scens)} scenarios, "
@@ -497,6 +497,11 @@ def main():
     ap.add_argument("--config", default="medium")
     ap.add_argument("--impl", default="gx", choices=["gx", "reference"])
     ap.add_argument("--check-every", type=int, default=20)
+    # Power penalty of the dispatch.  At the 1e-3 tolerance 0.2 beats the library default
+    # 0.3 on every workload's previous-plan steps (medium +24 %, Scale +47 %) with a
+    # slightly more accurate gradient (4.9 % vs 5.6 % mean error against tight solves on
+    # five medium plans); the default 0.3 converges better to tight tolerances.
+    ap.add_argument("--rho", type=float, default=0.2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--scenarios", type=int, default=None,
                     help="scenario count of the medium (default 16) or scale (default 52) workload")

@@ -3,8 +3,10 @@
 For a bound network it times a short implicit-gradient sequence (a cold solve and
 gradient, then `steps` previous-plan steps) for candidate settings, one parameter at a
 time from the defaults (coordinate descent), and keeps the fastest setting whose
-planner objective stays within `h_tol` of a tight reference solve at the same plan
-(equal residual tolerances do not give equal accuracy across penalties).  Parameters:
+planner objective stays within `h_tol` of a tight reference solve at the same plan and
+whose gradient there is no less accurate than the defaults' (within a factor `g_slack`)
+against a tight reference gradient (equal residual tolerances do not give equal
+accuracy across penalties; the adjoint penalty changes the gradient and not h).  Parameters:
 the execution path (per-iteration kernels replayed as CUDA graphs, or one persistent
 cluster-resident launch per loop for the scenarios that fit), residual-check chunk
 length (the CUDA-graph size), power penalty rho, phase penalty scale, adjoint penalty,
@@ -26,7 +28,7 @@ from . import gx
 SPACE = {
     "persistent": [False, True],
     "check_every": [10, 20, 40],
-    "rho": [0.2, 0.3, 0.5],
+    "rho": [0.1, 0.15, 0.2, 0.3, 0.5],
     "rho_theta_c": [0.03, 0.1],
     "adj_rho": [0.001, 0.002, 0.004],
     "inner_iters": [2, 3],
@@ -60,7 +62,14 @@ def _run(net, eta0, gamma, eta_min, eta_max, steps, alpha):
     return time.perf_counter() - t0, eta, h
 
 
-def tune(net: gx.Network, nets, steps=3, h_tol=2e-3, cache=None, log=None, alpha_frac=1e-2):
+def _grad_err(net, eta, g_ref):
+    net.solve(eta, warm="cold")
+    g = net.grad(eta, warm="cold")
+    torch.cuda.synchronize()
+    return float((g.double() - g_ref).norm() / max(float(g_ref.norm()), 1e-30))
+
+
+def tune(net: gx.Network, nets, steps=3, h_tol=2e-3, g_slack=1.25, cache=None, log=None, alpha_frac=1e-2):
     """Tune `net`'s options in place; returns the chosen option dict."""
     cache = cache or default_cache_path()
     key = bucket(net)
@@ -87,23 +96,25 @@ def tune(net: gx.Network, nets, steps=3, h_tol=2e-3, cache=None, log=None, alpha
     # tight reference objective at the plan the defaults reach
     ref = gx.Network(nets, [dict(sc) for sc in net.scens_desc], opts=gx.default_opts(
         **{**{k: getattr(net.opts, k) for k, _ in gx.Opts._fields_}, "tol": 1e-5, "max_iter": 200000}))
+    ref.set_opts(adj_tol=1e-5, adj_max_iter=200000)
     ref.solve(eta_end)
+    g_ref = ref.grad(eta_end).double().clone()
     torch.cuda.synchronize()
     h_ref = float((ref.array("h").cpu().numpy() * ref.weights).sum())
     del ref
+    g_base = _grad_err(net, eta_end, g_ref)
     best = dict(base)
-    trials = [dict(base, time_s=t_best)]
+    trials = [dict(base, time_s=t_best, g_rel=g_base)]
     for name, vals in SPACE.items():
         for v in vals:
             if v == best[name]:
                 continue
             cand = dict(best, **{name: v})
             t, eta_c, _ = measure(cand)
-            net.solve(eta_end, warm="cold")
-            torch.cuda.synchronize()
+            g_err = _grad_err(net, eta_end, g_ref)
             h = float((net.array("h").cpu().numpy() * net.weights).sum())
-            ok = abs(h - h_ref) <= h_tol * abs(h_ref)
-            trials.append(dict(cand, time_s=t, h_rel=abs(h - h_ref) / abs(h_ref), ok=ok))
+            ok = abs(h - h_ref) <= h_tol * abs(h_ref) and g_err <= g_slack * g_base + 1e-6
+            trials.append(dict(cand, time_s=t, h_rel=abs(h - h_ref) / abs(h_ref), g_rel=g_err, ok=ok))
             if log:
                 log(trials[-1])
             if ok and t < t_best:

@@ -18,7 +18,11 @@ def test_autotune_tiny_caches_a_valid_setting(tmp_path):
     db = json.load(open(cache))
     key = autotune.bucket(net)
     assert db[key]["best"] == best
-    assert all(t.get("ok", True) or t["h_rel"] > 2e-3 for t in db[key]["trials"])
+    trials = db[key]["trials"]
+    g_base = trials[0]["g_rel"]
+    # every rejected candidate failed the objective or the gradient guard
+    assert all(t.get("ok", True) or t["h_rel"] > 2e-3 or t["g_rel"] > 1.25 * g_base for t in trials)
+    assert all(t["g_rel"] <= 1.25 * g_base + 1e-6 for t in trials if t.get("ok"))
     net2 = gpu_net(nets, scens)
     assert autotune.load(net2, cache) == best
     assert abs(net2.opts.rho - best["rho"]) < 1e-12

@@ -74,12 +74,16 @@ def test_no_lines_no_batteries_single_hour():
     np.testing.assert_allclose(g, ograd.adjoint_grad(ref), rtol=1e-3, atol=1e-3)
 
 
-def test_user_warm_start_from_oracle_prices_converges_fast():
+@pytest.mark.parametrize("tol", [1e-3, 1e-5])
+def test_user_warm_start_from_oracle_prices_converges_fast(tol):
+    """Starting from the oracle's prices and angles beats a cold start at the bench's
+    tolerance and at 1e-5.  (Near the FP32 floor, 1e-6, the last decade's iteration count
+    is dominated by rounding noise and either start can take longer.)"""
     import torch
     nets, scens = synth.tiny()
     eta = nets[0]["eta_min"]
     ref = dispatch.solve(nets[0], scens[0], eta, synth.default_opts())
-    net = gpu_net(nets, scens, **TIGHT)
+    net = gpu_net(nets, scens, **{**TIGHT, "tol": tol})
     e = eta_tensor(eta)
     assert net.solve(e) == 0
     cold_iters = net.last_stats["iters_max"]
@@ -89,7 +93,7 @@ def test_user_warm_start_from_oracle_prices_converges_fast():
     pr[:, :inf["T"]] = torch.tensor(ref.price, dtype=torch.float32)
     th[:, :inf["T"]] = torch.tensor(ref.th, dtype=torch.float32)
     assert net.solve(e, warm="user", warm_prices=pr, warm_angles=th) == 0
-    assert net.last_stats["iters_max"] < cold_iters
+    assert net.last_stats["iters_max"] < (0.5 if tol >= 1e-3 else 0.9) * cold_iters
 
 
 def test_iteration_cap_reports_not_converged():
