@@ -25,6 +25,7 @@ import math
 import os
 import resource
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -64,7 +65,9 @@ class Clocks:
     def __init__(self, index=0):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        # raw samples: GX_BENCH_CLOCKS_DIR if set, else the system temporary directory
+        base = os.environ.get("GX_BENCH_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(base, f"clocks_bench_{os.getpid()}.csv")
 
     def start(self):
         try:
