@@ -865,9 +865,11 @@ __device__ __forceinline__ void gen_load4(const Ctx& c, const StatePtrs& X, cons
 }
 
 // RAMP: the batch has ramp-limited generators (whose injections are only summed here);
-// without them the flag test is compiled out.
+// without them the flag test is compiled out.  At most 128 registers, so four blocks fit
+// an SM: uncapped, the adjoint instance took 136, three blocks per SM, and a 16-scenario
+// medium grid (3.45 blocks per SM) ran part of its blocks as a second wave.
 template <int ADJ, int RAMP>
-__global__ void __launch_bounds__(kQBlock) k_bus4(const Ctx c, int want_res) {
+__global__ void __launch_bounds__(kQBlock, 4) k_bus4(const Ctx c, int want_res) {
     __shared__ __align__(16) int S[kPoolMax];
     const BusBlk bb = c.bus4_blk[blockIdx.x];
     if (c.done[bb.s]) return;  // block-uniform
