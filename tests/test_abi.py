@@ -87,11 +87,39 @@ def test_scaling_susceptance_validated_on_host(gx):
 def test_opts_validation(gx):
     o = gx.default_opts()
     assert o.eps > 0 and o.rho > 0 and o.inner_iters >= 1
+    assert o.adj_rho_theta_c == 0 and o.adj_rho_inner_c == 0  # 0: the forward's scales
     from paper_2410_13055_gb300 import synth
     nets, scens = synth.tiny()
     o.rho = -1.0
     with pytest.raises(gx.GxError):
         gx_create(gx, nets, scens, o)
+    o = gx.default_opts()
+    o.adj_rho_theta_c = -0.1
+    with pytest.raises(gx.GxError):
+        gx_create(gx, nets, scens, o)
+
+
+def test_state_ranges_on_host(gx):
+    """The forward and adjoint iteration states are two disjoint ranges of the workspace,
+    forward first, each holding at least the 16 state arrays' rows."""
+    from paper_2410_13055_gb300 import synth
+    nets, scens = synth.tiny()
+    h, K, nbytes = gx_create(gx, nets, scens)
+    off, nb = ctypes.c_size_t(), ctypes.c_size_t()
+    ranges = []
+    for which in (0, 1):
+        assert gx._lib.gx_network_state_range(h, which, ctypes.byref(off), ctypes.byref(nb)) == 0
+        ranges.append((off.value, nb.value))
+    (f0, fb), (a0, ab) = ranges
+    assert fb == ab and fb > 0 and f0 % 256 == 0 and a0 % 256 == 0
+    assert f0 + fb <= a0 and a0 + ab <= nbytes
+    n = nets[0]
+    N, L, G, B = int(n["n_bus"]), n["line_from"].size, n["gen_bus"].size, n["bat_bus"].size
+    Tp = (scens[0]["T"] + 3) // 4 * 4
+    rows = G + 4 * N + 4 * L + 7 * B  # generators; load, u, pbar, theta; line delta, sigma, q_f, q_t; battery
+    assert fb >= 4 * rows * Tp
+    assert gx._lib.gx_network_state_range(h, 2, ctypes.byref(off), ctypes.byref(nb)) == -1
+    gx._lib.gx_network_destroy(h)
 
 
 def gx_create(gx, nets, scens, opts=None):
