@@ -164,3 +164,27 @@ def gx_create(gx, nets, scens, opts=None):
     if rc != 0:
         raise gx.GxError(rc, "create")
     return h, gx._lib.gx_network_K(h), gx._lib.gx_network_device_bytes(h)
+
+
+def test_host_switches_validate_their_arguments(gx):
+    """Launch-mode switches and option changes on a created (unbound) network: valid
+    values are accepted, invalid ones return GX_ERR_INVALID_ARG, and the weighting of
+    the phase penalties is fixed at create."""
+    from paper_2410_13055_gb300 import synth
+    nets, scens = synth.tiny()
+    h, _, _ = gx_create(gx, nets, scens)
+    lib = gx._lib
+    for m in (0, 1, 2):
+        assert lib.gx_network_use_graphs(h, m) == 0
+    assert lib.gx_network_use_graphs(h, 3) == -1
+    assert lib.gx_network_use_persistent(h, 1) == 0 and lib.gx_network_use_persistent(h, 0) == 0
+    o = gx.default_opts()
+    o.adj_rho = 0.004
+    o.adj_rho_theta_c = 0.05
+    assert lib.gx_network_set_opts(h, ctypes.byref(o)) == 0
+    o.theta_weight = 1
+    assert lib.gx_network_set_opts(h, ctypes.byref(o)) == -1
+    o = gx.default_opts()
+    o.check_every = 0
+    assert lib.gx_network_set_opts(h, ctypes.byref(o)) == -1
+    lib.gx_network_destroy(h)
