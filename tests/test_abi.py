@@ -20,7 +20,8 @@ def gx():
 
 
 def declared_symbols():
-    txt = open(os.path.join(ROOT, "include", "gx.h")).read()
+    with open(os.path.join(ROOT, "include", "gx.h")) as f:
+        txt = f.read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
     return sorted(set(re.findall(r"\b(gx_[a-z_0-9]+)\s*\(", txt)))
 

@@ -66,10 +66,10 @@ def test_shards_balance_and_cover():
 @pytest.mark.timeout(300)
 def test_two_rank_gradient_allreduce_equals_full_batch():
     world, kappa = 2, 50.0
-    mgr = mp.Manager()
+    ctx = mp.get_context("spawn")  # the manager and the ranks alike: no fork of a threaded process
+    mgr = ctx.Manager()
     out = mgr.dict()
     port = _free_port()
-    ctx = mp.get_context("spawn")
     procs = [ctx.Process(target=_rank, args=(r, world, port, kappa, out)) for r in range(world)]
     for p in procs:
         p.start()
