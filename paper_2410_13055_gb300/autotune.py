@@ -62,6 +62,12 @@ def _run(net, eta0, gamma, eta_min, eta_max, steps, alpha):
     return time.perf_counter() - t0, eta, h
 
 
+def accept(h, h_ref, g_err, g_base, h_tol=2e-3, g_slack=1.25):
+    """The accuracy guard: the candidate's planner objective within h_tol of the tight
+    reference and its gradient error at most g_slack times the defaults'."""
+    return abs(h - h_ref) <= h_tol * abs(h_ref) and g_err <= g_slack * g_base + 1e-6
+
+
 def _grad_err(net, eta, g_ref):
     net.solve(eta, warm="cold")
     g = net.grad(eta, warm="cold")
@@ -113,7 +119,7 @@ def tune(net: gx.Network, nets, steps=3, h_tol=2e-3, g_slack=1.25, cache=None, l
             t, eta_c, _ = measure(cand)
             g_err = _grad_err(net, eta_end, g_ref)
             h = float((net.array("h").cpu().numpy() * net.weights).sum())
-            ok = abs(h - h_ref) <= h_tol * abs(h_ref) and g_err <= g_slack * g_base + 1e-6
+            ok = accept(h, h_ref, g_err, g_base, h_tol, g_slack)
             trials.append(dict(cand, time_s=t, h_rel=abs(h - h_ref) / abs(h_ref), g_rel=g_err, ok=ok))
             if log:
                 log(trials[-1])

@@ -47,3 +47,12 @@ def test_asset_classes_partition_the_plan():
     allix = np.concatenate(list(g.values()))
     assert np.array_equal(np.sort(allix), np.arange(nets[0]["K"]))
     assert g["gas"].size + g["solar"].size + g["wind"].size == nets[0]["gen_bus"].size
+
+
+def test_autotune_accuracy_guard():
+    from paper_2410_13055_gb300 import autotune
+    assert autotune.accept(100.1, 100.0, 0.03, 0.03)              # objective 1e-3 off, same gradient error
+    assert not autotune.accept(100.3, 100.0, 0.03, 0.03)          # objective 3e-3 off
+    assert autotune.accept(-100.1, -100.0, 0.0375, 0.03)          # gradient error at the 1.25x slack
+    assert not autotune.accept(100.0, 100.0, 0.04, 0.03)          # gradient error beyond the slack
+    assert autotune.accept(100.0, 100.0, 0.01, 0.03, g_slack=1.0)  # more accurate than the defaults
