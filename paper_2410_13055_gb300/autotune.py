@@ -23,7 +23,10 @@ import time
 import numpy as np
 import torch
 
-from . import gx
+from typing import TYPE_CHECKING
+
+if TYPE_CHECKING:  # the library is loaded by the functions that run it
+    from . import gx
 
 SPACE = {
     "persistent": [False, True],
@@ -100,6 +103,7 @@ def tune(net: gx.Network, nets, steps=3, h_tol=2e-3, g_slack=1.25, cache=None, l
 
     t_best, eta_end, _ = measure(base)
     # tight reference objective at the plan the defaults reach
+    from . import gx
     ref = gx.Network(nets, [dict(sc) for sc in net.scens_desc], opts=gx.default_opts(
         **{**{k: getattr(net.opts, k) for k, _ in gx.Opts._fields_}, "tol": 1e-5, "max_iter": 200000}))
     ref.set_opts(adj_tol=1e-5, adj_max_iter=200000)
