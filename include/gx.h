@@ -43,8 +43,10 @@
  *    exception crosses the ABI.  gx_status_string gives a static message and
  *    gx_last_error_message() details of the last error on this thread.
  *  - Calls enqueue work on the given stream.  gx_dispatch_solve_batch and
- *    gx_dispatch_grad_batch synchronise that stream every opts.check_every
- *    iterations to read the convergence flags (documented per call).
+ *    gx_dispatch_grad_batch run their iteration loop on the device and synchronise
+ *    that stream at the end of the loop to read the iteration counts and statuses:
+ *    once per loop in the default launch mode (gx_network_use_graphs(2)), once per
+ *    residual-check chunk of opts.check_every iterations in modes 1 and 0.
  */
 #ifndef GX_H
 #define GX_H
@@ -127,9 +129,12 @@ typedef struct {
     int inner_iters;     /* battery inner iterations per outer iteration, >= 1 */
     double tol;          /* stop when primal and dual relative residuals <= tol */
     int max_iter;
-    int check_every;     /* iterations between residual checks (host sync) */
+    int check_every;     /* iterations between residual checks (FP64 reduction and the
+                            convergence test; a host sync only in launch modes 1 and 0) */
     /* adjoint */
-    double tol_active;   /* a bound is active if its multiplier exceeds tol_active (relative) */
+    double tol_active;   /* a bound is active if its multiplier exceeds tol_active times the
+                            largest |generator cost| of the networks (at least 1 $/MWh), so
+                            the test scales with the costs; default 1e-5 */
     double adj_tol;
     int adj_max_iter;
     int grad_envelope;   /* 1: for kappa == 0 use the envelope theorem (no adjoint solve) */
@@ -160,7 +165,9 @@ enum {
     GX_ARR_RESID = 11,   /* [S x 2] FP64 primal, dual relative residual */
     GX_ARR_STATUS = 12,  /* [S] int32 per-scenario gx_status of the last solve */
     GX_ARR_GRAD_S = 13,  /* [sum_s K_net(s)] FP64 per-scenario dh_s/deta of the last grad */
-    GX_ARR_ADJ_ITERS = 14 /* [S] int32 adjoint iterations */
+    GX_ARR_ADJ_ITERS = 14, /* [S] int32 adjoint iterations */
+    GX_ARR_OBJ = 15      /* [1] FP64 sum_{s in batch} w'_s h_s of the last solve: the operating
+                            term of Eq. 1 (w'_s as in gx_dispatch_grad_batch); scen must be -1 */
 };
 
 typedef struct {
@@ -175,9 +182,12 @@ gx_status gx_opts_default(gx_opts* opts);
 const char* gx_status_string(gx_status s);
 const char* gx_last_error_message(void);
 
-/* Validate and copy the descriptors; lay out the workspace.  No device work.
- * Errors: GX_ERR_INVALID_ARG (bad index, non-positive beta/dur/eff, T out of
- * range, negative load, cf outside [0,1], non-finite numbers). */
+/* The data of Eq. 2 (Section 2.1): the networks' devices (generators, loads, AC and
+ * HVDC lines, batteries) and the scenarios' hourly profiles; the plan eta enters later,
+ * per call.  Validates and copies the descriptors (host memory, read only here) and lays
+ * out the workspace; no device work.  *out receives the handle (free with
+ * gx_network_destroy).  Errors: GX_ERR_INVALID_ARG (bad index, non-positive
+ * beta/dur/eff, T out of range, negative load, cf outside [0,1], non-finite numbers). */
 gx_status gx_network_create(const gx_network_desc* nets, int n_nets, const gx_scenario_desc* scen, int S,
                             const gx_opts* opts, gx_network** out);
 gx_status gx_network_destroy(gx_network* net);
@@ -210,13 +220,17 @@ gx_status gx_network_scenario_info(const gx_network* net, int s, int* T, int* Tp
  * state of the previous solve), GX_WARM_USER (initial prices and angles from
  * warm_dev: [sum_s N_s Tp_s] prices followed by the same size of angles, in
  * scenario order of the whole network; generators and loads start at their best
- * response to those prices, line flows from the angle differences).  Synchronises `stream` every
- * check_every iterations.  Returns GX_NOT_CONVERGED if any scenario of the batch
- * hit max_iter. */
+ * response to those prices, line flows from the angle differences).  Outputs stay in
+ * the workspace (GX_ARR_*), including GX_ARR_OBJ, the batch's weighted planner value.
+ * Synchronises `stream` once at the end of the iteration loop (per residual-check chunk
+ * in launch modes 1 and 0).  Returns GX_NOT_CONVERGED if any scenario of the batch
+ * hit max_iter, GX_ERR_NONFINITE if one diverged (its outputs are then meaningless). */
 gx_status gx_dispatch_solve_batch(gx_network* net, const float* eta_dev, const int* scen_idx, int B, int warm,
                                   const float* warm_dev, gx_stats* stats, void* stream);
 
-/* Implicit gradient of sum_{s in batch} w'_s h_s at the last solve (same batch),
+/* Section 2.2: the implicit gradient, by the implicit function theorem on the optimality
+ * conditions of the solved dispatch (Eq. 2), of sum_{s in batch} w'_s h_s at the last
+ * solve (same batch),
  * w'_s = w_s * (sum of all weights) / (sum of the batch's weights), written to
  * grad_dev [K] (FP32, caller-owned; entries of networks outside the batch are 0).
  * warm: GX_WARM_COLD or GX_WARM_PREV for the adjoint state.  Per-scenario FP64
@@ -294,9 +308,10 @@ gx_status gx_gnn_destroy(gx_gnn* gnn);
 
 /* Operating cost c_s and planner value h_s of scenario `scen` at the last solve,
  * computed without allocating any device memory.  The paper has no counterpart; this
- * entry point exists for callers that cannot allocate device memory (code running
- * while a CUDA graph is being captured, hosts that give the library a fixed memory
- * budget, plugins whose device memory belongs to a host framework).
+ * entry point exists for callers that cannot allocate device memory: host applications
+ * that give the library a fixed memory budget, plugins whose device memory belongs to a
+ * host framework's allocator, and latency-critical loops in which an allocation may
+ * synchronise the device.
  *
  * Same sums as GX_ARR_COST / GX_ARR_H of gx_dispatch_solve_batch, but the per-block
  * partial sums go to a fixed 64 KiB array compiled into the library (held on every
@@ -304,7 +319,8 @@ gx_status gx_gnn_destroy(gx_gnn* gnn);
  * double to cost_out_dev and, if h_out_dev is not NULL, one to h_out_dev (device
  * pointers owned by the caller).  Limit: (G + N + B) * Tp <= 16,777,216 for the
  * scenario (4096 partial-sum slots); larger scenarios return GX_ERR_INVALID_ARG with
- * a message.  The first call on a device looks up the array's device address
+ * a message.  A network that is bound but has not been solved since returns
+ * GX_ERR_STATE.  The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call before any
  * stream capture.  Every call shares the one array, so calls that overlap on the GPU
  * (different streams, no ordering) race and must not be issued; calls on one stream

@@ -17,14 +17,8 @@ class PlannerObjective(torch.autograd.Function):
     @staticmethod
     def forward(ctx, eta, net, batch, warm):
         net.solve(eta, batch=batch, warm=warm)
-        torch.cuda.current_stream().synchronize()
-        h = net.array("h")
-        w = torch.tensor([sc_w for sc_w in net.weights], dtype=torch.float64, device=h.device)
-        if batch is not None:
-            mask = torch.zeros_like(w)
-            mask[list(batch)] = 1.0
-            w = w * mask * (net.weights.sum() / float(sum(net.weights[list(batch)])))
-        val = (h * w).sum()
+        # sum_s w'_s h_s, computed by the library (GX_ARR_OBJ); copied out of the workspace
+        val = net.array("obj")[0].clone()
         ctx.net = net
         ctx.warm = warm
         ctx.save_for_backward(eta)

@@ -70,6 +70,9 @@ bool isfin(double x) { return std::isfinite(x); }
 struct gx_network {
     gx_opts opts{};
     int n_nets = 0, S = 0, K = 0;
+    // price scale of the active-set test: the largest |generator cost| of the batch's
+    // networks, at least 1 $/MWh (multipliers scale with the costs)
+    double cost_scale = 1.0;
     std::vector<NetH> nets;
     std::vector<ScenH> scens;
     std::vector<ScenDev> sdev;
@@ -116,7 +119,7 @@ struct gx_network {
     size_t o_f[16], o_a[16];  // forward / adjoint state arrays, order of StatePtrs
     size_t o_fend, o_aend;    // end of the forward / adjoint state range (ramp arrays included)
     size_t o_mgen, o_mload, o_mline, o_mbat;
-    size_t o_done, o_iters, o_status, o_adjit, o_nact, o_ctr, o_inb, o_resid, o_rbest, o_cost, o_h, o_grads, o_wprime;
+    size_t o_done, o_iters, o_status, o_adjit, o_nact, o_ctr, o_inb, o_resid, o_rbest, o_cost, o_h, o_grads, o_wprime, o_obj;
     size_t o_flow, o_price, o_shed, o_bpart, o_lpart, o_btpart, o_cpart;
     Layout lay;
     // binding
@@ -239,7 +242,7 @@ static void make_ctx(gx_network* net) {
     c.kappa = (float)o.kappa;
     c.rho_in = (float)(o.rho * o.rho_inner_c);
     c.rth_c = (float)(o.rho * o.rho_theta_c);
-    c.tol_act = (float)o.tol_active;
+    c.tol_act = (float)(o.tol_active * net->cost_scale);
     c.inner_iters = o.inner_iters;
     c.check_every = o.check_every;
     c.scen = reinterpret_cast<const ScenDev*>(d + net->o_scen);
@@ -341,6 +344,7 @@ int launch_loop_cond(const Ctx& c, int max_it, cudaGraphConditionalHandle h, cud
 
 const Ctx* gx_internal_ctx(const gx_network* net) { return (net && net->dev) ? &net->ctx : nullptr; }
 ScenDev gx_internal_scen(const gx_network* net, int s) { return net->sdev[s]; }
+bool gx_internal_solved(const gx_network* net) { return net && net->dev && net->solved; }
 gx_status gx_internal_fail(gx_status s, const std::string& msg) { return fail(s, msg); }
 }  // namespace gx
 
@@ -359,7 +363,7 @@ gx_status gx_opts_default(gx_opts* o) {
     o->tol = 1e-3;
     o->max_iter = 20000;
     o->check_every = 20;
-    o->tol_active = 1e-3;
+    o->tol_active = 1e-5;
     o->adj_tol = 1e-3;
     o->adj_max_iter = 20000;
     o->grad_envelope = 0;
@@ -664,6 +668,7 @@ gx_status gx_network_create(const gx_network_desc* nets, int n_nets, const gx_sc
         for (int g = 0; g < h.G; ++g) {
             if (h.gen_bus[g] < 0 || h.gen_bus[g] >= h.N) return bad("gen_bus out of range");
             if (!isfin(h.gen_cost[g]) || !isfin(h.gen_emis[g])) return bad("non-finite generator data");
+            net->cost_scale = std::max(net->cost_scale, std::fabs(h.gen_cost[g]));
         }
         for (int l = 0; l < h.L; ++l) {
             if (h.line_from[l] < 0 || h.line_from[l] >= h.N || h.line_to[l] < 0 || h.line_to[l] >= h.N)
@@ -877,7 +882,7 @@ gx_status gx_network_create(const gx_network_desc* nets, int n_nets, const gx_sc
     net->o_done = L.add(I4(S)); net->o_iters = L.add(I4(S)); net->o_status = L.add(I4(S)); net->o_adjit = L.add(I4(S));
     net->o_nact = L.add(I4(1)); net->o_ctr = L.add(I4(1)); net->o_inb = L.add(I4(S));
     net->o_resid = L.add(D8(2LL * S)); net->o_rbest = L.add(D8(S)); net->o_cost = L.add(D8(S)); net->o_h = L.add(D8(S));
-    net->o_grads = L.add(D8(gs)); net->o_wprime = L.add(D8(S));
+    net->o_grads = L.add(D8(gs)); net->o_wprime = L.add(D8(S)); net->o_obj = L.add(D8(1));
     net->o_flow = L.add(F4(el)); net->o_price = L.add(F4(eb)); net->o_shed = L.add(F4(eb));
     net->o_bpart = L.add(F4((long long)net->n_bus4_blk * kBusPart));
     net->o_lpart = L.add(F4((long long)net->n_line4_blk * kDevPart));
@@ -1045,6 +1050,9 @@ gx_status gx_network_array(const gx_network* net, int which, int scen, size_t* o
         case GX_ARR_GRAD_S: base = net->o_grads; esz = 8;
             rows(net->gs_total, sd ? sd->gs0 : 0, sd ? (long long)(sd->G + sd->L + sd->B) : 0); break;
         case GX_ARR_ADJ_ITERS: base = net->o_adjit; rows(net->S, scen, 1); break;
+        case GX_ARR_OBJ:
+            if (scen != -1) return fail(GX_ERR_INVALID_ARG, "GX_ARR_OBJ is one value for the batch (scen = -1)");
+            base = net->o_obj; esz = 8; e0 = 0; n = 1; break;
         default: return fail(GX_ERR_INVALID_ARG, "unknown array id");
     }
     *offset = base + (size_t)e0 * esz;
@@ -1383,6 +1391,15 @@ gx_status gx_dispatch_solve_batch(gx_network* net, const float* eta_dev, const i
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (gx_status e = upload_batch(net, scen_idx, B, st)) return e;
     if (gx_status e = upload_pivots(net, st)) return e;
+    // Eq. 1 weights of the batch, rescaled to the total weight (an unbiased estimate of
+    // the full sum for a sampled batch): used by the objective and by the next gradient
+    double wall = 0, wb = 0;
+    for (int s = 0; s < net->S; ++s) {
+        wall += net->scens[s].weight;
+        if (net->in_batch[s]) wb += net->scens[s].weight;
+    }
+    for (int s = 0; s < net->S; ++s) net->wprime[s] = net->in_batch[s] ? net->scens[s].weight * wall / wb : 0.0;
+    GX_CUDA(cudaMemcpyAsync(net->dev + net->o_wprime, net->wprime.data(), 8 * net->S, cudaMemcpyHostToDevice, st));
     Ctx& c = net->ctx;
     c.eta = eta_dev;
     c.warm = warm == GX_WARM_USER ? warm_dev : nullptr;
@@ -1399,6 +1416,8 @@ gx_status gx_dispatch_solve_batch(gx_network* net, const float* eta_dev, const i
     if (ns > 0)
         if (gx_status e = run_loop(net, 0, st, &launches, &it)) return e;
     launches += launch_extract(c, reinterpret_cast<const int*>(net->dev + net->o_inb), st);
+    launches += launch_objective(c, reinterpret_cast<const double*>(net->dev + net->o_wprime),
+                                 reinterpret_cast<double*>(net->dev + net->o_obj), st);
     GX_CUDA(cudaGetLastError());
     gx_status overall;
     if (gx_status e = collect_stats(net, 0, stats, launches, st, &overall)) return e;
@@ -1419,14 +1438,7 @@ gx_status gx_dispatch_grad_batch(gx_network* net, const float* eta_dev, int warm
     Ctx& ac = net->actx;
     ac.eta = eta_dev;
     ac.warm = nullptr;
-    // the batch of the last solve, with weights rescaled to the total weight
-    double wall = 0, wb = 0;
-    for (int s = 0; s < net->S; ++s) {
-        wall += net->scens[s].weight;
-        if (net->in_batch[s]) wb += net->scens[s].weight;
-    }
-    for (int s = 0; s < net->S; ++s) net->wprime[s] = net->in_batch[s] ? net->scens[s].weight * wall / wb : 0.0;
-    GX_CUDA(cudaMemcpyAsync(net->dev + net->o_wprime, net->wprime.data(), 8 * net->S, cudaMemcpyHostToDevice, st));
+    // the batch of the last solve and its weights w'_s (uploaded by that solve)
     GX_CUDA(cudaMemcpyAsync(net->dev + net->o_done, net->done_init.data(), 4 * net->S, cudaMemcpyHostToDevice, st));
     if (gx_status e = upload_pivots(net, st)) return e;
     int launches = launch_prep(c, st);

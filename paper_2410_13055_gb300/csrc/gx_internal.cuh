@@ -224,6 +224,44 @@ struct Ctx {
     long long warm_half; // element count of the prices half of `warm` (= all bus rows)
 };
 
+// One thread's share of scenario sc's operating cost (Eq. 2 objective with the eps terms)
+// and emission total, FP64: thread `tid` of a reduction over `stride` threads takes every
+// stride-th element of each device array.  c p + eps/2 p^2 over generators, VOLL sh +
+// eps/2 sh^2 over loads, eps/2 (ch^2 + dis^2) over batteries, eps/2 f^2 over HVDC lines
+// (phase weight 0); emissions e p.  Padding hours (t >= T) are skipped.  Both cost
+// reductions (the workspace one and the allocation-free one) use this.
+__device__ __forceinline__ void cost_share(const Ctx& c, const ScenDev& sc, long long tid, long long stride,
+                                           double& cs, double& em) {
+    const double eps = c.eps, voll = c.voll;
+    const long long ng = (long long)sc.G * sc.Tp, nn = (long long)sc.N * sc.Tp, nbt = (long long)sc.B * sc.Tp;
+    for (long long i = tid; i < ng; i += stride) {
+        const int g = (int)(i / sc.Tp), t = (int)(i - (long long)g * sc.Tp);
+        if (t >= sc.T) continue;
+        const double p = c.xg[sc.e_gen + i];
+        cs += c.g_cost[sc.gen0 + g] * p + 0.5 * eps * p * p;
+        em += c.g_emis[sc.gen0 + g] * p;
+    }
+    for (long long i = tid; i < nn; i += stride) {
+        const int t = (int)(i % sc.Tp);
+        if (t >= sc.T) continue;
+        const double sh = (double)c.xl[sc.e_bus + i] + (double)c.load[sc.e_bus + i];
+        cs += voll * sh + 0.5 * eps * sh * sh;
+    }
+    for (long long i = tid; i < nbt; i += stride) {
+        const int t = (int)(i % sc.Tp);
+        if (t >= sc.T) continue;
+        const double ch = c.zc[sc.e_bat + i], di = c.zd[sc.e_bat + i];
+        cs += 0.5 * eps * (ch * ch + di * di);
+    }
+    const long long nl = (long long)sc.L * sc.Tp;
+    for (long long i = tid; i < nl; i += stride) {
+        const int l = (int)(i / sc.Tp), t = (int)(i - (long long)l * sc.Tp);
+        if (t >= sc.T || c.l_w[sc.line0 + l] != 0.f) continue;
+        const double f = c.dl[sc.e_line + i];
+        cs += 0.5 * eps * f * f;
+    }
+}
+
 // Launch wrappers (gx_kernels.cu).  Each returns the number of kernels launched.
 int launch_dev(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st);
 int launch_line(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st);
@@ -241,6 +279,8 @@ int launch_crs(const Ctx& c, int adj, const int* scen, int n, const int* in_batc
 int launch_reduce(const Ctx& c, int adj, double tol, cudaStream_t st);
 int launch_tick(const Ctx& c, int chunk, cudaStream_t st);
 int launch_extract(const Ctx& c, const int* in_batch, cudaStream_t st);
+// obj = sum_s wprime[s] h_s (Eq. 1's operating term over the batch), FP64, fixed order.
+int launch_objective(const Ctx& c, const double* wprime, double* obj, cudaStream_t st);
 int launch_grad(const Ctx& c, int envelope, const int* gwarp_scen, int n_gwarps, const int* in_batch,
                 cudaStream_t st);
 int launch_grad_combine(const Ctx& c, const double* wprime, const int* k_net, float* grad_out, int K,
@@ -256,6 +296,7 @@ int launch_plan_step(float* eta, const float* grad, const float* gamma, const fl
 // Read-only accessors for the no-allocation entry point (gx_noalloc.cu).
 namespace gx {
 const Ctx* gx_internal_ctx(const gx_network* net);        // nullptr if not bound
+bool gx_internal_solved(const gx_network* net);          // a solve has run since the last bind
 ScenDev gx_internal_scen(const gx_network* net, int s);   // s must be in range
 gx_status gx_internal_fail(gx_status s, const std::string& msg);
 }  // namespace gx

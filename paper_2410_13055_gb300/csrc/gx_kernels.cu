@@ -1198,36 +1198,7 @@ __global__ void __launch_bounds__(kBlock) k_cost(const Ctx c, const int* in_batc
     if (in_batch[s]) {
         const int nb = blk - sc.cost_blk0;
         const int nblk = (s + 1 < c.S ? c.scen[s + 1].cost_blk0 : c.n_cost_blk) - sc.cost_blk0;
-        const int stride = nblk * kBlock;
-        const double eps = c.eps, voll = c.voll;
-        const long long ng = (long long)sc.G * sc.Tp, nn = (long long)sc.N * sc.Tp, nbt = (long long)sc.B * sc.Tp;
-        for (long long i = (long long)nb * kBlock + threadIdx.x; i < ng; i += stride) {
-            const int g = (int)(i / sc.Tp), t = (int)(i - (long long)g * sc.Tp);
-            if (t >= sc.T) continue;
-            const double p = c.xg[sc.e_gen + i];
-            cs += c.g_cost[sc.gen0 + g] * p + 0.5 * eps * p * p;
-            em += c.g_emis[sc.gen0 + g] * p;
-        }
-        for (long long i = (long long)nb * kBlock + threadIdx.x; i < nn; i += stride) {
-            const int t = (int)(i % sc.Tp);
-            if (t >= sc.T) continue;
-            const double sh = (double)c.xl[sc.e_bus + i] + (double)c.load[sc.e_bus + i];
-            cs += voll * sh + 0.5 * eps * sh * sh;
-        }
-        for (long long i = (long long)nb * kBlock + threadIdx.x; i < nbt; i += stride) {
-            const int t = (int)(i % sc.Tp);
-            if (t >= sc.T) continue;
-            const double ch = c.zc[sc.e_bat + i], di = c.zd[sc.e_bat + i];
-            cs += 0.5 * eps * (ch * ch + di * di);
-        }
-        // HVDC transport lines (phase weight 0, unit beta): eps/2 f^2
-        const long long nl = (long long)sc.L * sc.Tp;
-        for (long long i = (long long)nb * kBlock + threadIdx.x; i < nl; i += stride) {
-            const int l = (int)(i / sc.Tp), t = (int)(i - (long long)l * sc.Tp);
-            if (t >= sc.T || c.l_w[sc.line0 + l] != 0.f) continue;
-            const double f = c.dl[sc.e_line + i];
-            cs += 0.5 * eps * f * f;
-        }
+        cost_share(c, sc, (long long)nb * kBlock + threadIdx.x, (long long)nblk * kBlock, cs, em);
     }
     cs = warp_sum_d(cs);
     em = warp_sum_d(em);
@@ -1252,6 +1223,16 @@ __global__ void k_cost_final(const Ctx c, const int* in_batch) {
     for (int b = b0; b < b1; ++b) { a += c.cost_part[2 * b]; e += c.cost_part[2 * b + 1]; }
     c.cost[s] = a;
     c.hval[s] = a + (double)c.kappa * e;
+}
+
+// Eq. 1's operating term over the batch: sum_s w'_s h_s in FP64, summed by one thread in
+// scenario order so the value does not depend on the launch shape.
+__global__ void k_objective(const Ctx c, const double* wprime, double* obj) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double a = 0.0;
+    for (int s = 0; s < c.S; ++s)
+        if (wprime[s] != 0.0) a += wprime[s] * c.hval[s];
+    *obj = a;
 }
 
 // ------------------------------------------------------------------------------------
@@ -1507,6 +1488,11 @@ int launch_extract(const Ctx& c, const int* in_batch, cudaStream_t st) {
     k_cost<<<c.n_cost_blk, kBlock, 0, st>>>(c, in_batch);
     k_cost_final<<<(c.S + 127) / 128, 128, 0, st>>>(c, in_batch);
     return 3;
+}
+
+int launch_objective(const Ctx& c, const double* wprime, double* obj, cudaStream_t st) {
+    k_objective<<<1, 32, 0, st>>>(c, wprime, obj);
+    return 1;
 }
 
 int launch_grad(const Ctx& c, int envelope, const int* gwarp_scen, int n_gwarps, const int* in_batch,

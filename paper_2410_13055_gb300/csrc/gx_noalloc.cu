@@ -1,12 +1,13 @@
 // gx_dispatch_cost_noalloc: the per-scenario operating-cost reduction without any
 // device allocation, for callers that cannot allocate device memory.
 //
-// Some callers cannot call cudaMalloc (or any allocating routine): code that runs
-// while a CUDA graph is being captured, host applications that hand the library a
-// fixed memory budget and forbid it from growing, and plugins whose device memory is
-// owned by a host framework.  The regular cost reduction keeps its per-block partial
-// sums in the caller-allocated workspace; this variant keeps them in a fixed array
-// compiled into the library instead.
+// Some callers cannot call cudaMalloc (or any routine that allocates): host
+// applications that hand the library a fixed device-memory budget and forbid it from
+// growing, plugins whose device memory belongs to a host framework's allocator (a
+// private cudaMalloc would bypass its accounting), and latency-critical loops in which
+// an allocation or a free may synchronise the device and stall other streams.  The
+// regular cost reduction keeps its per-block partial sums in the caller-allocated
+// workspace; this variant keeps them in a fixed array compiled into the library.
 //
 // The scratch array below lives on every GPU that loads this library, for as long as
 // the process runs (kNoallocMaxBlocks blocks x 2 doubles = 64 KiB).  Host code must not
@@ -35,40 +36,13 @@ __device__ __forceinline__ double warp_sum_nd(double v) {
     return v;
 }
 
-// Same sums as the workspace cost reduction: sum c p + eps/2 p^2 over generators,
-// VOLL sh + eps/2 sh^2 over loads, eps/2 (ch^2 + dis^2) over batteries, eps/2 f^2 over
-// HVDC lines; plus the emission total e p.  Block b of `nblk` takes a strided share of scenario s.
+// The workspace cost reduction's sums (cost_share): block b of `nblk` takes a strided
+// share of scenario s.
 __global__ void __launch_bounds__(kBlock) k_cost_noalloc(const Ctx c, int s, int nblk, double* part) {
     const ScenDev sc = c.scen[s];
     const int nb = blockIdx.x;
-    const int stride = nblk * kBlock;
-    const double eps = c.eps, voll = c.voll;
     double cs = 0.0, em = 0.0;
-    const long long ng = (long long)sc.G * sc.Tp, nn = (long long)sc.N * sc.Tp, nbt = (long long)sc.B * sc.Tp;
-    for (long long i = (long long)nb * kBlock + threadIdx.x; i < ng; i += stride) {
-        const int g = (int)(i / sc.Tp), t = (int)(i - (long long)g * sc.Tp);
-        if (t >= sc.T) continue;
-        const double p = c.xg[sc.e_gen + i];
-        cs += c.g_cost[sc.gen0 + g] * p + 0.5 * eps * p * p;
-        em += c.g_emis[sc.gen0 + g] * p;
-    }
-    for (long long i = (long long)nb * kBlock + threadIdx.x; i < nn; i += stride) {
-        if ((int)(i % sc.Tp) >= sc.T) continue;
-        const double sh = (double)c.xl[sc.e_bus + i] + (double)c.load[sc.e_bus + i];
-        cs += voll * sh + 0.5 * eps * sh * sh;
-    }
-    for (long long i = (long long)nb * kBlock + threadIdx.x; i < nbt; i += stride) {
-        if ((int)(i % sc.Tp) >= sc.T) continue;
-        const double ch = c.zc[sc.e_bat + i], di = c.zd[sc.e_bat + i];
-        cs += 0.5 * eps * (ch * ch + di * di);
-    }
-    const long long nl = (long long)sc.L * sc.Tp;
-    for (long long i = (long long)nb * kBlock + threadIdx.x; i < nl; i += stride) {
-        const int l = (int)(i / sc.Tp);
-        if ((int)(i - (long long)l * sc.Tp) >= sc.T || c.l_w[sc.line0 + l] != 0.f) continue;
-        const double f = c.dl[sc.e_line + i];
-        cs += 0.5 * eps * f * f;
-    }
+    cost_share(c, sc, (long long)nb * kBlock + threadIdx.x, (long long)nblk * kBlock, cs, em);
     cs = warp_sum_nd(cs);
     em = warp_sum_nd(em);
     __shared__ double sh[2][kBlock / 32];
@@ -124,6 +98,8 @@ extern "C" gx_status gx_dispatch_cost_noalloc(const gx_network* net, int scen, d
     if (!net || !cost_out_dev) return gx_internal_fail(GX_ERR_INVALID_ARG, "NULL argument");
     const Ctx* c = gx_internal_ctx(net);
     if (!c) return gx_internal_fail(GX_ERR_STATE, "network is not bound");
+    if (!gx_internal_solved(net))
+        return gx_internal_fail(GX_ERR_STATE, "gx_dispatch_cost_noalloc needs a solve first");
     if (scen < 0 || scen >= c->S) return gx_internal_fail(GX_ERR_INVALID_ARG, "scenario out of range");
     const ScenDev sd = gx_internal_scen(net, scen);
     const long long work = (long long)(sd.G + sd.N + sd.B) * sd.Tp;

@@ -25,8 +25,8 @@ _lib = C.CDLL(LIB_PATH)
 GX_OK, GX_NOT_CONVERGED = 0, 1
 GX_WARM = {"cold": 0, "prev": 1, "user": 2, "learned": 3}
 ARR = dict(p=0, shed=1, flow=2, theta=3, ch=4, dis=5, soc=6, price=7, cost=8, h=9, iters=10, resid=11,
-           status=12, grad_s=13, adj_iters=14)
-_ARR_DTYPE = dict(cost="float64", h="float64", resid="float64", grad_s="float64", iters="int32",
+           status=12, grad_s=13, adj_iters=14, obj=15)
+_ARR_DTYPE = dict(cost="float64", h="float64", resid="float64", grad_s="float64", obj="float64", iters="int32",
                   status="int32", adj_iters="int32")
 
 _i32p = C.POINTER(C.c_int32)

@@ -78,24 +78,26 @@ def test_tiny_plan_trajectory_matches_golden():
 
 
 def test_medium_slice_parity():
-    """100-bus network, one scenario, 24 hours: dispatch, prices and the adjoint gradient."""
+    """100-bus network, one scenario, 24 hours: dispatch, prices and the adjoint gradient.
+
+    The gradient is held to the 1e-3 of the tolerance table on the whole vector and on every
+    entry (relative to the largest).  The adjoint runs to a 3e-6 residual: at the table's
+    parity setting of 1e-5 the FP32 message passing leaves entries at up to 7e-4 of the
+    largest, too close to the bound to be a stable test; at 3e-6 they fall below 1e-4."""
     nets, scens = synth.medium(S=1)
     nets, scens = synth.slice_hours(nets, scens, 0, 24)
     eta = nets[0]["eta_min"]
     # tight solves use the smaller phase penalty (faster to 1e-6; the default is tuned for 1e-3)
-    net, e, rc, refs = _solve_pair(nets, scens, eta, kappa=50.0, tol=1e-6, adj_tol=1e-5, rho_theta_c=0.01)
+    net, e, rc, refs = _solve_pair(nets, scens, eta, kappa=50.0, tol=1e-6, adj_tol=3e-6, rho_theta_c=0.01,
+                                   adj_max_iter=400000)
     ref = refs[0]
     g = solution(net, 0, ref_groups(ref.qp))
     assert abs(g["cost"] - ref.cost) / ref.cost <= 1e-4
     res = kkt.residuals(ref.qp, pack_x(ref.qp, g), g["price"], act_tol=ACT_TOL)
     assert res["primal"] <= 1e-3 and res["dual"] <= 1e-3, res
     gg = net.grad(e).double().cpu().numpy()
+    assert net.last_grad_status == 0, net.last_grad_stats
     g_ref = ograd.adjoint_grad(ref)
-    # One generator of this slice sits at a nearly degenerate active set (bounds with
-    # multipliers ~0.1 $/MWh in two hours) where the derivative is barely unique; it
-    # carries most of the vector error (1.3e-3); a few other entries land at 1.0-1.5e-3 of
-    # the largest entry.  98% of the entries are held to 1e-3 of the largest entry and
-    # the whole vector to 2e-3.
     err = np.abs(gg - g_ref) / np.max(np.abs(g_ref))
-    assert np.mean(err <= 1e-3) >= 0.98, np.sort(err)[-8:]
-    assert rel(gg, g_ref) <= 2e-3, (net.last_grad_stats, rel(gg, g_ref))
+    assert np.all(err <= 1e-3), np.sort(err)[-8:]
+    assert rel(gg, g_ref) <= 1e-3, (net.last_grad_stats, rel(gg, g_ref))
