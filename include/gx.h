@@ -264,17 +264,25 @@ gx_status gx_network_use_persistent(gx_network* net, int on);
  * per-iteration kernels (not resident, not launchable on this device, or switched off). */
 gx_status gx_network_persistent_info(const gx_network* net, int scen, int* cluster_ctas);
 
-/* Sampled kernel timing.  While enabled, the solve and gradient loops record CUDA
- * events on their stream around the bus, line and battery kernels of the last
- * iteration of every residual-check chunk and accumulate the elapsed times at the
- * chunk's synchronisation, and around each call's cluster-resident launches.  Kinds:
- * 0 = bus kernel, 1 = line kernel, 2 = battery kernel, 3 = cluster-resident launches
- * (all of them timed).  Enabling resets the counters.  Uses four CUDA events (created
- * here, no device memory); timing synchronises the stream after resident launches. */
+/* Sampled kernel timing (the network must be bound).  While enabled, the last iteration of
+ * every residual-check chunk stamps, per kernel kind, its earliest block start and latest
+ * block end with the device's global nanosecond timer (%globaltimer) inside the kernels,
+ * so the times are those of the launch mode in use (the whole-loop graph included), with
+ * no events between the kernels; the host reads them at the end of each loop.  Cluster-
+ * resident launches are timed with CUDA events around them.  Kinds: 0 = bus kernel,
+ * 1 = line kernel, 2 = battery (and ramp) kernels, 3 = cluster-resident launches.  The
+ * line and battery kernels run side by side in the graph modes, so kinds 1 and 2 overlap.
+ * Enabling resets the counters; switching timing on or off drops the cached graphs, whose
+ * kernels carry the timing pointers.  Uses four CUDA events and workspace memory, no
+ * device allocation. */
 gx_status gx_profile_enable(gx_network* net, int on);
-/* Arrays of 4.  ms[k]: summed event time of the sampled launches of kind k; samples[k]:
- * how many were sampled; launches[k]: all launches of kind k since enabling. */
+/* Arrays of 4.  ms[k]: summed time of the sampled launches of kind k; samples[k]: how many
+ * were sampled; launches[k]: all launches of kind k since enabling. */
 gx_status gx_profile_read(const gx_network* net, double* ms, long long* samples, long long* launches);
+/* counts [S]: for each scenario, how many of the sampled iterations (kinds 0-2) it was
+ * still iterating in, since timing was enabled.  A converged scenario's blocks exit at
+ * once, so a sampled launch only does the work of the scenarios counted here. */
+gx_status gx_profile_active(const gx_network* net, long long* counts);
 
 /* ------------------------------------------------------------------------------
  * Learned warm start (not in the paper): a 3-layer message-passing network over the

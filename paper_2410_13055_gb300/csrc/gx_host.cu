@@ -119,7 +119,7 @@ struct gx_network {
     size_t o_f[16], o_a[16];  // forward / adjoint state arrays, order of StatePtrs
     size_t o_fend, o_aend;    // end of the forward / adjoint state range (ramp arrays included)
     size_t o_mgen, o_mload, o_mline, o_mbat;
-    size_t o_done, o_iters, o_status, o_adjit, o_nact, o_ctr, o_inb, o_resid, o_rbest, o_cost, o_h, o_grads, o_wprime, o_obj;
+    size_t o_done, o_iters, o_status, o_adjit, o_nact, o_ctr, o_inb, o_resid, o_rbest, o_cost, o_h, o_grads, o_wprime, o_obj, o_stlo, o_sthi, o_pact;
     size_t o_flow, o_price, o_shed, o_bpart, o_lpart, o_btpart, o_cpart;
     Layout lay;
     // binding
@@ -132,7 +132,7 @@ struct gx_network {
     // CUDA graphs of one residual-check chunk, keyed by what their captured parameters depend on
     struct ChunkGraph {
         bool valid = false;
-        int adj = 0, chunk = 0, prof = 0, loop = 0;  // loop: the whole loop (conditional WHILE node)
+        int adj = 0, chunk = 0, loop = 0;  // loop: the whole loop (conditional WHILE node)
         const float* eta = nullptr;
         cudaGraphExec_t exec = nullptr;
     } graphs[4];
@@ -312,6 +312,9 @@ static void make_ctx(gx_network* net) {
     c.warm = nullptr;
     c.warm_half = net->bus_el;
     c.eta = nullptr;
+    c.stamp_lo = net->prof ? reinterpret_cast<unsigned long long*>(d + net->o_stlo) : nullptr;
+    c.stamp_hi = net->prof ? reinterpret_cast<unsigned long long*>(d + net->o_sthi) : nullptr;
+    c.prof_act = net->prof ? reinterpret_cast<long long*>(d + net->o_pact) : nullptr;
     // the adjoint iteration: same arrays, its own penalties and battery pivots
     Ctx& a = net->actx;
     a = c;
@@ -883,6 +886,7 @@ gx_status gx_network_create(const gx_network_desc* nets, int n_nets, const gx_sc
     net->o_nact = L.add(I4(1)); net->o_ctr = L.add(I4(1)); net->o_inb = L.add(I4(S));
     net->o_resid = L.add(D8(2LL * S)); net->o_rbest = L.add(D8(S)); net->o_cost = L.add(D8(S)); net->o_h = L.add(D8(S));
     net->o_grads = L.add(D8(gs)); net->o_wprime = L.add(D8(S)); net->o_obj = L.add(D8(1));
+    net->o_stlo = L.add(D8(3LL * kStampSlots)); net->o_sthi = L.add(D8(3LL * kStampSlots)); net->o_pact = L.add(D8(S));
     net->o_flow = L.add(F4(el)); net->o_price = L.add(F4(eb)); net->o_shed = L.add(F4(eb));
     net->o_bpart = L.add(F4((long long)net->n_bus4_blk * kBusPart));
     net->o_lpart = L.add(F4((long long)net->n_line4_blk * kDevPart));
@@ -1074,12 +1078,12 @@ gx_status gx_network_scenario_info(const gx_network* net, int s, int* T, int* Tp
     return GX_OK;
 }
 
-// Part of one residual-check chunk: iterations [j0, j1) of `chunk` (residual partials on
-// the chunk's last iteration), optionally preceded by the counter tick and followed by the
-// per-scenario reduction and the copy of the active count to the host.  With `prof` the
-// chunk's last iteration is bracketed by timing events (eager launches only).
+// Part of one residual-check chunk: iterations [j0, j1) of `chunk` (residual partials, and
+// the kernels' time stamps while timing is on, on the chunk's last iteration), optionally
+// preceded by the counter tick and followed by the per-scenario reduction and the copy of
+// the active count to the host.
 static gx_status enqueue_iters(gx_network* net, const Ctx& c, int adj, int chunk, int j0, int j1, bool tick,
-                               bool reduce, bool prof, cudaStream_t st, int* launches, bool to_host = true) {
+                               bool reduce, cudaStream_t st, int* launches, bool to_host = true) {
     const int mode = adj ? M_ADJ : M_FWD;
     const double tol = adj ? net->opts.adj_tol : net->opts.tol;
     if (tick) *launches += launch_tick(c, chunk, st);
@@ -1088,7 +1092,6 @@ static gx_status enqueue_iters(gx_network* net, const Ctx& c, int adj, int chunk
     const bool fork = (st == net->cap_stream) && (c.n_bat_warps > 0 || c.n_ramp_warps > 0) && c.n_line_blk > 0;
     for (int j = j0; j < j1; ++j) {
         const int want = j == chunk - 1;
-        const bool samp = prof && want;
         int nl = 0, nb = 0;
         if (fork) {
             GX_CUDA(cudaEventRecord(net->ev_fork, st));
@@ -1099,15 +1102,11 @@ static gx_status enqueue_iters(gx_network* net, const Ctx& c, int adj, int chunk
             nl = launch_line(c, mode, adj, want, st);
             GX_CUDA(cudaStreamWaitEvent(st, net->ev_join, 0));
         } else {
-            if (samp) GX_CUDA(cudaEventRecord(net->ev[0], st));
             nl = launch_line(c, mode, adj, want, st);
-            if (samp) GX_CUDA(cudaEventRecord(net->ev[1], st));
             nb = launch_bat(c, mode, adj, want, st);
             nb += launch_ramp(c, mode, adj, want, st);
-            if (samp) GX_CUDA(cudaEventRecord(net->ev[2], st));
         }
         const int nu = launch_bus(c, mode, adj, want, st);
-        if (samp) GX_CUDA(cudaEventRecord(net->ev[3], st));
         *launches += nl + nb + nu;
     }
     if (reduce) {
@@ -1118,12 +1117,12 @@ static gx_status enqueue_iters(gx_network* net, const Ctx& c, int adj, int chunk
     return GX_OK;
 }
 
-// The instantiated graph of a chunk (all of it, or all but its last iteration when the
-// kernels are being timed), captured on the library's own stream (capture is not allowed
-// on the legacy default stream).  Cached by everything its parameters depend on.
-static gx_status chunk_graph(gx_network* net, const Ctx& c, int adj, int chunk, bool prof, cudaGraphExec_t* out) {
+// The instantiated graph of a chunk (tick, iterations, reduction and the copy of the active
+// count), captured on the library's own stream (capture is not allowed on the legacy
+// default stream).  Cached by everything its parameters depend on.
+static gx_status chunk_graph(gx_network* net, const Ctx& c, int adj, int chunk, cudaGraphExec_t* out) {
     for (auto& g : net->graphs)
-        if (g.valid && !g.loop && g.adj == adj && g.chunk == chunk && g.prof == (int)prof && g.eta == c.eta) {
+        if (g.valid && !g.loop && g.adj == adj && g.chunk == chunk && g.eta == c.eta) {
             *out = g.exec;
             return GX_OK;
         }
@@ -1134,8 +1133,7 @@ static gx_status chunk_graph(gx_network* net, const Ctx& c, int adj, int chunk, 
     cudaGraph_t graph = nullptr;
     int dummy = 0;
     GX_CUDA(cudaStreamBeginCapture(net->cap_stream, cudaStreamCaptureModeThreadLocal));
-    gx_status e = prof ? enqueue_iters(net, c, adj, chunk, 0, chunk - 1, true, false, false, net->cap_stream, &dummy)
-                       : enqueue_iters(net, c, adj, chunk, 0, chunk, true, true, false, net->cap_stream, &dummy);
+    gx_status e = enqueue_iters(net, c, adj, chunk, 0, chunk, true, true, net->cap_stream, &dummy);
     cudaError_t ce = cudaStreamEndCapture(net->cap_stream, &graph);
     if (e) return e;
     if (ce != cudaSuccess) return fail(GX_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(ce));
@@ -1143,7 +1141,7 @@ static gx_status chunk_graph(gx_network* net, const Ctx& c, int adj, int chunk, 
     cudaGraphDestroy(graph);
     if (ce != cudaSuccess) return fail(GX_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ce));
     g.valid = true;
-    g.adj = adj; g.chunk = chunk; g.prof = prof; g.eta = c.eta;
+    g.adj = adj; g.chunk = chunk; g.eta = c.eta;
     *out = g.exec;
     return GX_OK;
 }
@@ -1183,7 +1181,7 @@ static gx_status loop_graph(gx_network* net, const Ctx& c, int adj, int every, i
     ce = cudaStreamBeginCaptureToGraph(net->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (ce != cudaSuccess) return bail(ce, "cudaStreamBeginCaptureToGraph");
     int dummy = 0;
-    gx_status e = enqueue_iters(net, c, adj, every, 0, every, true, true, false, net->cap_stream, &dummy, false);
+    gx_status e = enqueue_iters(net, c, adj, every, 0, every, true, true, net->cap_stream, &dummy, false);
     if (!e) launch_loop_cond(c, max_it, h, net->cap_stream);
     cudaGraph_t captured = nullptr;
     ce = cudaStreamEndCapture(net->cap_stream, &captured);
@@ -1256,15 +1254,16 @@ static gx_status run_crs(gx_network* net, int adj, cudaStream_t st, int* launche
 // scenarios still iterating.  While kernels are being timed, a chunk's last iteration
 // and its reduction run as eager launches bracketed by events (event times cannot be read
 // from graph-recorded events).
+static gx_status read_stamps(gx_network* net, int nchunks, cudaStream_t st);
+
 static gx_status run_loop(gx_network* net, int adj, cudaStream_t st, int* launches, int* iters_out) {
     const Ctx& c = adj ? net->actx : net->ctx;
     const int max_it = adj ? net->opts.adj_max_iter : net->opts.max_iter;
     const int every = net->opts.check_every;
-    const bool prof = net->prof;
     const int per_it = (c.n_line_blk > 0) + (c.n_bat_warps > 0) + (c.n_ramp_warps > 0) + (c.n_bus_blk > 0);
     int it = 0;
     GX_CUDA(cudaMemsetAsync(c.iter_ctr, 0, sizeof(int), st));
-    if (net->use_graphs == 2 && !prof && max_it % every == 0) {
+    if (net->use_graphs == 2 && max_it % every == 0) {
         cudaGraphExec_t exec = nullptr;
         if (gx_status e = loop_graph(net, c, adj, every, max_it, &exec)) return e;
         GX_CUDA(cudaGraphLaunch(exec, st));
@@ -1275,47 +1274,65 @@ static gx_status run_loop(gx_network* net, int adj, cudaStream_t st, int* launch
         // per body: tick, the iterations, the reduction and the condition kernel
         *launches += (it / every) * (3 + every * per_it);
         *iters_out = it;
+        if (net->prof) {
+            net->prof_launches[0] += (long long)it * (c.n_bus_blk > 0);
+            net->prof_launches[1] += (long long)it * (c.n_line_blk > 0);
+            net->prof_launches[2] += (long long)it * (c.n_bat_warps > 0 || c.n_ramp_warps > 0);
+            return read_stamps(net, it / every, st);
+        }
         return GX_OK;
     }
+    int nch = 0;
     while (it < max_it) {
         const int chunk = std::min(every, max_it - it);
         int nk = 0;
-        if (net->use_graphs && chunk == every && (!prof || chunk > 1)) {
+        if (net->use_graphs && chunk == every) {
             cudaGraphExec_t exec = nullptr;
-            if (gx_status e = chunk_graph(net, c, adj, chunk, prof, &exec)) return e;
+            if (gx_status e = chunk_graph(net, c, adj, chunk, &exec)) return e;
             GX_CUDA(cudaGraphLaunch(exec, st));
-            if (prof) {
-                nk = 1 + (chunk - 1) * per_it;
-                if (gx_status e = enqueue_iters(net, c, adj, chunk, chunk - 1, chunk, false, true, true, st, &nk))
-                    return e;
-            } else {
-                nk = 2 + chunk * per_it;
-            }
+            nk = 2 + chunk * per_it;
         } else {
-            if (gx_status e = enqueue_iters(net, c, adj, chunk, 0, chunk, true, true, prof, st, &nk)) return e;
+            if (gx_status e = enqueue_iters(net, c, adj, chunk, 0, chunk, true, true, st, &nk)) return e;
         }
         *launches += nk;
-        if (prof) {
-            net->prof_launches[0] += chunk * (c.n_bus_blk > 0);
-            net->prof_launches[1] += chunk * (c.n_line_blk > 0);
-            net->prof_launches[2] += chunk * (c.n_bat_warps > 0);
-            net->prof_samples[0] += (c.n_bus_blk > 0);
-            net->prof_samples[1] += (c.n_line_blk > 0);
-            net->prof_samples[2] += (c.n_bat_warps > 0);
-        }
         it += chunk;
+        ++nch;
         GX_CUDA(cudaGetLastError());
         GX_CUDA(cudaStreamSynchronize(st));
-        if (prof) {
-            float a = 0, b = 0, u = 0;
-            GX_CUDA(cudaEventElapsedTime(&a, net->ev[0], net->ev[1]));
-            GX_CUDA(cudaEventElapsedTime(&b, net->ev[1], net->ev[2]));
-            GX_CUDA(cudaEventElapsedTime(&u, net->ev[2], net->ev[3]));
-            net->prof_ms[1] += a; net->prof_ms[2] += b; net->prof_ms[0] += u;
-        }
         if (*net->h_nact == 0) break;
     }
     *iters_out = it;
+    if (net->prof) {
+        net->prof_launches[0] += (long long)it * (c.n_bus_blk > 0);
+        net->prof_launches[1] += (long long)it * (c.n_line_blk > 0);
+        net->prof_launches[2] += (long long)it * (c.n_bat_warps > 0 || c.n_ramp_warps > 0);
+        return read_stamps(net, nch, st);
+    }
+    return GX_OK;
+}
+
+// Sampled kernel timing: every residual-check chunk's last iteration writes, per kernel
+// kind, the earliest block start and the latest block end (%globaltimer, ns) to the chunk's
+// slot; the duration of that launch is their difference.  Accumulate the loop's chunks and
+// reset their slots for the next loop.
+static gx_status read_stamps(gx_network* net, int nchunks, cudaStream_t st) {
+    const int n = std::min(nchunks, kStampSlots);
+    if (n <= 0) return GX_OK;
+    std::vector<unsigned long long> lo(3 * n), hi(3 * n);
+    const Ctx& c = net->ctx;
+    GX_CUDA(cudaMemcpyAsync(lo.data(), c.stamp_lo, 8 * lo.size(), cudaMemcpyDeviceToHost, st));
+    GX_CUDA(cudaMemcpyAsync(hi.data(), c.stamp_hi, 8 * hi.size(), cudaMemcpyDeviceToHost, st));
+    GX_CUDA(cudaMemsetAsync(c.stamp_lo, 0xff, 8 * lo.size(), st));
+    GX_CUDA(cudaMemsetAsync(c.stamp_hi, 0, 8 * hi.size(), st));
+    GX_CUDA(cudaStreamSynchronize(st));
+    // kinds in the slots: 0 bus, 1 line, 2 battery and ramp (the order of prof_ms)
+    for (int k = 0; k < n; ++k)
+        for (int q = 0; q < 3; ++q) {
+            const unsigned long long a = lo[3 * k + q], b = hi[3 * k + q];
+            if (b == 0 || a == ~0ULL || b < a) continue;  // the kind did not run in that chunk
+            net->prof_ms[q] += (double)(b - a) * 1e-6;
+            net->prof_samples[q] += 1;
+        }
     return GX_OK;
 }
 
@@ -1511,10 +1528,32 @@ gx_status gx_network_persistent_info(const gx_network* net, int scen, int* clust
 
 gx_status gx_profile_enable(gx_network* net, int on) {
     if (!net) return fail(GX_ERR_INVALID_ARG, "net is NULL");
+    if (on && !net->dev) return fail(GX_ERR_STATE, "network is not bound");
     if (on && !net->ev[0])
         for (auto& e : net->ev) GX_CUDA(cudaEventCreate(&e));
+    const bool changed = net->prof != (on != 0);
     net->prof = on != 0;
     for (int k = 0; k < 4; ++k) { net->prof_ms[k] = 0; net->prof_samples[k] = 0; net->prof_launches[k] = 0; }
+    if (net->dev) {
+        // the stamp slots start empty and the active counts at zero; the kernels write them
+        // only while the context carries their pointers
+        GX_CUDA(cudaMemset(net->dev + net->o_stlo, 0xff, 8 * 3 * kStampSlots));
+        GX_CUDA(cudaMemset(net->dev + net->o_sthi, 0, 8 * 3 * kStampSlots));
+        GX_CUDA(cudaMemset(net->dev + net->o_pact, 0, 8 * (size_t)net->S));
+        for (Ctx* c : {&net->ctx, &net->actx}) {
+            c->stamp_lo = net->prof ? reinterpret_cast<unsigned long long*>(net->dev + net->o_stlo) : nullptr;
+            c->stamp_hi = net->prof ? reinterpret_cast<unsigned long long*>(net->dev + net->o_sthi) : nullptr;
+            c->prof_act = net->prof ? reinterpret_cast<long long*>(net->dev + net->o_pact) : nullptr;
+        }
+        if (changed) net->drop_graphs();  // the captured kernels carry the context by value
+    }
+    return GX_OK;
+}
+
+gx_status gx_profile_active(const gx_network* net, long long* counts) {
+    if (!net || !counts) return fail(GX_ERR_INVALID_ARG, "NULL argument");
+    if (!net->dev) return fail(GX_ERR_STATE, "network is not bound");
+    GX_CUDA(cudaMemcpy(counts, net->dev + net->o_pact, 8 * (size_t)net->S, cudaMemcpyDeviceToHost));
     return GX_OK;
 }
 

@@ -21,6 +21,7 @@ constexpr int kQBlock = 128;       // threads per block of the hour-quad line / 
 constexpr int kBatWarps = 2;       // batteries (warps) per block of the battery kernel
 constexpr int kMaxT = 256;         // hours per scenario handled by one warp (8 per lane)
 constexpr int kHplMax = kMaxT / 32;
+constexpr int kStampSlots = 4096;  // residual-check chunks of one loop with kernel time stamps (power of 2)
 constexpr int kBusPart = 6;        // floats per bus-block residual partial
 constexpr int kDevPart = 3;        // floats per line-block / battery-warp partial
 
@@ -222,7 +223,30 @@ struct Ctx {
     double* cost_part;  // [n_cost_blk * 2]
     const float* warm;  // user warm start [prices | angles] over bus rows, or nullptr
     long long warm_half; // element count of the prices half of `warm` (= all bus rows)
+    // sampled kernel timing (gx_profile_enable), nullptr while off: per residual-check chunk
+    // and kernel kind (0 bus, 1 line, 2 battery / ramp), the earliest block start and the
+    // latest block end of the chunk's last iteration (%globaltimer, ns); per scenario, the
+    // chunks it was iterating in
+    unsigned long long* stamp_lo;  // [kStampSlots * 3]
+    unsigned long long* stamp_hi;  // [kStampSlots * 3]
+    long long* prof_act;           // [S]
 };
+
+// Time stamps of the sampled (residual) iteration; the slot is the loop's current chunk.
+__device__ __forceinline__ unsigned long long gx_now() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ int stamp_slot(const Ctx& c) {
+    return ((*c.iter_ctr - 1) / c.check_every) & (kStampSlots - 1);
+}
+__device__ __forceinline__ void stamp_start(const Ctx& c, int kind) {
+    atomicMin(c.stamp_lo + 3 * stamp_slot(c) + kind, gx_now());
+}
+__device__ __forceinline__ void stamp_end(const Ctx& c, int kind) {
+    atomicMax(c.stamp_hi + 3 * stamp_slot(c) + kind, gx_now());
+}
 
 // One thread's share of scenario sc's operating cost (Eq. 2 objective with the eps terms)
 // and emission total, FP64: thread `tid` of a reduction over `stride` threads takes every

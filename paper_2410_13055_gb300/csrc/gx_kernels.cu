@@ -232,6 +232,8 @@ __global__ void __launch_bounds__(kBatWarps * 32) k_bat(const Ctx c, int want_re
     const int lane = L & 31, wb = L >> 5;  // lane within the warp, warp within the battery
     const int gw = blockIdx.x * (kBatWarps / kW) + (int)(threadIdx.x / NL);
     if (gw >= c.n_bat_warps) return;  // block-uniform when kW == 2 (one battery per block)
+    const bool stamp = (MODE == M_FWD || MODE == M_ADJ) && want_res && c.stamp_lo != nullptr;
+    if (stamp && L == 0) stamp_start(c, 2);
     const int s = c.bat_warp_scen[gw];
     if (c.done[s]) return;
     const ScenDev sc = c.scen[s];
@@ -482,6 +484,7 @@ __global__ void __launch_bounds__(kBatWarps * 32) k_bat(const Ctx c, int want_re
             c.bat_part[gw * kDevPart + 0] = dx2;
             c.bat_part[gw * kDevPart + 1] = x2;
             c.bat_part[gw * kDevPart + 2] = 0.f;
+            if (stamp) stamp_end(c, 2);
         }
     }
 }
@@ -780,6 +783,8 @@ __device__ __forceinline__ void ldm4(const uint8_t* p, int (&v)[4]) {
 template <int ADJ>
 __global__ void __launch_bounds__(kQBlock) k_line4(const Ctx c, int want_res) {
     const int blk = blockIdx.x;
+    const bool stamp = want_res && c.stamp_lo != nullptr;
+    if (stamp && threadIdx.x == 0) stamp_start(c, 1);
     const int s = c.line4_blk_scen[blk];
     if (c.done[s]) return;
     const ScenDev sc = c.scen[s];
@@ -840,6 +845,7 @@ __global__ void __launch_bounds__(kQBlock) k_line4(const Ctx c, int want_res) {
             c.line_part[blk * kDevPart + 0] = v[0];
             c.line_part[blk * kDevPart + 1] = v[1];
             c.line_part[blk * kDevPart + 2] = v[2];
+            if (stamp) stamp_end(c, 1);
         }
     }
 }
@@ -871,6 +877,8 @@ __device__ __forceinline__ void gen_load4(const Ctx& c, const StatePtrs& X, cons
 template <int ADJ, int RAMP>
 __global__ void __launch_bounds__(kQBlock, 4) k_bus4(const Ctx c, int want_res) {
     __shared__ __align__(16) int S[kPoolMax];
+    const bool stamp = want_res && c.stamp_lo != nullptr;
+    if (stamp && threadIdx.x == 0) stamp_start(c, 0);
     const BusBlk bb = c.bus4_blk[blockIdx.x];
     if (c.done[bb.s]) return;  // block-uniform
     const StatePtrs X = state<ADJ>(c);
@@ -1068,6 +1076,7 @@ __global__ void __launch_bounds__(kQBlock, 4) k_bus4(const Ctx c, int want_res) 
         if (threadIdx.x == 0) {
 #pragma unroll
             for (int q = 0; q < kBusPart; ++q) c.bus_part[blockIdx.x * kBusPart + q] = acc[q];
+            if (stamp) stamp_end(c, 0);
         }
     }
 }
@@ -1095,6 +1104,8 @@ __global__ void k_tick(int* ctr, int chunk) {
 __global__ void __launch_bounds__(kBlock) k_reduce(const Ctx c, int adj, double tol) {
     const int s = blockIdx.x;
     if (c.done[s]) return;
+    // timing on: the chunk's sampled iteration worked for this scenario
+    if (c.prof_act != nullptr && threadIdx.x == 0) c.prof_act[s] += 1;
     const int it = *c.iter_ctr;
     const int final_ = it >= c.max_it;
     const ScenDev sc = c.scen[s];

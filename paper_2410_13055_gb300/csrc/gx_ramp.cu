@@ -45,6 +45,8 @@ __global__ void __launch_bounds__(kBatWarps * 32) k_ramp(const Ctx c, int want_r
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * kBatWarps + (threadIdx.x >> 5);
     if (gw >= c.n_ramp_warps) return;
+    const bool stamp = (MODE == M_FWD || MODE == M_ADJ) && want_res && c.stamp_lo != nullptr;
+    if (stamp && lane == 0) stamp_start(c, 2);
     const int s = c.ramp_warp_scen[gw];
     if (c.done[s]) return;
     const ScenDev sc = c.scen[s];
@@ -239,6 +241,7 @@ __global__ void __launch_bounds__(kBatWarps * 32) k_ramp(const Ctx c, int want_r
             c.ramp_part[gw * kDevPart + 0] = dx2;
             c.ramp_part[gw * kDevPart + 1] = x2;
             c.ramp_part[gw * kDevPart + 2] = gscale;
+            if (stamp) stamp_end(c, 2);
         }
     }
 }

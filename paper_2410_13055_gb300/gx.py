@@ -90,6 +90,7 @@ _SIGS = {
     "gx_network_use_persistent": (C.c_int, [_vp, C.c_int]),
     "gx_network_persistent_info": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int)]),
     "gx_profile_read": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
+    "gx_profile_active": (C.c_int, [_vp, C.POINTER(C.c_longlong)]),
     "gx_dispatch_cost_noalloc": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp]),
     "gx_gnn_num_params": (_sz, []),
     "gx_gnn_create": (C.c_int, [_vp, C.c_int, C.c_int, C.POINTER(_vp)]),
@@ -334,6 +335,12 @@ class Network:
         _check(_lib.gx_profile_read(self._h, ms, sm, ln), "gx_profile_read", False)
         names = ["k_bus", "k_line", "k_bat", "k_crs"]
         return {names[k]: {"ms": ms[k], "samples": sm[k], "launches": ln[k]} for k in range(4) if sm[k] > 0}
+
+    def profile_active(self):
+        """Per scenario: sampled iterations it was still iterating in (gx_profile_active)."""
+        out = (C.c_longlong * self.S)()
+        _check(_lib.gx_profile_active(self._h, out), "gx_profile_active", False)
+        return np.array(out[:], dtype=np.int64)
 
     def plan_step(self, eta, grad, gamma, eta_min, eta_max, alpha, stream=None):
         rc = _lib.gx_plan_step(self._h, _ptr(eta), _ptr(grad), _ptr(gamma), _ptr(eta_min), _ptr(eta_max),

@@ -239,12 +239,17 @@ def batching(seed: int = 2, S: int = 64):
     return nets, scens
 
 
-def scale(seed: int = 3, S: int = 52, T: int = 168):
-    """2000 buses, 3000 lines, 8000 generators, 500 batteries, 2000 loads, 52 weeks of T=168."""
+def scale(seed: int = 3, S: int = 52, T: int = 168, scen_seed: int | None = None, weight: float | None = None):
+    """2000 buses, 3000 lines, 8000 generators, 500 batteries, 2000 loads, 52 weeks of T=168.
+
+    With `scen_seed`, the scenarios come from their own seed on the network of `seed`;
+    `weight` overrides the scenario weight 1/S (one shard of a larger set)."""
     rng = _rng(seed)
     net = _bus_network(rng, 2000, 3000, 8000, 500, T, gen_scale=0.75)
     base = rng.uniform(50.0, 150.0, size=2000)
-    scens = [_bus_scenario(rng, net, 0, T, 1.0 / S, base) for _ in range(S)]
+    srng = rng if scen_seed is None else _rng(scen_seed)
+    w = 1.0 / S if weight is None else weight
+    scens = [_bus_scenario(srng, net, 0, T, w, base) for _ in range(S)]
     return [net], scens
 
 
