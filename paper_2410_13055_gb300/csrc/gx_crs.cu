@@ -497,6 +497,9 @@ __global__ void __launch_bounds__(kCrsThreads, 1)
                 for (int r = 0; r < C; ++r) a[q] += m.red[r * kCrsRed + q];
             }
             const double rhod = c.rho, rth = c.rth_c;
+            // NaN / inf test on the raw sums, before the clamps (fmax would turn a NaN into 0)
+            bool finite = true;
+            for (int q = 0; q < 9; ++q) finite = finite && isfinite(a[q]);
             const double scale = ADJ ? fmax(sqrt(a[1]), 1e-30) : sd.load_norm;
             const double rp = sqrt(fmax(a[0] + a[8], 0.0)) / scale;
             const double dz2 = fmax(a[2] + a[6], 0.0);
@@ -506,7 +509,7 @@ __global__ void __launch_bounds__(kCrsThreads, 1)
             const double r = fmax(rp, rd);
             if (it <= every || !(r >= best)) best = r;
             int stop = 1;
-            if (!isfinite(rp) || !isfinite(rd) || r > 1e6 * best) c.status[s] = GX_ERR_NONFINITE;
+            if (!finite || !isfinite(rp) || !isfinite(rd) || r > 1e6 * best) c.status[s] = GX_ERR_NONFINITE;
             else if (rp <= tol && rd <= tol) c.status[s] = GX_OK;
             else if (it >= max_it) c.status[s] = GX_NOT_CONVERGED;
             else stop = 0;

@@ -1146,6 +1146,11 @@ __global__ void __launch_bounds__(kBlock) k_reduce(const Ctx c, int adj, double 
         // a: 0 |n| pbar^2, 1 adjoint scale, 2 bus dz^2, 3 dthbar^2 w, 4 |rho u|^2, 5 bus x^2,
         //    6 device dx^2, 7 device x^2, 8 phase mismatch (line kernel, one iteration lagged)
         const double rho = c.rho, rth = c.rth_c;
+        // a NaN or inf anywhere in the iterate reaches these sums; test them before the
+        // clamps below, which would turn a NaN into 0 (fmax returns its other argument)
+        bool finite = true;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) finite = finite && isfinite(a[q]);
         const double scale = adj ? fmax(sqrt(a[1]), 1e-30) : sc.load_norm;
         const double rp = sqrt(fmax(a[0] + a[8], 0.0)) / scale;
         const double dz2 = fmax(a[2] + a[6], 0.0);
@@ -1156,7 +1161,7 @@ __global__ void __launch_bounds__(kBlock) k_reduce(const Ctx c, int adj, double 
         double* best = c.rbest + s;
         if (it <= c.check_every || !(r >= *best)) *best = r;
         int* itp = adj ? c.adj_iters : c.iters;
-        if (!isfinite(rp) || !isfinite(rd) || r > 1e6 * *best) {
+        if (!finite || !isfinite(rp) || !isfinite(rd) || r > 1e6 * *best) {
             // non-finite or diverged by six orders of magnitude from the best residual seen
             c.status[s] = GX_ERR_NONFINITE;
             c.done[s] = 1;

@@ -151,13 +151,13 @@ def asset_classes(net_desc):
 
 
 def battery_cost_sweep(costs=None, kappa=200.0, iters=150, batch=4, alpha_frac=0.02, eval_every=10, seed=0,
-                       log=None):
+                       log=None, S=16, T=24):
     """Section 3.3: battery capital costs from low to high, each run warm-started from the
     previous cost's plan; expansion (MW above existing) per asset class at each cost."""
     import torch
     from .warmstart import gamma_for_battery_cost
     costs = list(costs) if costs is not None else list(np.linspace(40.0, 800.0, 20))
-    nets, net, pl, _ = _setup(kappa)
+    nets, net, pl, _ = _setup(kappa, S=S, T=T)
     T = net.info[0]["T"]
     groups = asset_classes(nets[0])
     eta = pl.eta_min.clone()
