@@ -251,6 +251,12 @@ def measure(config, args, steps, warmup, dist=None, learned=False, cold=True, sc
     flush = torch.empty(int(256e6) // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
     state = {"alpha": None, "launches": 0, "iters": [], "adj_iters": []}
     reduce_grad = dist is not None and shared
+    # kernel schedule picked by the autotuner (a fixed number of timed iterations per
+    # candidate; the candidates compute the same iterates), before the warm-up
+    tuned = None
+    if not args.no_tune and not args.persistent:
+        from paper_2410_13055_gb300 import autotune
+        tuned = autotune.tune_schedule(net, eta_min, iters=200)
 
     def step(warm):
         rc = net.solve(eta, warm=warm)
@@ -387,6 +393,9 @@ def measure(config, args, steps, warmup, dist=None, learned=False, cold=True, sc
                 "replays_headline_steps": [list(x) for x in e2e_its] == [[a, b] for a, b in zip(it_prev, ait_prev)],
                 "note": "headline's plan and solver state restored first; no L2 flush between its steps"},
         "clocks": clk, "gpu_launches": int(launches), "alpha": state["alpha"],
+        "schedule": {"chosen": net.schedule(), "by": "autotune.tune_schedule" if tuned else "bind default",
+                     "trials_us_per_iteration": ({f"bus{t['bus_staged']}_bat{t['bat_warps']}": t["us_per_iteration"]
+                                                  for t in tuned["trials"]} if tuned else None)},
     }
 
 
@@ -468,6 +477,7 @@ def run_gx(args):
                    "parallelism": f"x{ws} ranks, scenarios sharded (sharding.shard), weak scaling",
                    "path": head["path"]},
         "iterations": head["iterations"],
+        "schedule": head["schedule"],
         "modes": {"prev": head["value"], "cold": head["cold"],
                   "learned": head["learned"]["value"] if head["learned"] else None},
         "learned": head["learned"],
@@ -608,6 +618,8 @@ def main():
                     help="batching config: also time one network and launch sequence per scenario")
     ap.add_argument("--no-sub", action="store_true",
                     help="medium config: skip the scale and batching sub-records")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the library's default kernel schedule instead of autotuning it per workload")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -252,6 +252,27 @@ gx_status gx_plan_step(gx_network* net, float* eta_dev, const float* grad_dev, c
  * results are bitwise identical.  Other values: GX_ERR_INVALID_ARG. */
 gx_status gx_network_use_graphs(gx_network* net, int on);
 
+/* Kernel schedule of the per-iteration path (not in the paper; performance only: every
+ * schedule computes the same iterates, bitwise).
+ *   bus_staged  how the hour-quad bus kernel reads its block's device rows.  1: bulk
+ *               copies (TMA) of every row segment into shared memory, completing on an
+ *               mbarrier, so all of the block's rows are in flight at once; 2: the same
+ *               stage filled by per-thread 16-byte asynchronous copies; 0: each thread
+ *               loads its bus's device rows itself, one generator ahead.  Until a schedule
+ *               is set, bind picks 1 when the workspace exceeds the device's L2 cache (the
+ *               iteration streams from HBM) and 0 otherwise (L2-resident and
+ *               latency-bound, where 0 measured fastest).
+ *   bat_warps   warps per battery of the battery prox when the longest horizon exceeds
+ *               96 hours: 2 (default; hours split over 64 lanes, warp totals combined in
+ *               shared memory) or 1 (32 lanes, longer serial sweeps, no block barriers).
+ * Setting it drops the cached graphs.  Errors: GX_ERR_INVALID_ARG for other values. */
+typedef struct {
+    int bus_staged;
+    int bat_warps;
+} gx_schedule;
+gx_status gx_network_set_schedule(gx_network* net, const gx_schedule* sched);
+gx_status gx_network_get_schedule(const gx_network* net, gx_schedule* sched);
+
 /* Cluster-resident solver (default off).  A scenario whose state fits the shared memory
  * of a thread-block cluster (1 to 16 CTAs; each CTA holds every device for a range of
  * hours, batteries exchange their hours over distributed shared memory) runs its whole

@@ -8,10 +8,16 @@ whose gradient there is no less accurate than the defaults' (within a factor `g_
 against a tight reference gradient (equal residual tolerances do not give equal
 accuracy across penalties; the adjoint penalty changes the gradient and not h).  Parameters:
 the execution path (per-iteration kernels replayed as CUDA graphs, or one persistent
-cluster-resident launch per loop for the scenarios that fit), residual-check chunk
-length (the CUDA-graph size), power penalty rho, phase penalty scale, adjoint penalty,
-battery inner iterations.  Results are cached as JSON, keyed by (buses, hours,
+cluster-resident launch per loop for the scenarios that fit), the kernel schedule (how
+the bus kernel brings its device rows in: per-thread loads, bulk copies into shared
+memory, or per-thread asynchronous copies; one or two warps per battery), residual-check
+chunk length (the CUDA-graph size), power penalty rho, phase penalty scale, adjoint
+penalty, battery inner iterations.  Results are cached as JSON, keyed by (buses, hours,
 scenarios) rounded to powers of two.
+
+``tune_schedule`` is the quick form for the kernel schedule alone: schedules do not change
+the iterates (the bus kernel variants are bitwise equal), so it times a fixed number of
+iterations per candidate and keeps the fastest.
 """
 from __future__ import annotations
 
@@ -28,8 +34,12 @@ from typing import TYPE_CHECKING
 if TYPE_CHECKING:  # the library is loaded by the functions that run it
     from . import gx
 
+SCHEDULE = {"bus_staged": [0, 1, 2], "bat_warps": [2, 1]}
+
 SPACE = {
     "persistent": [False, True],
+    "bus_staged": SCHEDULE["bus_staged"],
+    "bat_warps": SCHEDULE["bat_warps"],
     "check_every": [10, 20, 40],
     "rho": [0.1, 0.15, 0.2, 0.3, 0.5],
     "rho_theta_c": [0.03, 0.1],
@@ -78,6 +88,55 @@ def _grad_err(net, eta, g_ref):
     return float((g.double() - g_ref).norm() / max(float(g_ref.norm()), 1e-30))
 
 
+def _apply(net, opts):
+    """Options, execution path and kernel schedule of a setting."""
+    net.set_opts(**{k: v for k, v in opts.items() if k not in ("persistent",) and k not in SCHEDULE})
+    if "persistent" in opts:
+        net.use_persistent(bool(opts["persistent"]))
+    sched = {k: int(v) for k, v in opts.items() if k in SCHEDULE}
+    if sched:
+        net.set_schedule(**sched)
+
+
+def tune_schedule(net: gx.Network, eta, iters=200, space=None, log=None):
+    """Pick the fastest kernel schedule for `net` at plan `eta`: for each candidate, time
+    `iters` forward and `iters` adjoint iterations with every scenario iterating (the
+    tolerances are set out of reach for the timing, then restored).  The schedules
+    compute the same iterates, so only time decides.  Leaves the state of the last
+    timing run in the workspace (callers start their solves cold).  Returns
+    dict(best=..., trials=[...])."""
+    space = space or SCHEDULE
+    keep = {k: getattr(net.opts, k) for k in ("tol", "adj_tol", "max_iter", "adj_max_iter")}
+    net.solve(eta, warm="cold")
+    net.grad(eta, warm="cold")
+    every = net.opts.check_every
+    n = max(every, iters // every * every)
+    net.set_opts(tol=1e-30, adj_tol=1e-30, max_iter=n, adj_max_iter=n)
+    cands = [dict(bus_staged=b, bat_warps=w) for b in space["bus_staged"] for w in space["bat_warps"]]
+    trials = []
+    for cand in cands:
+        net.set_schedule(**cand)
+        net.solve(eta, warm="prev")  # captures the loop graphs of this schedule, untimed
+        net.grad(eta, warm="prev")
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        net.solve(eta, warm="prev")
+        net.grad(eta, warm="prev")
+        b.record()
+        torch.cuda.synchronize()
+        us = 1e3 * a.elapsed_time(b) / (2 * n)
+        trials.append(dict(cand, us_per_iteration=round(us, 3)))
+        if log:
+            log(trials[-1])
+    best = min(trials, key=lambda t: t["us_per_iteration"])
+    best = {k: best[k] for k in SCHEDULE}
+    net.set_schedule(**best)
+    net.set_opts(**keep)
+    return dict(best=best, trials=trials, iterations=n)
+
+
 def tune(net: gx.Network, nets, steps=3, h_tol=2e-3, g_slack=1.25, cache=None, log=None, alpha_frac=1e-2):
     """Tune `net`'s options in place; returns the chosen option dict."""
     cache = cache or default_cache_path()
@@ -86,16 +145,16 @@ def tune(net: gx.Network, nets, steps=3, h_tol=2e-3, g_slack=1.25, cache=None, l
     eta_min = torch.tensor(np.concatenate([n["eta_min"] for n in nets]), dtype=torch.float32, device=dev)
     eta_max = torch.tensor(np.concatenate([n["eta_max"] for n in nets]), dtype=torch.float32, device=dev)
     gamma = torch.tensor(np.concatenate([n["gamma"] for n in nets]), dtype=torch.float32, device=dev)
-    base = {k: getattr(net.opts, k) for k in SPACE if k != "persistent"}
+    base = {k: getattr(net.opts, k) for k in SPACE if k != "persistent" and k not in SCHEDULE}
     base["persistent"] = False
+    base.update(net.schedule())
     g0 = torch.zeros_like(eta_min)
     net.solve(eta_min, warm="cold")
     net.grad(eta_min, out=g0)
     alpha = alpha_frac * float(eta_min.median()) / max(float((gamma + g0).abs().max()), 1e-30)
 
     def apply(opts):
-        net.set_opts(**{k: v for k, v in opts.items() if k != "persistent"})
-        net.use_persistent(opts["persistent"])
+        _apply(net, opts)
 
     def measure(opts):
         apply(opts)
@@ -149,8 +208,6 @@ def load(net: gx.Network, cache=None):
     db = json.load(open(cache))
     e = db.get(bucket(net))
     if e:
-        best = dict(e["best"])
-        net.use_persistent(bool(best.pop("persistent", False)))
-        net.set_opts(**best)
+        _apply(net, dict(e["best"]))
         return e["best"]
     return None

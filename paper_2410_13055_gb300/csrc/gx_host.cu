@@ -81,6 +81,7 @@ struct gx_network {
     std::vector<BusBlk> bus4_blk;      // bus-kernel block records (hour-quad kernel)
     std::vector<int> line4_blk_scen;   // scenario of each hour-quad line block
     int n_bus4_blk = 0, n_line4_blk = 0;
+    size_t bus4_smem = 0;              // dynamic shared memory of the staged bus kernel (record + stage)
     std::vector<int> pool;             // their pool records (words)
     std::vector<int2> prep;            // (pool word, eta index) of each generator plan value
     std::vector<uint8_t> firm;         // generator has capacity factor 1 in every hour of every scenario
@@ -119,7 +120,7 @@ struct gx_network {
     size_t o_f[16], o_a[16];  // forward / adjoint state arrays, order of StatePtrs
     size_t o_fend, o_aend;    // end of the forward / adjoint state range (ramp arrays included)
     size_t o_mgen, o_mload, o_mline, o_mbat;
-    size_t o_done, o_iters, o_status, o_adjit, o_nact, o_ctr, o_inb, o_resid, o_rbest, o_cost, o_h, o_grads, o_wprime, o_obj, o_stlo, o_sthi, o_pact;
+    size_t o_done, o_iters, o_status, o_adjit, o_nact, o_ctr, o_inb, o_err, o_resid, o_rbest, o_cost, o_h, o_grads, o_wprime, o_obj, o_stlo, o_sthi, o_pact;
     size_t o_flow, o_price, o_shed, o_bpart, o_lpart, o_btpart, o_cpart;
     Layout lay;
     // binding
@@ -141,6 +142,8 @@ struct gx_network {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int* h_nact = nullptr;  // pinned host copies: [0] active-scenario count, [1] iteration counter
     int use_graphs = 2;     // 0 eager launches, 1 one graph per chunk, 2 the whole loop as one graph
+    gx_schedule sched{1, 2};  // kernel schedule (gx_network_set_schedule)
+    bool sched_set = false;   // the caller chose the schedule (else bind picks it by workspace size)
     void drop_graphs() {
         for (auto& g : graphs) {
             if (g.exec) cudaGraphExecDestroy(g.exec);
@@ -315,6 +318,10 @@ static void make_ctx(gx_network* net) {
     c.stamp_lo = net->prof ? reinterpret_cast<unsigned long long*>(d + net->o_stlo) : nullptr;
     c.stamp_hi = net->prof ? reinterpret_cast<unsigned long long*>(d + net->o_sthi) : nullptr;
     c.prof_act = net->prof ? reinterpret_cast<long long*>(d + net->o_pact) : nullptr;
+    c.bus_staged = net->sched.bus_staged;
+    c.bus4_smem = (int)net->bus4_smem;
+    c.bat_warps = net->sched.bat_warps;
+    c.err = I(net->o_err);
     // the adjoint iteration: same arrays, its own penalties and battery pivots
     Ctx& a = net->actx;
     a = c;
@@ -511,7 +518,9 @@ static void build_crs_groups(gx_network* net) {
 // scenarios on the same network with the same bus range share one pool record.
 static void build_bus_blocks(gx_network* net) {
     auto fbits = [](float f) { int w; std::memcpy(&w, &f, 4); return w; };
-    std::map<std::tuple<int, int, int>, std::pair<int, int>> rec_of;  // (net, n0, n1) -> (offset, words)
+    // (quad, net, n0, n1, first quad of bus n0, end quad of bus n1, quads per row) -> (offset, words)
+    std::map<std::tuple<int, int, int, int, int, int, int>, std::pair<int, int>> rec_of;
+    net->bus4_smem = 0;
     net->bus_blk.clear();
     net->bus4_blk.clear();
     net->pool.clear();
@@ -535,13 +544,19 @@ static void build_bus_blocks(gx_network* net) {
             r.n0 = r.item0 / per_bus;
             const int n1 = last / per_bus;
             r.Tp = sd.Tp; r.T = sd.T; r.nitems = (int)nitems;
-            const auto key = std::make_tuple(sd.net, r.n0, n1);
+            const int qf = quad ? r.item0 - r.n0 * per_bus : 0;          // first quad of bus n0
+            const int ql = quad ? last + 1 - n1 * per_bus : 0;           // end quad of bus n1
+            const auto key = std::make_tuple(quad, sd.net, r.n0, n1, qf, ql, quad ? per_bus : 0);
             auto it = rec_of.find(key);
             if (it == rec_of.end()) {
                 const int nbus = n1 - r.n0 + 1;
                 const int gb = h.gptr[r.n0], gcnt = h.gptr[n1 + 1] - gb;
                 const int eb = h.eptr[r.n0], ecnt = h.eptr[n1 + 1] - eb;
                 const int bb = h.bptr[r.n0], bcnt = h.bptr[n1 + 1] - bb;
+                // row staging of the quad kernel: each bus's hour range in this block, and
+                // one copy per device row segment (generators twice: x and aux; line ends
+                // twice: delta and the end's phase copy)
+                const int ncopy = quad ? 2 * gcnt + 2 * ecnt + bcnt : 0;
                 int o[kPoolHdr] = {};
                 int w = kPoolHdr;
                 o[kPH_GP] = w; w += nbus + 1;
@@ -559,6 +574,12 @@ static void build_bus_blocks(gx_network* net) {
                 o[kPH_EBETA] = w; w += ecnt;
                 o[kPH_EW] = w; w += ecnt;
                 o[kPH_BROW] = w; w += bcnt;
+                o[kPH_SQ] = w; w += nbus;
+                o[kPH_SI] = w; w += nbus;
+                o[kPH_SG] = w; w += nbus;
+                o[kPH_SE] = w; w += nbus;
+                o[kPH_SB] = w; w += nbus;
+                o[kPH_CP] = w; w += 3 * ncopy;
                 const int words = (w + 3) / 4 * 4;
                 o[kPH_NBUS] = nbus; o[kPH_GCNT] = gcnt; o[kPH_ECNT] = ecnt; o[kPH_BCNT] = bcnt;
                 const int off = (int)net->pool.size();
@@ -598,6 +619,73 @@ static void build_bus_blocks(gx_network* net) {
                     p[o[kPH_EW] + k] = fbits(h.l_w[e >> 1]);
                 }
                 for (int k = 0; k < bcnt; ++k) p[o[kPH_BROW] + k] = h.bidx[bb + k];
+                if (quad) {
+                    int qg = 0, qe = 0, qb = 0;
+                    for (int k = 0; k < nbus; ++k) {
+                        const int n = r.n0 + k;
+                        const int s_it = std::max(n * per_bus, r.item0), e_it = std::min((n + 1) * per_bus, last + 1);
+                        p[o[kPH_SQ] + k] = e_it - s_it;
+                        p[o[kPH_SI] + k] = s_it - r.item0;
+                        p[o[kPH_SG] + k] = qg;
+                        p[o[kPH_SE] + k] = qe;
+                        p[o[kPH_SB] + k] = qb;
+                        qg += (h.gptr[n + 1] - h.gptr[n]) * (e_it - s_it);
+                        qe += (h.eptr[n + 1] - h.eptr[n]) * (e_it - s_it);
+                        qb += (h.bptr[n + 1] - h.bptr[n]) * (e_it - s_it);
+                    }
+                    const long long sbytes = 16LL * (2 * qg + 2 * qe + qb) + (4LL * qg + 15) / 16 * 16;
+                    int* cp = p + o[kPH_CP];
+                    int nc = 0;
+                    long long txf = 0, txa = 0;  // bytes copied in the forward / adjoint iteration
+                    auto add = [&](long long src, int dst, int nq, int flags, int arr) {
+                        cp[3 * nc] = (int)src;
+                        cp[3 * nc + 1] = dst;
+                        cp[3 * nc + 2] = (nq << 5) | (flags << 3) | arr;
+                        ++nc;
+                        // a generator's aux row: capacity factor (forward, not for firm units),
+                        // forward dispatch (adjoint); none for ramp-limited units
+                        const bool aux = arr == kCpGenAux;
+                        if (!aux || !(flags & (kCpRamp | kCpFirm))) txf += 16LL * nq;
+                        if (!aux || !(flags & kCpRamp)) txa += 16LL * nq;
+                    };
+                    for (int k = 0; k < nbus; ++k) {
+                        const int n = r.n0 + k, nq = p[o[kPH_SQ] + k];
+                        const int q0 = (r.item0 + p[o[kPH_SI] + k]) - n * per_bus;  // first quad in the row
+                        for (int j = h.gptr[n] - gb; j < h.gptr[n + 1] - gb; ++j) {
+                            const int g = h.gidx[gb + j], rr = j - (h.gptr[n] - gb);
+                            const long long src = (long long)g * sd.Tp + 4LL * q0;
+                            const int dst = p[o[kPH_SG] + k] + rr * nq;
+                            const int fl = (net->firm[h.gen0 + g] ? kCpFirm : 0) | (h.g_ramp[g] >= 0 ? kCpRamp : 0);
+                            add(src, dst, nq, fl, kCpGenX);
+                            add(src, qg + dst, nq, fl, kCpGenAux);
+                        }
+                        for (int j = h.eptr[n] - eb; j < h.eptr[n + 1] - eb; ++j) {
+                            const int e = h.eidx[eb + j], rr = j - (h.eptr[n] - eb);
+                            const long long src = (long long)(e >> 1) * sd.Tp + 4LL * q0;
+                            const int dst = p[o[kPH_SE] + k] + rr * nq;
+                            add(src, 2 * qg + dst, nq, 0, kCpDl);
+                            add(src, 2 * qg + qe + dst, nq, 0, (e & 1) ? kCpVt : kCpVf);
+                        }
+                        for (int j = h.bptr[n] - bb; j < h.bptr[n + 1] - bb; ++j) {
+                            const int b = h.bidx[bb + j], rr = j - (h.bptr[n] - bb);
+                            const long long src = (long long)b * sd.Tp + 4LL * q0;
+                            add(src, 2 * qg + 2 * qe + p[o[kPH_SB] + k] + rr * nq, nq, 0, kCpBat);
+                        }
+                    }
+                    const bool staged = sbytes <= kStageMax && words <= kPoolMax;
+                    p[kPH_NCP] = staged ? nc : 0;
+                    p[kPH_QG] = qg;
+                    p[kPH_QE] = qe;
+                    p[kPH_QB] = qb;
+                    p[kPH_SBYTES] = staged ? (int)sbytes : 0;
+                    p[kPH_TXF] = (int)txf;
+                    p[kPH_TXA] = (int)txa;
+                    // the launch's dynamic shared memory holds the largest record kept in
+                    // shared memory, with its stage if it has one
+                    if (words <= kPoolMax)
+                        net->bus4_smem = std::max<size_t>(net->bus4_smem,
+                                                          4 * (size_t)words + (staged ? (size_t)sbytes : 0));
+                }
                 it = rec_of.emplace(key, std::make_pair(off, words)).first;
             }
             r.pool = it->second.first;
@@ -883,7 +971,7 @@ gx_status gx_network_create(const gx_network_desc* nets, int n_nets, const gx_sc
     net->o_aend = L.total;
     net->o_mgen = L.add(B1(eg)); net->o_mload = L.add(B1(eb)); net->o_mline = L.add(B1(el)); net->o_mbat = L.add(B1(ebt));
     net->o_done = L.add(I4(S)); net->o_iters = L.add(I4(S)); net->o_status = L.add(I4(S)); net->o_adjit = L.add(I4(S));
-    net->o_nact = L.add(I4(1)); net->o_ctr = L.add(I4(1)); net->o_inb = L.add(I4(S));
+    net->o_nact = L.add(I4(1)); net->o_ctr = L.add(I4(1)); net->o_inb = L.add(I4(S)); net->o_err = L.add(I4(1));
     net->o_resid = L.add(D8(2LL * S)); net->o_rbest = L.add(D8(S)); net->o_cost = L.add(D8(S)); net->o_h = L.add(D8(S));
     net->o_grads = L.add(D8(gs)); net->o_wprime = L.add(D8(S)); net->o_obj = L.add(D8(1));
     net->o_stlo = L.add(D8(3LL * kStampSlots)); net->o_sthi = L.add(D8(3LL * kStampSlots)); net->o_pact = L.add(D8(S));
@@ -996,6 +1084,16 @@ gx_status gx_network_bind(gx_network* net, void* dev_mem, size_t bytes, void* st
     if (!net->cap_stream2) GX_CUDA(cudaStreamCreateWithFlags(&net->cap_stream2, cudaStreamNonBlocking));
     if (!net->ev_fork) GX_CUDA(cudaEventCreateWithFlags(&net->ev_fork, cudaEventDisableTiming));
     if (!net->ev_join) GX_CUDA(cudaEventCreateWithFlags(&net->ev_join, cudaEventDisableTiming));
+    if (net->bus4_smem > 0) GX_CUDA(bus_staged_prepare((int)net->bus4_smem));
+    if (!net->sched_set) {
+        // default bus kernel: stage the device rows when the iteration streams from HBM (the
+        // workspace exceeds L2); an L2-resident workspace is latency-bound, where the
+        // per-thread loads measured faster
+        int dev = 0, l2 = 0;
+        GX_CUDA(cudaGetDevice(&dev));
+        GX_CUDA(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
+        net->sched.bus_staged = net->lay.total > (size_t)l2 ? 1 : 0;
+    }
     make_ctx(net);
     for (auto& g : net->crs_groups) {
         g.ok = true;
@@ -1379,7 +1477,10 @@ static gx_status collect_stats(gx_network* net, int adj, gx_stats* stats, int la
                             cudaMemcpyDeviceToHost, st));
     GX_CUDA(cudaMemcpyAsync(sts.data(), net->dev + net->o_status, 4 * net->S, cudaMemcpyDeviceToHost, st));
     GX_CUDA(cudaMemcpyAsync(res.data(), net->dev + net->o_resid, 16 * net->S, cudaMemcpyDeviceToHost, st));
+    int err = 0;
+    GX_CUDA(cudaMemcpyAsync(&err, net->dev + net->o_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     GX_CUDA(cudaStreamSynchronize(st));
+    if (err) return fail(err, "a bounded device-side wait gave up (bulk copies of the bus kernel)");
     gx_stats sx{};
     sx.launches = launches;
     gx_status worst = GX_OK;
@@ -1406,6 +1507,7 @@ gx_status gx_dispatch_solve_batch(gx_network* net, const float* eta_dev, const i
     if (warm < GX_WARM_COLD || warm > GX_WARM_USER) return fail(GX_ERR_INVALID_ARG, "unsupported warm mode");
     if (warm == GX_WARM_USER && !warm_dev) return fail(GX_ERR_INVALID_ARG, "GX_WARM_USER needs warm_dev");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    GX_CUDA(cudaMemsetAsync(net->dev + net->o_err, 0, sizeof(int), st));
     if (gx_status e = upload_batch(net, scen_idx, B, st)) return e;
     if (gx_status e = upload_pivots(net, st)) return e;
     // Eq. 1 weights of the batch, rescaled to the total weight (an unbiased estimate of
@@ -1449,6 +1551,7 @@ gx_status gx_dispatch_grad_batch(gx_network* net, const float* eta_dev, int warm
     if (!net->solved) return fail(GX_ERR_STATE, "gx_dispatch_grad_batch needs a solve first");
     if (!eta_dev || !grad_dev) return fail(GX_ERR_INVALID_ARG, "NULL device pointer");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    GX_CUDA(cudaMemsetAsync(net->dev + net->o_err, 0, sizeof(int), st));
     Ctx& c = net->ctx;
     c.eta = eta_dev;
     c.warm = nullptr;
@@ -1510,6 +1613,22 @@ gx_status gx_network_use_graphs(gx_network* net, int on) {
     if (!net) return fail(GX_ERR_INVALID_ARG, "net is NULL");
     if (on < 0 || on > 2) return fail(GX_ERR_INVALID_ARG, "graph mode must be 0, 1 or 2");
     net->use_graphs = on;
+    return GX_OK;
+}
+
+gx_status gx_network_set_schedule(gx_network* net, const gx_schedule* sched) {
+    if (!net || !sched) return fail(GX_ERR_INVALID_ARG, "NULL argument");
+    if (sched->bus_staged < 0 || sched->bus_staged > 2) return fail(GX_ERR_INVALID_ARG, "bus_staged is 0, 1 or 2");
+    if (sched->bat_warps != 1 && sched->bat_warps != 2) return fail(GX_ERR_INVALID_ARG, "bat_warps is 1 or 2");
+    net->sched = *sched;
+    net->sched_set = true;
+    if (net->dev) make_ctx(net);  // drops the cached graphs, whose launches follow the schedule
+    return GX_OK;
+}
+
+gx_status gx_network_get_schedule(const gx_network* net, gx_schedule* sched) {
+    if (!net || !sched) return fail(GX_ERR_INVALID_ARG, "NULL argument");
+    *sched = net->sched;
     return GX_OK;
 }
 

@@ -36,9 +36,24 @@ enum : int {
     kPH_GROW, kPH_GCOST, kPH_GEMIS, kPH_GFIRM, kPH_GETA,  // [gcnt] generator row in its network, ...
     kPH_ECODE, kPH_EBETA, kPH_EW,       // [ecnt] line end 2*l + side, beta_l, phase weight w_l
     kPH_BROW,                           // [bcnt] battery row in its network
-    kPoolHdr = 20
+    // Row staging of the hour-quad bus kernel (records of quad blocks only).  Bus nl of the
+    // block covers block items [SI[nl], SI[nl] + SQ[nl]); its generators' row segments sit
+    // at stage quads SG[nl] + r * SQ[nl] of each generator region, likewise its line ends
+    // (SE) and batteries (SB).  Regions, in quads (16 bytes): generator x [0, QG), generator
+    // aux (capacity factor / forward dispatch) [QG, 2QG), line delta [2QG, 2QG+QE), line-end
+    // phase copy [2QG+QE, 2QG+2QE), battery x [2QG+2QE, +QB); then QG u32 generator masks.
+    // CP: NCP copies of (source offset from the scenario's row base, destination quad,
+    // quads << 5 | flags << 3 | array); SBYTES the stage's size, 0 = not staged.
+    kPH_SQ, kPH_SI, kPH_SG, kPH_SE, kPH_SB,  // [nbus]
+    kPH_CP, kPH_NCP, kPH_QG, kPH_QE, kPH_QB, kPH_SBYTES,
+    kPH_TXF, kPH_TXA,                   // bytes the bulk copies bring in: forward, adjoint
+    kPoolHdr = 32
 };
 constexpr int kPoolMax = 3072;  // longest record (words) staged in shared memory
+// staged copies: array ids and flags of a copy-list entry
+enum : int { kCpGenX = 0, kCpGenAux = 1, kCpDl = 2, kCpVf = 3, kCpVt = 4, kCpBat = 5 };
+enum : int { kCpFirm = 1, kCpRamp = 2 };   // (flags << 3): capacity factor 1 / ramp-limited generator
+constexpr int kStageMax = 40 * 1024;      // largest row stage (bytes) of one bus block
 
 // Cluster-resident solver: one thread-block cluster of C CTAs per scenario, CTA r owning
 // hours [r*H, (r+1)*H) of every device (H = ceil(T / C)), its state in shared memory.
@@ -230,6 +245,13 @@ struct Ctx {
     unsigned long long* stamp_lo;  // [kStampSlots * 3]
     unsigned long long* stamp_hi;  // [kStampSlots * 3]
     long long* prof_act;           // [S]
+    // hour-quad bus kernel: 1 = stage the block's device rows in shared memory with bulk
+    // copies (k_bus4t), 0 = per-thread loads (k_bus4); the staged launch's dynamic shared
+    // memory; a bounded device-side wait that gave up writes its status to *err
+    int bus_staged;
+    int bus4_smem;
+    int bat_warps;       // battery prox warps per battery for horizons over 96 hours (1 or 2)
+    int* err;
 };
 
 // Time stamps of the sampled (residual) iteration; the slot is the loop's current chunk.
@@ -293,6 +315,9 @@ int launch_bat(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st);
 int launch_ramp(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st);
 int launch_bus(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st);
 int launch_prep(const Ctx& c, cudaStream_t st);
+// Allow the staged bus kernel `smem` bytes of dynamic shared memory (once per process is
+// enough; called at bind).
+cudaError_t bus_staged_prepare(int smem);
 int launch_loop_cond(const Ctx& c, int max_it, cudaGraphConditionalHandle h, cudaStream_t st);
 // Cluster-resident solver (gx_crs.cu): iterate the scenarios in `scen` (in_batch ones
 // only) to convergence, C CTAs per scenario, hpl hours per lane of a battery warp.

@@ -1081,6 +1081,347 @@ __global__ void __launch_bounds__(kQBlock, 4) k_bus4(const Ctx c, int want_res) 
     }
 }
 
+// ------------------------------------------------------------------------------------
+// Staged bus kernel.  The same iteration as k_bus4, expression for expression and in the
+// same summation order (its iterates are bitwise those of k_bus4), with the block's device
+// rows brought into shared memory first.  In k_bus4 a thread walks its bus's devices with
+// one generator's loads in flight at a time, so a block waits for about 4 + (generators
+// per bus) dependent memory round trips.  Here warp 0 issues one bulk copy per device row
+// segment of the block (cp.async.bulk, completing on one mbarrier; the copy list is built
+// at create, in the pool record), so every row the block needs is in flight at once and
+// the block waits for three hops: its record, its bus state and the record, the rows.
+// Adjoint generator masks (one byte per hour: not 16-byte aligned) come with per-thread
+// 4-byte asynchronous copies.  A record too large for the stage runs the unstaged loads.
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+// One bounded probe of the barrier's phase (try_wait suspends the thread for a while).
+__device__ __forceinline__ bool mbar_try(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Global -> shared bulk copy (TMA engine); bytes a multiple of 16, both addresses 16-byte aligned.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+constexpr int kWaitProbes = 1 << 22;  // bounded mbarrier wait (each probe suspends briefly)
+
+// Whether a staged copy is issued: firm generators have no capacity-factor row to read and
+// ramp-limited ones no aux row at all (the bus only sums their injection).
+template <int ADJ>
+__device__ __forceinline__ bool copy_wanted(int code) {
+    if ((code & 7) != kCpGenAux) return true;
+    const int fl = (code >> 3) & 3;
+    if (fl & kCpRamp) return false;
+    return ADJ || !(fl & kCpFirm);
+}
+
+template <int ADJ, int RAMP>
+__global__ void __launch_bounds__(kQBlock, 4) k_bus4t(const Ctx c, int want_res) {
+    extern __shared__ __align__(16) int S[];  // the block's record, then its row stage
+    __shared__ __align__(8) unsigned long long bar;
+    const bool stamp = want_res && c.stamp_lo != nullptr;
+    if (stamp && threadIdx.x == 0) stamp_start(c, 0);
+    const BusBlk bb = c.bus4_blk[blockIdx.x];
+    const StatePtrs X = state<ADJ>(c);
+    // hop 2: the record, this thread's bus state and the done flag, all in flight together
+    const bool rec_smem = bb.words <= kPoolMax;
+    if (rec_smem) {
+        const int4* src = reinterpret_cast<const int4*>(c.pool + bb.pool);
+        int4* dst = reinterpret_cast<int4*>(S);
+        for (int k = threadIdx.x; k < (bb.words >> 2); k += kQBlock) dst[k] = src[k];
+    }
+    const int Tq = bb.Tp >> 2;
+    const int local = bb.item0 + threadIdx.x;
+    const int n = local / Tq;
+    const int t = (local - n * Tq) * 4;
+    const bool valid = local < bb.nitems;
+    const long long i = bb.e_bus + (long long)n * bb.Tp + t;
+    float pb[4], uu[4], thold[4], xl[4], Ld[4], xlf[4];
+    int ml[4] = {0, 0, 0, 0};
+    if (valid) {
+        ld4(X.pbar + i, pb); ld4(X.u + i, uu); ld4(X.thb + i, thold);
+        ld4(X.xl + i, xl); ld4(c.load + i, Ld);
+        if (ADJ) { ld4(c.xl + i, xlf); ldm4(c.m_load + i, ml); }
+    }
+    const int done = c.done[bb.s];
+    const bool bulk = c.bus_staged == 1;
+    if (threadIdx.x == 0 && bulk && rec_smem) {
+        // arm the barrier with the bytes the copies will bring (from the record's header,
+        // read directly: the staged copy of the record is not there yet)
+        const int* hdr = c.pool + bb.pool;
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+        if (hdr[kPH_SBYTES] > 0) mbar_expect_tx(&bar, (unsigned)hdr[ADJ ? kPH_TXA : kPH_TXF]);
+    }
+    __syncthreads();
+    if (done) return;  // block-uniform
+    const Pool P{rec_smem ? S : c.pool + bb.pool};
+    const int sbytes = P.p[kPH_SBYTES];
+    float4* stage = reinterpret_cast<float4*>(S + bb.words);
+    const int qg = P.p[kPH_QG], qe = P.p[kPH_QE], qb = P.p[kPH_QB];
+    uint32_t* mstage = reinterpret_cast<uint32_t*>(stage + 2 * qg + 2 * qe + qb);
+    // hop 3 (bulk): every device row segment of the block, the copy list split over the warps
+    if (sbytes > 0 && bulk) {
+        const int ncp = P.p[kPH_NCP];
+        const int* cpl = P.p + P.p[kPH_CP];
+        for (int k = threadIdx.x; k < ncp; k += kQBlock) {
+            const int rel = cpl[3 * k], dst = cpl[3 * k + 1], code = cpl[3 * k + 2];
+            if (!copy_wanted<ADJ>(code)) continue;
+            const float* src;
+            switch (code & 7) {
+                case kCpGenX: src = X.xg + bb.e_gen; break;
+                case kCpGenAux: src = (ADJ ? c.xg : c.cf) + bb.e_gen; break;
+                case kCpDl: src = X.dl + bb.e_line; break;
+                case kCpVf: src = X.vf + bb.e_line; break;
+                case kCpVt: src = X.vt + bb.e_line; break;
+                default: src = X.xb + bb.e_bat; break;
+            }
+            bulk_g2s(stage + dst, src + rel, 16u * (unsigned)(code >> 5), &bar);
+        }
+    }
+    const int nl = n - bb.n0;
+    const int nq = valid ? P.at(kPH_SQ, nl) : 0;
+    const int pos = valid ? (int)threadIdx.x - P.at(kPH_SI, nl) : 0;
+    const long long gt = bb.e_gen + t;  // generator rows: gt + row * Tp
+    const int g0 = valid ? P.at(kPH_GP, nl) : 0, g1 = valid ? P.at(kPH_GP, nl + 1) : 0;
+    if (sbytes > 0 && !bulk && valid) {
+        // hop 3 (per thread): this thread's own quads of its bus's device rows, 16-byte
+        // asynchronous copies into the same stage slots (each thread reads only its own)
+        const int sg = P.at(kPH_SG, nl), se = P.at(kPH_SE, nl), sb = P.at(kPH_SB, nl);
+        for (int q = g0; q < g1; ++q) {
+            const int slot = sg + (q - g0) * nq + pos;
+            const long long r = gt + (long long)P.at(kPH_GROW, q) * bb.Tp;
+            const int fl = P.at(kPH_GFIRM, q);
+            cp_async16(stage + slot, X.xg + r);
+            if (!(fl & 2) && (ADJ || !(fl & 1))) cp_async16(stage + qg + slot, (ADJ ? c.xg : c.cf) + r);
+        }
+        const int e0 = P.at(kPH_EP, nl), e1 = P.at(kPH_EP, nl + 1);
+        for (int q = e0; q < e1; ++q) {
+            const int e = P.at(kPH_ECODE, q);
+            const int slot = se + (q - e0) * nq + pos;
+            const long long r = bb.e_line + (long long)(e >> 1) * bb.Tp + t;
+            cp_async16(stage + 2 * qg + slot, X.dl + r);
+            cp_async16(stage + 2 * qg + qe + slot, ((e & 1) ? X.vt : X.vf) + r);
+        }
+        const int b0 = P.at(kPH_BP, nl), b1 = P.at(kPH_BP, nl + 1);
+        for (int q = b0; q < b1; ++q)
+            cp_async16(stage + 2 * qg + 2 * qe + sb + (q - b0) * nq + pos,
+                       X.xb + bb.e_bat + (long long)P.at(kPH_BROW, q) * bb.Tp + t);
+    }
+    if (ADJ && sbytes > 0 && valid) {
+        // adjoint generator masks: 4 bytes per quad, per-thread asynchronous copies
+        const int sg = P.at(kPH_SG, nl);
+        for (int q = g0; q < g1; ++q) {
+            if (RAMP && (P.at(kPH_GFIRM, q) & 2)) continue;
+            cp_async4(mstage + sg + (q - g0) * nq + pos, c.m_gen + gt + (long long)P.at(kPH_GROW, q) * bb.Tp);
+        }
+    }
+    if (sbytes > 0 && !bulk) cp_async_wait_all();
+    if (sbytes > 0 && bulk) {
+        bool ok = false;
+        for (int k = 0; k < kWaitProbes && !ok; ++k) ok = mbar_try(&bar, 0);
+        if (!ok) {
+            // the copies did not land: report, give them one more bounded wait, and leave
+            // without touching the iterate
+            if (threadIdx.x == 0) atomicExch(c.err, GX_ERR_TIMEOUT);
+            for (int k = 0; k < kWaitProbes && !ok; ++k) ok = mbar_try(&bar, 0);
+            if (ADJ) cp_async_wait_all();
+            return;
+        }
+        if (ADJ) cp_async_wait_all();
+    }
+    float acc[kBusPart] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (valid) {
+        const bool stg = sbytes > 0;
+        const float rho = c.rho, eps = c.eps;
+        const float inv_re = 1.f / (rho + eps);
+        bool hv[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) hv[h] = t + h < bb.T;
+        float sum[4] = {0.f, 0.f, 0.f, 0.f}, dx2[4] = {0.f, 0.f, 0.f, 0.f};
+        float x2 = 0.f, gscale = 0.f;
+        const int e0 = P.at(kPH_EP, nl), e1 = P.at(kPH_EP, nl + 1);
+        const int b0 = P.at(kPH_BP, nl), b1 = P.at(kPH_BP, nl + 1);
+        const int sg = stg ? P.at(kPH_SG, nl) : 0, se = stg ? P.at(kPH_SE, nl) : 0, sb = stg ? P.at(kPH_SB, nl) : 0;
+        for (int q = g0; q < g1; ++q) {
+            const int slot = sg + (q - g0) * nq + pos;
+            const long long r = gt + (long long)P.at(kPH_GROW, q) * bb.Tp;
+            float x[4], a[4], xn[4];
+            int mg[4] = {0, 0, 0, 0};
+            const bool rampg = RAMP && (P.at(kPH_GFIRM, q) & 2);
+            if (stg) {
+                const float4 v = stage[slot];
+                x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+            } else {
+                ld4(X.xg + r, x);
+            }
+            if (rampg) {
+                // ramp-limited: the ramp kernel wrote this iteration's injection (and keeps
+                // its own residual terms); the bus only sums it
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    sum[h] += x[h];
+                    x2 += x[h] * x[h];
+                }
+                continue;
+            }
+            if (ADJ || !(P.at(kPH_GFIRM, q) & 1)) {
+                if (stg) {
+                    const float4 v = stage[qg + slot];
+                    a[0] = v.x; a[1] = v.y; a[2] = v.z; a[3] = v.w;
+                } else {
+                    ld4((ADJ ? c.xg : c.cf) + r, a);
+                }
+            } else {
+                a[0] = a[1] = a[2] = a[3] = 1.f;
+            }
+            if (ADJ) {
+                if (stg) {
+                    const uint32_t m = mstage[slot];
+                    mg[0] = m & 0xff; mg[1] = (m >> 8) & 0xff; mg[2] = (m >> 16) & 0xff; mg[3] = m >> 24;
+                } else {
+                    ldm4(c.m_gen + r, mg);
+                }
+            }
+            const float gcost = P.atf(kPH_GCOST, q);
+            const float etag = ADJ ? 0.f : P.atf(kPH_GETA, q);
+            const float gemis = ADJ ? P.atf(kPH_GEMIS, q) : 0.f;
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const float v = x[h] - pb[h] - uu[h];
+                if (ADJ) {
+                    const float gh = gcost + eps * a[h] + c.kappa * gemis;
+                    const bool fixed = mg[h] != 0;
+                    xn[h] = fixed ? 0.f : (rho * v + gh) * inv_re;
+                    if (!fixed && hv[h]) gscale += (gh * inv_re) * (gh * inv_re);
+                } else {
+                    const float cap = a[h] * etag;
+                    const float pun = (rho * v - gcost) * inv_re;
+                    xn[h] = clampf(pun, 0.f, cap);
+                }
+                if (!hv[h]) xn[h] = 0.f;
+                sum[h] += xn[h];
+                dx2[h] += (xn[h] - x[h]) * (xn[h] - x[h]);
+                x2 += xn[h] * xn[h];
+            }
+            st4(X.xg + r, xn);
+        }
+        {
+            float xn[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const float v = xl[h] - pb[h] - uu[h];
+                if (ADJ) {
+                    const float gsh = c.voll + eps * (xlf[h] + Ld[h]);
+                    const bool fixed = ml[h] != 0;
+                    xn[h] = fixed ? 0.f : (rho * v + gsh) * inv_re;
+                    if (!fixed && hv[h]) gscale += (gsh * inv_re) * (gsh * inv_re);
+                } else {
+                    const float sun = (rho * (v + Ld[h]) - c.voll) * inv_re;
+                    xn[h] = clampf(sun, 0.f, Ld[h]) - Ld[h];
+                }
+                if (!hv[h]) xn[h] = 0.f;
+                sum[h] += xn[h];
+                dx2[h] += (xn[h] - xl[h]) * (xn[h] - xl[h]);
+                x2 += xn[h] * xn[h];
+            }
+            st4(X.xl + i, xn);
+        }
+        for (int q = b0; q < b1; ++q) {
+            float xb[4];
+            if (stg) {
+                const float4 v = stage[2 * qg + 2 * qe + sb + (q - b0) * nq + pos];
+                xb[0] = v.x; xb[1] = v.y; xb[2] = v.z; xb[3] = v.w;
+            } else {
+                ld4(X.xb + bb.e_bat + (long long)P.at(kPH_BROW, q) * bb.Tp + t, xb);
+            }
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                sum[h] += xb[h];
+                x2 += xb[h] * xb[h];
+            }
+        }
+        float ths[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int q = e0; q < e1; ++q) {
+            const int e = P.at(kPH_ECODE, q);
+            float d[4], qv[4];
+            if (stg) {
+                const int slot = se + (q - e0) * nq + pos;
+                const float4 v = stage[2 * qg + slot], w4 = stage[2 * qg + qe + slot];
+                d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
+                qv[0] = w4.x; qv[1] = w4.y; qv[2] = w4.z; qv[3] = w4.w;
+            } else {
+                const long long r = bb.e_line + (long long)(e >> 1) * bb.Tp + t;
+                ld4(X.dl + r, d);
+                ld4((e & 1) ? X.vt + r : X.vf + r, qv);
+            }
+            const float beta = P.atf(kPH_EBETA, q), w = P.atf(kPH_EW, q);
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const float pp = (e & 1) ? beta * d[h] : -beta * d[h];
+                sum[h] += pp;
+                x2 += pp * pp;
+                ths[h] += w * qv[h];
+            }
+        }
+        const float icnt = P.atf(kPH_IC, nl), iws = P.atf(kPH_IW, nl), drw = P.atf(kPH_DR, nl);
+        const float cnt = 1.f / icnt;
+        float pbn[4], un[4], thn[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            pbn[h] = sum[h] * icnt;
+            thn[h] = ths[h] * iws;
+            un[h] = uu[h] + pbn[h];
+            if (hv[h]) {
+                const float dpb = pbn[h] - pb[h];
+                acc[0] += cnt * pbn[h] * pbn[h];
+                acc[2] += dx2[h] - cnt * dpb * dpb;
+                acc[3] += (thn[h] - thold[h]) * (thn[h] - thold[h]) * drw;
+                acc[4] += cnt * (rho * un[h]) * (rho * un[h]);
+            }
+        }
+        acc[1] = gscale;
+        acc[5] = x2;
+        st4(X.pbar + i, pbn);
+        st4(X.u + i, un);
+        st4(X.thb + i, thn);
+    }
+    if (want_res) {
+        __shared__ float sh[kBusPart][kQBlock / 32];
+        block_sum<kBusPart, kQBlock>(acc, sh);
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int q = 0; q < kBusPart; ++q) c.bus_part[blockIdx.x * kBusPart + q] = acc[q];
+            if (stamp) stamp_end(c, 0);
+        }
+    }
+}
+
 // Write each generator's plan value max(eta_g, 0) into the pool records (once per call).
 __global__ void k_prep(const Ctx c) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1104,6 +1445,14 @@ __global__ void k_tick(int* ctr, int chunk) {
 __global__ void __launch_bounds__(kBlock) k_reduce(const Ctx c, int adj, double tol) {
     const int s = blockIdx.x;
     if (c.done[s]) return;
+    if (*c.err != 0) {  // a bounded wait in this chunk gave up: stop with its status
+        if (threadIdx.x == 0) {
+            c.status[s] = *c.err;
+            c.done[s] = 1;
+            (adj ? c.adj_iters : c.iters)[s] = *c.iter_ctr;
+        }
+        return;
+    }
     // timing on: the chunk's sampled iteration worked for this scenario
     if (c.prof_act != nullptr && threadIdx.x == 0) c.prof_act[s] += 1;
     const int it = *c.iter_ctr;
@@ -1441,7 +1790,7 @@ int launch_bat(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st) {
     if (mode == M_INIT || c.n_bat_warps <= 0) return 0;
     const int grid = (c.n_bat_warps + kBatWarps - 1) / kBatWarps;
     const int hpl = (c.max_bat_T + 31) / 32;
-    if ((mode == M_FWD || mode == M_ADJ) && hpl > 3) {
+    if ((mode == M_FWD || mode == M_ADJ) && hpl > 3 && c.bat_warps == 2) {
         const int grid2 = c.n_bat_warps;  // one battery (two warps) per block
         const int h2 = (c.max_bat_T + 63) / 64;
         if (adj) {
@@ -1469,7 +1818,16 @@ int launch_dev(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st) {
 int launch_bus(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st) {
     if (c.n_bus_blk <= 0) return 0;
     if (mode == M_FWD || mode == M_ADJ) {
-        if (c.n_ramp_warps > 0) {
+        const int sm = c.bus4_smem;
+        if (c.bus_staged != 0) {
+            if (c.n_ramp_warps > 0) {
+                if (adj) k_bus4t<1, 1><<<c.n_bus4_blk, kQBlock, sm, st>>>(c, want_res);
+                else k_bus4t<0, 1><<<c.n_bus4_blk, kQBlock, sm, st>>>(c, want_res);
+            } else {
+                if (adj) k_bus4t<1, 0><<<c.n_bus4_blk, kQBlock, sm, st>>>(c, want_res);
+                else k_bus4t<0, 0><<<c.n_bus4_blk, kQBlock, sm, st>>>(c, want_res);
+            }
+        } else if (c.n_ramp_warps > 0) {
             if (adj) k_bus4<1, 1><<<c.n_bus4_blk, kQBlock, 0, st>>>(c, want_res);
             else k_bus4<0, 1><<<c.n_bus4_blk, kQBlock, 0, st>>>(c, want_res);
         } else {
@@ -1480,6 +1838,18 @@ int launch_bus(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st) {
     }
     GX_DISPATCH_MODE_SETUP(k_bus, c.n_bus_blk, c, want_res);
     return 1;
+}
+
+cudaError_t bus_staged_prepare(int smem) {
+    cudaError_t e = cudaSuccess;
+    auto set = [&](const void* f) {
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    };
+    set((const void*)k_bus4t<0, 0>);
+    set((const void*)k_bus4t<1, 0>);
+    set((const void*)k_bus4t<0, 1>);
+    set((const void*)k_bus4t<1, 1>);
+    return e;
 }
 
 int launch_prep(const Ctx& c, cudaStream_t st) {

@@ -56,6 +56,10 @@ class Opts(C.Structure):
                 ("adj_rho_theta_c", C.c_double), ("adj_rho_inner_c", C.c_double)]
 
 
+class Schedule(C.Structure):
+    _fields_ = [("bus_staged", C.c_int), ("bat_warps", C.c_int)]
+
+
 class Stats(C.Structure):
     _fields_ = [("iters_max", C.c_int), ("n_converged", C.c_int), ("n_scen", C.c_int), ("launches", C.c_int),
                 ("max_primal", C.c_double), ("max_dual", C.c_double)]
@@ -88,6 +92,8 @@ _SIGS = {
     "gx_profile_enable": (C.c_int, [_vp, C.c_int]),
     "gx_network_use_graphs": (C.c_int, [_vp, C.c_int]),
     "gx_network_use_persistent": (C.c_int, [_vp, C.c_int]),
+    "gx_network_set_schedule": (C.c_int, [_vp, C.POINTER(Schedule)]),
+    "gx_network_get_schedule": (C.c_int, [_vp, C.POINTER(Schedule)]),
     "gx_network_persistent_info": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int)]),
     "gx_profile_read": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
     "gx_profile_active": (C.c_int, [_vp, C.POINTER(C.c_longlong)]),
@@ -308,6 +314,21 @@ class Network:
         residual-check chunk (device_loop=False), or kernel by kernel (on=False)."""
         mode = 0 if not on else (2 if device_loop else 1)
         _check(_lib.gx_network_use_graphs(self._h, mode), "gx_network_use_graphs", False)
+
+    def set_schedule(self, bus_staged=None, bat_warps=None):
+        """Kernel schedule (gx_network_set_schedule); None keeps a field as it is."""
+        sc = Schedule()
+        _check(_lib.gx_network_get_schedule(self._h, C.byref(sc)), "gx_network_get_schedule", False)
+        if bus_staged is not None:
+            sc.bus_staged = int(bus_staged)
+        if bat_warps is not None:
+            sc.bat_warps = int(bat_warps)
+        _check(_lib.gx_network_set_schedule(self._h, C.byref(sc)), "gx_network_set_schedule", False)
+
+    def schedule(self):
+        sc = Schedule()
+        _check(_lib.gx_network_get_schedule(self._h, C.byref(sc)), "gx_network_get_schedule", False)
+        return {"bus_staged": sc.bus_staged, "bat_warps": sc.bat_warps}
 
     def use_persistent(self, on=True):
         """Cluster-resident persistent launches for the scenarios that fit (default) or the

@@ -1,9 +1,12 @@
-"""The autotuner picks a setting that meets the accuracy guard and caches it."""
+"""The autotuner picks settings that meet the accuracy guard, caches them per shape bucket,
+and picks kernel schedules by time: a workspace that streams from HBM takes a staged bus
+kernel (device rows brought in by bulk or asynchronous copies)."""
 import json
 
+import numpy as np
 import pytest
 
-from gpu_util import gpu_net
+from gpu_util import eta_tensor, gpu_net
 from paper_2410_13055_gb300 import autotune, synth
 
 pytestmark = pytest.mark.gpu
@@ -26,3 +29,23 @@ def test_autotune_tiny_caches_a_valid_setting(tmp_path):
     net2 = gpu_net(nets, scens)
     assert autotune.load(net2, cache) == best
     assert abs(net2.opts.rho - best["rho"]) < 1e-12
+    assert net2.schedule() == {k: best[k] for k in autotune.SCHEDULE}
+
+
+def test_schedule_by_bucket():
+    """An HBM-streaming workspace (a 2000-bus network, 8 weekly scenarios: ~0.5 GB) takes a
+    staged bus kernel; every candidate was timed; the choice is the fastest trial."""
+    net_, scens = synth.custom(2000, 3000, 8000, 500, 168, S=8, seed=11)
+    big = gpu_net([net_], scens, kappa=50.0, tol=1e-3, adj_tol=1e-3, max_iter=50000, adj_max_iter=50000)
+    assert big.schedule()["bus_staged"] == 1  # bind's default for a workspace above L2
+    rb = autotune.tune_schedule(big, eta_tensor(net_["eta_min"]), iters=100)
+    assert len(rb["trials"]) == 6
+    fastest = min(rb["trials"], key=lambda t: t["us_per_iteration"])
+    assert rb["best"] == {k: fastest[k] for k in autotune.SCHEDULE} and big.schedule() == rb["best"]
+    assert rb["best"]["bus_staged"] in (1, 2), rb
+    nets, sc = synth.medium(S=4, T=48)
+    small = gpu_net(nets, sc, kappa=50.0, tol=1e-3, adj_tol=1e-3, max_iter=50000, adj_max_iter=50000)
+    assert small.schedule()["bus_staged"] == 0  # L2-resident
+    rs = autotune.tune_schedule(small, eta_tensor(nets[0]["eta_min"]), iters=100)
+    assert small.schedule() == rs["best"]
+    assert np.all([t["us_per_iteration"] > 0 for t in rs["trials"] + rb["trials"]])
