@@ -137,6 +137,52 @@ def tune_schedule(net: gx.Network, eta, iters=200, space=None, log=None):
     return dict(best=best, trials=trials, iterations=n)
 
 
+def tune_schedule_step(net: gx.Network, eta_next, reps=2, space=None, log=None):
+    """Pick the fastest kernel schedule on the workload's own step: from the current
+    (previous plan's) forward and adjoint state, each candidate solves at `eta_next` and
+    differentiates, warm-started ("prev"), `reps` times from the same restored state (the
+    first run of a candidate also captures its graphs); the state is restored at the end.
+    Unlike `tune_schedule`, this times the step's real mix of launches, including the
+    ones where most scenarios have converged.  Returns dict(best=..., trials=[...])."""
+    space = space or SCHEDULE
+    sx, sa = net.state(False).clone(), net.state(True).clone()
+    cands = [dict(bus_staged=b, bat_warps=w) for b in space["bus_staged"] for w in space["bat_warps"]]
+    trials = []
+    for cand in cands:
+        net.set_schedule(**cand)
+        best_ms = None
+        for _ in range(reps):
+            net.state(False).copy_(sx)
+            net.state(True).copy_(sa)
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            net.solve(eta_next, warm="prev")
+            net.grad(eta_next, warm="prev")
+            b.record()
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            best_ms = ms if best_ms is None else min(best_ms, ms)
+        trials.append(dict(cand, ms_per_step=round(best_ms, 4), iterations=(net.last_stats["iters_max"],
+                                                                           net.last_grad_stats["iters_max"])))
+        if log:
+            log(trials[-1])
+    best = min(trials, key=lambda t: t["ms_per_step"])
+    best = {k: best[k] for k in SCHEDULE}
+    net.set_schedule(**best)
+    # one more run captures the chosen schedule's graphs, so the caller's next step is not
+    # charged for it; then the state goes back to the previous plan's
+    net.state(False).copy_(sx)
+    net.state(True).copy_(sa)
+    net.solve(eta_next, warm="prev")
+    net.grad(eta_next, warm="prev")
+    net.state(False).copy_(sx)
+    net.state(True).copy_(sa)
+    torch.cuda.synchronize()
+    return dict(best=best, trials=trials)
+
+
 def tune(net: gx.Network, nets, steps=3, h_tol=2e-3, g_slack=1.25, cache=None, log=None, alpha_frac=1e-2):
     """Tune `net`'s options in place; returns the chosen option dict."""
     cache = cache or default_cache_path()

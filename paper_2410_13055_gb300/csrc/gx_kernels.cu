@@ -1086,10 +1086,11 @@ __global__ void __launch_bounds__(kQBlock, 4) k_bus4(const Ctx c, int want_res) 
 // same summation order (its iterates are bitwise those of k_bus4), with the block's device
 // rows brought into shared memory first.  In k_bus4 a thread walks its bus's devices with
 // one generator's loads in flight at a time, so a block waits for about 4 + (generators
-// per bus) dependent memory round trips.  Here warp 0 issues one bulk copy per device row
-// segment of the block (cp.async.bulk, completing on one mbarrier; the copy list is built
-// at create, in the pool record), so every row the block needs is in flight at once and
-// the block waits for three hops: its record, its bus state and the record, the rows.
+// per bus) dependent memory round trips.  Here the block issues one bulk copy per device
+// row segment (cp.async.bulk, completing on one mbarrier armed by thread 0; the copy list
+// is built at create, in the pool record), so every row the block needs is in flight at once and
+// the block waits for three hops: its block record; its pool record and the done flag; its
+// bus state and the rows together (a converged scenario's blocks stop after the second).
 // Adjoint generator masks (one byte per hour: not 16-byte aligned) come with per-thread
 // 4-byte asynchronous copies.  A record too large for the stage runs the unstaged loads.
 // ------------------------------------------------------------------------------------
@@ -1148,7 +1149,7 @@ __global__ void __launch_bounds__(kQBlock, 4) k_bus4t(const Ctx c, int want_res)
     if (stamp && threadIdx.x == 0) stamp_start(c, 0);
     const BusBlk bb = c.bus4_blk[blockIdx.x];
     const StatePtrs X = state<ADJ>(c);
-    // hop 2: the record, this thread's bus state and the done flag, all in flight together
+    // hop 2: the record and the done flag, in flight together
     const bool rec_smem = bb.words <= kPoolMax;
     if (rec_smem) {
         const int4* src = reinterpret_cast<const int4*>(c.pool + bb.pool);
@@ -1161,13 +1162,6 @@ __global__ void __launch_bounds__(kQBlock, 4) k_bus4t(const Ctx c, int want_res)
     const int t = (local - n * Tq) * 4;
     const bool valid = local < bb.nitems;
     const long long i = bb.e_bus + (long long)n * bb.Tp + t;
-    float pb[4], uu[4], thold[4], xl[4], Ld[4], xlf[4];
-    int ml[4] = {0, 0, 0, 0};
-    if (valid) {
-        ld4(X.pbar + i, pb); ld4(X.u + i, uu); ld4(X.thb + i, thold);
-        ld4(X.xl + i, xl); ld4(c.load + i, Ld);
-        if (ADJ) { ld4(c.xl + i, xlf); ldm4(c.m_load + i, ml); }
-    }
     const int done = c.done[bb.s];
     const bool bulk = c.bus_staged == 1;
     if (threadIdx.x == 0 && bulk && rec_smem) {
@@ -1179,7 +1173,15 @@ __global__ void __launch_bounds__(kQBlock, 4) k_bus4t(const Ctx c, int want_res)
         if (hdr[kPH_SBYTES] > 0) mbar_expect_tx(&bar, (unsigned)hdr[ADJ ? kPH_TXA : kPH_TXF]);
     }
     __syncthreads();
-    if (done) return;  // block-uniform
+    if (done) return;  // block-uniform: a converged scenario's blocks stop after two hops
+    // hop 3: this thread's bus state, in flight together with the row copies below
+    float pb[4], uu[4], thold[4], xl[4], Ld[4], xlf[4];
+    int ml[4] = {0, 0, 0, 0};
+    if (valid) {
+        ld4(X.pbar + i, pb); ld4(X.u + i, uu); ld4(X.thb + i, thold);
+        ld4(X.xl + i, xl); ld4(c.load + i, Ld);
+        if (ADJ) { ld4(c.xl + i, xlf); ldm4(c.m_load + i, ml); }
+    }
     const Pool P{rec_smem ? S : c.pool + bb.pool};
     const int sbytes = P.p[kPH_SBYTES];
     float4* stage = reinterpret_cast<float4*>(S + bb.words);
