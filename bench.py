@@ -401,8 +401,11 @@ def measure(config, args, steps, warmup, dist=None, learned=False, cold=True, sc
 
 
 def measure_learned(net, eta, grad, gamma, eta_min, eta_max, alpha, flush, dh, steps, dev):
-    """The learned start: the graph network trained by paper_2410_13055_gb300.train_warmstart
-    on this network (weights in paper_2410_13055_gb300/weights/), prediction included."""
+    """The learned start through the C ABI (GX_WARM_LEARNED): the graph network trained by
+    paper_2410_13055_gb300.train_warmstart on this network (weights in
+    paper_2410_13055_gb300/weights/), its prediction inside the solve, and the selection
+    rule (per scenario, the learned start or the previous plan's state, whichever has the
+    smaller residual at the first check).  Same plan steps as the headline's."""
     import torch
     from paper_2410_13055_gb300 import gx
     wpath = os.path.join(ROOT, "paper_2410_13055_gb300", "weights", "warmstart_medium.npy")
@@ -410,25 +413,27 @@ def measure_learned(net, eta, grad, gamma, eta_min, eta_max, alpha, flush, dh, s
         return None
     gnn = gx.WarmStartGNN(net, seed=0)
     gnn.set_params(np.load(wpath))
-    wbuf = torch.empty(2 * gnn.M, dtype=torch.float32, device=dev)
-    Mh = gnn.M
+    net.attach_gnn(gnn)
     eta_l = eta.clone()
-    it_l, ms_l = [], []
+    it_l, ms_l, kept = [], [], []
     torch.cuda.synchronize()
     for _ in range(max(1, min(steps, 5))):
         flush.fill_(1.0)
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record()
-        gnn.predict(eta_l, out=wbuf)
-        net.solve(eta_l, warm="user", warm_prices=wbuf[:Mh], warm_angles=wbuf[Mh:])
+        net.solve(eta_l, warm="learned")
         it_l.append(net.last_stats["iters_max"])
         net.grad(eta_l, out=grad, warm="prev")
         net.plan_step(eta_l, grad, gamma, eta_min, eta_max, alpha)
         b.record()
         torch.cuda.synchronize()
         ms_l.append(a.elapsed_time(b))
+        kept.append(float(np.mean(net.array("warm").cpu().numpy() == 1)))
+    net.attach_gnn(None)
     return {"value": round(dh / (float(np.mean(ms_l)) / 1e3), 1), "fwd_iters_median": float(np.median(it_l)),
+            "kept_learned_fraction": round(float(np.mean(kept)), 4),
+            "rule": "GX_WARM_LEARNED: per scenario, learned start or previous plan's by the first check's residual",
             "weights": "paper_2410_13055_gb300/weights/warmstart_medium.npy"}
 
 

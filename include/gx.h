@@ -166,8 +166,11 @@ enum {
     GX_ARR_STATUS = 12,  /* [S] int32 per-scenario gx_status of the last solve */
     GX_ARR_GRAD_S = 13,  /* [sum_s K_net(s)] FP64 per-scenario dh_s/deta of the last grad */
     GX_ARR_ADJ_ITERS = 14, /* [S] int32 adjoint iterations */
-    GX_ARR_OBJ = 15      /* [1] FP64 sum_{s in batch} w'_s h_s of the last solve: the operating
+    GX_ARR_OBJ = 15,     /* [1] FP64 sum_{s in batch} w'_s h_s of the last solve: the operating
                             term of Eq. 1 (w'_s as in gx_dispatch_grad_batch); scen must be -1 */
+    GX_ARR_WARM = 16     /* [S] int32 start each scenario kept in the last solve: 1 the learned
+                            start, 0 the previous plan's (GX_WARM_LEARNED's selection rule),
+                            -1 not a learned solve or outside the batch */
 };
 
 typedef struct {
@@ -220,7 +223,13 @@ gx_status gx_network_scenario_info(const gx_network* net, int s, int* T, int* Tp
  * state of the previous solve), GX_WARM_USER (initial prices and angles from
  * warm_dev: [sum_s N_s Tp_s] prices followed by the same size of angles, in
  * scenario order of the whole network; generators and loads start at their best
- * response to those prices, line flows from the angle differences).  Outputs stay in
+ * response to those prices, line flows from the angle differences), GX_WARM_LEARNED (the
+ * network attached with gx_network_attach_gnn predicts the prices and angles at eta_dev,
+ * applied as a user start; when a previous solution exists, every scenario first runs one
+ * residual-check chunk from the previous plan's state and one from the learned start and
+ * keeps the one with the smaller residual at its check (GX_ARR_WARM records the choice), the
+ * loop then continuing from iteration check_every; without an attached network,
+ * GX_ERR_STATE).  Outputs stay in
  * the workspace (GX_ARR_*), including GX_ARR_OBJ, the batch's weighted planner value.
  * Synchronises `stream` once at the end of the iteration loop (per residual-check chunk
  * in launch modes 1 and 0).  Returns GX_NOT_CONVERGED if any scenario of the batch
@@ -334,6 +343,11 @@ gx_status gx_gnn_predict(gx_gnn* gnn, const float* eta_dev, float* out_dev, void
 gx_status gx_gnn_train_step(gx_gnn* gnn, const float* eta_dev, const float* target_dev, float lr, float w_theta,
                             double* loss_host, void* stream);
 gx_status gx_gnn_destroy(gx_gnn* gnn);
+/* Attach (gnn != NULL) or detach (NULL) the learned start of GX_WARM_LEARNED.  The warm-
+ * start network must have been created for `net`, be bound, and outlive the attachment; its
+ * workspace also holds the forward state while a learned solve compares the two starts.
+ * Errors: GX_ERR_INVALID_ARG for a network created for another one. */
+gx_status gx_network_attach_gnn(gx_network* net, gx_gnn* gnn);
 
 /* Operating cost c_s and planner value h_s of scenario `scen` at the last solve,
  * computed without allocating any device memory.  The paper has no counterpart; this

@@ -414,6 +414,10 @@ struct gx_gnn {
     // offsets
     size_t o_P, o_G, o_m1, o_m2, o_win_t, o_wk_t, o_wk, o_X, o_Z0, o_Hs, o_Zs, o_Agg, o_Y, o_dY, o_dH, o_dZ, o_dCat,
         o_dAgg, o_loss;
+    // the network's learned start (GX_WARM_LEARNED): the prediction in the layout of a user
+    // start, and room for the network's forward iteration state and per-scenario flags
+    // while the solve compares the learned start with the previous plan's
+    size_t o_pred, o_save, save_bytes;
     int step = 0;
 };
 
@@ -464,6 +468,11 @@ gx_status gx_gnn_create(const gx_network* net, int hidden, int layers, gx_gnn** 
     g->o_dCat = lay_add(t, 4 * (size_t)M * 2 * kH);
     g->o_dAgg = lay_add(t, 4 * (size_t)M * kH);
     g->o_loss = lay_add(t, 8);
+    g->o_pred = lay_add(t, 4 * (size_t)M * 2);
+    size_t so = 0, sb = 0;
+    gx_network_state_range(net, 0, &so, &sb);
+    g->save_bytes = sb + 4 * 8 * (size_t)c->S;  // state, then done / status / iters / resid per scenario
+    g->o_save = lay_add(t, g->save_bytes);
     g->bytes = t;
     *out = g;
     return GX_OK;
@@ -560,6 +569,29 @@ gx_status gx_gnn_predict(gx_gnn* g, const float* eta_dev, float* out_dev, void* 
     if (e != cudaSuccess) return gx_internal_fail(GX_ERR_CUDA, std::string("gnn predict: ") + cudaGetErrorString(e));
     return GX_OK;
 }
+
+}  // extern "C"
+
+namespace gx {
+const gx_network* gx_gnn_internal_net(const gx_gnn* g) { return g ? g->net : nullptr; }
+gx_status gx_gnn_internal_predict(gx_gnn* g, const float* eta, cudaStream_t st, const float** pred) {
+    if (!g || !g->dev) return gx_internal_fail(GX_ERR_STATE, "the attached warm-start network is not bound");
+    gnn_forward(g, eta, st);
+    float* out = reinterpret_cast<float*>(g->dev + g->o_pred);
+    k_unpack<<<(unsigned)((g->M + 255) / 256), 256, 0, st>>>(reinterpret_cast<float*>(g->dev + g->o_Y), out, g->M);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return gx_internal_fail(GX_ERR_CUDA, std::string("gnn predict: ") + cudaGetErrorString(e));
+    *pred = out;
+    return GX_OK;
+}
+uint8_t* gx_gnn_internal_scratch(gx_gnn* g, size_t* bytes) {
+    if (!g || !g->dev) return nullptr;
+    *bytes = g->save_bytes;
+    return g->dev + g->o_save;
+}
+}  // namespace gx
+
+extern "C" {
 
 gx_status gx_gnn_train_step(gx_gnn* g, const float* eta_dev, const float* target_dev, float lr, float w_theta,
                             double* loss_host, void* stream) {

@@ -120,7 +120,7 @@ struct gx_network {
     size_t o_f[16], o_a[16];  // forward / adjoint state arrays, order of StatePtrs
     size_t o_fend, o_aend;    // end of the forward / adjoint state range (ramp arrays included)
     size_t o_mgen, o_mload, o_mline, o_mbat;
-    size_t o_done, o_iters, o_status, o_adjit, o_nact, o_ctr, o_inb, o_err, o_resid, o_rbest, o_cost, o_h, o_grads, o_wprime, o_obj, o_stlo, o_sthi, o_pact;
+    size_t o_done, o_iters, o_status, o_adjit, o_nact, o_ctr, o_inb, o_err, o_wsel, o_resid, o_rbest, o_cost, o_h, o_grads, o_wprime, o_obj, o_stlo, o_sthi, o_pact;
     size_t o_flow, o_price, o_shed, o_bpart, o_lpart, o_btpart, o_cpart;
     Layout lay;
     // binding
@@ -144,6 +144,7 @@ struct gx_network {
     int use_graphs = 2;     // 0 eager launches, 1 one graph per chunk, 2 the whole loop as one graph
     gx_schedule sched{1, 2};  // kernel schedule (gx_network_set_schedule)
     bool sched_set = false;   // the caller chose the schedule (else bind picks it by workspace size)
+    gx_gnn* gnn = nullptr;    // learned start (gx_network_attach_gnn)
     void drop_graphs() {
         for (auto& g : graphs) {
             if (g.exec) cudaGraphExecDestroy(g.exec);
@@ -972,6 +973,7 @@ gx_status gx_network_create(const gx_network_desc* nets, int n_nets, const gx_sc
     net->o_mgen = L.add(B1(eg)); net->o_mload = L.add(B1(eb)); net->o_mline = L.add(B1(el)); net->o_mbat = L.add(B1(ebt));
     net->o_done = L.add(I4(S)); net->o_iters = L.add(I4(S)); net->o_status = L.add(I4(S)); net->o_adjit = L.add(I4(S));
     net->o_nact = L.add(I4(1)); net->o_ctr = L.add(I4(1)); net->o_inb = L.add(I4(S)); net->o_err = L.add(I4(1));
+    net->o_wsel = L.add(I4(S));
     net->o_resid = L.add(D8(2LL * S)); net->o_rbest = L.add(D8(S)); net->o_cost = L.add(D8(S)); net->o_h = L.add(D8(S));
     net->o_grads = L.add(D8(gs)); net->o_wprime = L.add(D8(S)); net->o_obj = L.add(D8(1));
     net->o_stlo = L.add(D8(3LL * kStampSlots)); net->o_sthi = L.add(D8(3LL * kStampSlots)); net->o_pact = L.add(D8(S));
@@ -1152,6 +1154,7 @@ gx_status gx_network_array(const gx_network* net, int which, int scen, size_t* o
         case GX_ARR_GRAD_S: base = net->o_grads; esz = 8;
             rows(net->gs_total, sd ? sd->gs0 : 0, sd ? (long long)(sd->G + sd->L + sd->B) : 0); break;
         case GX_ARR_ADJ_ITERS: base = net->o_adjit; rows(net->S, scen, 1); break;
+        case GX_ARR_WARM: base = net->o_wsel; rows(net->S, scen, 1); break;
         case GX_ARR_OBJ:
             if (scen != -1) return fail(GX_ERR_INVALID_ARG, "GX_ARR_OBJ is one value for the batch (scen = -1)");
             base = net->o_obj; esz = 8; e0 = 0; n = 1; break;
@@ -1354,13 +1357,14 @@ static gx_status run_crs(gx_network* net, int adj, cudaStream_t st, int* launche
 // from graph-recorded events).
 static gx_status read_stamps(gx_network* net, int nchunks, cudaStream_t st);
 
-static gx_status run_loop(gx_network* net, int adj, cudaStream_t st, int* launches, int* iters_out) {
+static gx_status run_loop(gx_network* net, int adj, cudaStream_t st, int* launches, int* iters_out, int it0 = 0) {
     const Ctx& c = adj ? net->actx : net->ctx;
     const int max_it = adj ? net->opts.adj_max_iter : net->opts.max_iter;
     const int every = net->opts.check_every;
     const int per_it = (c.n_line_blk > 0) + (c.n_bat_warps > 0) + (c.n_ramp_warps > 0) + (c.n_bus_blk > 0);
-    int it = 0;
+    int it = it0;  // iterations already run (the learned start's trial chunk)
     GX_CUDA(cudaMemsetAsync(c.iter_ctr, 0, sizeof(int), st));
+    if (it0 > 0) *launches += launch_tick(c, it0, st);
     if (net->use_graphs == 2 && max_it % every == 0) {
         cudaGraphExec_t exec = nullptr;
         if (gx_status e = loop_graph(net, c, adj, every, max_it, &exec)) return e;
@@ -1370,7 +1374,7 @@ static gx_status run_loop(gx_network* net, int adj, cudaStream_t st, int* launch
         GX_CUDA(cudaStreamSynchronize(st));
         it = net->h_nact[1];
         // per body: tick, the iterations, the reduction and the condition kernel
-        *launches += (it / every) * (3 + every * per_it);
+        *launches += ((it - it0) / every) * (3 + every * per_it);
         *iters_out = it;
         if (net->prof) {
             net->prof_launches[0] += (long long)it * (c.n_bus_blk > 0);
@@ -1499,13 +1503,67 @@ static gx_status collect_stats(gx_network* net, int adj, gx_stats* stats, int la
     return GX_OK;
 }
 
+// GX_WARM_LEARNED with a previous solution (the selection rule of the learned start): one
+// residual-check chunk from the previous plan's state, whose state and flags are saved in
+// the warm-start network's scratch; then, for the scenarios still iterating, one chunk from
+// the learned start (the prediction `pred`, applied as a user start); each scenario keeps
+// the start with the smaller residual at its check, the others get the saved state back.
+// The main loop then continues from iteration check_every.
+static gx_status learned_trials(gx_network* net, const float* pred, cudaStream_t st, int* launches) {
+    Ctx& c = net->ctx;
+    const int every = net->opts.check_every;
+    size_t sv_bytes = 0;
+    uint8_t* sv = gx_gnn_internal_scratch(net->gnn, &sv_bytes);
+    const size_t state_bytes = net->o_fend - net->o_f[0];
+    if (!sv || sv_bytes < state_bytes + 32 * (size_t)net->S)
+        return fail(GX_ERR_STATE, "the attached warm-start network does not belong to this network");
+    int* sdone = reinterpret_cast<int*>(sv + state_bytes);
+    int* sstatus = sdone + net->S;
+    int* siters = sstatus + net->S;
+    double* sres = reinterpret_cast<double*>(siters + net->S + (net->S & 1));  // 8-byte aligned
+    // trial 1: the previous plan's state
+    GX_CUDA(cudaMemsetAsync(c.iter_ctr, 0, sizeof(int), st));
+    if (gx_status e = enqueue_iters(net, c, 0, every, 0, every, true, true, st, launches, false)) return e;
+    GX_CUDA(cudaMemcpyAsync(sv, net->dev + net->o_f[0], state_bytes, cudaMemcpyDeviceToDevice, st));
+    GX_CUDA(cudaMemcpyAsync(sdone, c.done, 4 * (size_t)net->S, cudaMemcpyDeviceToDevice, st));
+    GX_CUDA(cudaMemcpyAsync(sstatus, c.status, 4 * (size_t)net->S, cudaMemcpyDeviceToDevice, st));
+    GX_CUDA(cudaMemcpyAsync(siters, c.iters, 4 * (size_t)net->S, cudaMemcpyDeviceToDevice, st));
+    GX_CUDA(cudaMemcpyAsync(sres, c.resid, 16 * (size_t)net->S, cudaMemcpyDeviceToDevice, st));
+    // trial 2: the learned start (the start kernels skip scenarios trial 1 finished)
+    c.warm = pred;
+    *launches += launch_dev(c, M_RESET, 0, 0, st);
+    *launches += launch_bus(c, M_RESET, 0, 0, st);
+    *launches += launch_bus(c, M_INIT, 0, 0, st);
+    c.warm = nullptr;
+    GX_CUDA(cudaMemsetAsync(c.iter_ctr, 0, sizeof(int), st));
+    if (gx_status e = enqueue_iters(net, c, 0, every, 0, every, true, true, st, launches, false)) return e;
+    // the choice, and the previous plan's rows back where it won
+    WarmArrays w{};
+    for (int k = 0; k < 16; ++k) {
+        w.off[w.n] = (long long)((net->o_f[k] - net->o_f[0]) / 4);
+        w.kind[w.n++] = k == 0 ? 0 : (k == 1 || k >= 13) ? 1 : (k <= 5) ? 2 : 3;
+    }
+    if (net->tot_ramp > 0)
+        for (int k = 0; k < 4; ++k) {
+            w.off[w.n] = (long long)((net->o_rf[k] - net->o_f[0]) / 4);
+            w.kind[w.n++] = 4;
+        }
+    *launches += launch_warm_select(c, w, reinterpret_cast<float*>(net->dev + net->o_f[0]),
+                                    reinterpret_cast<const float*>(sv),
+                                    reinterpret_cast<const int*>(net->dev + net->o_inb), sdone, sstatus, siters, sres,
+                                    reinterpret_cast<int*>(net->dev + net->o_wsel), st);
+    return GX_OK;
+}
+
 gx_status gx_dispatch_solve_batch(gx_network* net, const float* eta_dev, const int* scen_idx, int B, int warm,
                                   const float* warm_dev, gx_stats* stats, void* stream) {
     if (!net) return fail(GX_ERR_INVALID_ARG, "net is NULL");
     if (!net->dev) return fail(GX_ERR_STATE, "network is not bound");
     if (!eta_dev) return fail(GX_ERR_INVALID_ARG, "eta_dev is NULL");
-    if (warm < GX_WARM_COLD || warm > GX_WARM_USER) return fail(GX_ERR_INVALID_ARG, "unsupported warm mode");
+    if (warm < GX_WARM_COLD || warm > GX_WARM_LEARNED) return fail(GX_ERR_INVALID_ARG, "unsupported warm mode");
     if (warm == GX_WARM_USER && !warm_dev) return fail(GX_ERR_INVALID_ARG, "GX_WARM_USER needs warm_dev");
+    if (warm == GX_WARM_LEARNED && !net->gnn)
+        return fail(GX_ERR_STATE, "GX_WARM_LEARNED needs a warm-start network (gx_network_attach_gnn)");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     GX_CUDA(cudaMemsetAsync(net->dev + net->o_err, 0, sizeof(int), st));
     if (gx_status e = upload_batch(net, scen_idx, B, st)) return e;
@@ -1524,7 +1582,25 @@ gx_status gx_dispatch_solve_batch(gx_network* net, const float* eta_dev, const i
     c.warm = warm == GX_WARM_USER ? warm_dev : nullptr;
     int launches = launch_prep(c, st);
     launches += launch_scale_prep(c, st);
-    if (warm != GX_WARM_PREV || !net->solved) {
+    GX_CUDA(cudaMemsetAsync(net->dev + net->o_wsel, 0xff, 4 * (size_t)net->S, st));  // -1: no learned start
+    const float* pred = nullptr;
+    if (warm == GX_WARM_LEARNED) {
+        if (gx_status e = gx_gnn_internal_predict(net->gnn, eta_dev, st, &pred)) return e;
+        launches += 5;
+    }
+    int it0 = 0;
+    if (warm == GX_WARM_LEARNED && net->solved) {
+        if (gx_status e = learned_trials(net, pred, st, &launches)) return e;
+        it0 = net->opts.check_every;
+    } else if (warm != GX_WARM_PREV || !net->solved) {
+        if (warm == GX_WARM_LEARNED) {
+            // no previous plan to compare with: the learned start for every scenario
+            c.warm = pred;
+            std::vector<int> one(net->S);
+            for (int s = 0; s < net->S; ++s) one[s] = net->in_batch[s] ? 1 : -1;
+            GX_CUDA(cudaMemcpyAsync(net->dev + net->o_wsel, one.data(), 4 * (size_t)net->S, cudaMemcpyHostToDevice, st));
+            GX_CUDA(cudaStreamSynchronize(st));  // `one` is pageable and local
+        }
         launches += launch_dev(c, M_RESET, 0, 0, st);
         launches += launch_bus(c, M_RESET, 0, 0, st);
         launches += launch_bus(c, M_INIT, 0, 0, st);
@@ -1533,7 +1609,7 @@ gx_status gx_dispatch_solve_batch(gx_network* net, const float* eta_dev, const i
     int it = 0, ns = 0;
     if (gx_status e = run_crs(net, 0, st, &launches, &ns)) return e;
     if (ns > 0)
-        if (gx_status e = run_loop(net, 0, st, &launches, &it)) return e;
+        if (gx_status e = run_loop(net, 0, st, &launches, &it, it0)) return e;
     launches += launch_extract(c, reinterpret_cast<const int*>(net->dev + net->o_inb), st);
     launches += launch_objective(c, reinterpret_cast<const double*>(net->dev + net->o_wprime),
                                  reinterpret_cast<double*>(net->dev + net->o_obj), st);
@@ -1629,6 +1705,14 @@ gx_status gx_network_set_schedule(gx_network* net, const gx_schedule* sched) {
 gx_status gx_network_get_schedule(const gx_network* net, gx_schedule* sched) {
     if (!net || !sched) return fail(GX_ERR_INVALID_ARG, "NULL argument");
     *sched = net->sched;
+    return GX_OK;
+}
+
+gx_status gx_network_attach_gnn(gx_network* net, gx_gnn* gnn) {
+    if (!net) return fail(GX_ERR_INVALID_ARG, "net is NULL");
+    if (gnn && gx_gnn_internal_net(gnn) != net)
+        return fail(GX_ERR_INVALID_ARG, "the warm-start network was created for another network");
+    net->gnn = gnn;
     return GX_OK;
 }
 

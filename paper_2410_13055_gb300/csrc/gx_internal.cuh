@@ -328,6 +328,19 @@ int launch_crs(const Ctx& c, int adj, const int* scen, int n, const int* in_batc
 int launch_reduce(const Ctx& c, int adj, double tol, cudaStream_t st);
 int launch_tick(const Ctx& c, int chunk, cudaStream_t st);
 int launch_extract(const Ctx& c, const int* in_batch, cudaStream_t st);
+// The forward state arrays inside the state range: float offset from the range's start and
+// row kind (0 generator, 1 bus, 2 line, 3 battery, 4 ramp rows).
+struct WarmArrays {
+    long long off[20];
+    int kind[20];
+    int n;
+};
+// GX_WARM_LEARNED's per-scenario choice after one trial chunk from each start: chosen[s] =
+// 1 learned start kept, 0 previous plan's (state rows and flags restored from `saved` and
+// the s* arrays), -1 outside the batch.
+int launch_warm_select(const Ctx& c, const WarmArrays& w, float* state, const float* saved, const int* in_batch,
+                       const int* sdone, const int* sstatus, const int* siters, const double* sres, int* chosen,
+                       cudaStream_t st);
 // obj = sum_s wprime[s] h_s (Eq. 1's operating term over the batch), FP64, fixed order.
 int launch_objective(const Ctx& c, const double* wprime, double* obj, cudaStream_t st);
 int launch_grad(const Ctx& c, int envelope, const int* gwarp_scen, int n_gwarps, const int* in_batch,
@@ -340,6 +353,15 @@ int launch_scale_grad(const Ctx& c, int envelope, const int* in_batch, cudaStrea
 int launch_plan_step(float* eta, const float* grad, const float* gamma, const float* lo, const float* hi, float alpha,
                      int K, cudaStream_t st);
 
+}  // namespace gx
+
+// The warm-start network's side of GX_WARM_LEARNED (gx_gnn.cu): its network, a prediction
+// into its own buffer ([prices | angles] over bus rows), and its scratch for the forward
+// state and per-scenario flags (nullptr if unbound).
+namespace gx {
+const gx_network* gx_gnn_internal_net(const gx_gnn* g);
+gx_status gx_gnn_internal_predict(gx_gnn* g, const float* eta, cudaStream_t st, const float** pred);
+uint8_t* gx_gnn_internal_scratch(gx_gnn* g, size_t* bytes);
 }  // namespace gx
 
 // Read-only accessors for the no-allocation entry point (gx_noalloc.cu).

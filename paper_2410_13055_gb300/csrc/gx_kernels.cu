@@ -1592,6 +1592,50 @@ __global__ void k_cost_final(const Ctx c, const int* in_batch) {
     c.hval[s] = a + (double)c.kappa * e;
 }
 
+// ------------------------------------------------------------------------------------
+// GX_WARM_LEARNED: after one residual-check chunk from the previous plan's state (saved,
+// with its flags) and one from the learned start, each scenario keeps the start whose
+// residual at that check is smaller; the losers get the saved state and flags back.
+// ------------------------------------------------------------------------------------
+__global__ void k_warm_choose(const Ctx c, const int* in_batch, const int* sdone, const int* sstatus,
+                              const int* siters, const double* sres, int* chosen) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= c.S) return;
+    if (!in_batch[s]) { chosen[s] = -1; return; }
+    const double rp = fmax(sres[2 * s], sres[2 * s + 1]);
+    const double rl = fmax(c.resid[2 * s], c.resid[2 * s + 1]);
+    // a scenario the previous plan's chunk already finished skipped the learned trial
+    const int keep = !sdone[s] && rl < rp;
+    chosen[s] = keep;
+    if (!keep) {
+        c.done[s] = sdone[s];
+        c.status[s] = sstatus[s];
+        c.iters[s] = siters[s];
+        c.resid[2 * s] = sres[2 * s];
+        c.resid[2 * s + 1] = sres[2 * s + 1];
+        c.rbest[s] = rp;
+    }
+}
+
+// Rows of scenario s in forward state array a, copied back from the saved state when the
+// previous plan's start won.  Grid (S, arrays).
+__global__ void k_warm_restore(const Ctx c, WarmArrays w, float* state, const float* saved, const int* chosen,
+                               const int* sdone) {
+    const int s = blockIdx.x, a = blockIdx.y;
+    if (chosen[s] != 0 || sdone[s]) return;  // learned kept, outside the batch, or untouched
+    const ScenDev sc = c.scen[s];
+    long long e0 = 0, n = 0;
+    switch (w.kind[a]) {
+        case 0: e0 = sc.e_gen; n = (long long)sc.G * sc.Tp; break;
+        case 1: e0 = sc.e_bus; n = (long long)sc.N * sc.Tp; break;
+        case 2: e0 = sc.e_line; n = (long long)sc.L * sc.Tp; break;
+        case 3: e0 = sc.e_bat; n = (long long)sc.B * sc.Tp; break;
+        default: e0 = sc.e_ramp; n = (long long)sc.R * sc.Tp; break;
+    }
+    const long long base = w.off[a] + e0;
+    for (long long k = threadIdx.x; k < n; k += blockDim.x) state[base + k] = saved[base + k];
+}
+
 // Eq. 1's operating term over the batch: sum_s w'_s h_s in FP64, summed by one thread in
 // scenario order so the value does not depend on the launch shape.
 __global__ void k_objective(const Ctx c, const double* wprime, double* obj) {
@@ -1876,6 +1920,14 @@ int launch_extract(const Ctx& c, const int* in_batch, cudaStream_t st) {
     k_cost<<<c.n_cost_blk, kBlock, 0, st>>>(c, in_batch);
     k_cost_final<<<(c.S + 127) / 128, 128, 0, st>>>(c, in_batch);
     return 3;
+}
+
+int launch_warm_select(const Ctx& c, const WarmArrays& w, float* state, const float* saved, const int* in_batch,
+                       const int* sdone, const int* sstatus, const int* siters, const double* sres, int* chosen,
+                       cudaStream_t st) {
+    k_warm_choose<<<(c.S + 127) / 128, 128, 0, st>>>(c, in_batch, sdone, sstatus, siters, sres, chosen);
+    k_warm_restore<<<dim3(c.S, w.n), 256, 0, st>>>(c, w, state, saved, chosen, sdone);
+    return 2;
 }
 
 int launch_objective(const Ctx& c, const double* wprime, double* obj, cudaStream_t st) {

@@ -25,9 +25,9 @@ _lib = C.CDLL(LIB_PATH)
 GX_OK, GX_NOT_CONVERGED = 0, 1
 GX_WARM = {"cold": 0, "prev": 1, "user": 2, "learned": 3}
 ARR = dict(p=0, shed=1, flow=2, theta=3, ch=4, dis=5, soc=6, price=7, cost=8, h=9, iters=10, resid=11,
-           status=12, grad_s=13, adj_iters=14, obj=15)
+           status=12, grad_s=13, adj_iters=14, obj=15, warm=16)
 _ARR_DTYPE = dict(cost="float64", h="float64", resid="float64", grad_s="float64", obj="float64", iters="int32",
-                  status="int32", adj_iters="int32")
+                  status="int32", adj_iters="int32", warm="int32")
 
 _i32p = C.POINTER(C.c_int32)
 _f64p = C.POINTER(C.c_double)
@@ -107,6 +107,7 @@ _SIGS = {
     "gx_gnn_predict": (C.c_int, [_vp, _vp, _vp, _vp]),
     "gx_gnn_train_step": (C.c_int, [_vp, _vp, _vp, C.c_float, C.c_float, C.POINTER(C.c_double), _vp]),
     "gx_gnn_destroy": (C.c_int, [_vp]),
+    "gx_network_attach_gnn": (C.c_int, [_vp, _vp]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -307,6 +308,12 @@ class Network:
         self.last_grad_stats = st.asdict()
         self.last_grad_status = rc
         return out
+
+    def attach_gnn(self, gnn):
+        """The learned start of warm="learned" (gx_network_attach_gnn); None detaches."""
+        _check(_lib.gx_network_attach_gnn(self._h, gnn._h if gnn is not None else None), "gx_network_attach_gnn",
+               False)
+        self._gnn = gnn  # keeps it alive while attached
 
     def use_graphs(self, on=True, device_loop=True):
         """Launch mode of the per-iteration kernels (gx_network_use_graphs): the whole loop

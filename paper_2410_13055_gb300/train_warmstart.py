@@ -64,26 +64,35 @@ def main(argv=None):
     ap.add_argument("--pairs", type=int, default=20)
     ap.add_argument("--costs", type=int, default=13)
     ap.add_argument("--w-theta", type=float, default=0.1)
+    ap.add_argument("--weights", default=None, help="evaluate these parameters instead of training")
     args = ap.parse_args(argv)
     t0 = time.time()
     nets, scens, net = build()
-    costs = list(np.linspace(100.0, 400.0, args.costs))
-    samples = make_dataset(net, nets, costs, steps=8, keep_every=2, n_perturb=2, sigma=0.1, seed=100)
-    t_data = time.time() - t0
     gnn = gx.WarmStartGNN(net, seed=7)
-    t1 = time.time()
-    hist = train(gnn, samples, epochs=args.epochs, lr=args.lr, w_theta=args.w_theta,
-                 log=lambda m: print(m, flush=True))
-    torch.cuda.synchronize()
-    t_train = time.time() - t1
+    samples, hist, t_data, t_train = [], [float("nan")], 0.0, 0.0
+    if args.weights:
+        gnn.set_params(np.load(args.weights))
+    else:
+        costs = list(np.linspace(100.0, 400.0, args.costs))
+        samples = make_dataset(net, nets, costs, steps=8, keep_every=2, n_perturb=2, sigma=0.1, seed=100)
+        t_data = time.time() - t0
+        t1 = time.time()
+        hist = train(gnn, samples, epochs=args.epochs, lr=args.lr, w_theta=args.w_theta,
+                     log=lambda m: print(m, flush=True))
+        torch.cuda.synchronize()
+        t_train = time.time() - t1
     if args.out:
         np.save(args.out, gnn.params())
     pairs = test_pairs(net, nets, args.pairs)
     rows = compare_starts(net, gnn, [(a, b) for _, a, b in pairs])
     summ = {}
-    for mode in ("cold", "prev", "learned"):
+    for mode in ("cold", "prev", "learned", "learned_only"):
         summ[mode] = {k: float(np.median([r[mode][k] for r in rows])) for k in ("fwd", "adj", "ms")}
-    wins = sum(1 for r in rows if r["learned"]["fwd"] + r["learned"]["adj"] < r["prev"]["fwd"] + r["prev"]["adj"])
+    summ["learned"]["kept_learned"] = float(np.mean([r["learned"]["kept_learned"] for r in rows]))
+    tot = lambda r, m: r[m]["fwd"] + r[m]["adj"]
+    wins = sum(1 for r in rows if tot(r, "learned") < tot(r, "prev"))
+    wins_only = sum(1 for r in rows if tot(r, "learned_only") < tot(r, "prev"))
+    wins_cold = sum(1 for r in rows if tot(r, "learned_only") < tot(r, "cold"))
     # prediction error on held-out plans (the first scenario-hours of each test plan)
     errs = []
     for _, _, eta_b in pairs:
@@ -94,7 +103,9 @@ def main(argv=None):
         errs.append(float(torch.sqrt(torch.mean((pred[:M].clamp(0, 200) - tgt[:M]) ** 2))))
     rep = dict(samples=len(samples), data_s=t_data, train_s=t_train, loss_first=hist[0], loss_last=hist[-1],
                price_rmse_test=float(np.median(errs)),
-               pairs=len(rows), kinds=[k for k, _, _ in pairs], median=summ, learned_beats_prev=wins, rows=rows)
+               pairs=len(rows), kinds=[k for k, _, _ in pairs], median=summ, learned_beats_prev=wins,
+               learned_only_beats_prev=wins_only, learned_only_beats_cold=wins_cold,
+               fallback_rate=1.0 - summ["learned"]["kept_learned"], rows=rows)
     print(json.dumps({k: v for k, v in rep.items() if k != "rows"}), flush=True)
     if args.report:
         json.dump(rep, open(args.report, "w"), indent=1)

@@ -98,17 +98,21 @@ def train(gnn: gx.WarmStartGNN, samples, epochs=30, lr=2e-3, w_theta=10.0, seed=
 
 def compare_starts(net, gnn, pairs):
     """For each (eta_a, eta_b): solve at eta_a, then at eta_b from a cold start, from
-    eta_a's state (previous plan) and from the network's prediction at eta_b.  Forward
-    and adjoint iterations and wall time (prediction included) per start."""
+    eta_a's state (previous plan), from the learned start with its selection rule
+    (GX_WARM_LEARNED: per scenario, the learned start or the previous plan's, whichever
+    has the smaller residual at the first check) and from the network's prediction alone
+    (a user start, no rule).  Forward and adjoint iterations, wall time (prediction
+    included) and, for the rule, the share of scenarios that kept the learned start."""
+    net.attach_gnn(gnn)
     rows = []
     for eta_a, eta_b in pairs:
         r = {}
-        for mode in ("cold", "prev", "learned"):
+        for mode in ("cold", "prev", "learned", "learned_only"):
             net.solve(eta_a, warm="cold")
             net.grad(eta_a)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            if mode == "learned":
+            if mode == "learned_only":
                 w = gnn.predict(eta_b)
                 M = w.numel() // 2
                 net.solve(eta_b, warm="user", warm_prices=w[:M], warm_angles=w[M:])
@@ -119,7 +123,8 @@ def compare_starts(net, gnn, pairs):
             # h = c part; measured faster than the previous plan's adjoint state)
             net.grad(eta_b, warm="cold")
             torch.cuda.synchronize()
-            r[mode] = dict(fwd=it_f, adj=net.last_grad_stats["iters_max"],
-                           ms=1e3 * (time.perf_counter() - t0))
+            r[mode] = dict(fwd=it_f, adj=net.last_grad_stats["iters_max"], ms=1e3 * (time.perf_counter() - t0))
+            if mode == "learned":
+                r[mode]["kept_learned"] = float(np.mean(net.array("warm").cpu().numpy() == 1))
         rows.append(r)
     return rows
