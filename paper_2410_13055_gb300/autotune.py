@@ -127,7 +127,17 @@ def tune_schedule(net: gx.Network, eta, iters=200, space=None, log=None):
         b.record()
         torch.cuda.synchronize()
         us = 1e3 * a.elapsed_time(b) / (2 * n)
-        trials.append(dict(cand, us_per_iteration=round(us, 3)))
+        # the same run again with the kernels' timer stamps on: per-launch kernel times
+        net.profile(True)
+        net.solve(eta, warm="prev")  # (switching the stamps on re-captures the graphs)
+        net.grad(eta, warm="prev")
+        net.profile(True)  # reset the counters, keep the graphs
+        net.solve(eta, warm="prev")
+        net.grad(eta, warm="prev")
+        prof = net.profile_read()
+        net.profile(False)
+        kern = {k + "_us": round(1e3 * v["ms"] / max(v["samples"], 1), 3) for k, v in prof.items() if k != "k_crs"}
+        trials.append(dict(cand, us_per_iteration=round(us, 3), **kern))
         if log:
             log(trials[-1])
     best = min(trials, key=lambda t: t["us_per_iteration"])
@@ -257,3 +267,27 @@ def load(net: gx.Network, cache=None):
         _apply(net, dict(e["best"]))
         return e["best"]
     return None
+
+
+def main(argv=None):
+    """python -m paper_2410_13055_gb300.autotune schedule --config medium|scale|batching
+    [--scenarios S] [--iters N]: every kernel schedule's time per iteration and per-launch
+    kernel times (timer stamps) with every scenario iterating, as JSON."""
+    import argparse
+    from . import gx, synth
+    ap = argparse.ArgumentParser()
+    ap.add_argument("what", choices=["schedule"])
+    ap.add_argument("--config", default="medium", choices=["medium", "scale", "batching"])
+    ap.add_argument("--scenarios", type=int, default=None)
+    ap.add_argument("--iters", type=int, default=200)
+    args = ap.parse_args(argv)
+    make = {"medium": synth.medium, "scale": synth.scale, "batching": synth.batching}[args.config]
+    nets, scens = make(S=args.scenarios) if args.scenarios else make()
+    net = gx.Network(nets, scens, kappa=50.0, tol=1e-3, adj_tol=1e-3, max_iter=50000, adj_max_iter=50000, rho=0.2)
+    eta = torch.tensor(np.concatenate([n["eta_min"] for n in nets]), dtype=torch.float32, device=net.device)
+    rep = tune_schedule(net, eta, iters=args.iters)
+    print(json.dumps(dict(config=args.config, scenarios=net.S, **rep)), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -53,7 +53,17 @@ constexpr int kPoolMax = 3072;  // longest record (words) staged in shared memor
 // staged copies: array ids and flags of a copy-list entry
 enum : int { kCpGenX = 0, kCpGenAux = 1, kCpDl = 2, kCpVf = 3, kCpVt = 4, kCpBat = 5 };
 enum : int { kCpFirm = 1, kCpRamp = 2 };   // (flags << 3): capacity factor 1 / ramp-limited generator
-constexpr int kStageMax = 40 * 1024;      // largest row stage (bytes) of one bus block
+// Largest row stage (bytes) of one bus block; blocks above it run unstaged.  The launch's
+// dynamic shared memory is the largest stage (plus its record), so this caps the staged bus
+// kernel's shared-memory occupancy.
+#ifndef GX_STAGE_MAX_KB
+#define GX_STAGE_MAX_KB 40
+#endif
+constexpr int kStageMax = GX_STAGE_MAX_KB * 1024;
+// minimum resident blocks per SM the staged bus kernel is compiled for (its register cap)
+#ifndef GX_BUS4T_MINB
+#define GX_BUS4T_MINB 4
+#endif
 
 // Cluster-resident solver: one thread-block cluster of C CTAs per scenario, CTA r owning
 // hours [r*H, (r+1)*H) of every device (H = ceil(T / C)), its state in shared memory.

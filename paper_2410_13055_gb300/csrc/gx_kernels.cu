@@ -1142,7 +1142,7 @@ __device__ __forceinline__ bool copy_wanted(int code) {
 }
 
 template <int ADJ, int RAMP>
-__global__ void __launch_bounds__(kQBlock, 4) k_bus4t(const Ctx c, int want_res) {
+__global__ void __launch_bounds__(kQBlock, GX_BUS4T_MINB) k_bus4t(const Ctx c, int want_res) {
     extern __shared__ __align__(16) int S[];  // the block's record, then its row stage
     __shared__ __align__(8) unsigned long long bar;
     const bool stamp = want_res && c.stamp_lo != nullptr;
