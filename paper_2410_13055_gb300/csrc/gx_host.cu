@@ -539,7 +539,7 @@ static void build_bus_blocks(gx_network* net) {
             BusBlk r{};
             r.e_bus = sd.e_bus; r.e_gen = sd.e_gen; r.e_line = sd.e_line; r.e_bat = sd.e_bat;
             r.s = s;
-            const int bs = quad ? kQBlock : kBlock;  // items per block
+            const int bs = quad ? kBusQBlock : kBlock;  // items per block
             r.item0 = b * bs;
             const int last = (int)std::min<long long>((long long)r.item0 + bs, nitems) - 1;
             r.n0 = r.item0 / per_bus;
@@ -879,7 +879,7 @@ gx_status gx_network_create(const gx_network_desc* nets, int n_nets, const gx_sc
         for (int b = 0; b < sd.line_nblk; ++b) net->line_blk_scen.push_back(s);
         net->n_line_blk += sd.line_nblk;
         sd.bus4_blk0 = net->n_bus4_blk;
-        sd.bus4_nblk = (int)(((long long)h.N * (sh.Tp / 4) + kQBlock - 1) / kQBlock);
+        sd.bus4_nblk = (int)(((long long)h.N * (sh.Tp / 4) + kBusQBlock - 1) / kBusQBlock);
         net->n_bus4_blk += sd.bus4_nblk;
         sd.line4_blk0 = net->n_line4_blk;
         sd.line4_nblk = (int)(((long long)h.L * (sh.Tp / 4) + kQBlock - 1) / kQBlock);

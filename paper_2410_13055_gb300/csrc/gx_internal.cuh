@@ -17,7 +17,15 @@ namespace gx {
 
 constexpr int kBlock = 256;        // threads per block of the bus / line / generic kernels
 constexpr int kLineItems = 2;     // line-hours per thread of the line kernel
-constexpr int kQBlock = 128;       // threads per block of the hour-quad line / bus kernels
+constexpr int kQBlock = 128;       // threads per block of the hour-quad line kernel
+// threads per block of the hour-quad bus kernels (each thread one bus-hour quad)
+#ifndef GX_BUS_QBLOCK
+#define GX_BUS_QBLOCK 128
+#endif
+constexpr int kBusQBlock = GX_BUS_QBLOCK;
+// resident blocks per SM the per-thread-load bus kernel is compiled for: 512 threads, so at
+// most 128 registers a thread
+constexpr int kBus4MinBlocks = 512 / kBusQBlock;
 constexpr int kBatWarps = 2;       // batteries (warps) per block of the battery kernel
 constexpr int kMaxT = 256;         // hours per scenario handled by one warp (8 per lane)
 constexpr int kHplMax = kMaxT / 32;

@@ -875,7 +875,7 @@ __device__ __forceinline__ void gen_load4(const Ctx& c, const StatePtrs& X, cons
 // an SM: uncapped, the adjoint instance took 136, three blocks per SM, and a 16-scenario
 // medium grid (3.45 blocks per SM) ran part of its blocks as a second wave.
 template <int ADJ, int RAMP>
-__global__ void __launch_bounds__(kQBlock, 4) k_bus4(const Ctx c, int want_res) {
+__global__ void __launch_bounds__(kBusQBlock, kBus4MinBlocks) k_bus4(const Ctx c, int want_res) {
     __shared__ __align__(16) int S[kPoolMax];
     const bool stamp = want_res && c.stamp_lo != nullptr;
     if (stamp && threadIdx.x == 0) stamp_start(c, 0);
@@ -886,7 +886,7 @@ __global__ void __launch_bounds__(kQBlock, 4) k_bus4(const Ctx c, int want_res) 
     if (staged) {
         const int4* src = reinterpret_cast<const int4*>(c.pool + bb.pool);
         int4* dst = reinterpret_cast<int4*>(S);
-        for (int k = threadIdx.x; k < (bb.words >> 2); k += kQBlock) dst[k] = src[k];
+        for (int k = threadIdx.x; k < (bb.words >> 2); k += kBusQBlock) dst[k] = src[k];
     }
     const int Tq = bb.Tp >> 2;
     const int local = bb.item0 + threadIdx.x;
@@ -1071,8 +1071,8 @@ __global__ void __launch_bounds__(kQBlock, 4) k_bus4(const Ctx c, int want_res) 
         st4(X.thb + i, thn);
     }
     if (want_res) {
-        __shared__ float sh[kBusPart][kQBlock / 32];
-        block_sum<kBusPart, kQBlock>(acc, sh);
+        __shared__ float sh[kBusPart][kBusQBlock / 32];
+        block_sum<kBusPart, kBusQBlock>(acc, sh);
         if (threadIdx.x == 0) {
 #pragma unroll
             for (int q = 0; q < kBusPart; ++q) c.bus_part[blockIdx.x * kBusPart + q] = acc[q];
@@ -1142,7 +1142,7 @@ __device__ __forceinline__ bool copy_wanted(int code) {
 }
 
 template <int ADJ, int RAMP>
-__global__ void __launch_bounds__(kQBlock, GX_BUS4T_MINB) k_bus4t(const Ctx c, int want_res) {
+__global__ void __launch_bounds__(kBusQBlock, GX_BUS4T_MINB * 128 / kBusQBlock) k_bus4t(const Ctx c, int want_res) {
     extern __shared__ __align__(16) int S[];  // the block's record, then its row stage
     __shared__ __align__(8) unsigned long long bar;
     const bool stamp = want_res && c.stamp_lo != nullptr;
@@ -1154,7 +1154,7 @@ __global__ void __launch_bounds__(kQBlock, GX_BUS4T_MINB) k_bus4t(const Ctx c, i
     if (rec_smem) {
         const int4* src = reinterpret_cast<const int4*>(c.pool + bb.pool);
         int4* dst = reinterpret_cast<int4*>(S);
-        for (int k = threadIdx.x; k < (bb.words >> 2); k += kQBlock) dst[k] = src[k];
+        for (int k = threadIdx.x; k < (bb.words >> 2); k += kBusQBlock) dst[k] = src[k];
     }
     const int Tq = bb.Tp >> 2;
     const int local = bb.item0 + threadIdx.x;
@@ -1191,7 +1191,7 @@ __global__ void __launch_bounds__(kQBlock, GX_BUS4T_MINB) k_bus4t(const Ctx c, i
     if (sbytes > 0 && bulk) {
         const int ncp = P.p[kPH_NCP];
         const int* cpl = P.p + P.p[kPH_CP];
-        for (int k = threadIdx.x; k < ncp; k += kQBlock) {
+        for (int k = threadIdx.x; k < ncp; k += kBusQBlock) {
             const int rel = cpl[3 * k], dst = cpl[3 * k + 1], code = cpl[3 * k + 2];
             if (!copy_wanted<ADJ>(code)) continue;
             const float* src;
@@ -1414,8 +1414,8 @@ __global__ void __launch_bounds__(kQBlock, GX_BUS4T_MINB) k_bus4t(const Ctx c, i
         st4(X.thb + i, thn);
     }
     if (want_res) {
-        __shared__ float sh[kBusPart][kQBlock / 32];
-        block_sum<kBusPart, kQBlock>(acc, sh);
+        __shared__ float sh[kBusPart][kBusQBlock / 32];
+        block_sum<kBusPart, kBusQBlock>(acc, sh);
         if (threadIdx.x == 0) {
 #pragma unroll
             for (int q = 0; q < kBusPart; ++q) c.bus_part[blockIdx.x * kBusPart + q] = acc[q];
@@ -1867,18 +1867,18 @@ int launch_bus(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st) {
         const int sm = c.bus4_smem;
         if (c.bus_staged != 0) {
             if (c.n_ramp_warps > 0) {
-                if (adj) k_bus4t<1, 1><<<c.n_bus4_blk, kQBlock, sm, st>>>(c, want_res);
-                else k_bus4t<0, 1><<<c.n_bus4_blk, kQBlock, sm, st>>>(c, want_res);
+                if (adj) k_bus4t<1, 1><<<c.n_bus4_blk, kBusQBlock, sm, st>>>(c, want_res);
+                else k_bus4t<0, 1><<<c.n_bus4_blk, kBusQBlock, sm, st>>>(c, want_res);
             } else {
-                if (adj) k_bus4t<1, 0><<<c.n_bus4_blk, kQBlock, sm, st>>>(c, want_res);
-                else k_bus4t<0, 0><<<c.n_bus4_blk, kQBlock, sm, st>>>(c, want_res);
+                if (adj) k_bus4t<1, 0><<<c.n_bus4_blk, kBusQBlock, sm, st>>>(c, want_res);
+                else k_bus4t<0, 0><<<c.n_bus4_blk, kBusQBlock, sm, st>>>(c, want_res);
             }
         } else if (c.n_ramp_warps > 0) {
-            if (adj) k_bus4<1, 1><<<c.n_bus4_blk, kQBlock, 0, st>>>(c, want_res);
-            else k_bus4<0, 1><<<c.n_bus4_blk, kQBlock, 0, st>>>(c, want_res);
+            if (adj) k_bus4<1, 1><<<c.n_bus4_blk, kBusQBlock, 0, st>>>(c, want_res);
+            else k_bus4<0, 1><<<c.n_bus4_blk, kBusQBlock, 0, st>>>(c, want_res);
         } else {
-            if (adj) k_bus4<1, 0><<<c.n_bus4_blk, kQBlock, 0, st>>>(c, want_res);
-            else k_bus4<0, 0><<<c.n_bus4_blk, kQBlock, 0, st>>>(c, want_res);
+            if (adj) k_bus4<1, 0><<<c.n_bus4_blk, kBusQBlock, 0, st>>>(c, want_res);
+            else k_bus4<0, 0><<<c.n_bus4_blk, kBusQBlock, 0, st>>>(c, want_res);
         }
         return 1;
     }
