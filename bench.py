@@ -483,6 +483,7 @@ def run_gx(args):
             dist.destroy_process_group()
         return
     cpu = cpu_baseline(args) if not args.no_cpu_baseline else None
+    cpu_ref = cpu_reference() if (not args.no_cpu_baseline and args.config == "medium") else None
     out = {
         "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
@@ -501,6 +502,7 @@ def run_gx(args):
         "learned": head["learned"],
         "roofline": head["roofline"],
         "cpu_baseline": cpu,
+        "cpu_reference": cpu_ref,
         "e2e": head["e2e"],
         "clocks": head["clocks"],
         "gpu_launches": head["gpu_launches"] + sum(r["gpu_launches"] for r in subs.values()),
@@ -580,6 +582,67 @@ def cpu_baseline(args, hours=24):
             "host_threads_available": os.cpu_count()}
 
 
+def _timed(fn):
+    r0 = resource.getrusage(resource.RUSAGE_SELF)
+    t0 = time.perf_counter()
+    out = fn()
+    wall = time.perf_counter() - t0
+    r1 = resource.getrusage(resource.RUSAGE_SELF)
+    cpu_s = (r1.ru_utime - r0.ru_utime) + (r1.ru_stime - r0.ru_stime)
+    return out, wall, _cores_used(cpu_s, wall)
+
+
+def cpu_probe(which):
+    """One CPU timing of the reference points (run in a child process so its thread count can
+    be fixed through the environment): the FP64 oracle on the 5-bus case, or on the medium
+    network's scenario 0, hours 0-23."""
+    if which == "tiny":
+        nets, scens = synth.tiny()
+        dh, wall, cores = _timed(lambda: oracle_step(nets, scens, 24))
+    else:
+        nets, scens, _ = build_workload("medium")
+        dh, wall, cores = _timed(lambda: oracle_step(nets, scens, 24))
+    print(json.dumps({"device_hours": dh, "wall_s": wall, "cores": cores}), flush=True)
+
+
+def cpu_reference():
+    """The CPU reference points of the measurement plan, on the host cores.
+
+    * HiGHS (scipy's LP solver) on one full medium scenario (100 buses, 168 h) with eps = 0:
+      the library LP at full size, where the interior-point oracle does not fit.  Dispatch
+      only: an LP solver gives no implicit gradient.
+    * The FP64 oracle (interior point + KKT adjoint gradient) on the 5-bus case (in full),
+      with every host thread and with one, and on the medium slice with one thread (the
+      all-thread slice is cpu_baseline)."""
+    from scipy.optimize import linprog
+    from oracle.qp import DispatchQP
+    out = {}
+    nets, scens, _ = build_workload("medium")
+    qp = DispatchQP(nets[0], scens[0], nets[0]["eta_min"], synth.default_opts(eps=0.0))
+    res, wall, cores = _timed(lambda: linprog(qp.q, A_ub=qp.Gm, b_ub=qp.h, A_eq=qp.A, b_eq=qp.b,
+                                              bounds=(None, None), method="highs"))
+    dh = synth.device_hours(nets, scens[:1])
+    out["highs_lp_medium_scenario"] = {"value": round(dh / wall, 2), "unit": UNIT, "wall_s": round(wall, 2),
+                                       "cores": cores, "status": int(res.status),
+                                       "sample": "medium network, scenario 0, 168 h, eps = 0 LP (dispatch only)"}
+    env1 = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    for name, which, env in (("oracle_tiny", "tiny", None), ("oracle_tiny_1thread", "tiny", env1),
+                             ("oracle_medium_slice_1thread", "slice", env1)):
+        r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--cpu-probe", which],
+                           capture_output=True, text=True, env=env or dict(os.environ), timeout=600)
+        try:
+            d = json.loads(r.stdout.strip().splitlines()[-1])
+            out[name] = {"value": round(d["device_hours"] / d["wall_s"], 2), "unit": UNIT,
+                         "wall_s": round(d["wall_s"], 2), "cores": d["cores"],
+                         "sample": ("5-bus case, 24 h, in full" if which == "tiny" else
+                                    "medium network, scenario 0, hours 0-23") +
+                                   ": FP64 interior-point dispatch + KKT adjoint gradient"}
+        except Exception:
+            out[name] = {"error": (r.stderr or r.stdout)[-300:]}
+    out["host_threads_available"] = os.cpu_count()
+    return out
+
+
 def run_reference(args):
     ws, rank = _dist()
     if rank != 0:
@@ -640,7 +703,11 @@ def main():
                     help="keep the library's default kernel schedule instead of autotuning it per workload")
     ap.add_argument("--bus-staged", type=int, default=None, choices=[0, 1, 2],
                     help="force the bus kernel variant (gx_network_set_schedule) instead of autotuning it")
+    ap.add_argument("--cpu-probe", default=None, choices=["tiny", "slice"], help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.cpu_probe:
+        cpu_probe(args.cpu_probe)
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
