@@ -288,7 +288,15 @@ def measure(config, args, steps, warmup, dist=None, learned=False, cold=True, sc
         net.set_schedule(bus_staged=args.bus_staged)
     elif not args.no_tune and not args.persistent:
         from paper_2410_13055_gb300 import autotune
-        tuned = autotune.tune_schedule_step(net, eta)
+        def plain_step(e):  # the timed step, without the bookkeeping
+            net.solve(e, warm="prev")
+            net.grad(e, out=grad, warm="prev")
+            if reduce_grad:
+                from paper_2410_13055_gb300.sharding import allreduce_sum
+                allreduce_sum(grad)
+            net.plan_step(e, grad, gamma, eta_min, eta_max, state["alpha"])
+
+        tuned = autotune.tune_schedule_step(net, eta, step=plain_step, flush=lambda: flush.fill_(1.0))
 
     def timed(warm, K):
         state["launches"], state["iters"], state["adj_iters"] = 0, [], []
@@ -404,7 +412,7 @@ def measure(config, args, steps, warmup, dist=None, learned=False, cold=True, sc
                 "replays_headline_steps": [list(x) for x in e2e_its] == [[a, b] for a, b in zip(it_prev, ait_prev)],
                 "note": "headline's plan and solver state restored first; no L2 flush between its steps"},
         "clocks": clk, "gpu_launches": int(launches), "alpha": state["alpha"],
-        "schedule": {"chosen": net.schedule(),
+        "schedule": {"chosen": net.schedule(), "default": tuned["default"] if tuned else None,
                      "by": "autotune.tune_schedule_step" if tuned else ("--bus-staged" if args.bus_staged is not None
                                                                         else "bind default"),
                      "trials_ms_per_step": ({f"bus{t['bus_staged']}_bat{t['bat_warps']}": t["ms_per_step"]
@@ -470,7 +478,7 @@ def run_gx(args):
     # steps each, in the same JSON line
     subs = {}
     if args.config == "medium" and not args.no_sub:
-        for cfg, k in (("scale", 3), ("batching", 5)):
+        for cfg, k in (("scale", 3), ("batching", 10)):
             r = measure(cfg, args, k, 3, dist, learned=False, cold=False)
             for key in ("clocks", "learned", "cold", "alpha"):
                 r.pop(key, None)

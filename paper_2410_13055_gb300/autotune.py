@@ -147,50 +147,69 @@ def tune_schedule(net: gx.Network, eta, iters=200, space=None, log=None):
     return dict(best=best, trials=trials, iterations=n)
 
 
-def tune_schedule_step(net: gx.Network, eta_next, reps=2, space=None, log=None):
-    """Pick the fastest kernel schedule on the workload's own step: from the current
-    (previous plan's) forward and adjoint state, each candidate solves at `eta_next` and
-    differentiates, warm-started ("prev"), `reps` times from the same restored state (the
-    first run of a candidate also captures its graphs); the state is restored at the end.
-    Unlike `tune_schedule`, this times the step's real mix of launches, including the
-    ones where most scenarios have converged.  Returns dict(best=..., trials=[...])."""
+def tune_schedule_step(net: gx.Network, eta, step=None, steps=2, reps=2, margin=0.02, space=None, log=None,
+                       flush=None):
+    """Pick the fastest kernel schedule on the workload's own steps.  From the current
+    (previous plan's) forward and adjoint state and plan `eta`, each candidate runs `steps`
+    consecutive previous-plan steps (`step(eta)`: solve, gradient and plan step in place;
+    default: solve and gradient only, at a fixed plan), `reps` times from the same restored
+    state and plan, keeping its best time; the first run of a candidate also captures its
+    graphs.  The schedule in force when the tuner is called (bind's default) is kept unless
+    a candidate is faster by more than `margin`: a single step's timing cannot tell apart
+    schedules closer than that.  `flush()`, if given, runs before each step outside its
+    timing (the caller's cache flush, so the steps are timed as the caller times them).
+    State and plan are restored at the end.  Unlike
+    `tune_schedule`, this times the steps' real mix of launches, including the ones where
+    most scenarios have converged.  Returns dict(best=..., default=..., trials=[...])."""
     space = space or SCHEDULE
-    sx, sa = net.state(False).clone(), net.state(True).clone()
+    if step is None:
+        def step(e):
+            net.solve(e, warm="prev")
+            net.grad(e, warm="prev")
+    default = net.schedule()
+    sx, sa, se = net.state(False).clone(), net.state(True).clone(), eta.clone()
+
+    def restore():
+        net.state(False).copy_(sx)
+        net.state(True).copy_(sa)
+        eta.copy_(se)
+
     cands = [dict(bus_staged=b, bat_warps=w) for b in space["bus_staged"] for w in space["bat_warps"]]
     trials = []
     for cand in cands:
         net.set_schedule(**cand)
         best_ms = None
         for _ in range(reps):
-            net.state(False).copy_(sx)
-            net.state(True).copy_(sa)
+            restore()
             torch.cuda.synchronize()
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record()
-            net.solve(eta_next, warm="prev")
-            net.grad(eta_next, warm="prev")
-            b.record()
+            evs = []
+            for _ in range(steps):
+                if flush is not None:
+                    flush()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record()
+                step(eta)
+                b.record()
+                evs.append((a, b))
             torch.cuda.synchronize()
-            ms = a.elapsed_time(b)
+            ms = sum(a.elapsed_time(b) for a, b in evs) / steps
             best_ms = ms if best_ms is None else min(best_ms, ms)
-        trials.append(dict(cand, ms_per_step=round(best_ms, 4), iterations=(net.last_stats["iters_max"],
-                                                                           net.last_grad_stats["iters_max"])))
+        trials.append(dict(cand, ms_per_step=round(best_ms, 4)))
         if log:
             log(trials[-1])
-    best = min(trials, key=lambda t: t["ms_per_step"])
-    best = {k: best[k] for k in SCHEDULE}
+    fastest = min(trials, key=lambda t: t["ms_per_step"])
+    t_def = next((t["ms_per_step"] for t in trials if {k: t[k] for k in SCHEDULE} == default), None)
+    pick = fastest if (t_def is None or fastest["ms_per_step"] < (1.0 - margin) * t_def) else dict(default)
+    best = {k: pick[k] for k in SCHEDULE}
     net.set_schedule(**best)
     # one more run captures the chosen schedule's graphs, so the caller's next step is not
-    # charged for it; then the state goes back to the previous plan's
-    net.state(False).copy_(sx)
-    net.state(True).copy_(sa)
-    net.solve(eta_next, warm="prev")
-    net.grad(eta_next, warm="prev")
-    net.state(False).copy_(sx)
-    net.state(True).copy_(sa)
+    # charged for it; then state and plan go back to the previous plan's
+    restore()
+    step(eta)
+    restore()
     torch.cuda.synchronize()
-    return dict(best=best, trials=trials)
+    return dict(best=best, default=default, trials=trials)
 
 
 def tune(net: gx.Network, nets, steps=3, h_tol=2e-3, g_slack=1.25, cache=None, log=None, alpha_frac=1e-2):

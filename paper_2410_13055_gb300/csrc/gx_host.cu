@@ -80,6 +80,8 @@ struct gx_network {
     std::vector<BusBlk> bus_blk;       // bus-kernel block records (single-hour kernel)
     std::vector<BusBlk> bus4_blk;      // bus-kernel block records (hour-quad kernel)
     std::vector<int> line4_blk_scen;   // scenario of each hour-quad line block
+    std::vector<LineBlk> line4_blk;    // its offsets
+    std::vector<BatW> bat_w;           // offsets of each battery warp
     int n_bus4_blk = 0, n_line4_blk = 0;
     size_t bus4_smem = 0;              // dynamic shared memory of the staged bus kernel (record + stage)
     std::vector<int> pool;             // their pool records (words)
@@ -110,7 +112,7 @@ struct gx_network {
     int max_ramp_T = 1;
     // workspace offsets
     size_t o_scen, o_bbs, o_lbs, o_bws, o_cbs, o_gwarp, o_knet, o_busblk, o_pool, o_prep, o_crs;
-    size_t o_bus4blk, o_l4bs;
+    size_t o_bus4blk, o_l4bs, o_l4blk, o_batw;
     size_t o_scl, o_sce, o_scb, o_scbm, o_scp, o_scd, o_scdl, o_scgw;
     size_t o_rgen, o_rrate, o_gramp, o_rws, o_rdd, o_ardd, o_rf[4], o_ra[4], o_rpart;
     size_t o_gbus, o_gcost, o_gemis, o_gfirm, o_lfrom, o_lto, o_lbeta, o_ldth, o_lw, o_bbus, o_bdur, o_beffc, o_beffd;
@@ -265,6 +267,8 @@ static void make_ctx(gx_network* net) {
     for (int k = 0; k < 4; ++k) { *rfs[k] = F(net->o_rf[k]); *ras[k] = F(net->o_ra[k]); }
     c.ramp_part = F(net->o_rpart);
     c.line4_blk_scen = I(net->o_l4bs);
+    c.line4_blk = reinterpret_cast<const LineBlk*>(d + net->o_l4blk);
+    c.bat_w = reinterpret_cast<const BatW*>(d + net->o_batw);
     c.n_bus4_blk = net->n_bus4_blk;
     c.n_line4_blk = net->n_line4_blk;
     c.pool = I(net->o_pool);
@@ -910,6 +914,27 @@ gx_status gx_network_create(const gx_network_desc* nets, int n_nets, const gx_sc
                 if (sc.cf[(size_t)g * sc.Tp + t] != 1.0f) { net->firm[n.gen0 + g] = 0; break; }
     }
     build_bus_blocks(net);
+    net->line4_blk.clear();
+    net->bat_w.clear();
+    for (int s = 0; s < S; ++s) {
+        const ScenDev& sd = net->sdev[s];
+        const NetH& h = net->nets[sd.net];
+        for (int b = 0; b < sd.line4_nblk; ++b) {
+            LineBlk r{};
+            r.e_line = sd.e_line; r.e_bus = sd.e_bus;
+            r.s = s; r.line0 = sd.line0; r.Tp = sd.Tp; r.T = sd.T;
+            r.L = sd.L; r.eta_l = sd.eta0 + sd.G; r.item0 = b * kQBlock;
+            net->line4_blk.push_back(r);
+        }
+        for (int b = 0; b < sd.B; ++b) {
+            BatW r{};
+            r.row0 = sd.e_bat + (long long)b * sd.Tp;
+            r.brow0 = sd.e_bus + (long long)h.bat_bus[b] * sd.Tp;
+            r.s = s; r.bg = sd.bat0 + b; r.T = sd.T; r.Tp = sd.Tp;
+            r.eta_b = sd.eta0 + sd.G + sd.L + b;
+            net->bat_w.push_back(r);
+        }
+    }
     net->sc_dres.insert(net->sc_dres.end(), net->sc_dres_pool.begin(), net->sc_dres_pool.end());
     build_crs_groups(net);
     net->k_net.resize(K);
@@ -935,6 +960,8 @@ gx_status gx_network_create(const gx_network_desc* nets, int n_nets, const gx_sc
     net->o_crs = L.add(I4((long long)net->crs_list.size()));
     net->o_bus4blk = L.add(sizeof(BusBlk) * std::max<size_t>(net->bus4_blk.size(), 1));
     net->o_l4bs = L.add(I4(net->n_line4_blk));
+    net->o_l4blk = L.add(sizeof(LineBlk) * std::max<size_t>(net->line4_blk.size(), 1));
+    net->o_batw = L.add(sizeof(BatW) * std::max<size_t>(net->bat_w.size(), 1));
     net->o_gbus = L.add(I4(gen0)); net->o_gcost = L.add(F4(gen0)); net->o_gemis = L.add(F4(gen0));
     net->o_gfirm = L.add(B1(gen0));
     net->o_lfrom = L.add(I4(line0)); net->o_lto = L.add(I4(line0)); net->o_lbeta = L.add(F4(line0));
@@ -1023,6 +1050,8 @@ gx_status gx_network_bind(gx_network* net, void* dev_mem, size_t bytes, void* st
     put(net->o_crs, net->crs_list.data(), 4 * net->crs_list.size());
     put(net->o_bus4blk, net->bus4_blk.data(), sizeof(BusBlk) * net->bus4_blk.size());
     put(net->o_l4bs, net->line4_blk_scen.data(), 4 * net->line4_blk_scen.size());
+    put(net->o_l4blk, net->line4_blk.data(), sizeof(LineBlk) * net->line4_blk.size());
+    put(net->o_batw, net->bat_w.data(), sizeof(BatW) * net->bat_w.size());
     put(net->o_scl, net->sc_line.data(), 4 * net->sc_line.size());
     put(net->o_sce, net->sc_eta.data(), 4 * net->sc_eta.size());
     put(net->o_scb, net->sc_b.data(), 8 * net->sc_b.size());

@@ -126,6 +126,19 @@ struct BusBlk {
     int words, Tp, T, nitems; // record length (words), padded / true horizon, N * Tp
 };
 
+// One per hour-quad line block and one per battery warp (built at create): every offset
+// the kernel needs before its state loads, so those loads follow one dependent read.
+struct LineBlk {
+    long long e_line, e_bus;   // element offsets of the scenario's line and bus rows
+    int s, line0, Tp, T;       // scenario, first line of its network (global), padded / true horizon
+    int L, eta_l, item0, pad;  // lines of the network, plan index of its first line, first line-quad
+};
+struct BatW {
+    long long row0, brow0;     // the battery's row and its bus's row
+    int s, bg, T, Tp;          // scenario, battery (global index), true / padded horizon
+    int eta_b, pad0, pad1, pad2;  // plan index of the battery's power
+};
+
 // Kernel modes.  FWD/ADJ advance the forward or adjoint message passing by one
 // iteration; RESET/INIT prepare a cold or user start; MASK records the active set.
 enum Mode : int { M_FWD = 0, M_ADJ = 1, M_RESET = 2, M_INIT = 3, M_MASK = 4 };
@@ -184,6 +197,8 @@ struct Ctx {
     const BusBlk* bus_blk;     // [n_bus_blk]
     const BusBlk* bus4_blk;    // [n_bus4_blk] hour-quad bus kernel
     const int* line4_blk_scen; // [n_line4_blk]
+    const LineBlk* line4_blk;  // [n_line4_blk]
+    const BatW* bat_w;         // [n_bat_warps]
     const int* ramp_warp_scen; // [n_ramp_warps]
     const int* r_gen;          // [ramping generators] generator index within its network
     const float* r_rate;       // [ramping generators] ramp limit / capacity per hour

@@ -234,22 +234,24 @@ __global__ void __launch_bounds__(kBatWarps * 32) k_bat(const Ctx c, int want_re
     if (gw >= c.n_bat_warps) return;  // block-uniform when kW == 2 (one battery per block)
     const bool stamp = (MODE == M_FWD || MODE == M_ADJ) && want_res && c.stamp_lo != nullptr;
     if (stamp && L == 0) stamp_start(c, 2);
-    const int s = c.bat_warp_scen[gw];
-    if (c.done[s]) return;
-    const ScenDev sc = c.scen[s];
+    // the warp's offsets in one record (its row, its bus's row); in the iterations the done
+    // flag is read with the state and tested before anything is stored
+    const BatW bw = c.bat_w[gw];
+    const int s = bw.s;
+    const int done = c.done[s];
+    if ((MODE != M_FWD && MODE != M_ADJ) && done) return;
     const StatePtrs X = state<ADJ>(c);
-    const int b = gw - sc.bat_w0;
-    const int bg = sc.bat0 + b;
-    const int T = sc.T;
+    const int bg = bw.bg;
+    const int T = bw.T;
     const int hpl = (T + NL - 1) / NL;
     const int t0 = L * hpl;
     __shared__ float xch[8];  // two-warp exchange: rs, forward (A, B), backward (A, B), partials
-    const long long row0 = sc.e_bat + (long long)b * sc.Tp;
-    const long long brow0 = sc.e_bus + (long long)c.b_bus[bg] * sc.Tp;
+    const long long row0 = bw.row0;
+    const long long brow0 = bw.brow0;
 
     if (MODE == M_RESET) {
         const bool neg = ADJ && c.adj_from_fwd;
-        for (int t = L; t < sc.Tp; t += NL) {
+        for (int t = L; t < bw.Tp; t += NL) {
             const long long r = row0 + t;
             X.xb[r] = 0.f; X.zc[r] = 0.f; X.zd[r] = 0.f; X.zs[r] = 0.f;
             // h = c part of the adjoint: box multipliers are the negated forward ones
@@ -277,7 +279,7 @@ __global__ void __launch_bounds__(kBatWarps * 32) k_bat(const Ctx c, int want_re
         }
         return;
     }
-    const float P = fmaxf(c.eta[sc.eta0 + sc.G + sc.L + b], 0.f);
+    const float P = fmaxf(c.eta[bw.eta_b], 0.f);
     const float E = c.b_dur[bg] * P;
     const float a = c.b_effc[bg], k = 1.f / c.b_effd[bg];
     const float Ah = eps + ri + rho;
@@ -319,6 +321,7 @@ __global__ void __launch_bounds__(kBatWarps * 32) k_bat(const Ctx c, int want_re
             hi[0][j] = P; hi[1][j] = P; hi[2][j] = E;
         }
     }
+    if (done) return;  // uniform over the battery's warps; nothing stored yet
 #pragma unroll
     for (int j = 0; j < kHpl; ++j) {
         const int t = t0 + j;
@@ -780,37 +783,45 @@ __device__ __forceinline__ void ldm4(const uint8_t* p, int (&v)[4]) {
     v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
 }
 
+// Resident blocks per SM the line kernel is compiled for (its register cap).
+#ifndef GX_LINE4_MINB
+#define GX_LINE4_MINB 1
+#endif
 template <int ADJ>
-__global__ void __launch_bounds__(kQBlock) k_line4(const Ctx c, int want_res) {
+__global__ void __launch_bounds__(kQBlock, GX_LINE4_MINB) k_line4(const Ctx c, int want_res) {
     const int blk = blockIdx.x;
     const bool stamp = want_res && c.stamp_lo != nullptr;
     if (stamp && threadIdx.x == 0) stamp_start(c, 1);
-    const int s = c.line4_blk_scen[blk];
-    if (c.done[s]) return;
-    const ScenDev sc = c.scen[s];
+    // the block's offsets in one record; the done flag, the line's ends and its state are
+    // then read together, and the flag tested before anything is stored
+    const LineBlk lb = c.line4_blk[blk];
+    const int done = c.done[lb.s];
     const StatePtrs X = state<ADJ>(c);
-    const int Tq = sc.Tp >> 2;
-    const int local = (blk - sc.line4_blk0) * kQBlock + threadIdx.x;
+    const int Tq = lb.Tp >> 2;
+    const int local = lb.item0 + threadIdx.x;
     const int l = local / Tq;
     const int t = (local - l * Tq) * 4;
     float dx2 = 0.f, x2 = 0.f, th2 = 0.f;
-    if (l < sc.L) {
-        const long long row = sc.e_line + (long long)l * sc.Tp + t;
-        const int lg = sc.line0 + l;
-        const long long bf = sc.e_bus + (long long)c.l_from[lg] * sc.Tp + t;
-        const long long bt = sc.e_bus + (long long)c.l_to[lg] * sc.Tp + t;
+    if (l < lb.L) {
+        const long long row = lb.e_line + (long long)l * lb.Tp + t;
+        const int lg = lb.line0 + l;
         float d[4], g[4], qf[4], qt[4], pbf[4], uf[4], zf[4], pbt[4], ut[4], zt[4];
         ld4(X.dl + row, d); ld4(X.sg + row, g); ld4(X.vf + row, qf); ld4(X.vt + row, qt);
-        ld4(X.pbar + bf, pbf); ld4(X.u + bf, uf); ld4(X.thb + bf, zf);
-        ld4(X.pbar + bt, pbt); ld4(X.u + bt, ut); ld4(X.thb + bt, zt);
+        const long long bf = lb.e_bus + (long long)c.l_from[lg] * lb.Tp + t;
+        const long long bt = lb.e_bus + (long long)c.l_to[lg] * lb.Tp + t;
         int mk[4] = {0, 0, 0, 0};
         if (ADJ) ldm4(c.m_line + row, mk);
         const float beta = c.l_beta[lg];
         const float w = c.l_w[lg];
+        const float etal = c.eta[lb.eta_l + l];
+        const float dthl = c.l_dth[lg];
+        ld4(X.pbar + bf, pbf); ld4(X.u + bf, uf); ld4(X.thb + bf, zf);
+        ld4(X.pbar + bt, pbt); ld4(X.u + bt, ut); ld4(X.thb + bt, zt);
+        if (done) return;  // block-uniform; no barrier or store has happened
         const bool dc = w == 0.f;  // HVDC transport line: no phase coupling, eps/2 f^2 cost
         const float rth = c.rth_c * w;
-        const float capf = fmaxf(c.eta[sc.eta0 + sc.G + l], 0.f) / beta;
-        const float cap = fminf(capf, c.l_dth[lg]);
+        const float capf = fmaxf(etal, 0.f) / beta;
+        const float cap = fminf(capf, dthl);
         const float den = 2.f * c.rho * beta * beta + 0.5f * rth + (dc ? c.eps : 0.f);
         float fs[4] = {0.f, 0.f, 0.f, 0.f};  // adjoint of a transport line: eps f* of grad h
         if (ADJ && dc) ld4(c.dl + row, fs);
@@ -818,7 +829,7 @@ __global__ void __launch_bounds__(kQBlock) k_line4(const Ctx c, int want_res) {
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
             dn[h] = gn[h] = nf[h] = nt[h] = 0.f;
-            if (t + h >= sc.T) continue;
+            if (t + h >= lb.T) continue;
             const float vf = qf[h] - zf[h], vt = qt[h] - zt[h];
             const float ef = 0.5f * (g[h] + d[h]) - zf[h], et = 0.5f * (g[h] - d[h]) - zt[h];
             if (!dc) th2 += beta * beta * (ef * ef + et * et);
@@ -837,6 +848,7 @@ __global__ void __launch_bounds__(kQBlock) k_line4(const Ctx c, int want_res) {
         }
         st4(X.dl + row, dn); st4(X.sg + row, gn); st4(X.vf + row, nf); st4(X.vt + row, nt);
     }
+    if (done) return;  // the threads past the network's lines
     if (want_res) {
         __shared__ float sh[3][kQBlock / 32];
         float v[3] = {dx2, x2, th2};
@@ -880,14 +892,11 @@ __global__ void __launch_bounds__(kBusQBlock, kBus4MinBlocks) k_bus4(const Ctx c
     const bool stamp = want_res && c.stamp_lo != nullptr;
     if (stamp && threadIdx.x == 0) stamp_start(c, 0);
     const BusBlk bb = c.bus4_blk[blockIdx.x];
-    if (c.done[bb.s]) return;  // block-uniform
+    // The done flag, the record copy and this thread's bus state are all issued before the
+    // flag is tested: one dependent round trip after the block record instead of two.
+    const int done = c.done[bb.s];
     const StatePtrs X = state<ADJ>(c);
     const bool staged = bb.words <= kPoolMax;
-    if (staged) {
-        const int4* src = reinterpret_cast<const int4*>(c.pool + bb.pool);
-        int4* dst = reinterpret_cast<int4*>(S);
-        for (int k = threadIdx.x; k < (bb.words >> 2); k += kBusQBlock) dst[k] = src[k];
-    }
     const int Tq = bb.Tp >> 2;
     const int local = bb.item0 + threadIdx.x;
     const int n = local / Tq;
@@ -901,6 +910,12 @@ __global__ void __launch_bounds__(kBusQBlock, kBus4MinBlocks) k_bus4(const Ctx c
         ld4(X.xl + i, xl); ld4(c.load + i, Ld);
         if (ADJ) { ld4(c.xl + i, xlf); ldm4(c.m_load + i, ml); }
     }
+    if (staged) {
+        const int4* src = reinterpret_cast<const int4*>(c.pool + bb.pool);
+        int4* dst = reinterpret_cast<int4*>(S);
+        for (int k = threadIdx.x; k < (bb.words >> 2); k += kBusQBlock) dst[k] = src[k];
+    }
+    if (done) return;  // block-uniform, before any barrier or store
     __syncthreads();
     float acc[kBusPart] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (valid) {
