@@ -317,7 +317,7 @@ gx_status gx_profile_active(const gx_network* net, long long* counts);
 /* ------------------------------------------------------------------------------
  * Learned warm start (not in the paper): a 3-layer message-passing network over the
  * bus-hour graph of a bound network (node (n, t) linked to (m, t) when a line joins
- * n and m; hidden width 64; BF16 tensor-core layers with FP32 accumulation) maps
+ * n and m; hidden width 64; BF16 tcgen05 tensor-core layers with FP32 accumulation) maps
  * plan-derived node features to nodal prices and angles.  Its predictions, in the
  * layout of GX_WARM_USER ([sum_s N_s Tp_s] prices then the same size of angles), warm
  * start gx_dispatch_solve_batch.  Parameters: FP32 master copy of gx_gnn_num_params()
@@ -334,12 +334,16 @@ gx_status gx_gnn_bind(gx_gnn* gnn, void* dev_mem, size_t bytes, uint64_t seed, v
 gx_status gx_gnn_set_params(gx_gnn* gnn, const float* host_params, size_t n, void* stream);
 /* which = 0: parameters, 1: gradients of the last gx_gnn_train_step (synchronises). */
 gx_status gx_gnn_get_params(const gx_gnn* gnn, float* host_out, size_t n, int which, void* stream);
-/* Predicted prices ($/MWh) and angles (rad) at plan eta_dev into out_dev [2 * bus rows]. */
+/* Predicted prices ($/MWh) and angles (rad) at plan eta_dev into out_dev [2 * bus rows].
+ * Asynchronous; the tensor-core layers' copy and MMA waits are bounded, and one that ran
+ * out (never expected) is returned as GX_ERR_TIMEOUT by the next gx_gnn_train_step that
+ * reads its loss. */
 gx_status gx_gnn_predict(gx_gnn* gnn, const float* eta_dev, float* out_dev, void* stream);
 /* One Adam step (lr > 0; lr = 0 only computes gradients) on the mean squared error
  * against target_dev (same layout as out_dev; prices compared in $/100 MWh units,
  * angles weighted by w_theta); padding hours are excluded.  loss_host (nullable)
- * receives the loss before the step (synchronises). */
+ * receives the loss before the step (synchronises); with it, GX_ERR_TIMEOUT reports a
+ * tensor-core wait that ran out in this step or an earlier prediction. */
 gx_status gx_gnn_train_step(gx_gnn* gnn, const float* eta_dev, const float* target_dev, float lr, float w_theta,
                             double* loss_host, void* stream);
 gx_status gx_gnn_destroy(gx_gnn* gnn);

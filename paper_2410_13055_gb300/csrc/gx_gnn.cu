@@ -10,10 +10,16 @@
 //   h_k = h_{k-1} + relu([h_{k-1}, mean_{m in N(n)} h_{k-1,m}] W_k + b_k)
 //   y = h_3 W_out + b_out,   y0 ~ price / 100, y1 ~ angle
 //
-// GEMMs use mma.sync.m16n8k16 with BF16 operands (activations converted on load,
-// weights kept as BF16 copies of FP32 master parameters) and FP32 accumulators.
+// The dense layers (forward, and the input gradient of the backward pass) run on the
+// 5th-generation tensor cores: tcgen05.mma with BF16 operands staged in shared memory by the
+// TMA engine and FP32 accumulators in tensor memory (k_dense).  Activations that feed a layer
+// are written in BF16 by their producer; the FP32 master parameters are copied into BF16
+// operand images after every update.  The weight gradients (a reduction over all rows) use
+// mma.sync.m16n8k16 with BF16 operands and FP32 accumulators.
 #include "gx_internal.cuh"
+#include "gx_async.cuh"
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -62,7 +68,8 @@ __device__ __forceinline__ int scen_of_row(const ScenDev* sc, int S, long long r
 }
 
 // ---------------------------------------------------------------- features
-__global__ void k_features(const Ctx c, const float* __restrict__ eta, float* __restrict__ X, long long M) {
+__global__ void k_features(const Ctx c, const float* __restrict__ eta, float* __restrict__ X,
+                           __nv_bfloat16* __restrict__ Xb, long long M) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= M) return;
     const int s = scen_of_row(c.scen, c.S, i);
@@ -105,71 +112,163 @@ __global__ void k_features(const Ctx c, const float* __restrict__ eta, float* __
     float4* o = reinterpret_cast<float4*>(X + i * kFin);
 #pragma unroll
     for (int k = 0; k < kFin / 4; ++k) o[k] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
+    __nv_bfloat162* ob = reinterpret_cast<__nv_bfloat162*>(Xb + i * kFin);
+#pragma unroll
+    for (int k = 0; k < kFin / 2; ++k) ob[k] = __floats2bfloat162_rn(f[2 * k], f[2 * k + 1]);
 }
 
 // ---------------------------------------------------------------- dense layers
-// Z = A Bt^T (+ bias); H = (resid +) relu(Z).  A: [M][K] FP32, split at K1 between two
-// row-major arrays (concatenation [A1, A2] without materialising it); Bt: [N][K] BF16.
-// One warp computes 16 rows x N columns; a block has 4 warps (64 rows).
-template <int K, int N>
-__global__ void __launch_bounds__(128) k_gemm_fwd(const float* __restrict__ A1, const float* __restrict__ A2, int K1,
-                                                  const __nv_bfloat16* __restrict__ Bt, const float* __restrict__ bias,
-                                                  const float* __restrict__ resid, float* __restrict__ Z,
-                                                  float* __restrict__ H, long long M, int relu) {
-    __shared__ __align__(16) __nv_bfloat16 sB[N * K];
-    for (int i = threadIdx.x; i < N * K / 8; i += blockDim.x)
-        reinterpret_cast<uint4*>(sB)[i] = reinterpret_cast<const uint4*>(Bt)[i];
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int g = lane >> 2, q = lane & 3;
-    const long long row0 = ((long long)blockIdx.x * 4 + warp) * 16;
-    if (row0 >= M) return;
-    const int K2 = K - K1;
-    auto Aat = [&](long long r, int k) -> float {
-        if (r >= M) return 0.f;
-        return k < K1 ? A1[r * K1 + k] : A2[r * K2 + (k - K1)];
-    };
-    float acc[N / 8][4];
-#pragma unroll
-    for (int j = 0; j < N / 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-#pragma unroll
-    for (int k0 = 0; k0 < K; k0 += 16) {
-        uint32_t a[4];
-        const long long r0 = row0 + g, r1 = row0 + g + 8;
-        const int c0 = k0 + 2 * q, c1 = k0 + 2 * q + 8;
-        a[0] = pack_bf16(Aat(r0, c0), Aat(r0, c0 + 1));
-        a[1] = pack_bf16(Aat(r1, c0), Aat(r1, c0 + 1));
-        a[2] = pack_bf16(Aat(r0, c1), Aat(r0, c1 + 1));
-        a[3] = pack_bf16(Aat(r1, c1), Aat(r1, c1 + 1));
-#pragma unroll
-        for (int j = 0; j < N / 8; ++j) {
-            const __nv_bfloat16* bp = sB + (j * 8 + g) * K + k0 + 2 * q;
-            const uint32_t b0 = *reinterpret_cast<const uint32_t*>(bp);
-            const uint32_t b1 = *reinterpret_cast<const uint32_t*>(bp + 8);
-            mma_bf16(acc[j], a, b0, b1);
-        }
+// One CTA of 128 threads computes a 128-row tile D = A B^T on the tensor cores
+// (tcgen05.mma, M = 128, N = 64 or 128, K = 16 per instruction):
+//  * A: NKB K-blocks of KW BF16 columns, brought by the TMA engine in the swizzled K-major
+//    layout (block 0 from tensor map a0, block 1 from a1, so the concatenation
+//    [h, neighbour mean] is never materialised); rows past M arrive as zeros;
+//  * B: the layer's weights as a pre-arranged BF16 image in the same layout (k_weight_images),
+//    brought by one bulk copy;
+//  * D: FP32 in tensor memory, row i in lane i; warp w reads the 32 lanes of its rows, so
+//    thread t of the CTA owns row row0 + t in the epilogue.
+// Epilogues: kEpiFwd  Z = D + b;  H = relu(Z) (+ resid);  and a BF16 copy of H for the next
+//                     layer's operand;
+//            kEpiBwd  dH[:, 0:64] += D[:, 0:64];  dAgg = D[:, 64:128]   (D = dZ W^T).
+enum : int { kEpiFwd = 0, kEpiBwd = 1 };
+
+struct DenseOut {
+    const float* bias;
+    const float* resid;
+    float* Z;
+    float* H;
+    __nv_bfloat16* Hb;
+    float* dH;
+    float* dAgg;
+    int* err;
+};
+
+template <int NKB, int KW, int N>
+struct DenseShape {
+    static constexpr uint32_t P = 2 * KW;  // bytes of a K-block row = its swizzle span
+    static constexpr uint32_t ATILE = 128 * P;
+    static constexpr uint32_t BTILE = N * P;
+    static constexpr uint32_t BBYTES = NKB * BTILE;  // the weight image
+    static constexpr uint32_t TX = NKB * (ATILE + BTILE);
+    static constexpr uint32_t NCOL = N;  // tensor-memory columns: a power of 2 >= 32
+    // dynamic shared memory: 1024-byte alignment slack, the tiles, two barriers and the
+    // tensor-memory address; at least enough that the CTAs resident on one SM never ask for
+    // more than its 512 tensor-memory columns (4 x 64, 6 x 64 or 3 x 128)
+    static constexpr uint32_t USED = 1024 + TX + 64;
+    static constexpr uint32_t MIN = N == 128 ? 60u * 1024u : 32u * 1024u;
+    static constexpr uint32_t SMEM = USED > MIN ? USED : MIN;
+    static_assert(KW == 16 || KW == 64, "K-blocks of 16 (32-byte swizzle) or 64 (128-byte swizzle) columns");
+    static_assert(N == 64 || N == 128, "N = 64 or 128");
+};
+
+template <int NKB, int KW, int N, int EPI>
+__global__ void __launch_bounds__(128) k_dense(const __grid_constant__ CUtensorMap a0,
+                                               const __grid_constant__ CUtensorMap a1,
+                                               const uint8_t* __restrict__ bimg, const DenseOut o, long long M) {
+    using Sh = DenseShape<NKB, KW, N>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sm = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
+    uint8_t* sA = sm;
+    uint8_t* sB = sm + NKB * Sh::ATILE;
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(sB + Sh::BBYTES);  // [0] copies, [1] MMAs
+    uint32_t* holder = reinterpret_cast<uint32_t*>(bar + 2);
+    int* copied = reinterpret_cast<int*>(holder + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long row0 = (long long)blockIdx.x * 128;
+    if (warp == 0) tmem_alloc(holder, Sh::NCOL);
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_fence_init();
     }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *holder;
+    if (tid == 0) {
+        mbar_expect_tx(&bar[0], Sh::TX);
+        bulk_g2s(sB, bimg, Sh::BBYTES, &bar[0]);
+        tma_load_2d(sA, &a0, 0, (int)row0, &bar[0]);
+        if (NKB > 1) tma_load_2d(sA + Sh::ATILE, &a1, 0, (int)row0, &bar[0]);
+        const bool ok = mbar_wait_bounded(&bar[0], 0);
+        if (ok) {
+            tc_fence_after();
+            constexpr uint32_t idesc = umma_idesc_bf16(128, N);
 #pragma unroll
-    for (int j = 0; j < N / 8; ++j) {
-        const int col = j * 8 + 2 * q;
+            for (int kb = 0; kb < NKB; ++kb)
 #pragma unroll
-        for (int hlf = 0; hlf < 2; ++hlf) {
-            const long long r = row0 + g + 8 * hlf;
-            if (r >= M) continue;
+                for (int ks = 0; ks < KW / 16; ++ks)
+                    umma_bf16(tmem, umma_sdesc(smem_addr(sA + kb * Sh::ATILE) + 32u * ks, Sh::P),
+                              umma_sdesc(smem_addr(sB + kb * Sh::BTILE) + 32u * ks, Sh::P), idesc,
+                              (kb | ks) != 0);
+            umma_commit(&bar[1]);
+        } else {
+            atomicExch(o.err, (int)GX_ERR_TIMEOUT);
+            mbar_wait_bounded(&bar[0], 0);  // let copies still in flight land before the CTA exits
+        }
+        *copied = ok ? 1 : 0;
+    }
+    __syncthreads();
+    if (*copied) {
+        const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bar[1], 0));
+        tc_fence_after();
+        if (!ok) {
+            if (lane == 0) atomicExch(o.err, (int)GX_ERR_TIMEOUT);
+        } else {
+            const long long r = row0 + tid;
+            const uint32_t tq = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+            for (int c = 0; c < N / 32; ++c) {
+                float v[32];
+                tmem_ld32(tq + 32u * c, v);  // warp-collective: rows past M take part too
+                if (r >= M) continue;
+                if (EPI == kEpiFwd) {
+                    const float4* b4 = reinterpret_cast<const float4*>(o.bias + 32 * c);
+                    const float4* r4 = o.resid ? reinterpret_cast<const float4*>(o.resid + r * N + 32 * c) : nullptr;
+                    float4* z4 = o.Z ? reinterpret_cast<float4*>(o.Z + r * N + 32 * c) : nullptr;
+                    float4* h4 = reinterpret_cast<float4*>(o.H + r * N + 32 * c);
+                    uint2* hb = o.Hb ? reinterpret_cast<uint2*>(o.Hb + r * N + 32 * c) : nullptr;
 #pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                float z = acc[j][2 * hlf + e] + (bias ? bias[col + e] : 0.f);
-                if (Z) Z[r * N + col + e] = z;
-                if (H) {
-                    float hv = relu ? fmaxf(z, 0.f) : z;
-                    if (resid) hv += resid[r * N + col + e];
-                    H[r * N + col + e] = hv;
+                    for (int q = 0; q < 8; ++q) {
+                        const float4 b = b4[q];
+                        const float4 z = make_float4(v[4 * q] + b.x, v[4 * q + 1] + b.y, v[4 * q + 2] + b.z,
+                                                     v[4 * q + 3] + b.w);
+                        if (z4) z4[q] = z;
+                        float4 h = make_float4(fmaxf(z.x, 0.f), fmaxf(z.y, 0.f), fmaxf(z.z, 0.f), fmaxf(z.w, 0.f));
+                        if (r4) {
+                            const float4 a = r4[q];
+                            h.x += a.x; h.y += a.y; h.z += a.z; h.w += a.w;
+                        }
+                        h4[q] = h;
+                        if (hb) {
+                            __nv_bfloat162 lo = __floats2bfloat162_rn(h.x, h.y), hi = __floats2bfloat162_rn(h.z, h.w);
+                            hb[q] = make_uint2(*reinterpret_cast<uint32_t*>(&lo), *reinterpret_cast<uint32_t*>(&hi));
+                        }
+                    }
+                } else {
+                    // columns [0, 64): the direct half, added into dH; [64, 128): the neighbour half
+                    float4* d4 = c < 2 ? reinterpret_cast<float4*>(o.dH + r * kH + 32 * c)
+                                       : reinterpret_cast<float4*>(o.dAgg + r * kH + 32 * (c - 2));
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        float4 d = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                        if (c < 2) {
+                            const float4 a = d4[q];
+                            d.x += a.x; d.y += a.y; d.z += a.z; d.w += a.w;
+                        }
+                        d4[q] = d;
+                    }
                 }
             }
         }
     }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, Sh::NCOL);
+    }
 }
-
 // dW[K][N] += A^T dZ over all rows (A = [A1, A2] split at K1, dZ: [M][N]).  Warp w owns
 // dW rows 16w..16w+15; the block reduces a chunk of kChunk rows with mma and adds its
 // partial into dW with atomics.
@@ -233,7 +332,8 @@ __global__ void k_colsum(const float* __restrict__ dZ, long long M, float* __res
 // out[i] = mean over neighbour buses m of in[(m, t)], or (transpose) out[i] += sum over
 // neighbours m of in[(m, t)] / deg(m).  One warp per node, two features per lane.
 template <int TRANSPOSE>
-__global__ void k_agg(const Ctx c, const float* __restrict__ in, float* __restrict__ out, long long M) {
+__global__ void k_agg(const Ctx c, const float* __restrict__ in, float* __restrict__ out,
+                      __nv_bfloat16* __restrict__ outb, long long M) {
     const long long i = (long long)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     if (i >= M) return;
     const int lane = threadIdx.x & 31;
@@ -261,6 +361,7 @@ __global__ void k_agg(const Ctx c, const float* __restrict__ in, float* __restri
     if (!TRANSPOSE) {
         const float w = e1 > e0 ? 1.f / (float)(e1 - e0) : 0.f;
         reinterpret_cast<float2*>(out + i * kH)[lane] = make_float2(a0 * w, a1 * w);
+        if (outb) reinterpret_cast<__nv_bfloat162*>(outb + i * kH)[lane] = __floats2bfloat162_rn(a0 * w, a1 * w);
     } else {
         float2* o = reinterpret_cast<float2*>(out + i * kH) + lane;
         const float2 prev = *o;
@@ -337,29 +438,14 @@ __global__ void k_head_back(const float* __restrict__ H, const float* __restrict
                     d0 * W[(2 * lane + 1) * 2] + d1 * W[(2 * lane + 1) * 2 + 1]);
 }
 
-// dZ = dH * (Z > 0)
+// dZ = dH * (Z > 0), and its BF16 copy (the operand of dZ W^T)
 __global__ void k_relu_back(const float* __restrict__ dH, const float* __restrict__ Z, float* __restrict__ dZ,
-                            long long n) {
+                            __nv_bfloat16* __restrict__ dZb, long long n) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) dZ[i] = Z[i] > 0.f ? dH[i] : 0.f;
-}
-
-// dH[:, 0:64] += dCat[:, 0:64]  (dCat is [M][128])
-__global__ void k_add_half(float* __restrict__ dH, const float* __restrict__ dCat, long long M) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= M * kH) return;
-    const long long r = i / kH;
-    const int k = (int)(i - r * kH);
-    dH[i] += dCat[r * 2 * kH + k];
-}
-
-// dAgg = dCat[:, 64:128] as a contiguous [M][64] array
-__global__ void k_take_half(const float* __restrict__ dCat, float* __restrict__ out, long long M) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= M * kH) return;
-    const long long r = i / kH;
-    const int k = (int)(i - r * kH);
-    out[i] = dCat[r * 2 * kH + kH + k];
+    if (i >= n) return;
+    const float d = Z[i] > 0.f ? dH[i] : 0.f;
+    dZ[i] = d;
+    dZb[i] = __float2bfloat16(d);
 }
 
 __global__ void k_adam(float* __restrict__ P, const float* __restrict__ G, float* __restrict__ m1,
@@ -374,21 +460,27 @@ __global__ void k_adam(float* __restrict__ P, const float* __restrict__ G, float
     P[i] -= lr * (a / c1) / (sqrtf(b / c2) + eps);
 }
 
-// BF16 copies of the GEMM weights: W_in^T [H][Fin]; W_k^T [H][2H] (forward) and W_k [2H][H]
-// (backward: dCat = dZ W_k^T uses B^T = W_k as stored).
-__global__ void k_to_bf16(const float* __restrict__ P, __nv_bfloat16* __restrict__ win_t,
-                          __nv_bfloat16* __restrict__ wk_t, __nv_bfloat16* __restrict__ wk) {
+// BF16 operand images of the dense layers' weights, in the swizzled K-major layout k_dense
+// reads (row n of B holds the weights of output n; see swz_offset):
+//   input layer   B[n][k] = W_in[k][n]   64 rows x 16 (32-byte swizzle)
+//   layer l       B[n][k] = W_l[k][n]    64 rows x 128: K-blocks [h | neighbour mean]
+//   layer l back  B[k][n] = W_l[k][n]    128 rows x 64 (dCat = dZ W_l^T)
+constexpr uint32_t kImgIn = kH * 2 * kFin;       // bytes
+constexpr uint32_t kImgLayer = 2 * kH * 2 * kH;  // bytes, forward or backward image of one layer
+__global__ void k_weight_images(const float* __restrict__ P, uint8_t* __restrict__ img_in,
+                                uint8_t* __restrict__ img_fwd, uint8_t* __restrict__ img_bwd) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < kFin * kH) {
         const int k = i / kH, n = i % kH;
-        win_t[n * kFin + k] = __float2bfloat16(P[kOffWin + i]);
+        *reinterpret_cast<__nv_bfloat16*>(img_in + swz_offset(n, k, 2 * kFin)) = __float2bfloat16(P[kOffWin + i]);
     }
     if (i < kLayers * 2 * kH * kH) {
         const int l = i / (2 * kH * kH), j = i % (2 * kH * kH);
         const int k = j / kH, n = j % kH;
-        const float v = P[kOffL0 + l * kLayerSz + j];
-        wk_t[l * 2 * kH * kH + n * 2 * kH + k] = __float2bfloat16(v);
-        wk[l * 2 * kH * kH + k * kH + n] = __float2bfloat16(v);
+        const __nv_bfloat16 v = __float2bfloat16(P[kOffL0 + l * kLayerSz + j]);
+        *reinterpret_cast<__nv_bfloat16*>(img_fwd + (size_t)l * kImgLayer + (k / kH) * (kH * 128) +
+                                          swz_offset(n, k % kH, 128)) = v;
+        *reinterpret_cast<__nv_bfloat16*>(img_bwd + (size_t)l * kImgLayer + swz_offset(k, n, 128)) = v;
     }
 }
 
@@ -412,8 +504,13 @@ struct gx_gnn {
     size_t bytes = 0;
     uint8_t* dev = nullptr;
     // offsets
-    size_t o_P, o_G, o_m1, o_m2, o_win_t, o_wk_t, o_wk, o_X, o_Z0, o_Hs, o_Zs, o_Agg, o_Y, o_dY, o_dH, o_dZ, o_dCat,
-        o_dAgg, o_loss;
+    size_t o_P, o_G, o_m1, o_m2, o_img_in, o_img_fwd, o_img_bwd, o_X, o_Z0, o_Hs, o_Zs, o_Agg, o_Y, o_dY, o_dH,
+        o_dZ, o_dAgg, o_loss, o_err;
+    // BF16 operands of the tensor-core layers: features, the two most recent hidden states
+    // (ping-pong), the neighbour mean of the current layer, dZ; and their TMA descriptors
+    size_t o_Xb, o_Hb, o_Agb, o_dZb;
+    enum { kMapX = 0, kMapH0, kMapH1, kMapAg, kMapdZ, kMaps };
+    CUtensorMap maps[kMaps];  // 128-byte aligned by its type
     // the network's learned start (GX_WARM_LEARNED): the prediction in the layout of a user
     // start, and room for the network's forward iteration state and per-scenario flags
     // while the solve compares the learned start with the previous plan's
@@ -426,6 +523,56 @@ size_t lay_add(size_t& total, size_t bytes) {
     const size_t o = total;
     total += (bytes + 255) / 256 * 256;
     return o;
+}
+}  // namespace
+
+namespace {
+// cuTensorMapEncodeTiled, through the runtime's driver entry point (no link to the driver library)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+// A [rows][cols] row-major BF16 array as 128-row boxes of all its columns, swizzled over
+// 2 * cols bytes (cols = 16 or 64: the layouts k_dense's descriptors describe).
+static gx_status encode_rows(CUtensorMap* m, void* dev, long long rows, int cols) {
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn) return gx_internal_fail(GX_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)cols, 128u};
+    const cuuint32_t es[2] = {1u, 1u};
+    const CUtensorMapSwizzle sw = cols == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_32B;
+    const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, dev, dims, strides, box, es,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return gx_internal_fail(GX_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    return GX_OK;
+}
+
+template <int NKB, int KW, int N, int EPI>
+static cudaError_t dense_prepare() {
+    return cudaFuncSetAttribute(k_dense<NKB, KW, N, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)DenseShape<NKB, KW, N>::SMEM);
+}
+
+template <int NKB, int KW, int N, int EPI>
+static void dense_launch(const CUtensorMap& a0, const CUtensorMap& a1, const uint8_t* img, const DenseOut& o,
+                         long long M, cudaStream_t st) {
+    const unsigned grid = (unsigned)((M + 127) / 128);
+    k_dense<NKB, KW, N, EPI><<<grid, 128, DenseShape<NKB, KW, N>::SMEM, st>>>(a0, a1, img, o, M);
 }
 }  // namespace
 
@@ -453,9 +600,9 @@ gx_status gx_gnn_create(const gx_network* net, int hidden, int layers, gx_gnn** 
     size_t t = 0;
     const size_t P = (size_t)kNParam * 4;
     g->o_P = lay_add(t, P); g->o_G = lay_add(t, P); g->o_m1 = lay_add(t, P); g->o_m2 = lay_add(t, P);
-    g->o_win_t = lay_add(t, 2 * kFin * kH);
-    g->o_wk_t = lay_add(t, 2 * (size_t)kLayers * 2 * kH * kH);
-    g->o_wk = lay_add(t, 2 * (size_t)kLayers * 2 * kH * kH);
+    g->o_img_in = lay_add(t, kImgIn);
+    g->o_img_fwd = lay_add(t, (size_t)kLayers * kImgLayer);
+    g->o_img_bwd = lay_add(t, (size_t)kLayers * kImgLayer);
     g->o_X = lay_add(t, 4 * (size_t)M * kFin);
     g->o_Z0 = lay_add(t, 4 * (size_t)M * kH);
     g->o_Hs = lay_add(t, 4 * (size_t)M * kH * (kLayers + 1));
@@ -465,7 +612,11 @@ gx_status gx_gnn_create(const gx_network* net, int hidden, int layers, gx_gnn** 
     g->o_dY = lay_add(t, 4 * (size_t)M * 2);
     g->o_dH = lay_add(t, 4 * (size_t)M * kH);
     g->o_dZ = lay_add(t, 4 * (size_t)M * kH);
-    g->o_dCat = lay_add(t, 4 * (size_t)M * 2 * kH);
+    g->o_Xb = lay_add(t, 2 * (size_t)M * kFin);
+    g->o_Hb = lay_add(t, 2 * (size_t)M * kH * 2);
+    g->o_Agb = lay_add(t, 2 * (size_t)M * kH);
+    g->o_dZb = lay_add(t, 2 * (size_t)M * kH);
+    g->o_err = lay_add(t, 4);
     g->o_dAgg = lay_add(t, 4 * (size_t)M * kH);
     g->o_loss = lay_add(t, 8);
     g->o_pred = lay_add(t, 4 * (size_t)M * 2);
@@ -487,12 +638,12 @@ gx_status gx_gnn_destroy(gx_gnn* g) {
 
 static gx_status gnn_refresh_bf16(gx_gnn* g, cudaStream_t st) {
     const int n = kLayers * 2 * kH * kH;
-    k_to_bf16<<<(n + 255) / 256, 256, 0, st>>>(reinterpret_cast<const float*>(g->dev + g->o_P),
-                                                reinterpret_cast<__nv_bfloat16*>(g->dev + g->o_win_t),
-                                                reinterpret_cast<__nv_bfloat16*>(g->dev + g->o_wk_t),
-                                                reinterpret_cast<__nv_bfloat16*>(g->dev + g->o_wk));
+    k_weight_images<<<(n + 255) / 256, 256, 0, st>>>(reinterpret_cast<const float*>(g->dev + g->o_P),
+                                                      g->dev + g->o_img_in, g->dev + g->o_img_fwd,
+                                                      g->dev + g->o_img_bwd);
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return gx_internal_fail(GX_ERR_CUDA, std::string("k_to_bf16: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess)
+        return gx_internal_fail(GX_ERR_CUDA, std::string("k_weight_images: ") + cudaGetErrorString(e));
     return GX_OK;
 }
 
@@ -520,10 +671,30 @@ gx_status gx_gnn_bind(gx_gnn* g, void* dev, size_t bytes, uint64_t seed, void* s
     if (!g || !dev) return gx_internal_fail(GX_ERR_INVALID_ARG, "NULL argument");
     if (reinterpret_cast<uintptr_t>(dev) % 256) return gx_internal_fail(GX_ERR_INVALID_ARG, "dev must be 256-byte aligned");
     if (bytes < g->bytes) return gx_internal_fail(GX_ERR_NO_MEMORY, "GNN workspace too small");
+    if (g->M > (1LL << 31) - 128) return gx_internal_fail(GX_ERR_INVALID_ARG, "too many bus-hours for the GNN");
     g->dev = reinterpret_cast<uint8_t*>(dev);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemsetAsync(g->dev, 0, g->bytes, st);
     if (e != cudaSuccess) return gx_internal_fail(GX_ERR_CUDA, cudaGetErrorString(e));
+    // tensor-core layers: TMA descriptors of the BF16 operands, shared-memory limits
+    const long long M = g->M;
+    uint8_t* Hb = g->dev + g->o_Hb;
+    gx_status sm = encode_rows(&g->maps[gx_gnn::kMapX], g->dev + g->o_Xb, M, kFin);
+    if (!sm) sm = encode_rows(&g->maps[gx_gnn::kMapH0], Hb, M, kH);
+    if (!sm) sm = encode_rows(&g->maps[gx_gnn::kMapH1], Hb + 2 * (size_t)M * kH, M, kH);
+    if (!sm) sm = encode_rows(&g->maps[gx_gnn::kMapAg], g->dev + g->o_Agb, M, kH);
+    if (!sm) sm = encode_rows(&g->maps[gx_gnn::kMapdZ], g->dev + g->o_dZb, M, kH);
+    if (sm) {
+        g->dev = nullptr;
+        return sm;
+    }
+    e = dense_prepare<1, kFin, kH, kEpiFwd>();
+    if (e == cudaSuccess) e = dense_prepare<2, kH, kH, kEpiFwd>();
+    if (e == cudaSuccess) e = dense_prepare<1, kH, 2 * kH, kEpiBwd>();
+    if (e != cudaSuccess) {
+        g->dev = nullptr;
+        return gx_internal_fail(GX_ERR_CUDA, std::string("k_dense attributes: ") + cudaGetErrorString(e));
+    }
     // He-style initialisation from a seeded host generator (biases 0)
     std::vector<float> P(kNParam, 0.f);
     std::mt19937_64 rng(seed);
@@ -537,25 +708,31 @@ gx_status gx_gnn_bind(gx_gnn* g, void* dev, size_t bytes, uint64_t seed, void* s
     return gx_gnn_set_params(g, P.data(), P.size(), stream);
 }
 
-static void gnn_forward(gx_gnn* g, const float* eta, cudaStream_t st) {
+// The network's forward pass; a tensor-core wait that runs out records GX_ERR_TIMEOUT in *err.
+static void gnn_forward(gx_gnn* g, const float* eta, cudaStream_t st, int* err) {
     const Ctx& c = *gx_internal_ctx(g->net);
     const long long M = g->M;
     auto F = [&](size_t o) { return reinterpret_cast<float*>(g->dev + o); };
-    auto B = [&](size_t o) { return reinterpret_cast<const __nv_bfloat16*>(g->dev + o); };
+    auto Bf = [&](size_t o) { return reinterpret_cast<__nv_bfloat16*>(g->dev + o); };
     float* P = F(g->o_P);
-    k_features<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(c, eta, F(g->o_X), M);
-    const unsigned gb = (unsigned)((M + 63) / 64);
+    __nv_bfloat16* Hb[2] = {Bf(g->o_Hb), Bf(g->o_Hb) + (size_t)M * kH};
+    const CUtensorMap* mapH[2] = {&g->maps[gx_gnn::kMapH0], &g->maps[gx_gnn::kMapH1]};
+    const CUtensorMap& mapAg = g->maps[gx_gnn::kMapAg];
+    k_features<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(c, eta, F(g->o_X), Bf(g->o_Xb), M);
     float* H0 = F(g->o_Hs);
-    k_gemm_fwd<kFin, kH><<<gb, 128, 0, st>>>(F(g->o_X), nullptr, kFin, B(g->o_win_t), P + kOffBin, nullptr,
-                                               F(g->o_Z0), H0, M, 1);
+    DenseOut o{P + kOffBin, nullptr, F(g->o_Z0), H0, Hb[0], nullptr, nullptr, err};
+    dense_launch<1, kFin, kH, kEpiFwd>(g->maps[gx_gnn::kMapX], g->maps[gx_gnn::kMapX], g->dev + g->o_img_in, o, M,
+                                        st);
     for (int l = 0; l < kLayers; ++l) {
         float* Hl = F(g->o_Hs) + (size_t)l * M * kH;
         float* Hn = F(g->o_Hs) + (size_t)(l + 1) * M * kH;
         float* Ag = F(g->o_Agg) + (size_t)l * M * kH;
-        float* Zl = F(g->o_Zs) + (size_t)l * M * kH;
-        k_agg<0><<<(unsigned)((M + 7) / 8), 256, 0, st>>>(c, Hl, Ag, M);
-        k_gemm_fwd<2 * kH, kH><<<gb, 128, 0, st>>>(Hl, Ag, kH, B(g->o_wk_t) + (size_t)l * 2 * kH * kH,
-                                                    P + kOffL0 + l * kLayerSz + 2 * kH * kH, Hl, Zl, Hn, M, 1);
+        k_agg<0><<<(unsigned)((M + 7) / 8), 256, 0, st>>>(c, Hl, Ag, Bf(g->o_Agb), M);
+        // H_{l+1} = H_l + relu([H_l, mean] W_l + b_l); its BF16 copy feeds the next layer
+        DenseOut ol{P + kOffL0 + l * kLayerSz + 2 * kH * kH, Hl, F(g->o_Zs) + (size_t)l * M * kH, Hn,
+                    l + 1 < kLayers ? Hb[(l + 1) & 1] : nullptr, nullptr, nullptr, err};
+        dense_launch<2, kH, kH, kEpiFwd>(*mapH[l & 1], mapAg, g->dev + g->o_img_fwd + (size_t)l * kImgLayer, ol, M,
+                                          st);
     }
     k_head<<<(unsigned)((M + 7) / 8), 256, 0, st>>>(F(g->o_Hs) + (size_t)kLayers * M * kH, P, F(g->o_Y), M);
 }
@@ -563,7 +740,7 @@ static void gnn_forward(gx_gnn* g, const float* eta, cudaStream_t st) {
 gx_status gx_gnn_predict(gx_gnn* g, const float* eta_dev, float* out_dev, void* stream) {
     if (!g || !g->dev || !eta_dev || !out_dev) return gx_internal_fail(GX_ERR_INVALID_ARG, "NULL argument or unbound");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    gnn_forward(g, eta_dev, st);
+    gnn_forward(g, eta_dev, st, reinterpret_cast<int*>(g->dev + g->o_err));
     k_unpack<<<(unsigned)((g->M + 255) / 256), 256, 0, st>>>(reinterpret_cast<float*>(g->dev + g->o_Y), out_dev, g->M);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return gx_internal_fail(GX_ERR_CUDA, std::string("gnn predict: ") + cudaGetErrorString(e));
@@ -576,7 +753,7 @@ namespace gx {
 const gx_network* gx_gnn_internal_net(const gx_gnn* g) { return g ? g->net : nullptr; }
 gx_status gx_gnn_internal_predict(gx_gnn* g, const float* eta, cudaStream_t st, const float** pred) {
     if (!g || !g->dev) return gx_internal_fail(GX_ERR_STATE, "the attached warm-start network is not bound");
-    gnn_forward(g, eta, st);
+    gnn_forward(g, eta, st, gx_internal_ctx(g->net)->err);  // reported with the solve's status
     float* out = reinterpret_cast<float*>(g->dev + g->o_pred);
     k_unpack<<<(unsigned)((g->M + 255) / 256), 256, 0, st>>>(reinterpret_cast<float*>(g->dev + g->o_Y), out, g->M);
     cudaError_t e = cudaGetLastError();
@@ -601,8 +778,9 @@ gx_status gx_gnn_train_step(gx_gnn* g, const float* eta_dev, const float* target
     const Ctx& c = *gx_internal_ctx(g->net);
     const long long M = g->M;
     auto F = [&](size_t o) { return reinterpret_cast<float*>(g->dev + o); };
-    auto B = [&](size_t o) { return reinterpret_cast<const __nv_bfloat16*>(g->dev + o); };
-    gnn_forward(g, eta_dev, st);
+    int* err = reinterpret_cast<int*>(g->dev + g->o_err);
+    __nv_bfloat16* dZb = reinterpret_cast<__nv_bfloat16*>(g->dev + g->o_dZb);
+    gnn_forward(g, eta_dev, st, err);
     float* P = F(g->o_P);
     float* G = F(g->o_G);
     cudaMemsetAsync(G, 0, 4 * (size_t)kNParam, st);
@@ -619,20 +797,19 @@ gx_status gx_gnn_train_step(gx_gnn* g, const float* eta_dev, const float* target
         float* Ag = F(g->o_Agg) + (size_t)l * M * kH;
         float* Zl = F(g->o_Zs) + (size_t)l * M * kH;
         float* dZ = F(g->o_dZ);
-        k_relu_back<<<ew, 256, 0, st>>>(dH, Zl, dZ, M * kH);
+        k_relu_back<<<ew, 256, 0, st>>>(dH, Zl, dZ, dZb, M * kH);
         float* GW = G + kOffL0 + l * kLayerSz;
         k_gemm_wgrad<2 * kH, kH><<<nchunk, 8 * 32, 0, st>>>(Hl, Ag, kH, dZ, M, GW);
         k_colsum<kH><<<nchunk, 256, 0, st>>>(dZ, M, GW + 2 * kH * kH);
-        // dCat = dZ W_l^T : B^T = W_l as stored ([2H][H], BF16)
-        k_gemm_fwd<kH, 2 * kH><<<(unsigned)((M + 63) / 64), 128, 0, st>>>(
-            dZ, nullptr, kH, B(g->o_wk) + (size_t)l * 2 * kH * kH, nullptr, nullptr, nullptr, F(g->o_dCat), M, 0);
-        // residual: dH stays; add the direct half and the transposed aggregation of the other half
-        k_add_half<<<ew, 256, 0, st>>>(dH, F(g->o_dCat), M);
-        k_take_half<<<ew, 256, 0, st>>>(F(g->o_dCat), F(g->o_dAgg), M);
-        k_agg<1><<<(unsigned)((M + 7) / 8), 256, 0, st>>>(c, F(g->o_dAgg), dH, M);
+        // [dH_direct, dAgg] = dZ W_l^T on the tensor cores; the residual keeps dH, the direct
+        // half is added into it, the neighbour half goes through the transposed aggregation
+        DenseOut ob{nullptr, nullptr, nullptr, nullptr, nullptr, dH, F(g->o_dAgg), err};
+        dense_launch<1, kH, 2 * kH, kEpiBwd>(g->maps[gx_gnn::kMapdZ], g->maps[gx_gnn::kMapdZ],
+                                              g->dev + g->o_img_bwd + (size_t)l * kImgLayer, ob, M, st);
+        k_agg<1><<<(unsigned)((M + 7) / 8), 256, 0, st>>>(c, F(g->o_dAgg), dH, nullptr, M);
     }
     float* dZ0 = F(g->o_dZ);
-    k_relu_back<<<ew, 256, 0, st>>>(dH, F(g->o_Z0), dZ0, M * kH);
+    k_relu_back<<<ew, 256, 0, st>>>(dH, F(g->o_Z0), dZ0, dZb, M * kH);
     k_gemm_wgrad<kFin, kH><<<nchunk, 32, 0, st>>>(F(g->o_X), nullptr, kFin, dZ0, M, G + kOffWin);
     k_colsum<kH><<<nchunk, 256, 0, st>>>(dZ0, M, G + kOffBin);
     if (lr > 0.f) {
@@ -645,9 +822,14 @@ gx_status gx_gnn_train_step(gx_gnn* g, const float* eta_dev, const float* target
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return gx_internal_fail(GX_ERR_CUDA, std::string("gnn train: ") + cudaGetErrorString(e));
     if (loss_host) {
+        // the loss, and the error word of this and earlier predictions / steps (then cleared)
+        int werr = 0;
         e = cudaMemcpyAsync(loss_host, g->dev + g->o_loss, 8, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&werr, err, 4, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess && werr) e = cudaMemsetAsync(err, 0, 4, st);
         if (e != cudaSuccess) return gx_internal_fail(GX_ERR_CUDA, cudaGetErrorString(e));
+        if (werr) return gx_internal_fail((gx_status)werr, "a tensor-core layer's copy or MMA wait ran out");
     }
     return GX_OK;
 }

@@ -16,6 +16,7 @@
 // reads 32 consecutive hours of one row: coalesced 128-byte transactions.  Bus arrays
 // (p_bar, u, theta_bar) are gathered by the device kernels through the same row layout.
 #include "gx_internal.cuh"
+#include "gx_async.cuh"
 
 #include <cfloat>
 
@@ -1109,42 +1110,6 @@ __global__ void __launch_bounds__(kBusQBlock, kBus4MinBlocks) k_bus4(const Ctx c
 // Adjoint generator masks (one byte per hour: not 16-byte aligned) come with per-thread
 // 4-byte asynchronous copies.  A record too large for the stage runs the unstaged loads.
 // ------------------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-// One bounded probe of the barrier's phase (try_wait suspends the thread for a while).
-__device__ __forceinline__ bool mbar_try(unsigned long long* bar, unsigned parity) {
-    unsigned ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Global -> shared bulk copy (TMA engine); bytes a multiple of 16, both addresses 16-byte aligned.
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_addr(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
-constexpr int kWaitProbes = 1 << 22;  // bounded mbarrier wait (each probe suspends briefly)
 
 // Whether a staged copy is issued: firm generators have no capacity-factor row to read and
 // ramp-limited ones no aux row at all (the bus only sums their injection).
