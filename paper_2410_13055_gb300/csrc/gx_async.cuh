@@ -77,25 +77,32 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 __host__ __device__ constexpr uint32_t swz_offset(uint32_t r, uint32_t k, uint32_t P) {
     return (r * P + 2 * k) ^ ((((r * P + 2 * k) >> 7) & (P / 16 - 1)) << 4);
 }
-// Matrix descriptor of a K-major swizzled operand starting at shared address `saddr` (the atom
-// base must be aligned to 8P bytes; a K step inside the row adds its byte offset to saddr).
-// Fields: start address >> 4 [0,14); leading-dimension offset [16,30) (unused by swizzled
-// K-major layouts, set to 1); stride offset between 8-row groups >> 4 [32,46); descriptor
-// version 1 [46,48); swizzle mode [61,64): 2 = 128 B, 4 = 64 B, 6 = 32 B.
-__device__ __forceinline__ uint64_t umma_sdesc(uint32_t saddr, uint32_t P) {
+// Matrix descriptor of a swizzled operand starting at shared address `saddr`; the atom base
+// must be aligned to 8P bytes (P: the swizzle span in bytes).  Fields: start address >> 4
+// [0,14); leading-dimension byte offset >> 4 [16,30); stride-dimension byte offset >> 4
+// [32,46); descriptor version 1 [46,48); swizzle mode [61,64): 2 = 128 B, 4 = 64 B, 6 = 32 B.
+//  * K-major (rows of P bytes along K, one row per M/N index): the stride offset is the
+//    distance between 8-row groups (8P); the leading offset is unused (1).  A K step inside
+//    the row adds its byte offset to saddr.
+//  * MN-major (rows of P bytes along M/N, one row per K index): the stride offset is the
+//    distance between 8-row groups along K, the leading offset the distance between
+//    consecutive P-byte groups along M/N.
+__device__ __forceinline__ uint64_t umma_sdesc(uint32_t saddr, uint32_t P, uint32_t lbo = 16, uint32_t sbo = 0) {
     const uint32_t mode = P == 128 ? 2u : P == 64 ? 4u : 6u;
+    if (sbo == 0) sbo = 8u * P;
     uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)1 << 16;
-    d |= (uint64_t)(((8u * P) >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
     d |= (uint64_t)1 << 46;
     d |= (uint64_t)mode << 61;
     return d;
 }
-// Instruction descriptor of kind::f16 with BF16 A and B (both K-major) and an FP32
-// accumulator: D format [4,6) = 1 (F32); A format [7,10) = 1 (BF16); B format [10,13) = 1;
-// N >> 3 at [17,23); M >> 4 at [24,29).
-__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// Instruction descriptor of kind::f16 with BF16 A and B and an FP32 accumulator: D format
+// [4,6) = 1 (F32); A format [7,10) = 1 (BF16); B format [10,13) = 1; A major [15] and B major
+// [16] (0 = K-major, 1 = MN-major); N >> 3 at [17,23); M >> 4 at [24,29).
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N, bool a_mn = false, bool b_mn = false) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn ? 1u : 0u) << 15) | ((b_mn ? 1u : 0u) << 16) |
+           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 // Tensor-memory allocation of `ncols` columns (a power of 2, >= 32) by one whole warp; the
 // base address is written to shared memory at `holder`.

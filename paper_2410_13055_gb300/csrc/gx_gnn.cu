@@ -14,14 +14,15 @@
 // 5th-generation tensor cores: tcgen05.mma with BF16 operands staged in shared memory by the
 // TMA engine and FP32 accumulators in tensor memory (k_dense).  Activations that feed a layer
 // are written in BF16 by their producer; the FP32 master parameters are copied into BF16
-// operand images after every update.  The weight gradients (a reduction over all rows) use
-// mma.sync.m16n8k16 with BF16 operands and FP32 accumulators.
+// operand images after every update.  The weight gradients, a reduction over all rows, run
+// on the tensor cores as well (k_wgrad: MN-major operands, a persistent CTA per SM).
 #include "gx_internal.cuh"
 #include "gx_async.cuh"
 
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <random>
@@ -44,19 +45,6 @@ constexpr int kOffBout = kOffWout + kH * 2;            // [2]
 constexpr int kNParam = kOffBout + 2;
 
 namespace {
-
-__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
-    __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
-    return *reinterpret_cast<uint32_t*>(&v);
-}
-
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
 
 __device__ __forceinline__ int scen_of_row(const ScenDev* sc, int S, long long row) {
     int lo = 0, hi = S - 1;
@@ -269,51 +257,115 @@ __global__ void __launch_bounds__(128) k_dense(const __grid_constant__ CUtensorM
         tmem_dealloc(tmem, Sh::NCOL);
     }
 }
-// dW[K][N] += A^T dZ over all rows (A = [A1, A2] split at K1, dZ: [M][N]).  Warp w owns
-// dW rows 16w..16w+15; the block reduces a chunk of kChunk rows with mma and adds its
-// partial into dW with atomics.
-constexpr int kChunk = 256;
-template <int K, int N>
-__global__ void k_gemm_wgrad(const float* __restrict__ A1, const float* __restrict__ A2, int K1,
-                             const float* __restrict__ dZ, long long M, float* __restrict__ dW) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int g = lane >> 2, q = lane & 3;
-    const int K2 = K - K1;
-    const int kk0 = warp * 16;
-    auto Aat = [&](long long r, int k) -> float {
-        if (r >= M) return 0.f;
-        return k < K1 ? A1[r * K1 + k] : A2[r * K2 + (k - K1)];
-    };
-    auto Dat = [&](long long r, int n) -> float { return r < M ? dZ[r * N + n] : 0.f; };
-    float acc[N / 8][4];
-#pragma unroll
-    for (int j = 0; j < N / 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-    const long long m_begin = (long long)blockIdx.x * kChunk;
-    for (long long m0 = m_begin; m0 < m_begin + kChunk && m0 < M; m0 += 16) {
-        // A operand: rows = kk (16 of this warp), cols = m (reduction)
-        uint32_t a[4];
-        const long long mc0 = m0 + 2 * q, mc1 = m0 + 2 * q + 8;
-        a[0] = pack_bf16(Aat(mc0, kk0 + g), Aat(mc0 + 1, kk0 + g));
-        a[1] = pack_bf16(Aat(mc0, kk0 + g + 8), Aat(mc0 + 1, kk0 + g + 8));
-        a[2] = pack_bf16(Aat(mc1, kk0 + g), Aat(mc1 + 1, kk0 + g));
-        a[3] = pack_bf16(Aat(mc1, kk0 + g + 8), Aat(mc1 + 1, kk0 + g + 8));
-#pragma unroll
-        for (int j = 0; j < N / 8; ++j) {
-            const int n = j * 8 + g;
-            const uint32_t b0 = pack_bf16(Dat(mc0, n), Dat(mc0 + 1, n));
-            const uint32_t b1 = pack_bf16(Dat(mc1, n), Dat(mc1 + 1, n));
-            mma_bf16(acc[j], a, b0, b1);
+// ---------------------------------------------------------------- weight gradients (tcgen05)
+// dW[k][n] += sum over rows m of A[m][k] dZ[m][n]: D = A^T dZ with the rows as the MMA's K
+// dimension, so both operands are MN-major tiles (a row of 64 BF16 columns = 128 bytes per
+// bus-hour), exactly the 128-row boxes the TMA engine brings from the row-major arrays.  A
+// persistent CTA per SM streams its row tiles through a kWStages-deep ring (warp 0 loads;
+// warp 1 issues the MMAs and releases each stage with a commit once its MMAs have read it)
+// into one 128 x 64 FP32 accumulator in tensor memory, then adds it into dW with atomics.
+//   KIN = 128: A = [h | neighbour mean] (two 64-column groups, kWTile bytes apart), dW [128][64]
+//   KIN = 16:  A = the features through a 64-column box (columns from 16 on arrive as zeros),
+//              dW [16][64]; accumulator rows from 16 on are not used
+constexpr int kWStages = 4;
+constexpr uint32_t kWTile = 128 * 128;    // bytes of one 128-row x 64-column BF16 tile
+constexpr uint32_t kWStage = 3 * kWTile;  // A group 0, A group 1, dZ
+constexpr uint32_t kWSmem = 1024 + kWStages * kWStage + 256;
+
+template <int KIN>
+__global__ void __launch_bounds__(128, 1) k_wgrad(const __grid_constant__ CUtensorMap a0,
+                                                  const __grid_constant__ CUtensorMap a1,
+                                                  const __grid_constant__ CUtensorMap dz, float* __restrict__ dW,
+                                                  long long M, int* __restrict__ err) {
+    static_assert(KIN == 128 || KIN == 16, "hidden layer or input layer");
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sm = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
+    unsigned long long* full = reinterpret_cast<unsigned long long*>(sm + kWStages * kWStage);
+    unsigned long long* empty = full + kWStages;
+    unsigned long long* done = empty + kWStages;
+    uint32_t* holder = reinterpret_cast<uint32_t*>(done + 1);
+    volatile int* failed = reinterpret_cast<volatile int*>(holder + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long ntiles = (M + 127) / 128;
+    constexpr uint32_t TX = (KIN == 128 ? 3u : 2u) * kWTile;
+    if (warp == 0) tmem_alloc(holder, 64);
+    if (tid == 0) {
+        for (int s = 0; s < kWStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
         }
+        mbar_init(done, 1);
+        *failed = 0;
+        mbar_fence_init();
     }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *holder;
+    if (warp == 0 && lane == 0) {
+        int it = 0;
+        for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+            const int s = it % kWStages, u = it / kWStages;
+            if (u > 0 && !mbar_wait_bounded(&empty[s], (u - 1) & 1)) {
+                *failed = 1;
+                break;
+            }
+            uint8_t* st = sm + s * kWStage;
+            mbar_expect_tx(&full[s], TX);
+            const int y = (int)(t * 128);
+            tma_load_2d(st, &a0, 0, y, &full[s]);
+            if (KIN == 128) tma_load_2d(st + kWTile, &a1, 0, y, &full[s]);
+            tma_load_2d(st + 2 * kWTile, &dz, 0, y, &full[s]);
+        }
+        // the CTA may not exit with copies in flight: the last fill of each stage has landed
+        for (int k = it > kWStages ? it - kWStages : 0; k < it; ++k)
+            mbar_wait_bounded(&full[k % kWStages], (k / kWStages) & 1);
+    } else if (warp == 1 && lane == 0) {
+        constexpr uint32_t idesc = umma_idesc_bf16(128, 64, true, true);
+        int it = 0;
+        for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+            const int s = it % kWStages, u = it / kWStages;
+            if (!mbar_wait_bounded(&full[s], u & 1)) {
+                *failed = 1;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t st = smem_addr(sm + s * kWStage);
 #pragma unroll
-    for (int j = 0; j < N / 8; ++j) {
-        const int col = j * 8 + 2 * q;
-        atomicAdd(&dW[(kk0 + g) * N + col], acc[j][0]);
-        atomicAdd(&dW[(kk0 + g) * N + col + 1], acc[j][1]);
-        atomicAdd(&dW[(kk0 + g + 8) * N + col], acc[j][2]);
-        atomicAdd(&dW[(kk0 + g + 8) * N + col + 1], acc[j][3]);
+            for (int j = 0; j < 8; ++j)  // 16 rows (the MMA's K) per instruction
+                umma_bf16(tmem, umma_sdesc(st + 2048u * j, 128, kWTile, 1024),
+                          umma_sdesc(st + 2 * kWTile + 2048u * j, 128, kWTile, 1024), idesc, (it | j) != 0);
+            umma_commit(&empty[s]);
+        }
+        umma_commit(done);
+    }
+    __syncthreads();
+    bool ok = *failed == 0 && mbar_wait_bounded(done, 0);
+    ok = __all_sync(0xffffffffu, ok);
+    tc_fence_after();
+    if (ok) {
+        const uint32_t tq = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+        for (int c = 0; c < 2; ++c) {
+            float v[32];
+            tmem_ld32(tq + 32u * c, v);  // warp-collective
+            if (tid < KIN) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) atomicAdd(&dW[tid * 64 + 32 * c + j], v[j]);
+            }
+        }
+    } else if (lane == 0) {
+        atomicExch(err, (int)GX_ERR_TIMEOUT);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 64);
     }
 }
+
+constexpr int kChunk = 256;  // rows per block of the bias-gradient column sums
 
 // column sums of dZ [M][N] into db[N] (FP32 atomics per block)
 template <int N>
@@ -506,10 +558,12 @@ struct gx_gnn {
     // offsets
     size_t o_P, o_G, o_m1, o_m2, o_img_in, o_img_fwd, o_img_bwd, o_X, o_Z0, o_Hs, o_Zs, o_Agg, o_Y, o_dY, o_dH,
         o_dZ, o_dAgg, o_loss, o_err;
-    // BF16 operands of the tensor-core layers: features, the two most recent hidden states
-    // (ping-pong), the neighbour mean of the current layer, dZ; and their TMA descriptors
+    // BF16 operands of the tensor-core layers: features, the inputs h_l and neighbour means
+    // of each layer (kept for the weight gradients), dZ; and their TMA descriptors (128-row
+    // boxes; the features also as a 64-column box for the weight gradient of W_in)
     size_t o_Xb, o_Hb, o_Agb, o_dZb;
-    enum { kMapX = 0, kMapH0, kMapH1, kMapAg, kMapdZ, kMaps };
+    enum { kMapX = 0, kMapXw, kMapH, kMapAg = kMapH + kLayers, kMapdZ = kMapAg + kLayers, kMaps };
+    int sms = 0;  // multiprocessors: CTAs of the persistent weight-gradient kernels
     CUtensorMap maps[kMaps];  // 128-byte aligned by its type
     // the network's learned start (GX_WARM_LEARNED): the prediction in the layout of a user
     // start, and room for the network's forward iteration state and per-scenario flags
@@ -545,16 +599,17 @@ static EncodeTiledFn encode_tiled() {
     return fn;
 }
 
-// A [rows][cols] row-major BF16 array as 128-row boxes of all its columns, swizzled over
-// 2 * cols bytes (cols = 16 or 64: the layouts k_dense's descriptors describe).
-static gx_status encode_rows(CUtensorMap* m, void* dev, long long rows, int cols) {
+// A [rows][cols] row-major BF16 array as boxes of 128 rows x box_cols columns (columns past
+// cols arrive as zeros), swizzled over 2 * box_cols bytes (box_cols = 16 or 64: the layouts
+// the tensor-core kernels' descriptors describe).
+static gx_status encode_rows(CUtensorMap* m, void* dev, long long rows, int cols, int box_cols) {
     EncodeTiledFn fn = encode_tiled();
     if (!fn) return gx_internal_fail(GX_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
     const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
-    const cuuint32_t box[2] = {(cuuint32_t)cols, 128u};
+    const cuuint32_t box[2] = {(cuuint32_t)box_cols, 128u};
     const cuuint32_t es[2] = {1u, 1u};
-    const CUtensorMapSwizzle sw = cols == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_32B;
+    const CUtensorMapSwizzle sw = box_cols == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_32B;
     const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, dev, dims, strides, box, es,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -613,8 +668,8 @@ gx_status gx_gnn_create(const gx_network* net, int hidden, int layers, gx_gnn** 
     g->o_dH = lay_add(t, 4 * (size_t)M * kH);
     g->o_dZ = lay_add(t, 4 * (size_t)M * kH);
     g->o_Xb = lay_add(t, 2 * (size_t)M * kFin);
-    g->o_Hb = lay_add(t, 2 * (size_t)M * kH * 2);
-    g->o_Agb = lay_add(t, 2 * (size_t)M * kH);
+    g->o_Hb = lay_add(t, 2 * (size_t)M * kH * kLayers);
+    g->o_Agb = lay_add(t, 2 * (size_t)M * kH * kLayers);
     g->o_dZb = lay_add(t, 2 * (size_t)M * kH);
     g->o_err = lay_add(t, 4);
     g->o_dAgg = lay_add(t, 4 * (size_t)M * kH);
@@ -678,19 +733,27 @@ gx_status gx_gnn_bind(gx_gnn* g, void* dev, size_t bytes, uint64_t seed, void* s
     if (e != cudaSuccess) return gx_internal_fail(GX_ERR_CUDA, cudaGetErrorString(e));
     // tensor-core layers: TMA descriptors of the BF16 operands, shared-memory limits
     const long long M = g->M;
-    uint8_t* Hb = g->dev + g->o_Hb;
-    gx_status sm = encode_rows(&g->maps[gx_gnn::kMapX], g->dev + g->o_Xb, M, kFin);
-    if (!sm) sm = encode_rows(&g->maps[gx_gnn::kMapH0], Hb, M, kH);
-    if (!sm) sm = encode_rows(&g->maps[gx_gnn::kMapH1], Hb + 2 * (size_t)M * kH, M, kH);
-    if (!sm) sm = encode_rows(&g->maps[gx_gnn::kMapAg], g->dev + g->o_Agb, M, kH);
-    if (!sm) sm = encode_rows(&g->maps[gx_gnn::kMapdZ], g->dev + g->o_dZb, M, kH);
+    gx_status sm = encode_rows(&g->maps[gx_gnn::kMapX], g->dev + g->o_Xb, M, kFin, kFin);
+    if (!sm) sm = encode_rows(&g->maps[gx_gnn::kMapXw], g->dev + g->o_Xb, M, kFin, kH);
+    for (int l = 0; l < kLayers && !sm; ++l) {
+        sm = encode_rows(&g->maps[gx_gnn::kMapH + l], g->dev + g->o_Hb + 2 * (size_t)l * M * kH, M, kH, kH);
+        if (!sm) sm = encode_rows(&g->maps[gx_gnn::kMapAg + l], g->dev + g->o_Agb + 2 * (size_t)l * M * kH, M, kH, kH);
+    }
+    if (!sm) sm = encode_rows(&g->maps[gx_gnn::kMapdZ], g->dev + g->o_dZb, M, kH, kH);
     if (sm) {
         g->dev = nullptr;
         return sm;
     }
-    e = dense_prepare<1, kFin, kH, kEpiFwd>();
+    int dev_id = 0;
+    e = cudaGetDevice(&dev_id);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, dev_id);
+    if (e == cudaSuccess) e = dense_prepare<1, kFin, kH, kEpiFwd>();
     if (e == cudaSuccess) e = dense_prepare<2, kH, kH, kEpiFwd>();
     if (e == cudaSuccess) e = dense_prepare<1, kH, 2 * kH, kEpiBwd>();
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_wgrad<2 * kH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_wgrad<kFin>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWSmem);
     if (e != cudaSuccess) {
         g->dev = nullptr;
         return gx_internal_fail(GX_ERR_CUDA, std::string("k_dense attributes: ") + cudaGetErrorString(e));
@@ -715,24 +778,23 @@ static void gnn_forward(gx_gnn* g, const float* eta, cudaStream_t st, int* err) 
     auto F = [&](size_t o) { return reinterpret_cast<float*>(g->dev + o); };
     auto Bf = [&](size_t o) { return reinterpret_cast<__nv_bfloat16*>(g->dev + o); };
     float* P = F(g->o_P);
-    __nv_bfloat16* Hb[2] = {Bf(g->o_Hb), Bf(g->o_Hb) + (size_t)M * kH};
-    const CUtensorMap* mapH[2] = {&g->maps[gx_gnn::kMapH0], &g->maps[gx_gnn::kMapH1]};
-    const CUtensorMap& mapAg = g->maps[gx_gnn::kMapAg];
+    auto Hb = [&](int l) { return Bf(g->o_Hb) + (size_t)l * M * kH; };
+    auto Agb = [&](int l) { return Bf(g->o_Agb) + (size_t)l * M * kH; };
     k_features<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(c, eta, F(g->o_X), Bf(g->o_Xb), M);
     float* H0 = F(g->o_Hs);
-    DenseOut o{P + kOffBin, nullptr, F(g->o_Z0), H0, Hb[0], nullptr, nullptr, err};
+    DenseOut o{P + kOffBin, nullptr, F(g->o_Z0), H0, Hb(0), nullptr, nullptr, err};
     dense_launch<1, kFin, kH, kEpiFwd>(g->maps[gx_gnn::kMapX], g->maps[gx_gnn::kMapX], g->dev + g->o_img_in, o, M,
                                         st);
     for (int l = 0; l < kLayers; ++l) {
         float* Hl = F(g->o_Hs) + (size_t)l * M * kH;
         float* Hn = F(g->o_Hs) + (size_t)(l + 1) * M * kH;
         float* Ag = F(g->o_Agg) + (size_t)l * M * kH;
-        k_agg<0><<<(unsigned)((M + 7) / 8), 256, 0, st>>>(c, Hl, Ag, Bf(g->o_Agb), M);
+        k_agg<0><<<(unsigned)((M + 7) / 8), 256, 0, st>>>(c, Hl, Ag, Agb(l), M);
         // H_{l+1} = H_l + relu([H_l, mean] W_l + b_l); its BF16 copy feeds the next layer
         DenseOut ol{P + kOffL0 + l * kLayerSz + 2 * kH * kH, Hl, F(g->o_Zs) + (size_t)l * M * kH, Hn,
-                    l + 1 < kLayers ? Hb[(l + 1) & 1] : nullptr, nullptr, nullptr, err};
-        dense_launch<2, kH, kH, kEpiFwd>(*mapH[l & 1], mapAg, g->dev + g->o_img_fwd + (size_t)l * kImgLayer, ol, M,
-                                          st);
+                    l + 1 < kLayers ? Hb(l + 1) : nullptr, nullptr, nullptr, err};
+        dense_launch<2, kH, kH, kEpiFwd>(g->maps[gx_gnn::kMapH + l], g->maps[gx_gnn::kMapAg + l],
+                                          g->dev + g->o_img_fwd + (size_t)l * kImgLayer, ol, M, st);
     }
     k_head<<<(unsigned)((M + 7) / 8), 256, 0, st>>>(F(g->o_Hs) + (size_t)kLayers * M * kH, P, F(g->o_Y), M);
 }
@@ -792,25 +854,28 @@ gx_status gx_gnn_train_step(gx_gnn* g, const float* eta_dev, const float* target
                                                          dH, M);
     const unsigned ew = (unsigned)((M * kH + 255) / 256);
     const unsigned nchunk = (unsigned)((M + kChunk - 1) / kChunk);
+    // persistent weight-gradient CTAs: one per SM, none without a row tile
+    const long long ntiles = (M + 127) / 128;
+    const unsigned wg = (unsigned)std::min<long long>(ntiles, std::max(g->sms, 1));
+    const CUtensorMap& mapdZ = g->maps[gx_gnn::kMapdZ];
     for (int l = kLayers - 1; l >= 0; --l) {
-        float* Hl = F(g->o_Hs) + (size_t)l * M * kH;
-        float* Ag = F(g->o_Agg) + (size_t)l * M * kH;
         float* Zl = F(g->o_Zs) + (size_t)l * M * kH;
         float* dZ = F(g->o_dZ);
         k_relu_back<<<ew, 256, 0, st>>>(dH, Zl, dZ, dZb, M * kH);
         float* GW = G + kOffL0 + l * kLayerSz;
-        k_gemm_wgrad<2 * kH, kH><<<nchunk, 8 * 32, 0, st>>>(Hl, Ag, kH, dZ, M, GW);
+        k_wgrad<2 * kH><<<wg, 128, kWSmem, st>>>(g->maps[gx_gnn::kMapH + l], g->maps[gx_gnn::kMapAg + l], mapdZ, GW,
+                                                   M, err);
         k_colsum<kH><<<nchunk, 256, 0, st>>>(dZ, M, GW + 2 * kH * kH);
         // [dH_direct, dAgg] = dZ W_l^T on the tensor cores; the residual keeps dH, the direct
         // half is added into it, the neighbour half goes through the transposed aggregation
         DenseOut ob{nullptr, nullptr, nullptr, nullptr, nullptr, dH, F(g->o_dAgg), err};
-        dense_launch<1, kH, 2 * kH, kEpiBwd>(g->maps[gx_gnn::kMapdZ], g->maps[gx_gnn::kMapdZ],
-                                              g->dev + g->o_img_bwd + (size_t)l * kImgLayer, ob, M, st);
+        dense_launch<1, kH, 2 * kH, kEpiBwd>(mapdZ, mapdZ, g->dev + g->o_img_bwd + (size_t)l * kImgLayer, ob, M, st);
         k_agg<1><<<(unsigned)((M + 7) / 8), 256, 0, st>>>(c, F(g->o_dAgg), dH, nullptr, M);
     }
     float* dZ0 = F(g->o_dZ);
     k_relu_back<<<ew, 256, 0, st>>>(dH, F(g->o_Z0), dZ0, dZb, M * kH);
-    k_gemm_wgrad<kFin, kH><<<nchunk, 32, 0, st>>>(F(g->o_X), nullptr, kFin, dZ0, M, G + kOffWin);
+    k_wgrad<kFin><<<wg, 128, kWSmem, st>>>(g->maps[gx_gnn::kMapXw], g->maps[gx_gnn::kMapXw], mapdZ, G + kOffWin, M,
+                                             err);
     k_colsum<kH><<<nchunk, 256, 0, st>>>(dZ0, M, G + kOffBin);
     if (lr > 0.f) {
         g->step += 1;
