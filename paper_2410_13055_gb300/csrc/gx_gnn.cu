@@ -139,10 +139,16 @@ struct DenseShape {
     static constexpr uint32_t BBYTES = NKB * BTILE;  // the weight image
     static constexpr uint32_t TX = NKB * (ATILE + BTILE);
     static constexpr uint32_t NCOL = N;  // tensor-memory columns: a power of 2 >= 32
-    // dynamic shared memory: 1024-byte alignment slack, the tiles, two barriers and the
-    // tensor-memory address; at least enough that the CTAs resident on one SM never ask for
-    // more than its 512 tensor-memory columns (4 x 64, 6 x 64 or 3 x 128)
-    static constexpr uint32_t USED = 1024 + TX + 64;
+    // epilogue stage: per warp 32 rows x 32 columns (row pitch 36 floats), placed over the
+    // tiles when they are large enough (every MMA has read them by then), else after them
+    static constexpr uint32_t EPITCH = 36;
+    static constexpr uint32_t ESTAGE = 4 * 32 * EPITCH * 4;
+    static constexpr uint32_t EOFF = TX >= ESTAGE ? 0 : TX;
+    static constexpr uint32_t BAROFF = TX > EOFF + ESTAGE ? TX : EOFF + ESTAGE;
+    // dynamic shared memory: 1024-byte alignment slack, the tiles (and stage), two barriers
+    // and the tensor-memory address; at least enough that the CTAs resident on one SM never
+    // ask for more than its 512 tensor-memory columns (4 x 64, 6 x 64 or 3 x 128)
+    static constexpr uint32_t USED = 1024 + BAROFF + 64;
     static constexpr uint32_t MIN = N == 128 ? 60u * 1024u : 32u * 1024u;
     static constexpr uint32_t SMEM = USED > MIN ? USED : MIN;
     static_assert(KW == 16 || KW == 64, "K-blocks of 16 (32-byte swizzle) or 64 (128-byte swizzle) columns");
@@ -158,7 +164,8 @@ __global__ void __launch_bounds__(128) k_dense(const __grid_constant__ CUtensorM
     uint8_t* sm = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
     uint8_t* sA = sm;
     uint8_t* sB = sm + NKB * Sh::ATILE;
-    unsigned long long* bar = reinterpret_cast<unsigned long long*>(sB + Sh::BBYTES);  // [0] copies, [1] MMAs
+    float* sE = reinterpret_cast<float*>(sm + Sh::EOFF) + (threadIdx.x >> 5) * 32 * Sh::EPITCH;
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(sm + Sh::BAROFF);  // [0] copies, [1] MMAs
     uint32_t* holder = reinterpret_cast<uint32_t*>(bar + 2);
     int* copied = reinterpret_cast<int*>(holder + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -203,50 +210,53 @@ __global__ void __launch_bounds__(128) k_dense(const __grid_constant__ CUtensorM
         if (!ok) {
             if (lane == 0) atomicExch(o.err, (int)GX_ERR_TIMEOUT);
         } else {
-            const long long r = row0 + tid;
+            // Each warp reads its 32 accumulator rows (a row per lane), transposes them through
+            // its shared-memory stage, and writes rows as 128-byte segments: lane l takes
+            // columns 4 (l % 8) .. +3 of rows 4 i + l / 8, i = 0..7.
             const uint32_t tq = tmem + ((uint32_t)(warp * 32) << 16);
+            const int cq = lane & 7, rq = lane >> 3;
 #pragma unroll 1
             for (int c = 0; c < N / 32; ++c) {
                 float v[32];
                 tmem_ld32(tq + 32u * c, v);  // warp-collective: rows past M take part too
-                if (r >= M) continue;
-                if (EPI == kEpiFwd) {
-                    const float4* b4 = reinterpret_cast<const float4*>(o.bias + 32 * c);
-                    const float4* r4 = o.resid ? reinterpret_cast<const float4*>(o.resid + r * N + 32 * c) : nullptr;
-                    float4* z4 = o.Z ? reinterpret_cast<float4*>(o.Z + r * N + 32 * c) : nullptr;
-                    float4* h4 = reinterpret_cast<float4*>(o.H + r * N + 32 * c);
-                    uint2* hb = o.Hb ? reinterpret_cast<uint2*>(o.Hb + r * N + 32 * c) : nullptr;
+                float4* mine = reinterpret_cast<float4*>(sE + lane * Sh::EPITCH);
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const float4 b = b4[q];
-                        const float4 z = make_float4(v[4 * q] + b.x, v[4 * q + 1] + b.y, v[4 * q + 2] + b.z,
-                                                     v[4 * q + 3] + b.w);
-                        if (z4) z4[q] = z;
+                for (int q = 0; q < 8; ++q) mine[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                __syncwarp();
+                const int col = 32 * c + 4 * cq;
+                float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (EPI == kEpiFwd) b = *reinterpret_cast<const float4*>(o.bias + col);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int lr = 4 * i + rq;
+                    const long long r = row0 + warp * 32 + lr;
+                    if (r >= M) continue;
+                    const float4 d = *reinterpret_cast<const float4*>(sE + lr * Sh::EPITCH + 4 * cq);
+                    if (EPI == kEpiFwd) {
+                        const float4 z = make_float4(d.x + b.x, d.y + b.y, d.z + b.z, d.w + b.w);
+                        if (o.Z) *reinterpret_cast<float4*>(o.Z + r * N + col) = z;
                         float4 h = make_float4(fmaxf(z.x, 0.f), fmaxf(z.y, 0.f), fmaxf(z.z, 0.f), fmaxf(z.w, 0.f));
-                        if (r4) {
-                            const float4 a = r4[q];
+                        if (o.resid) {
+                            const float4 a = *reinterpret_cast<const float4*>(o.resid + r * N + col);
                             h.x += a.x; h.y += a.y; h.z += a.z; h.w += a.w;
                         }
-                        h4[q] = h;
-                        if (hb) {
+                        *reinterpret_cast<float4*>(o.H + r * N + col) = h;
+                        if (o.Hb) {
                             __nv_bfloat162 lo = __floats2bfloat162_rn(h.x, h.y), hi = __floats2bfloat162_rn(h.z, h.w);
-                            hb[q] = make_uint2(*reinterpret_cast<uint32_t*>(&lo), *reinterpret_cast<uint32_t*>(&hi));
+                            *reinterpret_cast<uint2*>(o.Hb + r * N + col) =
+                                make_uint2(*reinterpret_cast<uint32_t*>(&lo), *reinterpret_cast<uint32_t*>(&hi));
                         }
-                    }
-                } else {
-                    // columns [0, 64): the direct half, added into dH; [64, 128): the neighbour half
-                    float4* d4 = c < 2 ? reinterpret_cast<float4*>(o.dH + r * kH + 32 * c)
-                                       : reinterpret_cast<float4*>(o.dAgg + r * kH + 32 * (c - 2));
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        float4 d = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-                        if (c < 2) {
-                            const float4 a = d4[q];
-                            d.x += a.x; d.y += a.y; d.z += a.z; d.w += a.w;
-                        }
-                        d4[q] = d;
+                    } else if (c < 2) {
+                        // columns [0, 64): the direct half, added into dH
+                        float4* p = reinterpret_cast<float4*>(o.dH + r * kH + col);
+                        const float4 a = *p;
+                        *p = make_float4(a.x + d.x, a.y + d.y, a.z + d.z, a.w + d.w);
+                    } else {
+                        // columns [64, 128): the neighbour half
+                        *reinterpret_cast<float4*>(o.dAgg + r * kH + col - kH) = d;
                     }
                 }
+                __syncwarp();
             }
         }
     }
@@ -465,29 +475,44 @@ __global__ void k_loss(const Ctx c, const float* __restrict__ Y, const float* __
     if ((threadIdx.x & 31) == 0 && l != 0.0) atomicAdd(loss, l * inv_count);
 }
 
-// dW_out += H^T dY, db_out += sum dY, dH = dY W_out^T
-__global__ void k_head_back(const float* __restrict__ H, const float* __restrict__ dY, const float* __restrict__ P,
-                            float* __restrict__ G, float* __restrict__ dH, long long M) {
-    const long long i = (long long)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
-    if (i >= M) return;
-    const int lane = threadIdx.x & 31;
-    const float2 h = reinterpret_cast<const float2*>(H + i * kH)[lane];
-    const float d0 = dY[2 * i], d1 = dY[2 * i + 1];
+// dW_out += H^T dY, db_out += sum dY, dH = dY W_out^T.  Warps stride over nodes (lane l owns
+// hidden units 2l, 2l + 1); the block sums its warps' partial weight gradients in shared
+// memory and adds them with one atomic per weight.
+constexpr int kHeadBlocks = 1024;
+__global__ void __launch_bounds__(256) k_head_back(const float* __restrict__ H, const float* __restrict__ dY,
+                                                   const float* __restrict__ P, float* __restrict__ G,
+                                                   float* __restrict__ dH, long long M) {
+    __shared__ float red[8][2 * kH + 2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float* W = P + kOffWout;
-    float* GW = G + kOffWout;
-    if (d0 != 0.f || d1 != 0.f) {
-        atomicAdd(&GW[(2 * lane) * 2 + 0], h.x * d0);
-        atomicAdd(&GW[(2 * lane) * 2 + 1], h.x * d1);
-        atomicAdd(&GW[(2 * lane + 1) * 2 + 0], h.y * d0);
-        atomicAdd(&GW[(2 * lane + 1) * 2 + 1], h.y * d1);
-        if (lane == 0) {
-            atomicAdd(&G[kOffBout], d0);
-            atomicAdd(&G[kOffBout + 1], d1);
-        }
+    const float w00 = W[(2 * lane) * 2], w01 = W[(2 * lane) * 2 + 1];
+    const float w10 = W[(2 * lane + 1) * 2], w11 = W[(2 * lane + 1) * 2 + 1];
+    float g00 = 0.f, g01 = 0.f, g10 = 0.f, g11 = 0.f, b0 = 0.f, b1 = 0.f;
+    for (long long i = (long long)blockIdx.x * 8 + warp; i < M; i += (long long)gridDim.x * 8) {
+        const float2 h = reinterpret_cast<const float2*>(H + i * kH)[lane];
+        const float d0 = dY[2 * i], d1 = dY[2 * i + 1];
+        g00 += h.x * d0; g01 += h.x * d1;
+        g10 += h.y * d0; g11 += h.y * d1;
+        b0 += d0; b1 += d1;
+        reinterpret_cast<float2*>(dH + i * kH)[lane] = make_float2(d0 * w00 + d1 * w01, d0 * w10 + d1 * w11);
     }
-    reinterpret_cast<float2*>(dH + i * kH)[lane] =
-        make_float2(d0 * W[(2 * lane) * 2] + d1 * W[(2 * lane) * 2 + 1],
-                    d0 * W[(2 * lane + 1) * 2] + d1 * W[(2 * lane + 1) * 2 + 1]);
+    red[warp][4 * lane] = g00;
+    red[warp][4 * lane + 1] = g01;
+    red[warp][4 * lane + 2] = g10;
+    red[warp][4 * lane + 3] = g11;
+    if (lane == 0) {
+        red[warp][2 * kH] = b0;
+        red[warp][2 * kH + 1] = b1;
+    }
+    __syncthreads();
+    // red[w][4 l + 2 u + o] is the gradient of W_out[2 l + u][o] = GW[(2 l + u) * 2 + o]
+    for (int k = threadIdx.x; k < 2 * kH + 2; k += blockDim.x) {
+        float t = 0.f;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) t += red[w][k];
+        if (k < 2 * kH) atomicAdd(&G[kOffWout + k], t);
+        else atomicAdd(&G[kOffBout + k - 2 * kH], t);
+    }
 }
 
 // dZ = dH * (Z > 0), and its BF16 copy (the operand of dZ W^T)
@@ -850,8 +875,8 @@ gx_status gx_gnn_train_step(gx_gnn* g, const float* eta_dev, const float* target
     k_loss<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(c, F(g->o_Y), target_dev, M, 1.0 / g->valid, w_theta,
                                                         F(g->o_dY), reinterpret_cast<double*>(g->dev + g->o_loss));
     float* dH = F(g->o_dH);
-    k_head_back<<<(unsigned)((M + 7) / 8), 256, 0, st>>>(F(g->o_Hs) + (size_t)kLayers * M * kH, F(g->o_dY), P, G,
-                                                         dH, M);
+    k_head_back<<<(unsigned)std::min<long long>((M + 7) / 8, kHeadBlocks), 256, 0, st>>>(
+        F(g->o_Hs) + (size_t)kLayers * M * kH, F(g->o_dY), P, G, dH, M);
     const unsigned ew = (unsigned)((M * kH + 255) / 256);
     const unsigned nchunk = (unsigned)((M + kChunk - 1) / kChunk);
     // persistent weight-gradient CTAs: one per SM, none without a row tile

@@ -55,8 +55,35 @@ def test_pairs(net, nets, n_pairs, seed=1000, steps=10, alpha_frac=4e-2):
     return pairs
 
 
+def time_kernels(reps=20, S=16):
+    """CUDA-event time of one prediction and one training step (with its loss read-back) of
+    the warm-start network on the medium network (S x 168 h scenarios)."""
+    nets, scens, net = build(S=S)
+    gnn = gx.WarmStartGNN(net, seed=7)
+    eta = torch.tensor(nets[0]["eta_min"], dtype=torch.float32, device="cuda")
+    out = torch.empty(2 * gnn.M, dtype=torch.float32, device="cuda")
+    tgt = torch.randn(2 * gnn.M, dtype=torch.float32, device="cuda", generator=torch.Generator(device="cuda").manual_seed(5))
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res = {"rows": gnn.M, "reps": reps}
+    for name, fn in (("predict_us", lambda: gnn.predict(eta, out)),
+                     ("train_step_us", lambda: gnn.train_step(eta, tgt, lr=1e-4))):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        res[name] = round(1e3 * a.elapsed_time(b) / reps, 1)
+    return res
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
+    ap.add_argument("--time-kernels", action="store_true",
+                    help="only time one prediction and one training step on the medium network")
+    ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--out", default=None)
     ap.add_argument("--report", default=None)
     ap.add_argument("--epochs", type=int, default=40)
@@ -66,6 +93,9 @@ def main(argv=None):
     ap.add_argument("--w-theta", type=float, default=0.1)
     ap.add_argument("--weights", default=None, help="evaluate these parameters instead of training")
     args = ap.parse_args(argv)
+    if args.time_kernels:
+        print(json.dumps(time_kernels(args.reps)), flush=True)
+        return
     t0 = time.time()
     nets, scens, net = build()
     gnn = gx.WarmStartGNN(net, seed=7)
