@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(kCrsThreads, 1)
         const int gg = sd.gen0 + g;
         m.xg[li] = X.xg[gi];
         if (ADJ) {
-            m.cap[li] = c.m_gen[gi] ? qnan() : c.g_cost[gg] + eps * c.xg[gi] + c.kappa * c.g_emis[gg];
+            m.cap[li] = c.ag[gi];  // adjoint coefficient, NaN where the bound is active
         } else {
             const float etag = fmaxf(c.eta[sd.eta0 + g], 0.f);
             m.cap[li] = c.g_firm[gg] ? etag : c.cf[gi] * etag;

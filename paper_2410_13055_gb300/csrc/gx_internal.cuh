@@ -48,8 +48,8 @@ enum : int {
     // block covers block items [SI[nl], SI[nl] + SQ[nl]); its generators' row segments sit
     // at stage quads SG[nl] + r * SQ[nl] of each generator region, likewise its line ends
     // (SE) and batteries (SB).  Regions, in quads (16 bytes): generator x [0, QG), generator
-    // aux (capacity factor / forward dispatch) [QG, 2QG), line delta [2QG, 2QG+QE), line-end
-    // phase copy [2QG+QE, 2QG+2QE), battery x [2QG+2QE, +QB); then QG u32 generator masks.
+    // aux (capacity factor / adjoint coefficient) [QG, 2QG), line delta [2QG, 2QG+QE), line-end
+    // phase copy [2QG+QE, 2QG+2QE), battery x [2QG+2QE, +QB).
     // CP: NCP copies of (source offset from the scenario's row base, destination quad,
     // quads << 5 | flags << 3 | array); SBYTES the stage's size, 0 = not staged.
     kPH_SQ, kPH_SI, kPH_SG, kPH_SE, kPH_SB,  // [nbus]
@@ -252,6 +252,11 @@ struct Ctx {
     const float* ramp_dd;
     // active set
     uint8_t* m_gen; uint8_t* m_load; uint8_t* m_line; uint8_t* m_bat;
+    // adjoint generator coefficient [gen rows], written with the active set: the adjoint's
+    // linear term c_g + eps p*_gt + kappa e_g of a free generator-hour, NaN where a bound is
+    // active (the variable is fixed at 0); one float row the adjoint bus kernels read in place
+    // of the forward dispatch and the byte mask
+    float* ag;
     // flags, outputs and partials
     int* done;          // [S] 1 = skip (converged or outside the batch)
     int* iters;         // [S]

@@ -581,17 +581,16 @@ __device__ __forceinline__ void bus_item(const Ctx& c, const BusBlk& bb, const S
     // generators, kGC at a time: all loads of a chunk before its stores
     for (int q0 = g0; q0 < g1; q0 += kGC) {
         float xv[kGC], av[kGC];
-        int ro[kGC], mv[kGC];
+        int ro[kGC];
 #pragma unroll
         for (int k = 0; k < kGC; ++k) {
             const int q = q0 + k;
-            xv[k] = 0.f; av[k] = 1.f; ro[k] = 0; mv[k] = 0;
+            xv[k] = 0.f; av[k] = 1.f; ro[k] = 0;
             if (q < g1) {
                 ro[k] = P.at(kPH_GROW, q) * bb.Tp;
                 xv[k] = X.xg[gt + ro[k]];
                 if (ADJ) {
-                    av[k] = c.xg[gt + ro[k]];
-                    mv[k] = c.m_gen[gt + ro[k]];
+                    av[k] = c.ag[gt + ro[k]];
                 } else if (MODE != M_INIT && !(P.at(kPH_GFIRM, q) & 1)) {
                     av[k] = c.cf[gt + ro[k]];
                 }
@@ -609,8 +608,8 @@ __device__ __forceinline__ void bus_item(const Ctx& c, const BusBlk& bb, const S
             if ((MODE == M_FWD || MODE == M_ADJ || MODE == M_MASK) && !rampg) {
                 const float v = x - pb - uu;
                 if (ADJ) {
-                    const float gh = P.atf(kPH_GCOST, q) + eps * av[k] + c.kappa * P.atf(kPH_GEMIS, q);
-                    const bool fixed = mv[k] != 0;
+                    const float gh = av[k];  // NaN: bound active, the variable is fixed at 0
+                    const bool fixed = gh != gh;
                     xn = fixed ? 0.f : (rho * v + gh) * inv_re;
                     if (!fixed) gscale += (gh * inv_re) * (gh * inv_re);
                 } else {
@@ -621,6 +620,9 @@ __device__ __forceinline__ void bus_item(const Ctx& c, const BusBlk& bb, const S
                         if (pun > cap && (rho + eps) * (pun - cap) > c.tol_act) code = A_UP;
                         else if (pun < 0.f && -(rho + eps) * pun > c.tol_act) code = A_LO;
                         c.m_gen[gt + ro[k]] = code;
+                        // the adjoint's linear term at the forward dispatch x (h = cost + kappa e)
+                        c.ag[gt + ro[k]] = code != A_FREE ? __int_as_float(0x7fc00000)
+                                                          : P.atf(kPH_GCOST, q) + eps * x + c.kappa * P.atf(kPH_GEMIS, q);
                     } else {
                         xn = clampf(pun, 0.f, cap);
                     }
@@ -866,16 +868,14 @@ __global__ void __launch_bounds__(kQBlock, GX_LINE4_MINB) k_line4(const Ctx c, i
 constexpr int kEC4 = 4;  // line ends loaded ahead by the quad bus kernel
 constexpr int kBC4 = 2;  // batteries loaded ahead
 
-// One generator's quad: stored injection, then (adjoint) the forward dispatch and the
-// active set, or (forward) the capacity factor (1 for firm generators).
+// One generator's quad: stored injection, then (adjoint) the adjoint coefficient (NaN where
+// the bound is active), or (forward) the capacity factor (1 for firm generators).
 template <int ADJ>
 __device__ __forceinline__ void gen_load4(const Ctx& c, const StatePtrs& X, const Pool& P, long long r, int q,
-                                          float (&x)[4], float (&a)[4], int (&m)[4]) {
+                                          float (&x)[4], float (&a)[4]) {
     ld4(X.xg + r, x);
-    m[0] = m[1] = m[2] = m[3] = 0;
     if (ADJ) {
-        ld4(c.xg + r, a);
-        ldm4(c.m_gen + r, m);
+        ld4(c.ag + r, a);
     } else if (!(P.at(kPH_GFIRM, q) & 1)) {
         ld4(c.cf + r, a);
     } else {
@@ -951,15 +951,13 @@ __global__ void __launch_bounds__(kBusQBlock, kBus4MinBlocks) k_bus4(const Ctx c
         for (int k = 0; k < kBC4; ++k)
             if (b0 + k < b1) ld4(X.xb + bb.e_bat + (long long)P.at(kPH_BROW, b0 + k) * bb.Tp + t, bx[k]);
         float xc[4], ac[4];
-        int mc[4];
-        if (g0 < g1) gen_load4<ADJ>(c, X, P, gt + (long long)P.at(kPH_GROW, g0) * bb.Tp, g0, xc, ac, mc);
+        if (g0 < g1) gen_load4<ADJ>(c, X, P, gt + (long long)P.at(kPH_GROW, g0) * bb.Tp, g0, xc, ac);
         for (int q = g0; q < g1; ++q) {
             const long long r = gt + (long long)P.at(kPH_GROW, q) * bb.Tp;
             float x[4], a[4], xn[4];
-            int mg[4];
 #pragma unroll
-            for (int h = 0; h < 4; ++h) { x[h] = xc[h]; a[h] = ac[h]; mg[h] = mc[h]; }
-            if (q + 1 < g1) gen_load4<ADJ>(c, X, P, gt + (long long)P.at(kPH_GROW, q + 1) * bb.Tp, q + 1, xc, ac, mc);
+            for (int h = 0; h < 4; ++h) { x[h] = xc[h]; a[h] = ac[h]; }
+            if (q + 1 < g1) gen_load4<ADJ>(c, X, P, gt + (long long)P.at(kPH_GROW, q + 1) * bb.Tp, q + 1, xc, ac);
             if (RAMP && (P.at(kPH_GFIRM, q) & 2)) {
                 // ramp-limited: the ramp kernel wrote this iteration's injection (and keeps
                 // its own residual terms); the bus only sums it
@@ -970,15 +968,14 @@ __global__ void __launch_bounds__(kBusQBlock, kBus4MinBlocks) k_bus4(const Ctx c
                 }
                 continue;
             }
-            const float gcost = P.atf(kPH_GCOST, q);
+            const float gcost = ADJ ? 0.f : P.atf(kPH_GCOST, q);
             const float etag = ADJ ? 0.f : P.atf(kPH_GETA, q);
-            const float gemis = ADJ ? P.atf(kPH_GEMIS, q) : 0.f;
 #pragma unroll
             for (int h = 0; h < 4; ++h) {
                 const float v = x[h] - pb[h] - uu[h];
                 if (ADJ) {
-                    const float gh = gcost + eps * a[h] + c.kappa * gemis;
-                    const bool fixed = mg[h] != 0;
+                    const float gh = a[h];  // NaN: bound active, the variable is fixed at 0
+                    const bool fixed = gh != gh;
                     xn[h] = fixed ? 0.f : (rho * v + gh) * inv_re;
                     if (!fixed && hv[h]) gscale += (gh * inv_re) * (gh * inv_re);
                 } else {
@@ -1107,8 +1104,9 @@ __global__ void __launch_bounds__(kBusQBlock, kBus4MinBlocks) k_bus4(const Ctx c
 // is built at create, in the pool record), so every row the block needs is in flight at once and
 // the block waits for three hops: its block record; its pool record and the done flag; its
 // bus state and the rows together (a converged scenario's blocks stop after the second).
-// Adjoint generator masks (one byte per hour: not 16-byte aligned) come with per-thread
-// 4-byte asynchronous copies.  A record too large for the stage runs the unstaged loads.
+// In the adjoint the generators' aux rows hold the adjoint coefficient (NaN where the bound
+// is active), so the active set travels with the bulk copies.  A record too large for the
+// stage runs the unstaged loads.
 // ------------------------------------------------------------------------------------
 
 // Whether a staged copy is issued: firm generators have no capacity-factor row to read and
@@ -1166,7 +1164,6 @@ __global__ void __launch_bounds__(kBusQBlock, GX_BUS4T_MINB * 128 / kBusQBlock) 
     const int sbytes = P.p[kPH_SBYTES];
     float4* stage = reinterpret_cast<float4*>(S + bb.words);
     const int qg = P.p[kPH_QG], qe = P.p[kPH_QE], qb = P.p[kPH_QB];
-    uint32_t* mstage = reinterpret_cast<uint32_t*>(stage + 2 * qg + 2 * qe + qb);
     // hop 3 (bulk): every device row segment of the block, the copy list split over the warps
     if (sbytes > 0 && bulk) {
         const int ncp = P.p[kPH_NCP];
@@ -1177,7 +1174,7 @@ __global__ void __launch_bounds__(kBusQBlock, GX_BUS4T_MINB * 128 / kBusQBlock) 
             const float* src;
             switch (code & 7) {
                 case kCpGenX: src = X.xg + bb.e_gen; break;
-                case kCpGenAux: src = (ADJ ? c.xg : c.cf) + bb.e_gen; break;
+                case kCpGenAux: src = (ADJ ? c.ag : c.cf) + bb.e_gen; break;
                 case kCpDl: src = X.dl + bb.e_line; break;
                 case kCpVf: src = X.vf + bb.e_line; break;
                 case kCpVt: src = X.vt + bb.e_line; break;
@@ -1200,7 +1197,7 @@ __global__ void __launch_bounds__(kBusQBlock, GX_BUS4T_MINB * 128 / kBusQBlock) 
             const long long r = gt + (long long)P.at(kPH_GROW, q) * bb.Tp;
             const int fl = P.at(kPH_GFIRM, q);
             cp_async16(stage + slot, X.xg + r);
-            if (!(fl & 2) && (ADJ || !(fl & 1))) cp_async16(stage + qg + slot, (ADJ ? c.xg : c.cf) + r);
+            if (!(fl & 2) && (ADJ || !(fl & 1))) cp_async16(stage + qg + slot, (ADJ ? c.ag : c.cf) + r);
         }
         const int e0 = P.at(kPH_EP, nl), e1 = P.at(kPH_EP, nl + 1);
         for (int q = e0; q < e1; ++q) {
@@ -1215,14 +1212,6 @@ __global__ void __launch_bounds__(kBusQBlock, GX_BUS4T_MINB * 128 / kBusQBlock) 
             cp_async16(stage + 2 * qg + 2 * qe + sb + (q - b0) * nq + pos,
                        X.xb + bb.e_bat + (long long)P.at(kPH_BROW, q) * bb.Tp + t);
     }
-    if (ADJ && sbytes > 0 && valid) {
-        // adjoint generator masks: 4 bytes per quad, per-thread asynchronous copies
-        const int sg = P.at(kPH_SG, nl);
-        for (int q = g0; q < g1; ++q) {
-            if (RAMP && (P.at(kPH_GFIRM, q) & 2)) continue;
-            cp_async4(mstage + sg + (q - g0) * nq + pos, c.m_gen + gt + (long long)P.at(kPH_GROW, q) * bb.Tp);
-        }
-    }
     if (sbytes > 0 && !bulk) cp_async_wait_all();
     if (sbytes > 0 && bulk) {
         bool ok = false;
@@ -1232,10 +1221,8 @@ __global__ void __launch_bounds__(kBusQBlock, GX_BUS4T_MINB * 128 / kBusQBlock) 
             // without touching the iterate
             if (threadIdx.x == 0) atomicExch(c.err, GX_ERR_TIMEOUT);
             for (int k = 0; k < kWaitProbes && !ok; ++k) ok = mbar_try(&bar, 0);
-            if (ADJ) cp_async_wait_all();
             return;
         }
-        if (ADJ) cp_async_wait_all();
     }
     float acc[kBusPart] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (valid) {
@@ -1254,7 +1241,6 @@ __global__ void __launch_bounds__(kBusQBlock, GX_BUS4T_MINB * 128 / kBusQBlock) 
             const int slot = sg + (q - g0) * nq + pos;
             const long long r = gt + (long long)P.at(kPH_GROW, q) * bb.Tp;
             float x[4], a[4], xn[4];
-            int mg[4] = {0, 0, 0, 0};
             const bool rampg = RAMP && (P.at(kPH_GFIRM, q) & 2);
             if (stg) {
                 const float4 v = stage[slot];
@@ -1277,28 +1263,19 @@ __global__ void __launch_bounds__(kBusQBlock, GX_BUS4T_MINB * 128 / kBusQBlock) 
                     const float4 v = stage[qg + slot];
                     a[0] = v.x; a[1] = v.y; a[2] = v.z; a[3] = v.w;
                 } else {
-                    ld4((ADJ ? c.xg : c.cf) + r, a);
+                    ld4((ADJ ? c.ag : c.cf) + r, a);
                 }
             } else {
                 a[0] = a[1] = a[2] = a[3] = 1.f;
             }
-            if (ADJ) {
-                if (stg) {
-                    const uint32_t m = mstage[slot];
-                    mg[0] = m & 0xff; mg[1] = (m >> 8) & 0xff; mg[2] = (m >> 16) & 0xff; mg[3] = m >> 24;
-                } else {
-                    ldm4(c.m_gen + r, mg);
-                }
-            }
-            const float gcost = P.atf(kPH_GCOST, q);
+            const float gcost = ADJ ? 0.f : P.atf(kPH_GCOST, q);
             const float etag = ADJ ? 0.f : P.atf(kPH_GETA, q);
-            const float gemis = ADJ ? P.atf(kPH_GEMIS, q) : 0.f;
 #pragma unroll
             for (int h = 0; h < 4; ++h) {
                 const float v = x[h] - pb[h] - uu[h];
                 if (ADJ) {
-                    const float gh = gcost + eps * a[h] + c.kappa * gemis;
-                    const bool fixed = mg[h] != 0;
+                    const float gh = a[h];  // NaN: bound active, the variable is fixed at 0
+                    const bool fixed = gh != gh;
                     xn[h] = fixed ? 0.f : (rho * v + gh) * inv_re;
                     if (!fixed && hv[h]) gscale += (gh * inv_re) * (gh * inv_re);
                 } else {
