@@ -38,7 +38,6 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
-__device__ __forceinline__ float qnan() { return __int_as_float(0x7fc00000); }
 
 struct Sm {
     double* red;
@@ -292,7 +291,7 @@ __global__ void __launch_bounds__(kCrsThreads, 1)
         m.pbar[li] = X.pbar[gi]; m.u[li] = X.u[gi]; m.thb[li] = X.thb[gi]; m.xl[li] = X.xl[gi];
         const float Lnt = c.load[gi];
         m.ld[li] = Lnt;
-        if (ADJ) m.aux[li] = c.m_load[gi] ? qnan() : c.voll + eps * (c.xl[gi] + Lnt);
+        if (ADJ) m.aux[li] = c.al[gi];  // adjoint coefficient, NaN where the bound is active
     }
     for (int q = tid; q < G * nh; q += kCrsThreads) {
         const int g = q / nh, hl = q - g * nh;

@@ -121,7 +121,7 @@ struct gx_network {
     size_t static_end;
     size_t o_f[16], o_a[16];  // forward / adjoint state arrays, order of StatePtrs
     size_t o_fend, o_aend;    // end of the forward / adjoint state range (ramp arrays included)
-    size_t o_mgen, o_mload, o_mline, o_mbat, o_ag;
+    size_t o_mgen, o_mload, o_mline, o_mbat, o_ag, o_al;
     size_t o_done, o_iters, o_status, o_adjit, o_nact, o_ctr, o_inb, o_err, o_wsel, o_resid, o_rbest, o_cost, o_h, o_grads, o_wprime, o_obj, o_stlo, o_sthi, o_pact;
     size_t o_flow, o_price, o_shed, o_bpart, o_lpart, o_btpart, o_cpart;
     Layout lay;
@@ -307,6 +307,7 @@ static void make_ctx(gx_network* net) {
     for (int k = 0; k < 16; ++k) { *fs[k] = F(net->o_f[k]); *as[k] = F(net->o_a[k]); }
     c.m_gen = U8(net->o_mgen); c.m_load = U8(net->o_mload); c.m_line = U8(net->o_mline); c.m_bat = U8(net->o_mbat);
     c.ag = reinterpret_cast<float*>(net->dev + net->o_ag);
+    c.al = reinterpret_cast<float*>(net->dev + net->o_al);
     c.done = I(net->o_done); c.iters = I(net->o_iters); c.status = I(net->o_status); c.adj_iters = I(net->o_adjit);
     c.n_active = I(net->o_nact);
     c.iter_ctr = I(net->o_ctr);
@@ -1000,6 +1001,7 @@ gx_status gx_network_create(const gx_network_desc* nets, int n_nets, const gx_sc
     net->o_aend = L.total;
     net->o_mgen = L.add(B1(eg)); net->o_mload = L.add(B1(eb)); net->o_mline = L.add(B1(el)); net->o_mbat = L.add(B1(ebt));
     net->o_ag = L.add(F4(eg));
+    net->o_al = L.add(F4(eb));
     net->o_done = L.add(I4(S)); net->o_iters = L.add(I4(S)); net->o_status = L.add(I4(S)); net->o_adjit = L.add(I4(S));
     net->o_nact = L.add(I4(1)); net->o_ctr = L.add(I4(1)); net->o_inb = L.add(I4(S)); net->o_err = L.add(I4(1));
     net->o_wsel = L.add(I4(S));

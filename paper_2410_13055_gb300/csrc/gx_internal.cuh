@@ -255,8 +255,10 @@ struct Ctx {
     // adjoint generator coefficient [gen rows], written with the active set: the adjoint's
     // linear term c_g + eps p*_gt + kappa e_g of a free generator-hour, NaN where a bound is
     // active (the variable is fixed at 0); one float row the adjoint bus kernels read in place
-    // of the forward dispatch and the byte mask
+    // of the forward dispatch and the byte mask; likewise for the load-shed variables [bus rows]:
+    // VOLL + eps shed*_nt, NaN where a bound is active
     float* ag;
+    float* al;
     // flags, outputs and partials
     int* done;          // [S] 1 = skip (converged or outside the batch)
     int* iters;         // [S]

@@ -518,8 +518,7 @@ constexpr int kBC = 2;  // batteries loaded ahead of the generator stores
 
 // Per-item inputs read before the block's staging barrier.
 struct BusIn {
-    float pb, uu, thold, xl, Lnt, xlf;
-    int ml;
+    float pb, uu, thold, xl, Lnt, al;
 };
 
 template <int MODE, int ADJ>
@@ -641,8 +640,8 @@ __device__ __forceinline__ void bus_item(const Ctx& c, const BusBlk& bb, const S
         if (MODE == M_FWD || MODE == M_ADJ || MODE == M_MASK) {
             const float v = x - pb - uu;
             if (ADJ) {
-                const float gsh = c.voll + eps * (in.xlf + Lnt);
-                const bool fixed = in.ml != 0;
+                const float gsh = in.al;  // NaN: bound active, the variable is fixed at 0
+                const bool fixed = gsh != gsh;
                 xn = fixed ? 0.f : (rho * v + gsh) * inv_re;
                 if (!fixed) gscale += (gsh * inv_re) * (gsh * inv_re);
             } else {
@@ -652,6 +651,8 @@ __device__ __forceinline__ void bus_item(const Ctx& c, const BusBlk& bb, const S
                     if (sun > Lnt && (rho + eps) * (sun - Lnt) > c.tol_act) code = A_UP;
                     else if (sun < 0.f && -(rho + eps) * sun > c.tol_act) code = A_LO;
                     c.m_load[i] = code;
+                    // the adjoint's linear term at the forward shed x + L
+                    c.al[i] = code != A_FREE ? __int_as_float(0x7fc00000) : c.voll + eps * (x + Lnt);
                 } else {
                     xn = clampf(sun, 0.f, Lnt) - Lnt;
                 }
@@ -741,14 +742,14 @@ __global__ void __launch_bounds__(kBlock, 4) k_bus(const Ctx c, int want_res) {
     const int t = local - n * bb.Tp;
     const bool valid = (local < bb.nitems) && (t < bb.T);
     const long long i = bb.e_bus + local;
-    BusIn in{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
+    BusIn in{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (valid) {
         if (MODE != M_INIT) in.Lnt = c.load[i];
         if (MODE == M_FWD || MODE == M_ADJ || MODE == M_MASK) {
             in.pb = X.pbar[i]; in.uu = X.u[i]; in.thold = X.thb[i];
         }
         if (MODE != M_RESET) in.xl = X.xl[i];
-        if (ADJ && MODE == M_ADJ) { in.xlf = c.xl[i]; in.ml = c.m_load[i]; }
+        if (ADJ && MODE == M_ADJ) in.al = c.al[i];
     }
     __syncthreads();
     float acc[kBusPart] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -904,12 +905,12 @@ __global__ void __launch_bounds__(kBusQBlock, kBus4MinBlocks) k_bus4(const Ctx c
     const int t = (local - n * Tq) * 4;
     const bool valid = local < bb.nitems;
     const long long i = bb.e_bus + (long long)n * bb.Tp + t;
-    float pb[4], uu[4], thold[4], xl[4], Ld[4], xlf[4];
-    int ml[4] = {0, 0, 0, 0};
+    float pb[4], uu[4], thold[4], xl[4], Ld[4], al[4];
     if (valid) {
         ld4(X.pbar + i, pb); ld4(X.u + i, uu); ld4(X.thb + i, thold);
-        ld4(X.xl + i, xl); ld4(c.load + i, Ld);
-        if (ADJ) { ld4(c.xl + i, xlf); ldm4(c.m_load + i, ml); }
+        ld4(X.xl + i, xl);
+        if (ADJ) ld4(c.al + i, al);  // the adjoint needs the load only through its coefficient
+        else ld4(c.load + i, Ld);
     }
     if (staged) {
         const int4* src = reinterpret_cast<const int4*>(c.pool + bb.pool);
@@ -996,8 +997,8 @@ __global__ void __launch_bounds__(kBusQBlock, kBus4MinBlocks) k_bus4(const Ctx c
             for (int h = 0; h < 4; ++h) {
                 const float v = xl[h] - pb[h] - uu[h];
                 if (ADJ) {
-                    const float gsh = c.voll + eps * (xlf[h] + Ld[h]);
-                    const bool fixed = ml[h] != 0;
+                    const float gsh = al[h];  // NaN: bound active, the variable is fixed at 0
+                    const bool fixed = gsh != gsh;
                     xn[h] = fixed ? 0.f : (rho * v + gsh) * inv_re;
                     if (!fixed && hv[h]) gscale += (gsh * inv_re) * (gsh * inv_re);
                 } else {
@@ -1153,17 +1154,17 @@ __global__ void __launch_bounds__(kBusQBlock, GX_BUS4T_MINB * 128 / kBusQBlock) 
     __syncthreads();
     if (done) return;  // block-uniform: a converged scenario's blocks stop after two hops
     // hop 3: this thread's bus state, in flight together with the row copies below
-    float pb[4], uu[4], thold[4], xl[4], Ld[4], xlf[4];
-    int ml[4] = {0, 0, 0, 0};
+    float pb[4], uu[4], thold[4], xl[4], Ld[4], al[4];
     if (valid) {
         ld4(X.pbar + i, pb); ld4(X.u + i, uu); ld4(X.thb + i, thold);
-        ld4(X.xl + i, xl); ld4(c.load + i, Ld);
-        if (ADJ) { ld4(c.xl + i, xlf); ldm4(c.m_load + i, ml); }
+        ld4(X.xl + i, xl);
+        if (ADJ) ld4(c.al + i, al);  // the adjoint needs the load only through its coefficient
+        else ld4(c.load + i, Ld);
     }
     const Pool P{rec_smem ? S : c.pool + bb.pool};
     const int sbytes = P.p[kPH_SBYTES];
     float4* stage = reinterpret_cast<float4*>(S + bb.words);
-    const int qg = P.p[kPH_QG], qe = P.p[kPH_QE], qb = P.p[kPH_QB];
+    const int qg = P.p[kPH_QG], qe = P.p[kPH_QE];
     // hop 3 (bulk): every device row segment of the block, the copy list split over the warps
     if (sbytes > 0 && bulk) {
         const int ncp = P.p[kPH_NCP];
@@ -1296,8 +1297,8 @@ __global__ void __launch_bounds__(kBusQBlock, GX_BUS4T_MINB * 128 / kBusQBlock) 
             for (int h = 0; h < 4; ++h) {
                 const float v = xl[h] - pb[h] - uu[h];
                 if (ADJ) {
-                    const float gsh = c.voll + eps * (xlf[h] + Ld[h]);
-                    const bool fixed = ml[h] != 0;
+                    const float gsh = al[h];  // NaN: bound active, the variable is fixed at 0
+                    const bool fixed = gsh != gsh;
                     xn[h] = fixed ? 0.f : (rho * v + gsh) * inv_re;
                     if (!fixed && hv[h]) gscale += (gsh * inv_re) * (gsh * inv_re);
                 } else {
