@@ -926,6 +926,16 @@ gx_status gx_network_create(const gx_network_desc* nets, int n_nets, const gx_sc
             r.e_line = sd.e_line; r.e_bus = sd.e_bus;
             r.s = s; r.line0 = sd.line0; r.Tp = sd.Tp; r.T = sd.T;
             r.L = sd.L; r.eta_l = sd.eta0 + sd.G; r.item0 = b * kQBlock;
+            const int tq = sd.Tp / 4;
+            r.l0 = r.item0 / tq;
+            const int l1 = std::min(sd.L - 1, (r.item0 + kQBlock - 1) / tq);
+            if (l1 - r.l0 + 1 <= kLineBlkLines) {
+                r.nends = l1 - r.l0 + 1;
+                for (int j = 0; j < r.nends; ++j) {
+                    r.ends[2 * j] = h.line_from[r.l0 + j];
+                    r.ends[2 * j + 1] = h.line_to[r.l0 + j];
+                }
+            }
             net->line4_blk.push_back(r);
         }
         for (int b = 0; b < sd.B; ++b) {

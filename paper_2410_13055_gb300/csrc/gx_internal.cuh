@@ -128,10 +128,19 @@ struct BusBlk {
 
 // One per hour-quad line block and one per battery warp (built at create): every offset
 // the kernel needs before its state loads, so those loads follow one dependent read.
+// Lines one hour-quad line block can carry the end buses of (a block of kQBlock quads covers at
+// most kQBlock / (Tp / 4) + 1 lines: horizons of 64 hours and more).
+constexpr int kLineBlkLines = 8;
 struct LineBlk {
     long long e_line, e_bus;   // element offsets of the scenario's line and bus rows
     int s, line0, Tp, T;       // scenario, first line of its network (global), padded / true horizon
-    int L, eta_l, item0, pad;  // lines of the network, plan index of its first line, first line-quad
+    int L, eta_l, item0, l0;   // lines of the network, plan index of its first line, first line-quad,
+                               // first line of the block (local)
+    // from and to bus of lines l0 .. l0 + nends - 1, so the block stages them once and its
+    // threads issue their bus-row loads together with their state loads; nends = 0: read
+    // each line's ends from the network arrays
+    int nends, pad[3];
+    int ends[2 * kLineBlkLines];
 };
 struct BatW {
     long long row0, brow0;     // the battery's row and its bus's row

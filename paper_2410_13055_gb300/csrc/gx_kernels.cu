@@ -796,9 +796,13 @@ __global__ void __launch_bounds__(kQBlock, GX_LINE4_MINB) k_line4(const Ctx c, i
     const int blk = blockIdx.x;
     const bool stamp = want_res && c.stamp_lo != nullptr;
     if (stamp && threadIdx.x == 0) stamp_start(c, 1);
-    // the block's offsets in one record; the done flag, the line's ends and its state are
-    // then read together, and the flag tested before anything is stored
+    // The block's offsets and its lines' end buses in one record (the ends staged in shared
+    // memory); then the done flag, the line's state and its end buses' rows are read together,
+    // and the flag tested before anything is stored.
+    __shared__ int s_end[2 * kLineBlkLines];
     const LineBlk lb = c.line4_blk[blk];
+    if (threadIdx.x < 2 * kLineBlkLines) s_end[threadIdx.x] = c.line4_blk[blk].ends[threadIdx.x];
+    __syncthreads();
     const int done = c.done[lb.s];
     const StatePtrs X = state<ADJ>(c);
     const int Tq = lb.Tp >> 2;
@@ -811,8 +815,10 @@ __global__ void __launch_bounds__(kQBlock, GX_LINE4_MINB) k_line4(const Ctx c, i
         const int lg = lb.line0 + l;
         float d[4], g[4], qf[4], qt[4], pbf[4], uf[4], zf[4], pbt[4], ut[4], zt[4];
         ld4(X.dl + row, d); ld4(X.sg + row, g); ld4(X.vf + row, qf); ld4(X.vt + row, qt);
-        const long long bf = lb.e_bus + (long long)c.l_from[lg] * lb.Tp + t;
-        const long long bt = lb.e_bus + (long long)c.l_to[lg] * lb.Tp + t;
+        const int end_f = lb.nends ? s_end[2 * (l - lb.l0)] : c.l_from[lg];
+        const int end_t = lb.nends ? s_end[2 * (l - lb.l0) + 1] : c.l_to[lg];
+        const long long bf = lb.e_bus + (long long)end_f * lb.Tp + t;
+        const long long bt = lb.e_bus + (long long)end_t * lb.Tp + t;
         int mk[4] = {0, 0, 0, 0};
         if (ADJ) ldm4(c.m_line + row, mk);
         const float beta = c.l_beta[lg];
@@ -821,7 +827,7 @@ __global__ void __launch_bounds__(kQBlock, GX_LINE4_MINB) k_line4(const Ctx c, i
         const float dthl = c.l_dth[lg];
         ld4(X.pbar + bf, pbf); ld4(X.u + bf, uf); ld4(X.thb + bf, zf);
         ld4(X.pbar + bt, pbt); ld4(X.u + bt, ut); ld4(X.thb + bt, zt);
-        if (done) return;  // block-uniform; no barrier or store has happened
+        if (done) return;  // block-uniform; nothing has been stored
         const bool dc = w == 0.f;  // HVDC transport line: no phase coupling, eps/2 f^2 cost
         const float rth = c.rth_c * w;
         const float capf = fmaxf(etal, 0.f) / beta;
