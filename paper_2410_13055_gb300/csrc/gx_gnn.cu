@@ -391,8 +391,9 @@ __global__ void k_colsum(const float* __restrict__ dZ, long long M, float* __res
 }
 
 // ---------------------------------------------------------------- aggregation
-// out[i] = mean over neighbour buses m of in[(m, t)], or (transpose) out[i] += sum over
-// neighbours m of in[(m, t)] / deg(m).  One warp per node, two features per lane.
+// outb[i] = BF16 of the mean over neighbour buses m of in[(m, t)] (the next layer's operand;
+// also out[i] in FP32 when out is given), or (transpose) out[i] += sum over neighbours m of
+// in[(m, t)] / deg(m).  One warp per node, two features per lane.
 template <int TRANSPOSE>
 __global__ void k_agg(const Ctx c, const float* __restrict__ in, float* __restrict__ out,
                       __nv_bfloat16* __restrict__ outb, long long M) {
@@ -422,8 +423,8 @@ __global__ void k_agg(const Ctx c, const float* __restrict__ in, float* __restri
     }
     if (!TRANSPOSE) {
         const float w = e1 > e0 ? 1.f / (float)(e1 - e0) : 0.f;
-        reinterpret_cast<float2*>(out + i * kH)[lane] = make_float2(a0 * w, a1 * w);
-        if (outb) reinterpret_cast<__nv_bfloat162*>(outb + i * kH)[lane] = __floats2bfloat162_rn(a0 * w, a1 * w);
+        if (out) reinterpret_cast<float2*>(out + i * kH)[lane] = make_float2(a0 * w, a1 * w);
+        reinterpret_cast<__nv_bfloat162*>(outb + i * kH)[lane] = __floats2bfloat162_rn(a0 * w, a1 * w);
     } else {
         float2* o = reinterpret_cast<float2*>(out + i * kH) + lane;
         const float2 prev = *o;
@@ -581,7 +582,7 @@ struct gx_gnn {
     size_t bytes = 0;
     uint8_t* dev = nullptr;
     // offsets
-    size_t o_P, o_G, o_m1, o_m2, o_img_in, o_img_fwd, o_img_bwd, o_X, o_Z0, o_Hs, o_Zs, o_Agg, o_Y, o_dY, o_dH,
+    size_t o_P, o_G, o_m1, o_m2, o_img_in, o_img_fwd, o_img_bwd, o_X, o_Z0, o_Hs, o_Zs, o_Y, o_dY, o_dH,
         o_dZ, o_dAgg, o_loss, o_err;
     // BF16 operands of the tensor-core layers: features, the inputs h_l and neighbour means
     // of each layer (kept for the weight gradients), dZ; and their TMA descriptors (128-row
@@ -687,7 +688,6 @@ gx_status gx_gnn_create(const gx_network* net, int hidden, int layers, gx_gnn** 
     g->o_Z0 = lay_add(t, 4 * (size_t)M * kH);
     g->o_Hs = lay_add(t, 4 * (size_t)M * kH * (kLayers + 1));
     g->o_Zs = lay_add(t, 4 * (size_t)M * kH * kLayers);
-    g->o_Agg = lay_add(t, 4 * (size_t)M * kH * kLayers);
     g->o_Y = lay_add(t, 4 * (size_t)M * 2);
     g->o_dY = lay_add(t, 4 * (size_t)M * 2);
     g->o_dH = lay_add(t, 4 * (size_t)M * kH);
@@ -813,8 +813,7 @@ static void gnn_forward(gx_gnn* g, const float* eta, cudaStream_t st, int* err) 
     for (int l = 0; l < kLayers; ++l) {
         float* Hl = F(g->o_Hs) + (size_t)l * M * kH;
         float* Hn = F(g->o_Hs) + (size_t)(l + 1) * M * kH;
-        float* Ag = F(g->o_Agg) + (size_t)l * M * kH;
-        k_agg<0><<<(unsigned)((M + 7) / 8), 256, 0, st>>>(c, Hl, Ag, Agb(l), M);
+        k_agg<0><<<(unsigned)((M + 7) / 8), 256, 0, st>>>(c, Hl, nullptr, Agb(l), M);
         // H_{l+1} = H_l + relu([H_l, mean] W_l + b_l); its BF16 copy feeds the next layer
         DenseOut ol{P + kOffL0 + l * kLayerSz + 2 * kH * kH, Hl, F(g->o_Zs) + (size_t)l * M * kH, Hn,
                     l + 1 < kLayers ? Hb(l + 1) : nullptr, nullptr, nullptr, err};
