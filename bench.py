@@ -232,7 +232,7 @@ def roofline(config, prof, active, per_scen, n_scen, iters_per_step, ms_per_step
                       "ms_per_step": round(ms_per_step, 3)}}
 
 
-def measure(config, args, steps, warmup, dist=None, learned=False, cold=True, scenarios=None):
+def measure(config, args, steps, warmup, dist=None, learned=False, cold=True, scenarios=None, accuracy=False):
     """Time `steps` previous-plan implicit-gradient steps of one workload (after `warmup`
     steps from a cold start), then a profiled pass of the same steps (kernel times and the
     roofline), an end-to-end pass through host buffers, and optionally cold and learned
@@ -372,6 +372,7 @@ def measure(config, args, steps, warmup, dist=None, learned=False, cold=True, sc
     torch.cuda.synchronize()
     e2e_ms = a.elapsed_time(b) / steps
 
+    acc = accuracy_check(net, eta, grad, args.rho) if accuracy else None
     rec_learned = None
     if learned:
         rec_learned = measure_learned(net, eta, grad, gamma, eta_min, eta_max, state["alpha"], flush, dh, steps, dev)
@@ -411,13 +412,51 @@ def measure(config, args, steps, warmup, dist=None, learned=False, cold=True, sc
                 "d2h_bytes_per_step": int(2 * eta.numel() * 4 + net.S * 8),
                 "replays_headline_steps": [list(x) for x in e2e_its] == [[a, b] for a, b in zip(it_prev, ait_prev)],
                 "note": "headline's plan and solver state restored first; no L2 flush between its steps"},
-        "clocks": clk, "gpu_launches": int(launches), "alpha": state["alpha"],
+        "clocks": clk, "gpu_launches": int(launches), "alpha": state["alpha"], "accuracy": acc,
         "schedule": {"chosen": net.schedule(), "default": tuned["default"] if tuned else None,
                      "by": "autotune.tune_schedule_step" if tuned else ("--bus-staged" if args.bus_staged is not None
                                                                         else "bind default"),
                      "trials_ms_per_step": ({f"bus{t['bus_staged']}_bat{t['bat_warps']}": t["ms_per_step"]
                                              for t in tuned["trials"]} if tuned else None)},
     }
+
+
+def accuracy_check(net, eta, grad, rho, tight=1e-5, cap=40000, ref_rho=0.3):
+    """How far the metric's 1e-3 stop is from a tight solve, at the plan the headline's e2e pass
+    ends on (outside every timed region; the plan and iteration state are restored after).
+    Metric side: previous-plan solves to 1e-3 at the bench's power penalty, as the next step
+    would run them.  Reference: cold solves to `tight` at the library's default penalty, which
+    converges further in FP32 (the fixed point does not depend on the penalty); the residuals
+    it reached are reported with it."""
+    import torch
+    snap = (eta.clone(), net.state(False).clone(), net.state(True).clone())
+    g_m, g_t = torch.empty_like(grad), torch.empty_like(grad)
+    net.solve(eta, warm="prev")
+    obj_m = float(net.array("obj")[0])
+    net.grad(eta, out=g_m, warm="prev")
+    its_m = (net.last_stats["iters_max"], net.last_grad_stats["iters_max"])
+    net.set_opts(rho=ref_rho, tol=tight, adj_tol=tight, max_iter=cap, adj_max_iter=cap)
+    try:
+        net.solve(eta, warm="cold")
+        fwd = dict(net.last_stats)
+        obj_t = float(net.array("obj")[0])
+        net.grad(eta, out=g_t, warm="cold")
+        adj = dict(net.last_grad_stats)
+    finally:
+        net.set_opts(rho=rho, tol=1e-3, adj_tol=1e-3, max_iter=50000, adj_max_iter=50000)
+        eta.copy_(snap[0]); net.state(False).copy_(snap[1]); net.state(True).copy_(snap[2])
+    gm, gt = g_m.double(), g_t.double()
+    return {"plan": "the plan the headline's e2e pass ends on",
+            "grad_rel_err_l2": round(float((gm - gt).norm() / gt.norm().clamp_min(1e-30)), 6),
+            "grad_rel_err_max_entry": round(float((gm - gt).abs().max() / gt.abs().max().clamp_min(1e-30)), 6),
+            "obj_rel_err": float(abs(obj_m - obj_t) / max(abs(obj_t), 1e-30)),
+            "iterations_at_1e-3": list(its_m),
+            "reference": {"tol": tight, "rho": ref_rho, "start": "cold", "cap": cap,
+                          "forward_converged": f"{fwd['n_converged']}/{fwd['n_scen']}",
+                          "adjoint_converged": f"{adj['n_converged']}/{adj['n_scen']}",
+                          "forward_residual_max": [fwd["max_primal"], fwd["max_dual"]],
+                          "adjoint_residual_max": [adj["max_primal"], adj["max_dual"]],
+                          "iterations": [fwd["iters_max"], adj["iters_max"]]}}
 
 
 def measure_learned(net, eta, grad, gamma, eta_min, eta_max, alpha, flush, dh, steps, dev):
@@ -468,7 +507,7 @@ def run_gx(args):
         dist.init_process_group("nccl")
     head = measure(args.config, args, args.steps, args.warmup, dist,
                    learned=(args.config == "medium" and not args.quick and ws == 1), cold=not args.quick,
-                   scenarios=args.scenarios)
+                   scenarios=args.scenarios, accuracy=(not args.quick and ws == 1))
     if args.quick:
         if rank == 0:
             print(json.dumps({"quick": True, "ms_per_step": head["ms_per_step"], "iterations": head["iterations"],
@@ -480,7 +519,7 @@ def run_gx(args):
     if args.config == "medium" and not args.no_sub:
         for cfg, k in (("scale", 3), ("batching", 10)):
             r = measure(cfg, args, k, 3, dist, learned=False, cold=False)
-            for key in ("clocks", "learned", "cold", "alpha"):
+            for key in ("clocks", "learned", "cold", "alpha", "accuracy"):
                 r.pop(key, None)
             subs[cfg] = r
     per_scen = None
@@ -508,6 +547,7 @@ def run_gx(args):
         "modes": {"prev": head["value"], "cold": head["cold"],
                   "learned": head["learned"]["value"] if head["learned"] else None},
         "learned": head["learned"],
+        "accuracy": head["accuracy"],
         "roofline": head["roofline"],
         "cpu_baseline": cpu,
         "cpu_reference": cpu_ref,
