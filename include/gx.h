@@ -145,6 +145,7 @@ typedef struct {
     double adj_rho_theta_c;  /* phase penalty scale of the adjoint iteration (rho_theta_l =
                                 adj_rho * adj_rho_theta_c * w_l); 0: rho_theta_c */
     double adj_rho_inner_c;  /* battery and ramp inner penalty scale of the adjoint; 0: rho_inner_c */
+    int adj_inner_iters;     /* battery inner iterations per adjoint iteration; 0: inner_iters */
 } gx_opts;
 
 enum { GX_WARM_COLD = 0, GX_WARM_PREV = 1, GX_WARM_USER = 2, GX_WARM_LEARNED = 3 };

@@ -333,6 +333,7 @@ static void make_ctx(gx_network* net) {
     Ctx& a = net->actx;
     a = c;
     a.rho = (float)o.adj_rho;
+    a.inner_iters = o.adj_inner_iters > 0 ? o.adj_inner_iters : o.inner_iters;
     a.rho_in = (float)(o.adj_rho * adj_inner_c(o));
     a.rth_c = (float)(o.adj_rho * adj_theta_c(o));
     a.bat_dd = F(net->o_add);
@@ -387,6 +388,7 @@ gx_status gx_opts_default(gx_opts* o) {
     o->adj_rho = 0.002;
     o->adj_rho_theta_c = 0.0;
     o->adj_rho_inner_c = 0.0;
+    o->adj_inner_iters = 0;
     return GX_OK;
 }
 
@@ -415,6 +417,8 @@ static gx_status check_opts(const gx_opts* o) {
     if (!(o->rho_theta_c > 0 && isfin(o->rho_theta_c))) return fail(GX_ERR_INVALID_ARG, "opts.rho_theta_c must be > 0");
     if (!(o->rho_inner_c > 0 && isfin(o->rho_inner_c))) return fail(GX_ERR_INVALID_ARG, "opts.rho_inner_c must be > 0");
     if (o->inner_iters < 1 || o->inner_iters > 1000) return fail(GX_ERR_INVALID_ARG, "opts.inner_iters in [1, 1000]");
+    if (o->adj_inner_iters < 0 || o->adj_inner_iters > 1000)
+        return fail(GX_ERR_INVALID_ARG, "opts.adj_inner_iters in [0, 1000] (0: inner_iters)");
     if (!(o->tol > 0) || !(o->adj_tol > 0)) return fail(GX_ERR_INVALID_ARG, "tolerances must be > 0");
     if (o->max_iter < 1 || o->adj_max_iter < 1) return fail(GX_ERR_INVALID_ARG, "max_iter must be >= 1");
     if (o->check_every < 1) return fail(GX_ERR_INVALID_ARG, "check_every must be >= 1");

@@ -53,7 +53,7 @@ class Opts(C.Structure):
                 ("tol", C.c_double), ("max_iter", C.c_int), ("check_every", C.c_int),
                 ("tol_active", C.c_double), ("adj_tol", C.c_double), ("adj_max_iter", C.c_int),
                 ("grad_envelope", C.c_int), ("adj_rho", C.c_double),
-                ("adj_rho_theta_c", C.c_double), ("adj_rho_inner_c", C.c_double)]
+                ("adj_rho_theta_c", C.c_double), ("adj_rho_inner_c", C.c_double), ("adj_inner_iters", C.c_int)]
 
 
 class Schedule(C.Structure):
