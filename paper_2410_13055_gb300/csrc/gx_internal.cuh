@@ -327,33 +327,59 @@ __device__ __forceinline__ void stamp_end(const Ctx& c, int kind) {
 // reductions (the workspace one and the allocation-free one) use this.
 __device__ __forceinline__ void cost_share(const Ctx& c, const ScenDev& sc, long long tid, long long stride,
                                            double& cs, double& em) {
-    const double eps = c.eps, voll = c.voll;
-    const long long ng = (long long)sc.G * sc.Tp, nn = (long long)sc.N * sc.Tp, nbt = (long long)sc.B * sc.Tp;
-    for (long long i = tid; i < ng; i += stride) {
-        const int g = (int)(i / sc.Tp), t = (int)(i - (long long)g * sc.Tp);
-        if (t >= sc.T) continue;
-        const double p = c.xg[sc.e_gen + i];
-        cs += c.g_cost[sc.gen0 + g] * p + 0.5 * eps * p * p;
-        em += c.g_emis[sc.gen0 + g] * p;
+    // One 4-hour quad per step (rows are padded to whole quads): the quad's terms in FP32,
+    // their sum added in FP64, so the sums run at the FP32 rate and accumulate in FP64.
+    const float eps = (float)c.eps, voll = (float)c.voll;
+    const unsigned Tq = (unsigned)sc.Tp >> 2;
+    const long long ng = (long long)sc.G * Tq, nn = (long long)sc.N * Tq, nbt = (long long)sc.B * Tq;
+    for (long long q = tid; q < ng; q += stride) {
+        const unsigned g = (unsigned)q / Tq, t0 = 4u * ((unsigned)q - g * Tq);
+        const float4 p = *reinterpret_cast<const float4*>(c.xg + sc.e_gen + 4 * q);
+        const float pv[4] = {p.x, p.y, p.z, p.w};
+        const float cg = c.g_cost[sc.gen0 + g], eg = c.g_emis[sc.gen0 + g];
+        float a = 0.f, e = 0.f;
+#pragma unroll
+        for (int h = 0; h < 4; ++h)
+            if ((int)(t0 + h) < sc.T) {
+                a += cg * pv[h] + 0.5f * eps * pv[h] * pv[h];
+                e += eg * pv[h];
+            }
+        cs += (double)a;
+        em += (double)e;
     }
-    for (long long i = tid; i < nn; i += stride) {
-        const int t = (int)(i % sc.Tp);
-        if (t >= sc.T) continue;
-        const double sh = (double)c.xl[sc.e_bus + i] + (double)c.load[sc.e_bus + i];
-        cs += voll * sh + 0.5 * eps * sh * sh;
+    for (long long q = tid; q < nn; q += stride) {
+        const unsigned t0 = 4u * ((unsigned)q % Tq);
+        const float4 x = *reinterpret_cast<const float4*>(c.xl + sc.e_bus + 4 * q);
+        const float4 L = *reinterpret_cast<const float4*>(c.load + sc.e_bus + 4 * q);
+        const float sv[4] = {x.x + L.x, x.y + L.y, x.z + L.z, x.w + L.w};
+        float a = 0.f;
+#pragma unroll
+        for (int h = 0; h < 4; ++h)
+            if ((int)(t0 + h) < sc.T) a += voll * sv[h] + 0.5f * eps * sv[h] * sv[h];
+        cs += (double)a;
     }
-    for (long long i = tid; i < nbt; i += stride) {
-        const int t = (int)(i % sc.Tp);
-        if (t >= sc.T) continue;
-        const double ch = c.zc[sc.e_bat + i], di = c.zd[sc.e_bat + i];
-        cs += 0.5 * eps * (ch * ch + di * di);
+    for (long long q = tid; q < nbt; q += stride) {
+        const unsigned t0 = 4u * ((unsigned)q % Tq);
+        const float4 ch = *reinterpret_cast<const float4*>(c.zc + sc.e_bat + 4 * q);
+        const float4 di = *reinterpret_cast<const float4*>(c.zd + sc.e_bat + 4 * q);
+        const float cv[4] = {ch.x, ch.y, ch.z, ch.w}, dv[4] = {di.x, di.y, di.z, di.w};
+        float a = 0.f;
+#pragma unroll
+        for (int h = 0; h < 4; ++h)
+            if ((int)(t0 + h) < sc.T) a += 0.5f * eps * (cv[h] * cv[h] + dv[h] * dv[h]);
+        cs += (double)a;
     }
-    const long long nl = (long long)sc.L * sc.Tp;
-    for (long long i = tid; i < nl; i += stride) {
-        const int l = (int)(i / sc.Tp), t = (int)(i - (long long)l * sc.Tp);
-        if (t >= sc.T || c.l_w[sc.line0 + l] != 0.f) continue;
-        const double f = c.dl[sc.e_line + i];
-        cs += 0.5 * eps * f * f;
+    const long long nl = (long long)sc.L * Tq;
+    for (long long q = tid; q < nl; q += stride) {
+        const unsigned l = (unsigned)q / Tq, t0 = 4u * ((unsigned)q - l * Tq);
+        if (c.l_w[sc.line0 + l] != 0.f) continue;  // AC lines carry no cost; HVDC links eps/2 f^2
+        const float4 f = *reinterpret_cast<const float4*>(c.dl + sc.e_line + 4 * q);
+        const float fv[4] = {f.x, f.y, f.z, f.w};
+        float a = 0.f;
+#pragma unroll
+        for (int h = 0; h < 4; ++h)
+            if ((int)(t0 + h) < sc.T) a += 0.5f * eps * fv[h] * fv[h];
+        cs += (double)a;
     }
 }
 
