@@ -76,6 +76,25 @@ def agg_matrix(net, T):
     return A
 
 
+def agg_matrix_sparse(net, T):
+    """The same matrix as agg_matrix in CSR form, for graphs too large to hold densely: entry
+    ((n, t), (m, t)) = 1/deg(n) for every line joining n and m (parallel lines add up)."""
+    import scipy.sparse as sp
+    N = int(net["n_bus"])
+    adj = neighbours(net)
+    rows, cols, vals = [], [], []
+    for n in range(N):
+        if not adj[n]:
+            continue
+        w = 1.0 / len(adj[n])
+        for m in adj[n]:
+            for t in range(T):
+                rows.append(n * T + t)
+                cols.append(m * T + t)
+                vals.append(w)
+    return sp.csr_matrix((vals, (rows, cols)), shape=(N * T, N * T))  # duplicates are summed
+
+
 def init_params(rng, H=64, L=3, F=F_IN):
     p = {"W_in": rng.standard_normal((F, H)) * np.sqrt(2.0 / F), "b_in": np.zeros(H)}
     for k in range(L):

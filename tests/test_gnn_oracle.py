@@ -39,3 +39,26 @@ def test_gnn_features_and_aggregation():
     A = gnn.agg_matrix(nets[0], 24)
     # rows are means: each row sums to 1 (every tiny bus has a line)
     np.testing.assert_allclose(A.sum(1), 1.0)
+
+
+def test_sparse_aggregation_equals_dense_and_propagates_alike():
+    """agg_matrix_sparse holds agg_matrix's entries (each row of a connected bus sums to 1),
+    and forward/backward give the same results with either form."""
+    nets, scens = synth.tiny()
+    net = nets[0]
+    A = gnn.agg_matrix(net, 24)
+    As = gnn.agg_matrix_sparse(net, 24)
+    assert np.array_equal(As.toarray(), A)
+    rs = A.sum(axis=1)
+    assert np.allclose(rs[rs > 0], 1.0)
+    X = gnn.features(net, scens[0], net["eta_min"])
+    rng = np.random.default_rng(3)
+    p = gnn.init_params(rng, H=16)
+    target = rng.standard_normal((X.shape[0], 2))
+    yd, _ = gnn.forward(p, X, A)
+    ys, _ = gnn.forward(p, X, As)
+    assert np.allclose(yd, ys, rtol=1e-12, atol=1e-12)
+    gd = gnn.backward(p, X, A, target)
+    gs = gnn.backward(p, X, As, target)
+    for k in gd:
+        assert np.allclose(gd[k], gs[k], rtol=1e-12, atol=1e-12), k
