@@ -101,3 +101,47 @@ def test_medium_slice_parity():
     err = np.abs(gg - g_ref) / np.max(np.abs(g_ref))
     assert np.all(err <= 1e-3), np.sort(err)[-8:]
     assert rel(gg, g_ref) <= 1e-3, (net.last_grad_stats, rel(gg, g_ref))
+
+
+def test_batching_full_size_sampled_parity():
+    """The full batching workload (64 scenarios, each on its own network of 50-500 buses, 24, 72
+    or 168 hours) solved and differentiated in one batch, in the launch configuration bench.py
+    times (whole-loop graphs, the bind-time bus-kernel schedule), then checked on the sampled
+    scenarios the oracle can solve one by one (the two smallest): objective, FP64 KKT residuals
+    of the GPU dispatch, and the per-scenario gradient dh_s/deta (GX_ARR_GRAD_S).
+
+    Tolerances sit above this batch's FP32 floor: the 135-bus scenario's forward residual
+    levels off near 1.2e-6 and its adjoint near 5e-6, so the forward runs to 3e-6 and the
+    adjoint to 1e-5 (the parity setting of the other tests); scenarios that have not reached
+    them within the caps stop there without affecting the sampled ones."""
+    import torch
+    from oracle.dispatch import net_slices
+    nets, scens = synth.batching()
+    eta = np.concatenate([n["eta_min"] for n in nets]) * 1.05
+    kappa = 50.0
+    net = gpu_net(nets, scens, kappa=kappa, tol=3e-6, adj_tol=1e-5, rho_theta_c=0.01, max_iter=100000,
+                  adj_max_iter=100000, check_every=50)
+    e = eta_tensor(eta)
+    size = [int(nets[sc["net"]]["n_bus"]) * sc["T"] for sc in scens]
+    sampled = [int(s) for s in np.argsort(size)[:2]]
+    assert net.solve(e) in (0, 1)
+    torch.cuda.synchronize()
+    fwd_status = net.array("status").cpu().numpy().copy()
+    net.grad(e)
+    torch.cuda.synchronize()
+    adj_status = net.array("status").cpu().numpy().copy()
+    offs = net_slices(nets)
+    opts = synth.default_opts(kappa=kappa)
+    for s in sampled:
+        assert fwd_status[s] == 0 and adj_status[s] == 0, (s, fwd_status[s], adj_status[s])
+        k = scens[s]["net"]
+        ref = dispatch.solve(nets[k], scens[s], eta[offs[k]:offs[k + 1]], opts)
+        g = solution(net, s, ref_groups(ref.qp))
+        assert abs(g["cost"] - ref.cost) / ref.cost <= 1e-4, (s, g["cost"], ref.cost)
+        res = kkt.residuals(ref.qp, pack_x(ref.qp, g), g["price"], act_tol=ACT_TOL)
+        assert res["primal"] <= 1e-3 and res["dual"] <= 1e-3, (s, res)
+        gs = net.array("grad_s", s).cpu().numpy()
+        g_ref = ograd.adjoint_grad(ref)
+        assert gs.shape == g_ref.shape, (gs.shape, g_ref.shape)
+        assert rel(gs, g_ref) <= 1e-3, (s, rel(gs, g_ref))
+        assert np.max(np.abs(gs - g_ref)) <= 1e-3 * np.max(np.abs(g_ref)), s
