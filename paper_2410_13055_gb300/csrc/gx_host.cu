@@ -85,6 +85,8 @@ struct gx_network {
     int n_bus4_blk = 0, n_line4_blk = 0;
     size_t bus4_smem = 0;              // dynamic shared memory of the staged bus kernel (record + stage)
     std::vector<int> pool;             // their pool records (words)
+    std::vector<int> bus_cpl;          // per hour-quad bus block: copy-list header and list (fixed stride)
+    int bus_cpl_stride = 0, bus_cpl_max = 0;
     std::vector<int2> prep;            // (pool word, eta index) of each generator plan value
     std::vector<uint8_t> firm;         // generator has capacity factor 1 in every hour of every scenario
     // lines whose susceptance scales with capacity (gx_scale.cu)
@@ -112,7 +114,7 @@ struct gx_network {
     int max_ramp_T = 1;
     // workspace offsets
     size_t o_scen, o_bbs, o_lbs, o_bws, o_cbs, o_gwarp, o_knet, o_busblk, o_pool, o_prep, o_crs;
-    size_t o_bus4blk, o_l4bs, o_l4blk, o_batw;
+    size_t o_bus4blk, o_l4bs, o_l4blk, o_batw, o_buscpl, o_busdone;
     size_t o_scl, o_sce, o_scb, o_scbm, o_scp, o_scd, o_scdl, o_scgw;
     size_t o_rgen, o_rrate, o_gramp, o_rws, o_rdd, o_ardd, o_rf[4], o_ra[4], o_rpart;
     size_t o_gbus, o_gcost, o_gemis, o_gfirm, o_lfrom, o_lto, o_lbeta, o_ldth, o_lw, o_bbus, o_bdur, o_beffc, o_beffd;
@@ -255,6 +257,10 @@ static void make_ctx(gx_network* net) {
     c.bus_blk_scen = I(net->o_bbs);
     c.bus_blk = reinterpret_cast<const BusBlk*>(d + net->o_busblk);
     c.bus4_blk = reinterpret_cast<const BusBlk*>(d + net->o_bus4blk);
+    c.bus_cpl = net->bus_cpl.empty() ? nullptr : reinterpret_cast<const int*>(d + net->o_buscpl);
+    c.bus_cpl_stride = net->bus_cpl_stride;
+    c.bus_cpl_max = net->bus_cpl_max;
+    c.bus_done = reinterpret_cast<int*>(d + net->o_busdone);
     c.n_ramp_warps = net->n_ramp_warps;
     c.ramp_warp_scen = I(net->o_rws);
     c.r_gen = I(net->o_rgen);
@@ -527,6 +533,52 @@ static void build_crs_groups(gx_network* net) {
 
 // Bus-kernel block records and the pool records of the bus ranges they cover.  Blocks of
 // scenarios on the same network with the same bus range share one pool record.
+// Per-block copy lists of the bulk-staged bus kernel at a fixed stride: block b's header
+// (copies, forward bytes, adjoint bytes, 0) and copies at b * stride, where a block can read
+// them before it knows its record's offset.  Blocks whose record is not kept in shared memory
+// get an empty list and use the record path.  Built only while the lists stay small (they
+// repeat each scenario's records); above the cap the kernel reads the lists from the records.
+constexpr size_t kBusCplMaxBytes = 16u << 20;
+
+static void build_bus_copy_lists(gx_network* net) {
+    net->bus_cpl.clear();
+    net->bus_cpl_stride = 0;
+    net->bus_cpl_max = 0;
+    // a block takes the list path if its record fits shared memory and its list fits the
+    // threads' copy slots (unstaged records: an empty list, only the record is copied)
+    auto listed = [&](const BusBlk& r) {
+        if (r.words > kPoolMax) return false;
+        const int* p = net->pool.data() + r.pool;
+        return p[kPH_SBYTES] == 0 || p[kPH_NCP] <= kCplPerThread * kBusQBlock;
+    };
+    int maxcp = 0, nlisted = 0;
+    for (const BusBlk& r : net->bus4_blk) {
+        if (!listed(r)) continue;
+        const int* p = net->pool.data() + r.pool;
+        ++nlisted;
+        if (p[kPH_SBYTES] > 0) maxcp = std::max(maxcp, p[kPH_NCP]);
+    }
+    const int stride = (4 + 3 * maxcp + 3) / 4 * 4;
+    if (nlisted == 0 || (size_t)stride * 4 * net->bus4_blk.size() > kBusCplMaxBytes) return;
+    net->bus_cpl.assign((size_t)stride * net->bus4_blk.size(), 0);
+    for (size_t b = 0; b < net->bus4_blk.size(); ++b) {
+        const BusBlk& r = net->bus4_blk[b];
+        int* q = net->bus_cpl.data() + b * stride;
+        if (!listed(r)) {
+            q[3] = 1;
+            continue;
+        }
+        const int* p = net->pool.data() + r.pool;
+        const int ncp = p[kPH_SBYTES] > 0 ? p[kPH_NCP] : 0;
+        q[0] = ncp;
+        q[1] = p[kPH_SBYTES] > 0 ? p[kPH_TXF] : 0;
+        q[2] = p[kPH_SBYTES] > 0 ? p[kPH_TXA] : 0;
+        std::memcpy(q + 4, p + p[kPH_CP], sizeof(int) * 3 * (size_t)ncp);
+    }
+    net->bus_cpl_stride = stride;
+    net->bus_cpl_max = maxcp;
+}
+
 static void build_bus_blocks(gx_network* net) {
     auto fbits = [](float f) { int w; std::memcpy(&w, &f, 4); return w; };
     // (quad, net, n0, n1, first quad of bus n0, end quad of bus n1, quads per row) -> (offset, words)
@@ -920,6 +972,7 @@ gx_status gx_network_create(const gx_network_desc* nets, int n_nets, const gx_sc
                 if (sc.cf[(size_t)g * sc.Tp + t] != 1.0f) { net->firm[n.gen0 + g] = 0; break; }
     }
     build_bus_blocks(net);
+    build_bus_copy_lists(net);
     net->line4_blk.clear();
     net->bat_w.clear();
     for (int s = 0; s < S; ++s) {
@@ -975,6 +1028,8 @@ gx_status gx_network_create(const gx_network_desc* nets, int n_nets, const gx_sc
     net->o_prep = L.add(8 * std::max<size_t>(net->prep.size(), 1));
     net->o_crs = L.add(I4((long long)net->crs_list.size()));
     net->o_bus4blk = L.add(sizeof(BusBlk) * std::max<size_t>(net->bus4_blk.size(), 1));
+    net->o_buscpl = L.add(I4(std::max<long long>((long long)net->bus_cpl.size(), 1)));
+    net->o_busdone = L.add(I4(std::max<long long>((long long)net->bus4_blk.size(), 1)));
     net->o_l4bs = L.add(I4(net->n_line4_blk));
     net->o_l4blk = L.add(sizeof(LineBlk) * std::max<size_t>(net->line4_blk.size(), 1));
     net->o_batw = L.add(sizeof(BatW) * std::max<size_t>(net->bat_w.size(), 1));
@@ -1067,6 +1122,7 @@ gx_status gx_network_bind(gx_network* net, void* dev_mem, size_t bytes, void* st
     put(net->o_prep, net->prep.data(), 8 * net->prep.size());
     put(net->o_crs, net->crs_list.data(), 4 * net->crs_list.size());
     put(net->o_bus4blk, net->bus4_blk.data(), sizeof(BusBlk) * net->bus4_blk.size());
+    put(net->o_buscpl, net->bus_cpl.data(), 4 * net->bus_cpl.size());
     put(net->o_l4bs, net->line4_blk_scen.data(), 4 * net->line4_blk_scen.size());
     put(net->o_l4blk, net->line4_blk.data(), sizeof(LineBlk) * net->line4_blk.size());
     put(net->o_batw, net->bat_w.data(), sizeof(BatW) * net->bat_w.size());

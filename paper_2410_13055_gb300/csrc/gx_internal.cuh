@@ -58,6 +58,9 @@ enum : int {
     kPoolHdr = 32
 };
 constexpr int kPoolMax = 3072;  // longest record (words) staged in shared memory
+// copies per thread of the staged bus kernel's per-block lists (a block with more copies than
+// kCplPerThread * kBusQBlock, or a record too long for shared memory, takes the record path)
+constexpr int kCplPerThread = 2;
 // staged copies: array ids and flags of a copy-list entry
 enum : int { kCpGenX = 0, kCpGenAux = 1, kCpDl = 2, kCpVf = 3, kCpVt = 4, kCpBat = 5 };
 enum : int { kCpFirm = 1, kCpRamp = 2 };   // (flags << 3): capacity factor 1 / ramp-limited generator
@@ -299,6 +302,14 @@ struct Ctx {
     // memory; a bounded device-side wait that gave up writes its status to *err
     int bus_staged;
     int bus4_smem;
+    // Bulk-staged bus kernel, per block at a fixed stride (built where the lists are small):
+    // header (copies, forward bytes, adjoint bytes, 1 = take the record path) then the block's
+    // copy list, so a block reads its list together with its block record; and per-block done
+    // flags, refreshed from the scenario flags at every chunk start.  bus_cpl == nullptr: every
+    // block reads its list from its record.
+    const int* bus_cpl;
+    int bus_cpl_stride, bus_cpl_max;  // ints per block; most copies of a block
+    int* bus_done;                    // [n_bus4_blk]
     int bat_warps;       // battery prox warps per battery for horizons over 96 hours (1 or 2)
     int* err;
 };

@@ -1126,7 +1126,34 @@ __device__ __forceinline__ bool copy_wanted(int code) {
     return ADJ || !(fl & kCpFirm);
 }
 
-template <int ADJ, int RAMP>
+// Source row base of a staged copy (copy-list code: array id in the low 3 bits).
+template <int ADJ>
+__device__ __forceinline__ const float* stage_src(const Ctx& c, const StatePtrs& X, const BusBlk& bb, int code) {
+    switch (code & 7) {
+        case kCpGenX: return X.xg + bb.e_gen;
+        case kCpGenAux: return (ADJ ? c.ag : c.cf) + bb.e_gen;
+        case kCpDl: return X.dl + bb.e_line;
+        case kCpVf: return X.vf + bb.e_line;
+        case kCpVt: return X.vt + bb.e_line;
+        default: return X.xb + bb.e_bat;
+    }
+}
+
+// Bounded wait for the block's bulk copies.  On expiry: report, give them one more bounded
+// wait, and return false (the caller leaves without touching the iterate).
+template <int ADJ>
+__device__ __forceinline__ bool bulk_wait(const Ctx& c, unsigned long long* bar) {
+    bool ok = false;
+    for (int k = 0; k < kWaitProbes && !ok; ++k) ok = mbar_try(bar, 0);
+    if (ok) return true;
+    if (threadIdx.x == 0) atomicExch(c.err, GX_ERR_TIMEOUT);
+    for (int k = 0; k < kWaitProbes && !ok; ++k) ok = mbar_try(bar, 0);
+    return false;
+}
+
+// LIST: the block's copy list and done flag come from its own slot (c.bus_cpl); compiled
+// apart so that the record-path instance keeps its registers.
+template <int ADJ, int RAMP, int LIST>
 __global__ void __launch_bounds__(kBusQBlock, GX_BUS4T_MINB * 128 / kBusQBlock) k_bus4t(const Ctx c, int want_res) {
     extern __shared__ __align__(16) int S[];  // the block's record, then its row stage
     __shared__ __align__(8) unsigned long long bar;
@@ -1134,9 +1161,33 @@ __global__ void __launch_bounds__(kBusQBlock, GX_BUS4T_MINB * 128 / kBusQBlock) 
     if (stamp && threadIdx.x == 0) stamp_start(c, 0);
     const BusBlk bb = c.bus4_blk[blockIdx.x];
     const StatePtrs X = state<ADJ>(c);
-    // hop 2: the record and the done flag, in flight together
+    const bool bulk = c.bus_staged == 1;
     const bool rec_smem = bb.words <= kPoolMax;
-    if (rec_smem) {
+    // Bulk schedule with per-block copy lists: the block's list and its done flag sit at its
+    // own slot, so they are read together with the block record (hop 1), and the record and
+    // the rows arrive together one hop later.  Otherwise the list comes from the record.
+    const int* cpl = (LIST && bulk) ? c.bus_cpl + (long long)blockIdx.x * c.bus_cpl_stride : nullptr;
+    int cp_n = 0, cp_tx = 0, fdone = 0, cp_rec = 1;
+    int cp_e[kCplPerThread][3];
+    if (LIST && cpl) {
+        cp_n = cpl[0];
+        cp_tx = cpl[ADJ ? 2 : 1];
+        cp_rec = cpl[3];
+        fdone = c.bus_done[blockIdx.x];
+#pragma unroll
+        for (int j = 0; j < kCplPerThread; ++j) {
+            const int k = (int)threadIdx.x + j * kBusQBlock;
+            cp_e[j][0] = cp_e[j][1] = cp_e[j][2] = 0;
+            if (k < c.bus_cpl_max) {
+                cp_e[j][0] = cpl[4 + 3 * k];
+                cp_e[j][1] = cpl[4 + 3 * k + 1];
+                cp_e[j][2] = cpl[4 + 3 * k + 2];
+            }
+        }
+    }
+    const bool fast = LIST && cpl != nullptr && cp_rec == 0;  // a listed block's record fits shared memory
+    // hop 2 (record path): the record and the done flag, in flight together
+    if (!fast && rec_smem) {
         const int4* src = reinterpret_cast<const int4*>(c.pool + bb.pool);
         int4* dst = reinterpret_cast<int4*>(S);
         for (int k = threadIdx.x; k < (bb.words >> 2); k += kBusQBlock) dst[k] = src[k];
@@ -1147,19 +1198,34 @@ __global__ void __launch_bounds__(kBusQBlock, GX_BUS4T_MINB * 128 / kBusQBlock) 
     const int t = (local - n * Tq) * 4;
     const bool valid = local < bb.nitems;
     const long long i = bb.e_bus + (long long)n * bb.Tp + t;
-    const int done = c.done[bb.s];
-    const bool bulk = c.bus_staged == 1;
+    const int done = fast ? fdone : c.done[bb.s];
     if (threadIdx.x == 0 && bulk && rec_smem) {
-        // arm the barrier with the bytes the copies will bring (from the record's header,
-        // read directly: the staged copy of the record is not there yet)
-        const int* hdr = c.pool + bb.pool;
         mbar_init(&bar, 1);
         mbar_fence_init();
-        if (hdr[kPH_SBYTES] > 0) mbar_expect_tx(&bar, (unsigned)hdr[ADJ ? kPH_TXA : kPH_TXF]);
+        if (fast) {
+            mbar_expect_tx(&bar, 4u * (unsigned)bb.words + (unsigned)cp_tx);  // the record and the rows
+        } else {
+            // the bytes the copies will bring, from the record's header read directly (the
+            // staged copy of the record is not there yet)
+            const int* hdr = c.pool + bb.pool;
+            if (hdr[kPH_SBYTES] > 0) mbar_expect_tx(&bar, (unsigned)hdr[ADJ ? kPH_TXA : kPH_TXF]);
+        }
     }
     __syncthreads();
-    if (done) return;  // block-uniform: a converged scenario's blocks stop after two hops
-    // hop 3: this thread's bus state, in flight together with the row copies below
+    if (done) return;  // block-uniform: a converged scenario's blocks stop here
+    float4* stage = reinterpret_cast<float4*>(S + bb.words);
+    if (fast) {
+        // hop 2 (list path): the record and every device row segment of the block
+        if (threadIdx.x == 0) bulk_g2s(S, c.pool + bb.pool, 4u * (unsigned)bb.words, &bar);
+#pragma unroll
+        for (int j = 0; j < kCplPerThread; ++j) {
+            const int k = (int)threadIdx.x + j * kBusQBlock;
+            if (k < cp_n && copy_wanted<ADJ>(cp_e[j][2]))
+                bulk_g2s(stage + cp_e[j][1], stage_src<ADJ>(c, X, bb, cp_e[j][2]) + cp_e[j][0],
+                         16u * (unsigned)(cp_e[j][2] >> 5), &bar);
+        }
+    }
+    // this thread's bus state, in flight together with the row copies
     float pb[4], uu[4], thold[4], xl[4], Ld[4], al[4];
     if (valid) {
         ld4(X.pbar + i, pb); ld4(X.u + i, uu); ld4(X.thb + i, thold);
@@ -1167,27 +1233,19 @@ __global__ void __launch_bounds__(kBusQBlock, GX_BUS4T_MINB * 128 / kBusQBlock) 
         if (ADJ) ld4(c.al + i, al);  // the adjoint needs the load only through its coefficient
         else ld4(c.load + i, Ld);
     }
+    if (fast && !bulk_wait<ADJ>(c, &bar)) return;
     const Pool P{rec_smem ? S : c.pool + bb.pool};
     const int sbytes = P.p[kPH_SBYTES];
-    float4* stage = reinterpret_cast<float4*>(S + bb.words);
     const int qg = P.p[kPH_QG], qe = P.p[kPH_QE];
-    // hop 3 (bulk): every device row segment of the block, the copy list split over the warps
-    if (sbytes > 0 && bulk) {
+    // hop 3 (bulk, record path): every device row segment of the block, the copy list split
+    // over the warps
+    if (!fast && sbytes > 0 && bulk) {
         const int ncp = P.p[kPH_NCP];
-        const int* cpl = P.p + P.p[kPH_CP];
+        const int* rcpl = P.p + P.p[kPH_CP];
         for (int k = threadIdx.x; k < ncp; k += kBusQBlock) {
-            const int rel = cpl[3 * k], dst = cpl[3 * k + 1], code = cpl[3 * k + 2];
+            const int rel = rcpl[3 * k], dst = rcpl[3 * k + 1], code = rcpl[3 * k + 2];
             if (!copy_wanted<ADJ>(code)) continue;
-            const float* src;
-            switch (code & 7) {
-                case kCpGenX: src = X.xg + bb.e_gen; break;
-                case kCpGenAux: src = (ADJ ? c.ag : c.cf) + bb.e_gen; break;
-                case kCpDl: src = X.dl + bb.e_line; break;
-                case kCpVf: src = X.vf + bb.e_line; break;
-                case kCpVt: src = X.vt + bb.e_line; break;
-                default: src = X.xb + bb.e_bat; break;
-            }
-            bulk_g2s(stage + dst, src + rel, 16u * (unsigned)(code >> 5), &bar);
+            bulk_g2s(stage + dst, stage_src<ADJ>(c, X, bb, code) + rel, 16u * (unsigned)(code >> 5), &bar);
         }
     }
     const int nl = n - bb.n0;
@@ -1220,17 +1278,7 @@ __global__ void __launch_bounds__(kBusQBlock, GX_BUS4T_MINB * 128 / kBusQBlock) 
                        X.xb + bb.e_bat + (long long)P.at(kPH_BROW, q) * bb.Tp + t);
     }
     if (sbytes > 0 && !bulk) cp_async_wait_all();
-    if (sbytes > 0 && bulk) {
-        bool ok = false;
-        for (int k = 0; k < kWaitProbes && !ok; ++k) ok = mbar_try(&bar, 0);
-        if (!ok) {
-            // the copies did not land: report, give them one more bounded wait, and leave
-            // without touching the iterate
-            if (threadIdx.x == 0) atomicExch(c.err, GX_ERR_TIMEOUT);
-            for (int k = 0; k < kWaitProbes && !ok; ++k) ok = mbar_try(&bar, 0);
-            return;
-        }
-    }
+    if (!fast && sbytes > 0 && bulk && !bulk_wait<ADJ>(c, &bar)) return;
     float acc[kBusPart] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (valid) {
         const bool stg = sbytes > 0;
@@ -1403,9 +1451,13 @@ __global__ void k_prep(const Ctx c) {
 //            (scale = |L|_2 forward, |x|_2 adjoint)
 //   dual   = sqrt(rho^2 |z^k - z^{k-1}|^2 + sum_j (rho_th_j dthbar / beta_j)^2) / |rho u|_2
 // ------------------------------------------------------------------------------------
-// Advance the loop's device iteration counter by one chunk (one thread).
-__global__ void k_tick(int* ctr, int chunk) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) *ctr += chunk;
+// Chunk start: advance the loop's device iteration counter by one chunk (one thread), and
+// refresh the staged bus kernel's per-block done flags from the scenario flags (which change
+// only at the reductions that end chunks, or between calls).
+__global__ void k_tick(const Ctx c, int chunk) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) *c.iter_ctr += chunk;
+    for (int b = i; b < c.n_bus4_blk; b += gridDim.x * blockDim.x) c.bus_done[b] = c.done[c.bus4_blk[b].s];
 }
 
 __global__ void __launch_bounds__(kBlock) k_reduce(const Ctx c, int adj, double tol) {
@@ -1830,13 +1882,20 @@ int launch_bus(const Ctx& c, int mode, int adj, int want_res, cudaStream_t st) {
     if (mode == M_FWD || mode == M_ADJ) {
         const int sm = c.bus4_smem;
         if (c.bus_staged != 0) {
+            const bool list = c.bus_staged == 1 && c.bus_cpl != nullptr;
+#define GX_BUS4T(A, R)                                                                  \
+    do {                                                                                \
+        if (list) k_bus4t<A, R, 1><<<c.n_bus4_blk, kBusQBlock, sm, st>>>(c, want_res);  \
+        else k_bus4t<A, R, 0><<<c.n_bus4_blk, kBusQBlock, sm, st>>>(c, want_res);       \
+    } while (0)
             if (c.n_ramp_warps > 0) {
-                if (adj) k_bus4t<1, 1><<<c.n_bus4_blk, kBusQBlock, sm, st>>>(c, want_res);
-                else k_bus4t<0, 1><<<c.n_bus4_blk, kBusQBlock, sm, st>>>(c, want_res);
+                if (adj) GX_BUS4T(1, 1);
+                else GX_BUS4T(0, 1);
             } else {
-                if (adj) k_bus4t<1, 0><<<c.n_bus4_blk, kBusQBlock, sm, st>>>(c, want_res);
-                else k_bus4t<0, 0><<<c.n_bus4_blk, kBusQBlock, sm, st>>>(c, want_res);
+                if (adj) GX_BUS4T(1, 0);
+                else GX_BUS4T(0, 0);
             }
+#undef GX_BUS4T
         } else if (c.n_ramp_warps > 0) {
             if (adj) k_bus4<1, 1><<<c.n_bus4_blk, kBusQBlock, 0, st>>>(c, want_res);
             else k_bus4<0, 1><<<c.n_bus4_blk, kBusQBlock, 0, st>>>(c, want_res);
@@ -1855,10 +1914,14 @@ cudaError_t bus_staged_prepare(int smem) {
     auto set = [&](const void* f) {
         if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     };
-    set((const void*)k_bus4t<0, 0>);
-    set((const void*)k_bus4t<1, 0>);
-    set((const void*)k_bus4t<0, 1>);
-    set((const void*)k_bus4t<1, 1>);
+    set((const void*)k_bus4t<0, 0, 0>);
+    set((const void*)k_bus4t<1, 0, 0>);
+    set((const void*)k_bus4t<0, 1, 0>);
+    set((const void*)k_bus4t<1, 1, 0>);
+    set((const void*)k_bus4t<0, 0, 1>);
+    set((const void*)k_bus4t<1, 0, 1>);
+    set((const void*)k_bus4t<0, 1, 1>);
+    set((const void*)k_bus4t<1, 1, 1>);
     return e;
 }
 
@@ -1874,7 +1937,9 @@ int launch_reduce(const Ctx& c, int adj, double tol, cudaStream_t st) {
 }
 
 int launch_tick(const Ctx& c, int chunk, cudaStream_t st) {
-    k_tick<<<1, 32, 0, st>>>(c.iter_ctr, chunk);
+    int grid = (c.n_bus4_blk + kBlock - 1) / kBlock;
+    grid = grid < 1 ? 1 : grid > 256 ? 256 : grid;
+    k_tick<<<grid, kBlock, 0, st>>>(c, chunk);
     return 1;
 }
 
