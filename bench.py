@@ -168,12 +168,12 @@ def algorithmic_bytes(nets, scens):
 # DRAM bytes (read + write) per launch from one ncu capture of the solver kernels; valid only
 # while gx_kernels.cu is the source that was profiled.
 PROFILED = {
-    "sha256_prefix": "ecade3455df667f6",
+    "sha256_prefix": "8e66a2280c707af5",
     # forward launches, all scenarios iterating, cold cache (ncu flushes before each pass)
     "medium": {"scenarios": 16, "source": "profiles/launches_medium_bench.md (dram capture, same command)",
-               "traffic": {"k_bus": 16.35e6, "k_line": 9.79e6, "k_bat": 5.33e6}},
+               "traffic": {"k_bus": 16.84e6, "k_line": 9.80e6, "k_bat": 5.33e6}},
     "scale": {"scenarios": 13, "source": "profiles/bus_kernel_staged_scale13.md",
-              "traffic": {"k_bus": 388.1e6, "k_line": 210.6e6, "k_bat": 43.9e6}},
+              "traffic": {"k_bus": 387.8e6, "k_line": 209.0e6, "k_bat": 43.9e6}},
 }
 
 

@@ -87,6 +87,7 @@ struct gx_network {
     std::vector<int> pool;             // their pool records (words)
     std::vector<int> bus_cpl;          // per hour-quad bus block: copy-list header and list (fixed stride)
     int bus_cpl_stride = 0, bus_cpl_max = 0;
+    bool l2_resident = false;          // the bound workspace fits the device's L2 (set at bind)
     std::vector<int2> prep;            // (pool word, eta index) of each generator plan value
     std::vector<uint8_t> firm;         // generator has capacity factor 1 in every hour of every scenario
     // lines whose susceptance scales with capacity (gx_scale.cu)
@@ -257,7 +258,7 @@ static void make_ctx(gx_network* net) {
     c.bus_blk_scen = I(net->o_bbs);
     c.bus_blk = reinterpret_cast<const BusBlk*>(d + net->o_busblk);
     c.bus4_blk = reinterpret_cast<const BusBlk*>(d + net->o_bus4blk);
-    c.bus_cpl = net->bus_cpl.empty() ? nullptr : reinterpret_cast<const int*>(d + net->o_buscpl);
+    c.bus_cpl = (net->bus_cpl.empty() || !net->l2_resident) ? nullptr : reinterpret_cast<const int*>(d + net->o_buscpl);
     c.bus_cpl_stride = net->bus_cpl_stride;
     c.bus_cpl_max = net->bus_cpl_max;
     c.bus_done = reinterpret_cast<int*>(d + net->o_busdone);
@@ -1190,14 +1191,17 @@ gx_status gx_network_bind(gx_network* net, void* dev_mem, size_t bytes, void* st
     if (!net->ev_fork) GX_CUDA(cudaEventCreateWithFlags(&net->ev_fork, cudaEventDisableTiming));
     if (!net->ev_join) GX_CUDA(cudaEventCreateWithFlags(&net->ev_join, cudaEventDisableTiming));
     if (net->bus4_smem > 0) GX_CUDA(bus_staged_prepare((int)net->bus4_smem));
-    if (!net->sched_set) {
-        // default bus kernel: stage the device rows when the iteration streams from HBM (the
-        // workspace exceeds L2); an L2-resident workspace is latency-bound, where the
-        // per-thread loads measured faster
+    {
         int dev = 0, l2 = 0;
         GX_CUDA(cudaGetDevice(&dev));
         GX_CUDA(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
-        net->sched.bus_staged = net->lay.total > (size_t)l2 ? 1 : 0;
+        // An L2-resident workspace is latency-bound: there the staged kernel reads its copy
+        // lists from per-block slots (one dependent hop fewer, more registers); a workspace
+        // that streams from HBM keeps the record path and its occupancy.
+        net->l2_resident = net->lay.total <= (size_t)l2;
+        // default bus kernel until a schedule is set: stage the device rows when the iteration
+        // streams from HBM; the autotuner picks per workload
+        if (!net->sched_set) net->sched.bus_staged = net->l2_resident ? 0 : 1;
     }
     make_ctx(net);
     for (auto& g : net->crs_groups) {
