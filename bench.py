@@ -297,7 +297,8 @@ def measure(config, args, steps, warmup, dist=None, learned=False, cold=True, sc
                 allreduce_sum(grad)
             net.plan_step(e, grad, gamma, eta_min, eta_max, state["alpha"])
 
-        tuned = autotune.tune_schedule_step(net, eta, step=plain_step, flush=lambda: flush.fill_(1.0))
+        tuned = autotune.tune_schedule_step(net, eta, step=plain_step, steps=args.tune_steps, reps=args.tune_reps,
+                                            flush=lambda: flush.fill_(1.0))
 
     def timed(warm, K):
         state["launches"], state["iters"], state["adj_iters"] = 0, [], []
@@ -754,6 +755,8 @@ def main():
                     help="batching config: also time one network and launch sequence per scenario")
     ap.add_argument("--no-sub", action="store_true",
                     help="medium config: skip the scale and batching sub-records")
+    ap.add_argument("--tune-steps", type=int, default=2, help="previous-plan steps per schedule trial")
+    ap.add_argument("--tune-reps", type=int, default=2, help="repetitions of each schedule trial (best kept)")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the library's default kernel schedule instead of autotuning it per workload")
     ap.add_argument("--bus-staged", type=int, default=None, choices=[0, 1, 2],
