@@ -556,10 +556,11 @@ def run_gx(args):
         "cpu_reference": cpu_ref,
         "e2e": head["e2e"],
         "clocks": head["clocks"],
-        "gpu_launches": head["gpu_launches"] + sum(r["gpu_launches"] for r in subs.values()),
+        "gpu_launches": head["gpu_launches"],
         "workloads": subs or None,
-        "batching": per_scen,
     }
+    if per_scen is not None:
+        out["per_scenario"] = per_scen
     print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()
