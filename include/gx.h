@@ -201,6 +201,12 @@ int gx_network_S(const gx_network* net);
 /* Upload static data into dev_mem (>= gx_network_device_bytes, 256-byte aligned)
  * and zero the state.  Asynchronous on `stream`. */
 gx_status gx_network_bind(gx_network* net, void* dev_mem, size_t bytes, void* stream);
+/* Drop the previous solution, as a fresh bind does, without touching the workspace's data:
+ * the next GX_WARM_PREV solve starts cold, the next GX_WARM_LEARNED solve takes the learned
+ * start for every scenario (no selection trial), and gx_dispatch_grad_batch needs a new
+ * solve (its GX_WARM_PREV then starts cold too).  Host only, no device work.  Errors:
+ * GX_ERR_STATE if the network is not bound. */
+gx_status gx_network_forget(gx_network* net);
 /* Replace the options (rho, tolerances, ...); model constants eps/voll/kappa too.
  * Recomputes the battery factorisation on the next solve. */
 gx_status gx_network_set_opts(gx_network* net, const gx_opts* opts);

@@ -1216,6 +1216,13 @@ gx_status gx_network_bind(gx_network* net, void* dev_mem, size_t bytes, void* st
     return GX_OK;
 }
 
+gx_status gx_network_forget(gx_network* net) {
+    if (!net || !net->dev) return fail(GX_ERR_STATE, "network is not bound");
+    net->solved = false;
+    net->adj_ready = false;
+    return GX_OK;
+}
+
 gx_status gx_network_set_opts(gx_network* net, const gx_opts* opts) {
     if (!net || !opts) return fail(GX_ERR_INVALID_ARG, "NULL argument");
     if (gx_status st = check_opts(opts)) return st;

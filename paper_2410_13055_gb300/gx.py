@@ -82,6 +82,7 @@ _SIGS = {
     "gx_network_S": (C.c_int, [_vp]),
     "gx_network_bind": (C.c_int, [_vp, _vp, _sz, _vp]),
     "gx_network_set_opts": (C.c_int, [_vp, C.POINTER(Opts)]),
+    "gx_network_forget": (C.c_int, [_vp]),
     "gx_network_array": (C.c_int, [_vp, C.c_int, C.c_int, C.POINTER(_sz), C.POINTER(_sz)]),
     "gx_network_state_range": (C.c_int, [_vp, C.c_int, C.POINTER(_sz), C.POINTER(_sz)]),
     "gx_network_scenario_info": (C.c_int, [_vp, C.c_int] + [C.POINTER(C.c_int)] * 7),
@@ -248,6 +249,11 @@ class Network:
                 setattr(opts, k, v)
         _check(_lib.gx_network_set_opts(self._h, C.byref(opts)), "gx_network_set_opts", False)
         self.opts = opts
+
+    def forget(self):
+        """Drop the previous solution: the next warm="prev" solve starts cold, and warm="learned"
+        takes the learned start for every scenario."""
+        _check(_lib.gx_network_forget(self._h), "gx_network_forget", False)
 
     def state(self, adjoint=False):
         """A float32 torch view (no copy) of the forward or adjoint iteration state; clone it

@@ -61,6 +61,8 @@ def test_create_validates_on_host(gx):
     # solve before bind is an ordering error, not a crash
     st = gx.Stats()
     assert gx._lib.gx_dispatch_solve_batch(h, ctypes.c_void_p(16), None, 0, 0, None, ctypes.byref(st), None) == -6
+    assert gx._lib.gx_network_forget(h) == -6
+    assert gx._lib.gx_network_forget(None) == -6
     gx._lib.gx_network_destroy(h)
 
 

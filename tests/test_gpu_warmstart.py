@@ -87,6 +87,15 @@ def test_learned_mode_selection_rule_through_the_abi():
     assert np.all(it_l[chosen == 0] == it_prev[chosen == 0]), (chosen, it_l, it_prev)
     assert np.all(it_l <= np.maximum(it_prev, every) + 5000)
     assert np.allclose(net.array("cost").cpu().numpy(), cost_prev, rtol=2e-3)
+    # with the previous solution dropped, every scenario takes the learned start again
+    net.forget()
+    with pytest.raises(gx.GxError) as e:
+        net.grad(e2, warm="prev")
+    assert e.value.status == -6
+    assert net.solve(e2, warm="learned") == 0
+    torch.cuda.synchronize()
+    assert np.all(net.array("warm").cpu().numpy() == 1)
+    assert np.all(net.array("status").cpu().numpy() == 0)
 
 
 def test_exact_prices_do_not_beat_the_previous_plan_start():
