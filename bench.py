@@ -174,13 +174,16 @@ PROFILED = {
                "traffic": {"k_bus": 16.84e6, "k_line": 9.80e6, "k_bat": 5.33e6}},
     "scale": {"scenarios": 13, "source": "profiles/bus_kernel_staged_scale13.md",
               "traffic": {"k_bus": 387.8e6, "k_line": 209.0e6, "k_bat": 43.9e6}},
+    "batching": {"scenarios": 64, "source": "profiles/solver_kernels_batching64.md",
+                 "traffic": {"k_bus": 103.86e6, "k_line": 56.73e6, "k_bat": 19.05e6}},
 }
 
 
 def profiled_traffic(config, n_scen, kernel):
-    """DRAM bytes per launch from the capture of this workload, scaled by scenarios (both
-    captures are above L2, where traffic grows in proportion to the scenarios); None if
-    the kernels changed since, or the workload has no capture."""
+    """DRAM bytes per launch from the capture of this workload, scaled by scenarios (the Scale
+    capture is of 13 of its 52 identical-size weeks, above L2, where traffic grows in
+    proportion; the others are of the whole workload); None if the kernels changed since, or
+    the workload has no capture."""
     import hashlib
     src = os.path.join(ROOT, "paper_2410_13055_gb300", "csrc", "gx_kernels.cu")
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]

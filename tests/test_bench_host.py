@@ -80,7 +80,7 @@ def test_profiled_traffic_gate(monkeypatch):
 
 def test_profiled_captures_are_well_formed():
     assert len(bench.PROFILED["sha256_prefix"]) == 16
-    for cfg in ("medium", "scale"):
+    for cfg in ("medium", "scale", "batching"):
         cap = bench.PROFILED[cfg]
         assert cap["scenarios"] > 0 and cap["source"].startswith("profiles/")
         assert os.path.exists(os.path.join(ROOT, cap["source"].split(" ")[0]))
