@@ -487,7 +487,9 @@ def measure_learned(net, eta, grad, gamma, eta_min, eta_max, alpha, flush, dh, s
     paper_2410_13055_gb300.train_warmstart on this network (weights in
     paper_2410_13055_gb300/weights/), its prediction inside the solve, and the selection
     rule (per scenario, the learned start or the previous plan's state, whichever has the
-    smaller residual at the first check).  Same plan steps as the headline's."""
+    smaller residual at the first check), on the plan path continued from the headline's.
+    Then the learned start alone (no previous solution: gx_network_forget) against a cold
+    start on the same plans, both checked against one tight solve at the first of them."""
     import torch
     from paper_2410_13055_gb300 import gx
     wpath = os.path.join(ROOT, "paper_2410_13055_gb300", "weights", "warmstart_medium.npy")
