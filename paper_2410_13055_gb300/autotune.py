@@ -147,6 +147,16 @@ def tune_schedule(net: gx.Network, eta, iters=200, space=None, log=None):
     return dict(best=best, trials=trials, iterations=n)
 
 
+def pick_schedule(trials, default, margin):
+    """The schedule to keep from timed trials (dicts with the schedule's keys and
+    `ms_per_step`): the fastest, if it beats the default schedule's time by more than
+    `margin` (a fraction) or the default was not timed; else the default."""
+    fastest = min(trials, key=lambda t: t["ms_per_step"])
+    t_def = next((t["ms_per_step"] for t in trials if {k: t[k] for k in SCHEDULE} == default), None)
+    pick = fastest if (t_def is None or fastest["ms_per_step"] < (1.0 - margin) * t_def) else dict(default)
+    return {k: pick[k] for k in SCHEDULE}
+
+
 def tune_schedule_step(net: gx.Network, eta, step=None, steps=2, reps=2, margin=0.02, space=None, log=None,
                        flush=None):
     """Pick the fastest kernel schedule on the workload's own steps.  From the current
@@ -198,10 +208,7 @@ def tune_schedule_step(net: gx.Network, eta, step=None, steps=2, reps=2, margin=
         trials.append(dict(cand, ms_per_step=round(best_ms, 4)))
         if log:
             log(trials[-1])
-    fastest = min(trials, key=lambda t: t["ms_per_step"])
-    t_def = next((t["ms_per_step"] for t in trials if {k: t[k] for k in SCHEDULE} == default), None)
-    pick = fastest if (t_def is None or fastest["ms_per_step"] < (1.0 - margin) * t_def) else dict(default)
-    best = {k: pick[k] for k in SCHEDULE}
+    best = pick_schedule(trials, default, margin)
     net.set_schedule(**best)
     # one more run captures the chosen schedule's graphs, so the caller's next step is not
     # charged for it; then state and plan go back to the previous plan's
