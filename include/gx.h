@@ -201,7 +201,8 @@ int gx_network_S(const gx_network* net);
 /* Upload static data into dev_mem (>= gx_network_device_bytes, 256-byte aligned)
  * and zero the state.  Asynchronous on `stream`. */
 gx_status gx_network_bind(gx_network* net, void* dev_mem, size_t bytes, void* stream);
-/* Drop the previous solution, as a fresh bind does, without touching the workspace's data:
+/* Drop the previous solution that the warm starts of the interactive planning loop reuse
+ * (Section 2.2; Section 3.2 on warm starts), as a fresh bind does, without touching the workspace's data:
  * the next GX_WARM_PREV solve starts cold, the next GX_WARM_LEARNED solve takes the learned
  * start for every scenario (no selection trial), and gx_dispatch_grad_batch needs a new
  * solve (its GX_WARM_PREV then starts cold too).  Host only, no device work.  Errors:
