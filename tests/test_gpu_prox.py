@@ -32,7 +32,7 @@ def golden_min(f, lo, hi, iters=200):
     return 0.5 * (a + b)
 
 
-def start_prices(net, scen, T, rng):
+def start_prices(net, T, rng):
     N = int(net["n_bus"])
     lam = rng.uniform(10.0, 120.0, size=(N, T))
     cost = net["gen_cost"]
@@ -113,7 +113,7 @@ def _case(case):
     nets, scens = synth.tiny() if case == "tiny" else synth.medium(S=1, T=24)
     net_d, sc = nets[0], scens[0]
     rng = np.random.default_rng(11)
-    lam = start_prices(net_d, sc, sc["T"], rng)
+    lam = start_prices(net_d, sc["T"], rng)
     theta = rng.uniform(-0.05, 0.05, size=(int(net_d["n_bus"]), sc["T"])).astype(np.float32)
     eta = net_d["eta_min"].astype(np.float32) * np.float32(1.1)
     return nets, scens, lam, theta, eta
